@@ -1,0 +1,372 @@
+"""Plain FP64 CPU oracle of the NN-QST maximum-likelihood iteration (arXiv:2207.05341).
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import, call or
+execute this module: only the tests, the smoke check and the benchmark's CPU
+baseline leg use it.  It shares no code with the CUDA library.
+
+Everything is NumPy in float64 / complex128, written for clarity and checked
+against the paper's mathematics by the tests in ``tests/test_oracle_*.py``:
+a brute-force Kronecker expansion of the POVM map, closed forms, invariants,
+central finite differences of the loss and a hand-computed Rprop sequence.
+
+The steps follow the paper in this order:
+  Sec. 3.1  network: input f (the measured frequencies, length K^N), hidden
+            width 2N with LeakyReLU, linear output of 4^N reals;
+  Sec. 3.2  the 4^N reals become a Hermitian T, then either the unified
+            decomposition rho = T^dag T / Tr(T^dag T)   (eq. unified_DP, "Chol_H")
+            or the P-order absolute projection
+            rho = Q |Lambda|^P Q^dag / Tr|Lambda|^P     (eq. abs_P, "A_P");
+  Sec. 3.3  probabilities P_k = Tr[(M_k1 x ... x M_kN) rho]  (eq. PS);
+  Sec. 3.1  loss L = -sum_k f_k log P_k;
+  Sec. 4.1  LeakyReLU hidden layer, Rprop with learning rate 0.001.
+
+Readings where the paper is silent (each also listed in the design notes):
+  * the 4^N outputs t become R = t reshaped row-major to d x d, and
+    T_ii = R_ii, T_ij = R_ij + i R_ji (i > j), T_ji = conj(T_ij);
+  * the output layer is linear; the LeakyReLU negative slope is 0.01;
+  * Rprop: initial step lr, factors (0.5, 1.2), step bounds [1e-6, 50],
+    sign(g * g_prev) decides the factor, and the gradient is zeroed where the
+    sign flipped;
+  * qubit 1 is the most significant factor of the Kronecker product and the
+    most significant base-K digit of the outcome index k;
+  * eq. PS writes b_i Tr[M_j B] for the second term; the Born rule of Sec. 2.1
+    gives the coefficient (M_i)_{21} = c_i there, which is what is used;
+  * terms with f_k = 0 contribute nothing to L; for A_P with P <= 1 the
+    eigenvalue magnitudes are floored at eps * max|lambda| (eps = 1e-15).
+
+Parity unpinned: long multi-step Rprop trajectories (a sign-driven optimiser
+amplifies rounding); single steps, gradients and final fidelities are pinned.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+LEAKY_SLOPE = 0.01
+RPROP_LR = 1e-3
+RPROP_ETAS = (0.5, 1.2)
+RPROP_STEP_BOUNDS = (1e-6, 50.0)
+ABS_P_EPS = 1e-15
+
+_I2 = np.eye(2, dtype=complex)
+_SX = np.array([[0, 1], [1, 0]], dtype=complex)
+_SY = np.array([[0, -1j], [1j, 0]], dtype=complex)
+_SZ = np.array([[1, 0], [0, -1]], dtype=complex)
+
+
+# --------------------------------------------------------------------------
+# Measurement model (Sec. 2.1, Sec. 3.3, Sec. 4.1)
+# --------------------------------------------------------------------------
+
+def tetrahedral_povm() -> np.ndarray:
+    """Sec. 4.1: M_a = (I + s_a . sigma) / 4 with the four listed tetrahedron vectors s_a.
+
+    Returns a (4, 2, 2) complex array.
+    """
+    s = np.array([[1, 1, 1], [-1, -1, 1], [-1, 1, -1], [1, -1, -1]], dtype=float) / np.sqrt(3.0)
+    return np.stack([(_I2 + s[a, 0] * _SX + s[a, 1] * _SY + s[a, 2] * _SZ) / 4.0 for a in range(4)])
+
+
+def _pair_axes(N: int) -> list[int]:
+    # rho reshaped to (2,)*2N has axes i_1..i_N, j_1..j_N; this order puts (i_q, j_q) side by side.
+    return [ax for q in range(N) for ax in (q, N + q)]
+
+
+def born_probabilities(rho: np.ndarray, povm: np.ndarray) -> np.ndarray:
+    """Sec. 3.3 eq. PS for N qubits: P_k = Tr[(M_k1 x ... x M_kN) rho], complex result.
+
+    The trace against a product operator factorises over qubits: for qubit q the
+    pair of indices (i_q, j_q) of rho is contracted with (M_{k_q})_{j_q i_q}
+    (Born rule of Sec. 2.1, Tr[M X] = sum_ij M_ji X_ij).  The contraction is
+    applied one qubit at a time, so the cost is N * K * 4^N instead of K^N 4^N.
+    The imaginary part is returned too; it vanishes for Hermitian rho.
+    """
+    d = rho.shape[0]
+    N = d.bit_length() - 1
+    K = povm.shape[0]
+    A = np.empty((K, 4), dtype=complex)
+    for a in range(K):
+        for i in range(2):
+            for j in range(2):
+                A[a, 2 * i + j] = povm[a][j, i]
+    t = rho.reshape((2,) * (2 * N)).transpose(_pair_axes(N)).reshape((4,) * N)
+    for q in range(N):
+        t = np.moveaxis(np.tensordot(A, t, axes=([1], [q])), 0, q)
+    return t.reshape(-1)
+
+
+def povm_adjoint(g: np.ndarray, povm: np.ndarray) -> np.ndarray:
+    """G = sum_k g_k (M_k1 x ... x M_kN): the adjoint of the real-linear map rho -> Re P.
+
+    With <A, B> = Re Tr(A^dag B) on Hermitian matrices, sum_k g_k P_k = <G, rho>.
+    Applied one qubit at a time like born_probabilities.
+    """
+    K = povm.shape[0]
+    N = round(np.log(g.size) / np.log(K))
+    B = np.empty((4, K), dtype=complex)
+    for a in range(K):
+        for i in range(2):
+            for j in range(2):
+                B[2 * i + j, a] = povm[a][i, j]
+    t = np.asarray(g, dtype=complex).reshape((K,) * N)
+    for q in range(N):
+        t = np.moveaxis(np.tensordot(B, t, axes=([1], [q])), 0, q)
+    inv = np.argsort(_pair_axes(N))
+    d = 1 << N
+    return t.reshape((2,) * (2 * N)).transpose(inv).reshape(d, d)
+
+
+# --------------------------------------------------------------------------
+# Network (Sec. 3.1, Sec. 4.1)
+# --------------------------------------------------------------------------
+
+def unpack_theta(theta: np.ndarray, N: int):
+    """Split the flat parameter vector [W1 (H x n) | W2^T (H x n) | b2 (n) | b1 (H)]."""
+    n, H = 4 ** N, 2 * N
+    o = 0
+    W1 = theta[o:o + H * n].reshape(H, n); o += H * n
+    W2T = theta[o:o + H * n].reshape(H, n); o += H * n
+    b2 = theta[o:o + n]; o += n
+    b1 = theta[o:o + H]; o += H
+    assert o == theta.size
+    return W1, W2T, b2, b1
+
+
+def pack_theta(W1, W2T, b2, b1) -> np.ndarray:
+    return np.concatenate([np.ravel(W1), np.ravel(W2T), np.ravel(b2), np.ravel(b1)])
+
+
+def leaky_relu(x: np.ndarray) -> np.ndarray:
+    return np.where(x > 0, x, LEAKY_SLOPE * x)
+
+
+def network_forward(theta: np.ndarray, f: np.ndarray, N: int):
+    """Sec. 3.1: K^N inputs -> 2N hidden (LeakyReLU) -> 4^N linear outputs.
+
+    Returns (pre, h, t): hidden pre-activation, hidden activation, output.
+    """
+    W1, W2T, b2, b1 = unpack_theta(theta, N)
+    pre = W1 @ f + b1
+    h = leaky_relu(pre)
+    t = W2T.T @ h + b2
+    return pre, h, t
+
+
+def hermitian_from_output(t: np.ndarray) -> np.ndarray:
+    """Sec. 3.1/3.2: the 4^N real outputs become a Hermitian d x d matrix T.
+
+    R = t reshaped row-major to d x d; the diagonal of T is R's diagonal, the
+    strict lower triangle is R_ij + i R_ji and the upper triangle its conjugate.
+    """
+    d = int(round(np.sqrt(t.size)))
+    R = t.reshape(d, d)
+    L = np.tril(R, -1) + 1j * np.tril(R.T, -1)
+    return L + L.conj().T + np.diag(np.diag(R))
+
+
+def output_grad_from_hermitian(Gam: np.ndarray) -> np.ndarray:
+    """Pull a gradient back through hermitian_from_output.
+
+    Gam is the Hermitian matrix with dL = Re Tr[Gam dT] for Hermitian dT.
+    Then dL/dR_ii = Gam_ii, and for i > j: dL/dR_ij = 2 Re Gam_ij and
+    dL/dR_ji = 2 Im Gam_ij.  Returned flat, row-major, like t.
+    """
+    d = Gam.shape[0]
+    dR = np.zeros((d, d))
+    il = np.tril_indices(d, -1)
+    dR[il] = 2.0 * Gam[il].real
+    dR[(il[1], il[0])] = 2.0 * Gam[il].imag
+    dR[np.diag_indices(d)] = np.diag(Gam).real
+    return dR.ravel()
+
+
+# --------------------------------------------------------------------------
+# State mapping (Sec. 3.2)
+# --------------------------------------------------------------------------
+
+def chol_h(T: np.ndarray) -> np.ndarray:
+    """Sec. 3.2 eq. unified_DP: rho = T^dag T / Tr(T^dag T) for Hermitian T."""
+    X = T.conj().T @ T
+    return X / np.trace(X).real
+
+
+def abs_p(T: np.ndarray, P: float) -> np.ndarray:
+    """Sec. 3.2 eq. abs_P: T = Q Lambda Q^dag, rho = Q |Lambda|^P Q^dag / Tr |Lambda|^P."""
+    lam, Q = np.linalg.eigh(T)
+    a = np.abs(lam)
+    if P <= 1.0:
+        a = np.maximum(a, ABS_P_EPS * a.max())
+    s = a ** P
+    return (Q * (s / s.sum())) @ Q.conj().T
+
+
+def _abs_p_backward(T: np.ndarray, P: float, G_rho: np.ndarray) -> np.ndarray:
+    """Gradient of L through eq. abs_P: returns Gam with dL = Re Tr[Gam dT].
+
+    S = Q diag(g(lambda)) Q^dag with g = |lambda|^P, rho = S / s, s = Tr S.
+    dL/dS = (G_rho - <G_rho, rho> I) / s; through the spectral function the
+    Daleckii-Krein formula gives Gam = Q (D o (Q^dag (dL/dS) Q)) Q^dag with
+    D_ij = (g_i - g_j) / (lambda_i - lambda_j), or g'(lambda_i) when equal.
+    """
+    lam, Q = np.linalg.eigh(T)
+    a = np.abs(lam)
+    floor = ABS_P_EPS * a.max() if P <= 1.0 else 0.0
+    a_used = np.maximum(a, floor)
+    g = a_used ** P
+    gp = np.where(a > floor, P * a_used ** (P - 1.0) * np.sign(lam), 0.0)
+    s = g.sum()
+    rho = (Q * (g / s)) @ Q.conj().T
+    inner = np.real(np.vdot(G_rho, rho))
+    dS = (G_rho - inner * np.eye(T.shape[0])) / s
+    C = Q.conj().T @ dS @ Q
+    li, lj = np.meshgrid(lam, lam, indexing="ij")
+    gi, gj = np.meshgrid(g, g, indexing="ij")
+    dl = li - lj
+    same = np.abs(dl) <= 1e-13 * max(1.0, np.abs(lam).max())
+    D = np.where(same, np.add.outer(gp, gp) / 2.0, (gi - gj) / np.where(same, 1.0, dl))
+    Gam = Q @ (D * C) @ Q.conj().T
+    return 0.5 * (Gam + Gam.conj().T)
+
+
+# --------------------------------------------------------------------------
+# Likelihood and its gradient (Sec. 2.1 eq. MLE, Sec. 3.1)
+# --------------------------------------------------------------------------
+
+def nll(p: np.ndarray, f: np.ndarray) -> float:
+    """Sec. 3.1 loss L = -sum_k f_k log p_k, terms with f_k = 0 omitted."""
+    m = f > 0
+    return float(-np.sum(f[m] * np.log(p[m])))
+
+
+def state_from_theta(theta, f, N, mapping="chol_h", P=2.0):
+    pre, h, t = network_forward(theta, f, N)
+    T = hermitian_from_output(t)
+    rho = chol_h(T) if mapping == "chol_h" else abs_p(T, P)
+    return rho
+
+
+def loss_and_grad(theta, f, povm, N, mapping="chol_h", P=2.0):
+    """One forward and backward pass of the Sec. 3 network through the likelihood.
+
+    Returns (L, dL/dtheta, aux) with aux holding rho, p and the intermediates.
+    The backward pass is the chain rule written out step by step:
+      dL/dp_k   = -f_k / p_k
+      dL/drho   = sum_k dL/dp_k M_k                      (POVM adjoint)
+      Chol_H:   rho = X / Tr X, X = T^dag T:
+                dL/dX = (dL/drho - <dL/drho, rho> I) / Tr X,  Gam = T G_X + G_X T
+      A_P:      Daleckii-Krein (see _abs_p_backward)
+      t         <- Gam (output_grad_from_hermitian)
+      W2^T, b2, h <- t;  pre <- h (LeakyReLU');  W1, b1 <- pre.
+    """
+    W1, W2T, b2, b1 = unpack_theta(theta, N)
+    pre, h, t = network_forward(theta, f, N)
+    T = hermitian_from_output(t)
+    d = T.shape[0]
+    if mapping == "chol_h":
+        X = T.conj().T @ T
+        tX = np.trace(X).real
+        rho = X / tX
+    else:
+        rho = abs_p(T, P)
+    p = born_probabilities(rho, povm).real
+    L = nll(p, f)
+
+    gp = np.zeros_like(p)
+    m = f > 0
+    gp[m] = -f[m] / p[m]
+    G_rho = povm_adjoint(gp, povm)
+    if mapping == "chol_h":
+        inner = np.real(np.vdot(G_rho, rho))
+        G_X = (G_rho - inner * np.eye(d)) / tX
+        Gam = T @ G_X + G_X @ T
+    else:
+        Gam = _abs_p_backward(T, P, G_rho)
+    dt = output_grad_from_hermitian(Gam)
+
+    db2 = dt
+    dW2T = np.outer(h, dt)
+    dh = W2T @ dt
+    dpre = dh * np.where(pre > 0, 1.0, LEAKY_SLOPE)
+    db1 = dpre
+    dW1 = np.outer(dpre, f)
+    grad = pack_theta(dW1, dW2T, db2, db1)
+    aux = dict(rho=rho, p=p, T=T, t=t, h=h, pre=pre, Gam=Gam, dt=dt)
+    return L, grad, aux
+
+
+# --------------------------------------------------------------------------
+# Optimiser (Sec. 4.1: Rprop, learning rate 0.001)
+# --------------------------------------------------------------------------
+
+class RpropState:
+    """Per-parameter Rprop state: the step sizes and the previous (masked) gradient's sign."""
+
+    def __init__(self, size: int, lr: float = RPROP_LR):
+        self.step = np.full(size, lr, dtype=np.float64)
+        self.prev_sign = np.zeros(size, dtype=np.int8)
+
+
+def rprop_update(theta, grad, state: RpropState,
+                 etas=RPROP_ETAS, bounds=RPROP_STEP_BOUNDS):
+    """One Rprop update (sign-based step adaptation).
+
+    For each parameter: c = sign(g) * sign(g_prev); the step grows by etas[1]
+    when c > 0, shrinks by etas[0] when c < 0, and stays otherwise; it is then
+    clamped to ``bounds``.  Where c < 0 the gradient is treated as 0 (no move
+    this time, and it is remembered as 0).  The parameter moves by
+    -sign(g) * step.  Returns the new theta; ``state`` is updated in place.
+    """
+    sg = np.sign(grad).astype(np.int8)
+    c = sg * state.prev_sign
+    factor = np.where(c > 0, etas[1], np.where(c < 0, etas[0], 1.0))
+    state.step = np.clip(state.step * factor, bounds[0], bounds[1])
+    sg = np.where(c < 0, 0, sg).astype(np.int8)
+    state.prev_sign = sg
+    return theta - sg * state.step
+
+
+def reconstruct(theta0, f, povm, N, iters, mapping="chol_h", P=2.0, callback=None):
+    """The NN-QST loop of Fig. 1: forward, likelihood, backward, Rprop, repeated.
+
+    Returns (theta, rho, losses).  ``callback(it, rho)`` runs after each step
+    if given (for fidelity tracking).
+    """
+    theta = np.array(theta0, dtype=np.float64)
+    st = RpropState(theta.size)
+    losses = []
+    for it in range(iters):
+        L, g, aux = loss_and_grad(theta, f, povm, N, mapping, P)
+        losses.append(L)
+        theta = rprop_update(theta, g, st)
+        if callback is not None:
+            callback(it, aux["rho"])
+    rho = state_from_theta(theta, f, N, mapping, P)
+    return theta, rho, np.array(losses)
+
+
+# --------------------------------------------------------------------------
+# Evaluation (Sec. 2.3)
+# --------------------------------------------------------------------------
+
+def _psd_sqrt(A: np.ndarray) -> np.ndarray:
+    w, V = np.linalg.eigh(0.5 * (A + A.conj().T))
+    return (V * np.sqrt(np.clip(w, 0.0, None))) @ V.conj().T
+
+
+def fidelity(rho_hat: np.ndarray, rho: np.ndarray) -> float:
+    """Sec. 2.3 eq. F_QF: (Tr sqrt(sqrt(rho_hat) rho sqrt(rho_hat)))^2.
+
+    Evaluated as the squared sum of singular values of sqrt(rho_hat) sqrt(rho),
+    which equals the trace in eq. F_QF and avoids a second matrix square root.
+    """
+    s = np.linalg.svd(_psd_sqrt(rho_hat) @ _psd_sqrt(rho), compute_uv=False)
+    return float(np.sum(s) ** 2)
+
+
+def fidelity_pure(rho_hat: np.ndarray, psi: np.ndarray) -> float:
+    """Sec. 2.3: for a pure target the fidelity reduces to <psi| rho_hat |psi>."""
+    return float(np.real(np.vdot(psi, rho_hat @ psi)))
+
+
+def classical_fidelity(P_hat: np.ndarray, P: np.ndarray) -> float:
+    """Sec. 2.3 eq. F_CF: (sum_k sqrt(P_hat_k P_k))^2, an upper bound on F_q."""
+    return float(np.sum(np.sqrt(np.clip(P_hat, 0, None) * np.clip(P, 0, None))) ** 2)

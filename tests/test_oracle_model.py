@@ -1,0 +1,174 @@
+"""Pins of the oracle's network, state mapping, likelihood, gradient and Rprop (Sec. 3.1, 3.2, 4.1)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2207_05341_gb300 import synth
+
+
+def test_hermitian_map_is_a_bijection():
+    rng = np.random.default_rng(1)
+    for d in (1, 2, 4, 8):
+        t = rng.standard_normal(d * d)
+        T = O.hermitian_from_output(t)
+        assert np.allclose(T, T.conj().T)
+        R = t.reshape(d, d)
+        for i in range(d):
+            assert T[i, i] == R[i, i]
+            for j in range(i):
+                assert T[i, j] == R[i, j] + 1j * R[j, i]
+        # Frobenius norm: sum R_ii^2 + 2 sum_{i != j} R_ij^2
+        want = np.sum(np.diag(R) ** 2) + 2 * (np.sum(R ** 2) - np.sum(np.diag(R) ** 2))
+        assert abs(np.linalg.norm(T) ** 2 - want) < 1e-12 * want
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_state_maps_are_physical_and_agree(seed):
+    d = 8
+    T = synth.random_hermitian(d, seed)
+    for rho in (O.chol_h(T), O.abs_p(T, 0.5), O.abs_p(T, 1.5), O.abs_p(T, 3.0)):
+        assert np.allclose(rho, rho.conj().T, atol=1e-14)
+        assert abs(np.trace(rho).real - 1) < 1e-13
+        assert np.linalg.eigvalsh(rho).min() > -1e-14
+    # Sec. 3.2: Chol_H is A_P with P = 2
+    np.testing.assert_allclose(O.chol_h(T), O.abs_p(T, 2.0), atol=1e-13)
+    # A_4 is T^4 / Tr T^4 (a matrix power), A_1 is |T| / Tr|T|
+    T4 = np.linalg.matrix_power(T, 4)
+    np.testing.assert_allclose(O.abs_p(T, 4.0), T4 / np.trace(T4).real, atol=1e-13)
+    w, V = np.linalg.eigh(T)
+    absT = (V * np.abs(w)) @ V.conj().T
+    np.testing.assert_allclose(O.abs_p(T, 1.0), absT / np.trace(absT).real, atol=1e-13)
+    # diagonal T maps to |lambda|^P / sum
+    lam = np.array([0.3, -1.2, 2.0, 0.1])
+    np.testing.assert_allclose(np.diag(O.abs_p(np.diag(lam).astype(complex), 1.5)).real,
+                               np.abs(lam) ** 1.5 / np.sum(np.abs(lam) ** 1.5), atol=1e-15)
+
+
+def test_loss_gibbs_inequality_and_one_qubit_closed_form():
+    M = O.tetrahedral_povm()
+    rng = np.random.default_rng(2)
+    f = rng.dirichlet(np.ones(16))
+    H = -np.sum(f * np.log(f))
+    for s in range(5):
+        p = O.born_probabilities(synth.ginibre_mixed(2, 2, s), M).real
+        assert O.nll(p, f) >= H - 1e-14
+    assert abs(O.nll(f, f) - H) < 1e-14
+    # zero-frequency outcomes contribute nothing
+    f0 = f.copy(); f0[3] = 0; f0 /= f0.sum()
+    p = rng.dirichlet(np.ones(16))
+    assert abs(O.nll(p, f0) + np.sum(np.delete(f0 * np.log(p), 3))) < 1e-14
+    # N = 1: rho = (I + r.sigma)/2, L = -sum f_a log((1 + s_a.r)/4)
+    s = np.array([[1, 1, 1], [-1, -1, 1], [-1, 1, -1], [1, -1, -1]]) / np.sqrt(3)
+    r = np.array([0.2, -0.3, 0.5])
+    sx = np.array([[0, 1], [1, 0]]); sy = np.array([[0, -1j], [1j, 0]]); sz = np.diag([1, -1])
+    rho = (np.eye(2) + r[0] * sx + r[1] * sy + r[2] * sz) / 2
+    fa = np.array([0.1, 0.2, 0.3, 0.4])
+    assert abs(O.nll(O.born_probabilities(rho, M).real, fa) + np.sum(fa * np.log((1 + s @ r) / 4))) < 1e-15
+
+
+def _fd_check(N, mapping, P, idx=None, seed=0, h=1e-6, rtol=2e-6):
+    M = O.tetrahedral_povm()
+    rho = synth.ginibre_mixed(N, max(1, (1 << N) // 2), 50 + seed)
+    f = O.born_probabilities(rho, M).real
+    theta = synth.init_theta(N, 60 + seed)
+    L, g, _ = O.loss_and_grad(theta, f, M, N, mapping, P)
+    if idx is None:
+        idx = np.arange(theta.size)
+    for i in idx:
+        tp = theta.copy(); tp[i] += h
+        tm = theta.copy(); tm[i] -= h
+        Lp = O.loss_and_grad(tp, f, M, N, mapping, P)[0]
+        Lm = O.loss_and_grad(tm, f, M, N, mapping, P)[0]
+        fd = (Lp - Lm) / (2 * h)
+        assert abs(fd - g[i]) <= rtol * max(1.0, np.abs(g).max()), (i, fd, g[i])
+
+
+@pytest.mark.parametrize("N", [1, 2])
+def test_gradient_central_fd_chol_h_all_coordinates(N):
+    _fd_check(N, "chol_h", 2.0)
+
+
+def test_gradient_central_fd_chol_h_n3_sampled():
+    idx = np.random.default_rng(0).choice(synth.theta_size(3), 80, replace=False)
+    _fd_check(3, "chol_h", 2.0, idx=idx, seed=3)
+
+
+@pytest.mark.parametrize("P", [1.5, 2.0, 3.0])
+def test_gradient_central_fd_abs_p(P):
+    _fd_check(2, "abs_p", P, seed=int(P * 10))
+
+
+def test_gradient_identity_g_x_orthogonal_to_x():
+    """dL/dX is orthogonal to X: scaling T leaves rho and hence L unchanged."""
+    M = O.tetrahedral_povm()
+    N = 3
+    f = O.born_probabilities(synth.ginibre_mixed(N, 3, 1), M).real
+    theta = synth.init_theta(N, 2)
+    L, g, aux = O.loss_and_grad(theta, f, M, N)
+    # dL/dT along T: Re Tr[Gam T] = 2 <G_X, X> = 0
+    assert abs(np.real(np.trace(aux["Gam"] @ aux["T"]))) < 1e-10 * np.abs(aux["Gam"]).max()
+
+
+def test_rprop_hand_computed_sequence():
+    """A hand-worked Rprop sequence: grow by 1.2, shrink by 0.5 and skip on a sign flip."""
+    st = O.RpropState(1, lr=0.1)
+    x = np.zeros(1)
+    seq = [(2.0, -0.1, 0.1), (3.0, -0.22, 0.12), (1.0, -0.364, 0.144),
+           (-1.0, -0.364, 0.072), (-1.0, -0.292, 0.072), (0.0, -0.292, 0.072),
+           (-5.0, -0.22, 0.072), (-5.0, -0.1336, 0.0864)]
+    for g, want_x, want_step in seq:
+        x = O.rprop_update(x, np.array([g]), st)
+        assert abs(x[0] - want_x) < 1e-12 and abs(st.step[0] - want_step) < 1e-12, (g, x, st.step)
+    # bounds
+    st = O.RpropState(2, lr=40.0)
+    x = np.zeros(2)
+    for _ in range(3):
+        x = O.rprop_update(x, np.array([1.0, 1.0]), st)
+    assert st.step[0] == 50.0
+    st = O.RpropState(1, lr=2e-6)
+    x = np.zeros(1)
+    for g in (1.0, -1.0, 0.0, 1.0, -1.0):
+        x = O.rprop_update(x, np.array([g]), st)
+    assert st.step[0] == 1e-6
+
+
+def test_fidelity_properties_and_printed_formulas(golden_dir):
+    rho = synth.ginibre_mixed(3, 3, 1)
+    sig = synth.ginibre_mixed(3, 2, 2)
+    # rank-deficient states: sqrt of ~1e-17 eigenvalues limits agreement to ~1e-8
+    assert abs(O.fidelity(rho, sig) - O.fidelity(sig, rho)) < 1e-7
+    assert abs(O.fidelity(rho, rho) - 1) < 1e-7
+    psi = synth.haar_pure(3, 4)
+    assert abs(O.fidelity(rho, synth.pure_density(psi)) - O.fidelity_pure(rho, psi)) < 1e-7
+    M = O.tetrahedral_povm()
+    Fc = O.classical_fidelity(O.born_probabilities(rho, M).real, O.born_probabilities(sig, M).real)
+    assert O.fidelity(rho, sig) <= Fc + 1e-12
+    # Fig. 6 caption: ideal fidelity of a depolarised 8-qubit pure state vs the pure state
+    N = 8
+    d = 1 << N
+    psi = synth.haar_pure(N, 1)
+    for lam in (0.0, 0.1, 0.3):
+        rl = synth.depolarized(psi, lam)
+        assert abs(O.fidelity_pure(rl, psi) - (1 - (1 - 1 / d) * lam)) < 1e-12
+    # Fig. 3 caption: purity of the white-noise 10-qubit state
+    N = 10
+    d = 1 << N
+    psi = synth.product_plus(N)
+    for p in (0.0, 0.4, 1.0):
+        r = synth.white_noise(psi, p)
+        assert abs(np.sum(np.abs(r) ** 2) - ((1 - 1 / d) * p * p + 1 / d)) < 1e-12
+
+
+def test_reconstruction_from_exact_probabilities_reaches_target():
+    """Sec. 4.2: Chol_H reaches fidelity ~1 from exact (noise-free) probabilities."""
+    M = O.tetrahedral_povm()
+    N = 2
+    psi = synth.haar_pure(N, 1)
+    rho_t = synth.pure_density(psi)
+    f = O.born_probabilities(rho_t, M).real
+    theta0 = synth.init_theta(N, 1)
+    _, rho, losses = O.reconstruct(theta0, f, M, N, 1000)
+    assert O.fidelity_pure(rho, psi) > 0.99
+    assert losses[-1] < losses[0]
