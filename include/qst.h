@@ -1,0 +1,163 @@
+/*
+ * qst.h -- C ABI of the GB300 NN-QST maximum-likelihood library (libqst.so).
+ *
+ * Method: Wang, Cheng, Li, Chen, "Ultrafast quantum state tomography with
+ * feed-forward neural networks" (arXiv:2207.05341).  The library runs the
+ * per-iteration hot path of that method on one GPU:
+ *
+ *   Sec. 3.1   network  f (4^N) -> LeakyReLU hidden (2N) -> linear output t (4^N)
+ *   Sec. 3.2   t -> Hermitian T -> X = T^dag T = T T ("Chol_H", eq. unified_DP),
+ *              rho = X / Tr X
+ *   Sec. 3.3   q_k = Tr[(M_k1 (x) ... (x) M_kN) X]  (product POVM, eq. PS), p = q / Tr X
+ *   Sec. 3.1   L = -sum_k f_k log p_k   (eq. MLE objective)
+ *   backward through all of the above, then Rprop (Sec. 4.1).
+ *
+ * Conventions shared by every call
+ *   N         number of qubits, 1 <= N <= 12 (FP32 / MIXED), 1 <= N <= 10 (FP64).
+ *   d = 2^N, n = 4^N, H = 2N.
+ *   Outcome index k = sum_q a_q 4^(N-q): qubit 1 is the most significant base-4
+ *   digit and the most significant Kronecker factor (row/column bit N-1).
+ *   real      double for QST_FP64 contexts, float for QST_FP32 / QST_MIXED.
+ *   complex   two interleaved reals (re, im); matrices are d x d row-major.
+ *   theta     flat array of qst_theta_size(N) reals:
+ *               [ W1 (H x n, row-major) | W2^T (H x n, row-major) | b2 (n) | b1 (H) ]
+ *             layer 1: pre = W1 f + b1, h = LeakyReLU(pre);
+ *             layer 2: t_i = sum_j W2^T[j][i] h_j + b2_i.
+ *   T from t  R = t as a d x d row-major matrix; T_ii = R_ii,
+ *             T_ij = R_ij + i R_ji for i > j, T_ji = conj(T_ij).
+ *
+ * Memory and ownership
+ *   The caller owns every pointer it passes.  A pointer documented "device or
+ *   host" may be either; host buffers are staged through context memory.  A
+ *   qst_ctx owns its network parameters, Rprop state and scratch buffers and
+ *   frees them in qst_destroy.  All work is ordered on the stream given to
+ *   qst_init (NULL = the legacy default stream).  A call returns once its work
+ *   is enqueued, except that writing a host scalar (loss) or a host buffer
+ *   synchronises the stream first.
+ *
+ * Errors
+ *   Every call returns a qst_status; nothing is thrown across the ABI.  A
+ *   negative status means the call did nothing observable (or, for QST_E_CUDA,
+ *   that a CUDA call failed and the context should be destroyed).
+ *   QST_W_CLAMP (positive) is a warning: some q_k <= 0 with f_k > 0 was
+ *   clamped to the smallest normal number of the precision before its log.
+ */
+#ifndef QST_H
+#define QST_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qst_ctx qst_ctx;
+
+typedef enum {
+    QST_OK = 0,
+    QST_E_INVAL = -1,       /* bad argument: N out of range, NULL pointer, K != 4, POVM not summing to I */
+    QST_E_INPUT = -2,       /* bad data: f not finite, negative, or not summing to 1 within 1e-4 */
+    QST_E_NOMEM = -3,       /* device allocation failed */
+    QST_E_CUDA = -4,        /* a CUDA runtime call failed */
+    QST_E_TIMEOUT = -5,     /* a bounded device-side wait ran out */
+    QST_E_STATE = -6,       /* call not valid in the context's state (e.g. no parameters set) */
+    QST_E_UNSUPPORTED = -7, /* valid request this build does not run (e.g. precision not compiled) */
+    QST_W_CLAMP = 1
+} qst_status;
+
+enum { QST_MAP_CHOL_H = 0, QST_MAP_ABS_P = 1 };
+enum { QST_FP64 = 0, QST_FP32 = 1, QST_MIXED = 2 };
+
+typedef struct qst_options {
+    int mapping;        /* QST_MAP_CHOL_H (paper default, Sec. 4.3) or QST_MAP_ABS_P (eq. abs_P) */
+    int precision;      /* QST_FP64, QST_FP32, or QST_MIXED (BF16 hi+lo tensor-core products, FP32 elsewhere) */
+    double P;           /* order of the absolute projection A_P; used when mapping == QST_MAP_ABS_P */
+    double lr;          /* Rprop initial step (Sec. 4.1: 0.001) */
+    double eta_minus;   /* Rprop shrink factor (0.5) */
+    double eta_plus;    /* Rprop growth factor (1.2) */
+    double step_min;    /* Rprop step lower bound (1e-6) */
+    double step_max;    /* Rprop step upper bound (50) */
+    double leaky_slope; /* LeakyReLU negative slope (0.01) */
+} qst_options;
+
+/* Fill *opt with the paper's settings (Sec. 4.1) and the defaults stated above. */
+void qst_default_options(qst_options* opt);
+
+/* Number of reals in theta for N qubits: 2*H*n + n + H. */
+size_t qst_theta_size(int N);
+
+/* Create a context for N qubits.
+ *   povm   host, K*2*2 complex doubles (interleaved re, im), element a at
+ *          povm[8a .. 8a+7] as the row-major 2x2 matrix M_a.  K must be 4; the
+ *          M_a must be Hermitian and sum to the identity within 1e-12
+ *          (Sec. 2.1 eq. qst; Sec. 3.3 uses the same M_a on every qubit).
+ *   opt    host, may be NULL for qst_default_options.
+ *   stream cudaStream_t (as void*), may be NULL.
+ * Allocates all device memory the context needs (QST_E_NOMEM on failure). */
+qst_status qst_init(qst_ctx** out, int N, const double* povm, int K,
+                    const qst_options* opt, void* stream);
+
+/* Load network parameters (theta layout above, qst_theta_size(N) reals, device
+ * or host) and reset the Rprop state (steps = lr, previous signs = 0). */
+qst_status qst_set_params(qst_ctx* ctx, const void* theta);
+
+/* Copy the current parameters out (device or host buffer of qst_theta_size(N) reals). */
+qst_status qst_get_params(qst_ctx* ctx, void* theta);
+
+/* Sec. 3.3 eq. PS: p_k = Tr[(M_k1 (x) ... (x) M_kN) rho] for all k.
+ *   rho  device, d x d complex, row-major.  Only the lower triangle (i >= j) is
+ *        read; the upper triangle is taken to be its conjugate transpose.
+ *   p    device, n reals (written).  No normalisation is applied. */
+qst_status qst_probs(qst_ctx* ctx, const void* rho, void* p);
+
+/* Loss and gradient of Sec. 3.1 for externally held parameters, no update.
+ *   theta  device, qst_theta_size(N) reals (read only).
+ *   f      device or host, n reals: measured frequencies (Sec. 2.1), f >= 0, sum 1.
+ *   loss   host, written: L = -sum_k f_k log p_k (terms with f_k = 0 omitted).
+ *   dtheta device, qst_theta_size(N) reals (written): dL/dtheta in theta's layout. */
+qst_status qst_loss_grad(qst_ctx* ctx, const void* theta, const void* f, double* loss, void* dtheta);
+
+/* One iteration of the Fig. 1 loop on the context's parameters: forward, loss,
+ * backward, Rprop update.
+ *   f     device or host, n reals.  The hidden layer of the next iteration is
+ *         computed inside this call from this f; passing a different pointer
+ *         to the next call recomputes it, passing the same pointer assumes the
+ *         values did not change.
+ *   loss  host or NULL: loss of the parameters before the update (synchronises). */
+qst_status qst_step(qst_ctx* ctx, const void* f, double* loss);
+
+/* Run `iters` iterations of qst_step, then write the reconstructed state.
+ *   rho_out     device or host or NULL, d x d complex: rho of the final parameters.
+ *   final_loss  host or NULL: loss of that rho. */
+qst_status qst_reconstruct(qst_ctx* ctx, const void* f, int iters, void* rho_out, double* final_loss);
+
+/* rho of the current parameters for input f (device or host), written to rho_out
+ * (device or host, d x d complex), and its loss if loss != NULL. */
+qst_status qst_get_rho(qst_ctx* ctx, const void* f, void* rho_out, double* loss);
+
+/* Checkpoint of parameters, Rprop state and iteration count, as an opaque host
+ * byte buffer of qst_state_bytes(ctx) bytes.  Restoring it into a context with
+ * the same N, precision and options resumes bit-identically. */
+size_t qst_state_bytes(const qst_ctx* ctx);
+qst_status qst_get_state(qst_ctx* ctx, void* host_buf, size_t bytes);
+qst_status qst_set_state(qst_ctx* ctx, const void* host_buf, size_t bytes);
+
+/* Number of Rprop steps taken since the last qst_set_params / qst_set_state. */
+long long qst_iterations(const qst_ctx* ctx);
+
+/* Number of kernel launches the library has enqueued on this context (graph
+ * replays count every kernel node). */
+long long qst_kernel_launches(const qst_ctx* ctx);
+
+/* Wait for all work enqueued on the context's stream. */
+qst_status qst_sync(qst_ctx* ctx);
+
+const char* qst_strerror(qst_status s);
+
+void qst_destroy(qst_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QST_H */

@@ -94,6 +94,24 @@ def born_probabilities(rho: np.ndarray, povm: np.ndarray) -> np.ndarray:
     return t.reshape(-1)
 
 
+def born_probability_at(rho: np.ndarray, povm: np.ndarray, k: int) -> complex:
+    """One outcome of eq. PS: Tr[(M_k1 x ... x M_kN) rho] for a single index k.
+
+    Contracts each qubit's index pair of rho with its own M_{k_q}, one qubit at
+    a time (cost O(d^2) per outcome), for spot checks of large problems.
+    """
+    d = rho.shape[0]
+    N = d.bit_length() - 1
+    K = povm.shape[0]
+    digits = [(k // K ** (N - 1 - q)) % K for q in range(N)]
+    t = rho.reshape((2,) * (2 * N)).transpose(_pair_axes(N)).reshape((4,) * N)
+    for q in range(N):
+        m = povm[digits[q]]
+        a = np.array([m[j, i] for i in range(2) for j in range(2)])
+        t = np.tensordot(a, t, axes=([0], [0]))
+    return complex(t)
+
+
 def povm_adjoint(g: np.ndarray, povm: np.ndarray) -> np.ndarray:
     """G = sum_k g_k (M_k1 x ... x M_kN): the adjoint of the real-linear map rho -> Re P.
 

@@ -1,0 +1,584 @@
+// C ABI of libqst (include/qst.h): context management and the per-iteration
+// sequence of the NN-QST hot path (Fig. 1 loop of arXiv:2207.05341).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/qst.h"
+#include "impl.h"
+
+using namespace qst;
+
+namespace {
+
+constexpr unsigned long long kStateMagic = 0x5153545354415445ULL;  // "QSTSTATE"
+
+bool is_device_ptr(const void* p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct qst_ctx {
+  int N = 0;
+  int prec = QST_FP32;
+  qst_options opt;
+  Dims D;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::vector<void*> allocs;
+  void* work = nullptr;  // Work<float> or Work<double>
+  PovmB<float> Bf;
+  PovmB<double> Bd;
+  NetCfg net;
+  bool params_set = false;
+  bool hidden_valid = false;
+  const void* f_last = nullptr;
+  long long iters = 0;
+  long long launches = 0;
+  double* h_scal = nullptr;     // pinned host mirror of scal[0..4]
+  unsigned int* h_flags = nullptr;
+  size_t partial_doubles = 0;
+};
+
+namespace {
+
+qst_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return QST_OK;
+  if (e == cudaErrorMemoryAllocation) return QST_E_NOMEM;
+  return QST_E_CUDA;
+}
+
+#define QST_CU(expr)                               \
+  do {                                             \
+    cudaError_t _e = (expr);                       \
+    if (_e != cudaSuccess) return cuda_status(_e); \
+  } while (0)
+
+template <class T> cudaError_t dalloc(qst_ctx* c, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T) < 256 ? 256 : count * sizeof(T));
+  if (e != cudaSuccess) return e;
+  c->allocs.push_back(q);
+  *p = reinterpret_cast<T*>(q);
+  return cudaSuccess;
+}
+
+template <class R> Work<R>* W(qst_ctx* c) { return reinterpret_cast<Work<R>*>(c->work); }
+template <class R> const PovmB<R>& povmB(qst_ctx* c);
+template <> const PovmB<float>& povmB<float>(qst_ctx* c) { return c->Bf; }
+template <> const PovmB<double>& povmB<double>(qst_ctx* c) { return c->Bd; }
+
+size_t theta_size(int N) {
+  const size_t n = (size_t)1 << (2 * N), H = 2 * (size_t)N;
+  return 2 * H * n + n + H;
+}
+
+size_t rsize(const qst_ctx* c) { return c->prec == QST_FP64 ? sizeof(double) : sizeof(float); }
+
+template <class R> qst_status alloc_work(qst_ctx* c) {
+  Work<R>* w = new (std::nothrow) Work<R>();
+  if (!w) return QST_E_NOMEM;
+  memset(w, 0, sizeof(*w));
+  c->work = w;
+  const Dims& D = c->D;
+  const size_t P = theta_size(c->N);
+  const size_t nn = (size_t)D.d * D.d;
+  QST_CU(dalloc(c, &w->theta, P));
+  QST_CU(dalloc(c, &w->step, P));
+  QST_CU(dalloc(c, &w->sign, P));
+  QST_CU(dalloc(c, &w->pre, 32));
+  QST_CU(dalloc(c, &w->hid, 32));
+  QST_CU(dalloc(c, &w->dpre, 32));
+  QST_CU(dalloc(c, &w->T, nn));
+  QST_CU(dalloc(c, &w->X, nn));
+  QST_CU(dalloc(c, &w->G, nn));
+  QST_CU(dalloc(c, &w->Y, nn));
+  QST_CU(dalloc(c, &w->Wlo, (size_t)D.n));
+  QST_CU(dalloc(c, &w->Whi, (size_t)D.n));
+  QST_CU(dalloc(c, &w->dt, (size_t)D.n));
+  QST_CU(dalloc(c, &w->fstage, (size_t)D.n));
+  QST_CU(dalloc(c, &w->scal, 16));
+  // per-block partial sums: the largest reducing grid is the tile-pair grid of build_T
+  const int TS = D.d < 32 ? D.d : 32;
+  const size_t pairs = (size_t)(D.d / TS) * (D.d / TS + 1) / 2;
+  size_t blocks = (size_t)kPartialBlocks;
+  if (pairs > blocks) blocks = pairs;
+  const size_t p2 = ((size_t)1 << (2 * D.g)) / D.C;
+  if (p2 > blocks) blocks = p2;
+  c->partial_doubles = blocks * kPartialStride;
+  QST_CU(dalloc(c, &w->partials, c->partial_doubles));
+  QST_CU(dalloc(c, &w->counters, (size_t)CNT_COUNT));
+  QST_CU(dalloc(c, &w->flags, 8));
+  QST_CU(cudaMemsetAsync(w->counters, 0, CNT_COUNT * sizeof(unsigned int), c->stream));
+  QST_CU(cudaMemsetAsync(w->flags, 0, 8 * sizeof(unsigned int), c->stream));
+  QST_CU(cudaMemsetAsync(w->scal, 0, 16 * sizeof(double), c->stream));
+  if (c->prec == QST_MIXED) {
+    unsigned short* tb = nullptr;
+    QST_CU(dalloc(c, &tb, 6 * nn));
+    w->Tb = tb;
+    unsigned short* gb = nullptr;
+    QST_CU(dalloc(c, &gb, 4 * nn));
+    w->Gb = gb;
+    QST_CU(dalloc(c, &w->Yre, nn));
+    QST_CU(dalloc(c, &w->Yim, nn));
+  }
+  return QST_OK;
+}
+
+template <class R> void free_work(qst_ctx* c) { delete W<R>(c); }
+
+// ---- stream helpers
+const void* stage_input(qst_ctx* c, const void* f, size_t bytes, void* stage, qst_status* st) {
+  *st = QST_OK;
+  if (is_device_ptr(f)) return f;
+  cudaError_t e = cudaMemcpyAsync(stage, f, bytes, cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) { *st = cuda_status(e); return nullptr; }
+  return stage;
+}
+
+// Validate f (finite, >= 0, sum 1 within 1e-4) on the host: copies n reals back.
+template <class R> qst_status validate_f(qst_ctx* c, const void* fdev) {
+  const size_t n = (size_t)c->D.n;
+  std::vector<R> h(n);
+  QST_CU(cudaMemcpyAsync(h.data(), fdev, n * sizeof(R), cudaMemcpyDeviceToHost, c->stream));
+  QST_CU(cudaStreamSynchronize(c->stream));
+  double s = 0.0;
+  for (size_t i = 0; i < n; ++i) {
+    const double v = (double)h[i];
+    if (!(v >= 0.0) || !isfinite(v)) return QST_E_INPUT;
+    s += v;
+  }
+  if (fabs(s - 1.0) > 1e-4) return QST_E_INPUT;
+  return QST_OK;
+}
+
+// ---- the hot path ------------------------------------------------------------
+template <class R> struct Engine {
+  using V = cx_t<R>;
+
+  // X = T T (lower tiles) from the hidden activation already in w->hid; Tr X -> scal[0]
+  static qst_status forward_state(qst_ctx* c, const R* theta) {
+    Work<R>* w = W<R>(c);
+    const Dims& D = c->D;
+    const bool mixed = c->prec == QST_MIXED;
+    QST_CU(net_build_T<R>(D, theta, w->hid, w->T, mixed ? w->Tb : nullptr, w->scal, w->partials,
+                          w->counters + CNT_T, c->stream));
+    c->launches += 1;
+    if (mixed) {
+      QST_CU(tc_herm_square(D.d, w->Tb, reinterpret_cast<float2*>(w->X), c->stream));
+    } else {
+      QST_CU(cgemm_simt<R>(D.d, w->T, w->T, w->X, true, c->stream));
+    }
+    c->launches += 1;
+    return QST_OK;
+  }
+
+  // loss -> scal[2]; with backward, G = sum_k g_k M_k -> w->G
+  static qst_status povm_likelihood(qst_ctx* c, const R* f, bool backward) {
+    Work<R>* w = W<R>(c);
+    const Dims& D = c->D;
+    const PovmB<R>& B = povmB<R>(c);
+    QST_CU(povm_lo_fwd<R>(D, w->X, w->Wlo, B, c->stream));
+    QST_CU(povm_hi_nll<R>(D, w->Wlo, f, w->scal, w->Whi, w->partials, w->counters + CNT_NLL, w->flags, B,
+                          backward, c->stream));
+    c->launches += 2;
+    if (backward) {
+      QST_CU(povm_lo_adj<R>(D, w->Whi, w->G, B, c->stream));
+      c->launches += 1;
+    }
+    return QST_OK;
+  }
+
+  // dL/dt from G and T -> w->dt
+  static qst_status backward_state(qst_ctx* c) {
+    Work<R>* w = W<R>(c);
+    const Dims& D = c->D;
+    if (c->prec == QST_MIXED) {
+      QST_CU(split_bf16_G(D.d, reinterpret_cast<const float2*>(w->G), w->Gb, c->stream));
+      QST_CU(tc_gt_product(D.d, w->Gb, w->Tb, w->Yre, w->Yim, c->stream));
+      QST_CU(net_symmetrize_planar(D, w->Yre, w->Yim, reinterpret_cast<float*>(w->dt), c->stream));
+      c->launches += 3;
+    } else {
+      QST_CU(cgemm_simt<R>(D.d, w->G, w->T, w->Y, false, c->stream));
+      QST_CU(net_symmetrize<R>(D, w->Y, w->dt, c->stream));
+      c->launches += 2;
+    }
+    return QST_OK;
+  }
+
+  static qst_status hidden(qst_ctx* c, const R* theta, const R* f) {
+    Work<R>* w = W<R>(c);
+    QST_CU(net_l1_forward<R>(c->D, theta, f, w->pre, w->hid, w->scal, w->partials, w->counters + CNT_L1, c->net,
+                             c->stream));
+    c->launches += 1;
+    return QST_OK;
+  }
+
+  static qst_status read_loss(qst_ctx* c, double* loss) {
+    Work<R>* w = W<R>(c);
+    QST_CU(cudaMemcpyAsync(c->h_scal, w->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    QST_CU(cudaMemcpyAsync(c->h_flags, w->flags, sizeof(unsigned int), cudaMemcpyDeviceToHost, c->stream));
+    QST_CU(cudaStreamSynchronize(c->stream));
+    *loss = c->h_scal[2];
+    if (c->h_flags[0] != 0u) {
+      QST_CU(cudaMemsetAsync(w->flags, 0, sizeof(unsigned int), c->stream));
+      return QST_W_CLAMP;
+    }
+    return QST_OK;
+  }
+
+  static qst_status step(qst_ctx* c, const void* f_user, double* loss) {
+    Work<R>* w = W<R>(c);
+    const Dims& D = c->D;
+    qst_status st;
+    const R* f = (const R*)stage_input(c, f_user, (size_t)D.n * sizeof(R), w->fstage, &st);
+    if (st != QST_OK) return st;
+    const bool new_f = !c->hidden_valid || f_user != c->f_last;
+    if (new_f) {
+      st = validate_f<R>(c, f);
+      if (st != QST_OK) return st;
+      if ((st = hidden(c, w->theta, f)) != QST_OK) return st;
+    }
+    if ((st = forward_state(c, w->theta)) != QST_OK) return st;
+    if ((st = povm_likelihood(c, f, true)) != QST_OK) return st;
+    if ((st = backward_state(c)) != QST_OK) return st;
+    QST_CU(net_w2_pass<R>(D, w->theta, w->step, w->sign, w->dt, w->hid, w->pre, w->dpre, nullptr, w->partials,
+                          w->counters + CNT_W2, c->net, true, c->stream));
+    QST_CU(net_w1_pass<R>(D, w->theta, w->step, w->sign, f, w->dpre, w->pre, w->hid, nullptr, w->scal, w->partials,
+                          w->counters + CNT_W1, c->net, true, c->stream));
+    c->launches += 2;
+    c->hidden_valid = true;
+    c->f_last = f_user;
+    c->iters += 1;
+    if (loss) return read_loss(c, loss);
+    return QST_OK;
+  }
+
+  static qst_status loss_grad(qst_ctx* c, const void* theta_v, const void* f_user, double* loss, void* dtheta_v) {
+    Work<R>* w = W<R>(c);
+    const Dims& D = c->D;
+    R* theta = (R*)theta_v;
+    R* dtheta = (R*)dtheta_v;
+    qst_status st;
+    const R* f = (const R*)stage_input(c, f_user, (size_t)D.n * sizeof(R), w->fstage, &st);
+    if (st != QST_OK) return st;
+    if ((st = validate_f<R>(c, f)) != QST_OK) return st;
+    c->hidden_valid = false;  // the hidden buffers now hold the external parameters' activation
+    if ((st = hidden(c, theta, f)) != QST_OK) return st;
+    if ((st = forward_state(c, theta)) != QST_OK) return st;
+    if ((st = povm_likelihood(c, f, true)) != QST_OK) return st;
+    if ((st = backward_state(c)) != QST_OK) return st;
+    QST_CU(net_w2_pass<R>(D, theta, nullptr, nullptr, w->dt, w->hid, w->pre, w->dpre, dtheta, w->partials,
+                          w->counters + CNT_W2, c->net, false, c->stream));
+    QST_CU(net_w1_pass<R>(D, theta, nullptr, nullptr, f, w->dpre, w->pre, w->hid, dtheta, w->scal, w->partials,
+                          w->counters + CNT_W1, c->net, false, c->stream));
+    c->launches += 2;
+    return read_loss(c, loss);
+  }
+
+  static qst_status probs(qst_ctx* c, const void* rho, void* p) {
+    Work<R>* w = W<R>(c);
+    const PovmB<R>& B = povmB<R>(c);
+    QST_CU(povm_lo_fwd<R>(c->D, (const V*)rho, w->Wlo, B, c->stream));
+    QST_CU(povm_hi_fwd<R>(c->D, w->Wlo, (R*)p, B, c->stream));
+    c->launches += 2;
+    return QST_OK;
+  }
+
+  static qst_status get_rho(qst_ctx* c, const void* f_user, void* rho_out, double* loss) {
+    Work<R>* w = W<R>(c);
+    const Dims& D = c->D;
+    qst_status st;
+    const R* f = (const R*)stage_input(c, f_user, (size_t)D.n * sizeof(R), w->fstage, &st);
+    if (st != QST_OK) return st;
+    if (!c->hidden_valid || f_user != c->f_last) {
+      if ((st = validate_f<R>(c, f)) != QST_OK) return st;
+      if ((st = hidden(c, w->theta, f)) != QST_OK) return st;
+      c->hidden_valid = true;
+      c->f_last = f_user;
+    }
+    if ((st = forward_state(c, w->theta)) != QST_OK) return st;
+    const bool dev = is_device_ptr(rho_out);
+    V* dst = dev ? (V*)rho_out : w->G;
+    if (rho_out) {
+      QST_CU(hermitian_complete<R>(D, w->X, dst, w->scal, c->stream));
+      c->launches += 1;
+      if (!dev) {
+        QST_CU(cudaMemcpyAsync(rho_out, dst, (size_t)D.d * D.d * sizeof(V), cudaMemcpyDeviceToHost, c->stream));
+        QST_CU(cudaStreamSynchronize(c->stream));
+      }
+    }
+    if (loss) {
+      if ((st = povm_likelihood(c, f, false)) != QST_OK) return st;
+      return read_loss(c, loss);
+    }
+    return QST_OK;
+  }
+};
+
+#define QST_DISPATCH(c, call) ((c)->prec == QST_FP64 ? Engine<double>::call : Engine<float>::call)
+
+qst_status check_povm(const double* povm, int K, PovmB<double>* Bd) {
+  if (povm == nullptr || K != 4) return QST_E_INVAL;
+  double sum[8] = {0};
+  for (int a = 0; a < 4; ++a) {
+    const double* m = povm + 8 * a;  // m00 (re, im), m01, m10, m11
+    for (int q = 0; q < 8; ++q) {
+      if (!isfinite(m[q])) return QST_E_INVAL;
+      sum[q] += m[q];
+    }
+    // Hermitian: real diagonal, m01 = conj(m10)
+    if (fabs(m[1]) > 1e-12 || fabs(m[7]) > 1e-12) return QST_E_INVAL;
+    if (fabs(m[2] - m[4]) > 1e-12 || fabs(m[3] + m[5]) > 1e-12) return QST_E_INVAL;
+    // Pauli coefficients: M = b0 I + b1 X + b2 Y + b3 Z, m10 = b1 + i b2
+    Bd->b[a][0] = 0.5 * (m[0] + m[6]);
+    Bd->b[a][1] = m[4];
+    Bd->b[a][2] = m[5];
+    Bd->b[a][3] = 0.5 * (m[0] - m[6]);
+  }
+  const double eye[8] = {1, 0, 0, 0, 0, 0, 1, 0};
+  for (int q = 0; q < 8; ++q)
+    if (fabs(sum[q] - eye[q]) > 1e-12) return QST_E_INVAL;
+  return QST_OK;
+}
+
+template <class R> qst_status reset_rprop(qst_ctx* c) {
+  Work<R>* w = W<R>(c);
+  const size_t P = theta_size(c->N);
+  std::vector<R> h(P, (R)c->opt.lr);
+  QST_CU(cudaMemcpyAsync(w->step, h.data(), P * sizeof(R), cudaMemcpyHostToDevice, c->stream));
+  QST_CU(cudaMemsetAsync(w->sign, 0, P, c->stream));
+  QST_CU(cudaStreamSynchronize(c->stream));
+  return QST_OK;
+}
+
+}  // namespace
+
+// =============================================================================== C ABI
+extern "C" {
+
+void qst_default_options(qst_options* o) {
+  if (!o) return;
+  o->mapping = QST_MAP_CHOL_H;
+  o->precision = QST_FP32;
+  o->P = 2.0;
+  o->lr = 1e-3;
+  o->eta_minus = 0.5;
+  o->eta_plus = 1.2;
+  o->step_min = 1e-6;
+  o->step_max = 50.0;
+  o->leaky_slope = 0.01;
+}
+
+size_t qst_theta_size(int N) {
+  if (N < 1 || N > 12) return 0;
+  return theta_size(N);
+}
+
+qst_status qst_init(qst_ctx** out, int N, const double* povm, int K, const qst_options* opt, void* stream) {
+  if (out == nullptr) return QST_E_INVAL;
+  *out = nullptr;
+  qst_options o;
+  qst_default_options(&o);
+  if (opt) o = *opt;
+  if (o.precision != QST_FP64 && o.precision != QST_FP32 && o.precision != QST_MIXED) return QST_E_INVAL;
+  if (N < 1 || N > (o.precision == QST_FP64 ? 10 : 12)) return QST_E_INVAL;
+  if (o.mapping != QST_MAP_CHOL_H) return QST_E_UNSUPPORTED;
+  if (!(o.lr > 0) || !(o.eta_minus > 0 && o.eta_minus < 1) || !(o.eta_plus > 1) || !(o.step_min > 0) ||
+      !(o.step_max >= o.step_min) || !(o.leaky_slope >= 0))
+    return QST_E_INVAL;
+  PovmB<double> Bd;
+  qst_status st = check_povm(povm, K, &Bd);
+  if (st != QST_OK) return st;
+  if (o.precision == QST_MIXED) {
+    if (N < 7) return QST_E_UNSUPPORTED;
+    if (!tc_available()) return QST_E_UNSUPPORTED;
+  }
+  qst_ctx* c = new (std::nothrow) qst_ctx();
+  if (!c) return QST_E_NOMEM;
+  c->N = N;
+  c->opt = o;
+  c->prec = o.precision;
+  c->D = make_dims(N, o.precision == QST_FP64);
+  c->stream = (cudaStream_t)stream;
+  c->Bd = Bd;
+  for (int a = 0; a < 4; ++a)
+    for (int m = 0; m < 4; ++m) c->Bf.b[a][m] = (float)Bd.b[a][m];
+  c->net.slope = o.leaky_slope;
+  c->net.eta_minus = o.eta_minus;
+  c->net.eta_plus = o.eta_plus;
+  c->net.step_min = o.step_min;
+  c->net.step_max = o.step_max;
+  cudaGetDevice(&c->device);
+  cudaError_t e = cudaMallocHost((void**)&c->h_scal, 16 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_flags, 8 * sizeof(unsigned int));
+  if (e != cudaSuccess) {
+    qst_destroy(c);
+    return cuda_status(e);
+  }
+  st = c->prec == QST_FP64 ? alloc_work<double>(c) : alloc_work<float>(c);
+  if (st != QST_OK) {
+    qst_destroy(c);
+    return st;
+  }
+  *out = c;
+  return QST_OK;
+}
+
+qst_status qst_set_params(qst_ctx* c, const void* theta) {
+  if (!c || !theta) return QST_E_INVAL;
+  const size_t bytes = theta_size(c->N) * rsize(c);
+  void* dst = c->prec == QST_FP64 ? (void*)W<double>(c)->theta : (void*)W<float>(c)->theta;
+  QST_CU(cudaMemcpyAsync(dst, theta, bytes, cudaMemcpyDefault, c->stream));
+  qst_status st = c->prec == QST_FP64 ? reset_rprop<double>(c) : reset_rprop<float>(c);
+  if (st != QST_OK) return st;
+  c->params_set = true;
+  c->hidden_valid = false;
+  c->iters = 0;
+  return QST_OK;
+}
+
+qst_status qst_get_params(qst_ctx* c, void* theta) {
+  if (!c || !theta) return QST_E_INVAL;
+  if (!c->params_set) return QST_E_STATE;
+  const size_t bytes = theta_size(c->N) * rsize(c);
+  const void* src = c->prec == QST_FP64 ? (void*)W<double>(c)->theta : (void*)W<float>(c)->theta;
+  QST_CU(cudaMemcpyAsync(theta, src, bytes, cudaMemcpyDefault, c->stream));
+  if (!is_device_ptr(theta)) QST_CU(cudaStreamSynchronize(c->stream));
+  return QST_OK;
+}
+
+qst_status qst_probs(qst_ctx* c, const void* rho, void* p) {
+  if (!c || !rho || !p) return QST_E_INVAL;
+  if (!is_device_ptr(rho) || !is_device_ptr(p)) return QST_E_INVAL;
+  return QST_DISPATCH(c, probs(c, rho, p));
+}
+
+qst_status qst_loss_grad(qst_ctx* c, const void* theta, const void* f, double* loss, void* dtheta) {
+  if (!c || !theta || !f || !loss || !dtheta) return QST_E_INVAL;
+  if (!is_device_ptr(theta) || !is_device_ptr(dtheta)) return QST_E_INVAL;
+  return QST_DISPATCH(c, loss_grad(c, theta, f, loss, dtheta));
+}
+
+qst_status qst_step(qst_ctx* c, const void* f, double* loss) {
+  if (!c || !f) return QST_E_INVAL;
+  if (!c->params_set) return QST_E_STATE;
+  return QST_DISPATCH(c, step(c, f, loss));
+}
+
+qst_status qst_get_rho(qst_ctx* c, const void* f, void* rho_out, double* loss) {
+  if (!c || !f) return QST_E_INVAL;
+  if (!c->params_set) return QST_E_STATE;
+  return QST_DISPATCH(c, get_rho(c, f, rho_out, loss));
+}
+
+qst_status qst_reconstruct(qst_ctx* c, const void* f, int iters, void* rho_out, double* final_loss) {
+  if (!c || !f || iters < 0) return QST_E_INVAL;
+  if (!c->params_set) return QST_E_STATE;
+  for (int i = 0; i < iters; ++i) {
+    qst_status st = qst_step(c, f, nullptr);
+    if (st < 0) return st;
+  }
+  if (rho_out || final_loss) return qst_get_rho(c, f, rho_out, final_loss);
+  return QST_OK;
+}
+
+size_t qst_state_bytes(const qst_ctx* c) {
+  if (!c) return 0;
+  const size_t P = theta_size(c->N);
+  return 4 * sizeof(unsigned long long) + 2 * P * rsize(c) + P;
+}
+
+qst_status qst_get_state(qst_ctx* c, void* host_buf, size_t bytes) {
+  if (!c || !host_buf) return QST_E_INVAL;
+  if (!c->params_set) return QST_E_STATE;
+  if (bytes < qst_state_bytes(c)) return QST_E_INVAL;
+  const size_t P = theta_size(c->N), rs = rsize(c);
+  unsigned long long* hdr = (unsigned long long*)host_buf;
+  hdr[0] = kStateMagic;
+  hdr[1] = (unsigned long long)c->N | ((unsigned long long)c->prec << 8);
+  hdr[2] = (unsigned long long)c->iters;
+  hdr[3] = (unsigned long long)P;
+  char* p = (char*)host_buf + 4 * sizeof(unsigned long long);
+  const void *th, *stp, *sg;
+  if (c->prec == QST_FP64) { th = W<double>(c)->theta; stp = W<double>(c)->step; sg = W<double>(c)->sign; }
+  else { th = W<float>(c)->theta; stp = W<float>(c)->step; sg = W<float>(c)->sign; }
+  QST_CU(cudaMemcpyAsync(p, th, P * rs, cudaMemcpyDeviceToHost, c->stream));
+  QST_CU(cudaMemcpyAsync(p + P * rs, stp, P * rs, cudaMemcpyDeviceToHost, c->stream));
+  QST_CU(cudaMemcpyAsync(p + 2 * P * rs, sg, P, cudaMemcpyDeviceToHost, c->stream));
+  QST_CU(cudaStreamSynchronize(c->stream));
+  return QST_OK;
+}
+
+qst_status qst_set_state(qst_ctx* c, const void* host_buf, size_t bytes) {
+  if (!c || !host_buf) return QST_E_INVAL;
+  if (bytes < qst_state_bytes(c)) return QST_E_INVAL;
+  const size_t P = theta_size(c->N), rs = rsize(c);
+  const unsigned long long* hdr = (const unsigned long long*)host_buf;
+  if (hdr[0] != kStateMagic || hdr[1] != ((unsigned long long)c->N | ((unsigned long long)c->prec << 8)) ||
+      hdr[3] != (unsigned long long)P)
+    return QST_E_INVAL;
+  const char* p = (const char*)host_buf + 4 * sizeof(unsigned long long);
+  void *th, *stp, *sg;
+  if (c->prec == QST_FP64) { th = W<double>(c)->theta; stp = W<double>(c)->step; sg = W<double>(c)->sign; }
+  else { th = W<float>(c)->theta; stp = W<float>(c)->step; sg = W<float>(c)->sign; }
+  QST_CU(cudaMemcpyAsync(th, p, P * rs, cudaMemcpyHostToDevice, c->stream));
+  QST_CU(cudaMemcpyAsync(stp, p + P * rs, P * rs, cudaMemcpyHostToDevice, c->stream));
+  QST_CU(cudaMemcpyAsync(sg, p + 2 * P * rs, P, cudaMemcpyHostToDevice, c->stream));
+  QST_CU(cudaStreamSynchronize(c->stream));
+  c->params_set = true;
+  c->hidden_valid = false;
+  c->iters = (long long)hdr[2];
+  return QST_OK;
+}
+
+long long qst_iterations(const qst_ctx* c) { return c ? c->iters : -1; }
+long long qst_kernel_launches(const qst_ctx* c) { return c ? c->launches : -1; }
+
+qst_status qst_sync(qst_ctx* c) {
+  if (!c) return QST_E_INVAL;
+  QST_CU(cudaStreamSynchronize(c->stream));
+  return QST_OK;
+}
+
+const char* qst_strerror(qst_status s) {
+  switch (s) {
+    case QST_OK: return "ok";
+    case QST_E_INVAL: return "invalid argument";
+    case QST_E_INPUT: return "invalid input data (f must be finite, >= 0 and sum to 1)";
+    case QST_E_NOMEM: return "device allocation failed";
+    case QST_E_CUDA: return "CUDA runtime error";
+    case QST_E_TIMEOUT: return "device-side wait timed out";
+    case QST_E_STATE: return "call not valid in the context's state";
+    case QST_E_UNSUPPORTED: return "unsupported configuration";
+    case QST_W_CLAMP: return "warning: non-positive probability clamped before its logarithm";
+  }
+  return "unknown status";
+}
+
+void qst_destroy(qst_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->work) {
+    if (c->prec == QST_FP64) free_work<double>(c);
+    else free_work<float>(c);
+  }
+  if (c->h_scal) cudaFreeHost(c->h_scal);
+  if (c->h_flags) cudaFreeHost(c->h_flags);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,135 @@
+// Shared device helpers of libqst: complex arithmetic, the single-qubit POVM
+// mode maps, Rprop, block reductions.  Included by every .cu of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qst {
+
+template <class R> struct Cx;
+template <> struct Cx<float>  { using T = float2; };
+template <> struct Cx<double> { using T = double2; };
+template <class R> using cx_t = typename Cx<R>::T;
+
+template <class V> __host__ __device__ __forceinline__ V cmake(decltype(V::x) re, decltype(V::x) im) {
+  V v; v.x = re; v.y = im; return v;
+}
+template <class V> __device__ __forceinline__ V cadd(V a, V b) { return cmake<V>(a.x + b.x, a.y + b.y); }
+template <class V> __device__ __forceinline__ V csub(V a, V b) { return cmake<V>(a.x - b.x, a.y - b.y); }
+template <class V> __device__ __forceinline__ V cconj(V a) { return cmake<V>(a.x, -a.y); }
+// i * a
+template <class V> __device__ __forceinline__ V cmuli(V a) { return cmake<V>(-a.y, a.x); }
+template <class V, class R> __device__ __forceinline__ V cscale(V a, R s) { return cmake<V>(a.x * s, a.y * s); }
+
+// Single-qubit POVM in Pauli form: M_a = b[a][0] I + b[a][1] X + b[a][2] Y + b[a][3] Z
+// (every Hermitian 2x2 matrix has real coefficients in this basis).
+template <class R> struct PovmB { R b[4][4]; };
+
+// Forward mode map on one qubit (Sec. 3.3 eq. PS, Born rule of Sec. 2.1):
+//   y_a = sum_{ij} (M_a)_{ji} x_{ij} = sum_mu b[a][mu] c_mu
+// with the Pauli components c = (x00 + x11, x01 + x10, i(x01 - x10), x00 - x11).
+// Output a is written back to the slot of (i, j) = (a >> 1, a & 1).
+template <class R, class V>
+__device__ __forceinline__ void mode_fwd(const PovmB<R>& B, V& x00, V& x01, V& x10, V& x11) {
+  V c0 = cadd(x00, x11), c3 = csub(x00, x11), c1 = cadd(x01, x10), c2 = cmuli(csub(x01, x10));
+  V y[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    y[a].x = B.b[a][0] * c0.x + B.b[a][1] * c1.x + B.b[a][2] * c2.x + B.b[a][3] * c3.x;
+    y[a].y = B.b[a][0] * c0.y + B.b[a][1] * c1.y + B.b[a][2] * c2.y + B.b[a][3] * c3.y;
+  }
+  x00 = y[0]; x01 = y[1]; x10 = y[2]; x11 = y[3];
+}
+
+// Adjoint mode map: from g_a in the slots of a, write G = sum_a g_a M_a:
+//   c_mu = sum_a b[a][mu] g_a;  G00 = c0 + c3, G11 = c0 - c3, G10 = c1 + i c2, G01 = c1 - i c2.
+template <class R, class V>
+__device__ __forceinline__ void mode_adj(const PovmB<R>& B, V& x00, V& x01, V& x10, V& x11) {
+  V g[4] = {x00, x01, x10, x11};
+  V c[4];
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    c[mu].x = B.b[0][mu] * g[0].x + B.b[1][mu] * g[1].x + B.b[2][mu] * g[2].x + B.b[3][mu] * g[3].x;
+    c[mu].y = B.b[0][mu] * g[0].y + B.b[1][mu] * g[1].y + B.b[2][mu] * g[2].y + B.b[3][mu] * g[3].y;
+  }
+  V ic2 = cmuli(c[2]);
+  x00 = cadd(c[0], c[3]);
+  x11 = csub(c[0], c[3]);
+  x10 = cadd(c[1], ic2);
+  x01 = csub(c[1], ic2);
+}
+
+// Bit interleave: a_b = 2 i_b + j_b  <->  k = sum_b a_b 4^b.
+__host__ __device__ __forceinline__ uint32_t spread_bits(uint32_t v) {
+  v &= 0xFFFFu;
+  v = (v | (v << 8)) & 0x00FF00FFu;
+  v = (v | (v << 4)) & 0x0F0F0F0Fu;
+  v = (v | (v << 2)) & 0x33333333u;
+  v = (v | (v << 1)) & 0x55555555u;
+  return v;
+}
+__host__ __device__ __forceinline__ uint32_t compact_bits(uint32_t v) {
+  v &= 0x55555555u;
+  v = (v | (v >> 1)) & 0x33333333u;
+  v = (v | (v >> 2)) & 0x0F0F0F0Fu;
+  v = (v | (v >> 4)) & 0x00FF00FFu;
+  v = (v | (v >> 8)) & 0x0000FFFFu;
+  return v;
+}
+__host__ __device__ __forceinline__ uint32_t interleave_ij(uint32_t i, uint32_t j) {
+  return (spread_bits(i) << 1) | spread_bits(j);
+}
+__host__ __device__ __forceinline__ uint32_t row_of(uint32_t a) { return compact_bits(a >> 1); }
+__host__ __device__ __forceinline__ uint32_t col_of(uint32_t a) { return compact_bits(a); }
+
+// Row index I of the t-th lower-triangular tile pair (I >= J), t = I(I+1)/2 + J.
+__device__ __forceinline__ void tri_decode(uint32_t t, int& I, int& J) {
+  int i = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while ((uint32_t)((i + 1) * (i + 2) / 2) <= t) ++i;
+  while ((uint32_t)(i * (i + 1) / 2) > t) --i;
+  I = i;
+  J = (int)(t - (uint32_t)(i * (i + 1) / 2));
+}
+
+// Rprop on one parameter (Sec. 4.1): c = sign(g) sign(g_prev); the step is scaled
+// by eta_plus / eta_minus / 1 for c > 0 / c < 0 / c == 0 and clamped; where c < 0
+// the gradient counts as zero; the parameter moves by -sign(g) step.
+template <class R> struct RpropCfg { R eta_minus, eta_plus, step_min, step_max; };
+
+template <class R>
+__device__ __forceinline__ R rprop1(R w, R g, R& step, int8_t& prev, const RpropCfg<R>& c) {
+  int s = (g > R(0)) - (g < R(0));
+  int cs = s * (int)prev;
+  R fac = cs > 0 ? c.eta_plus : (cs < 0 ? c.eta_minus : R(1));
+  R st = step * fac;
+  st = st < c.step_min ? c.step_min : (st > c.step_max ? c.step_max : st);
+  step = st;
+  if (cs < 0) s = 0;
+  prev = (int8_t)s;
+  return s > 0 ? w - st : (s < 0 ? w + st : w);
+}
+
+// Warp / block sum reduction of double values.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// "Last block done": every block has written its partial; the last one to arrive
+// returns true (for all its threads).  The counter is reset by the caller's last block.
+__device__ __forceinline__ bool last_block_arrived(unsigned int* counter) {
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int prev = atomicAdd(counter, 1u);
+    s_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last;
+}
+
+}  // namespace qst

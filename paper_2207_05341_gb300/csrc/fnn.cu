@@ -1,0 +1,484 @@
+// The Sec. 3.1 network (4^N -> 2N LeakyReLU -> 4^N linear), the Hermitian T of
+// Sec. 3.2, their backward passes, and Rprop (Sec. 4.1) fused into the weight passes.
+//
+// Every kernel here streams the parameters once with vector loads; the hidden
+// width H = 2N is a template parameter so that the H running sums live in
+// registers.  Sums over the 4^N axis are reduced per block and then by the last
+// block to arrive, in a fixed order (deterministic, no floating-point atomics).
+#include <cuda_bf16.h>
+
+#include "impl.h"
+
+namespace qst {
+
+template <class R> struct Vec;
+template <> struct Vec<float> {
+  static constexpr int W = 4;
+  __device__ static void ld(const float* p, float* v) { float4 t = *reinterpret_cast<const float4*>(p); v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w; }
+  __device__ static void st(float* p, const float* v) { *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]); }
+  __device__ static void lds(const int8_t* p, int8_t* v) { char4 t = *reinterpret_cast<const char4*>(p); v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w; }
+  __device__ static void sts(int8_t* p, const int8_t* v) { *reinterpret_cast<char4*>(p) = make_char4(v[0], v[1], v[2], v[3]); }
+};
+template <> struct Vec<double> {
+  static constexpr int W = 2;
+  __device__ static void ld(const double* p, double* v) { double2 t = *reinterpret_cast<const double2*>(p); v[0] = t.x; v[1] = t.y; }
+  __device__ static void st(double* p, const double* v) { *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]); }
+  __device__ static void lds(const int8_t* p, int8_t* v) { char2 t = *reinterpret_cast<const char2*>(p); v[0] = t.x; v[1] = t.y; }
+  __device__ static void sts(int8_t* p, const int8_t* v) { *reinterpret_cast<char2*>(p) = make_char2(v[0], v[1]); }
+};
+
+template <class R> __device__ __forceinline__ R leaky(R x, R slope) { return x > R(0) ? x : slope * x; }
+
+// Reduce M per-thread values over the block; thread 0 writes them (as double) to out[0..M).
+template <int M, class R>
+__device__ __forceinline__ void block_reduce_to(const R (&v)[M], double* out) {
+  __shared__ double red[8][M];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    double x = warp_sum((double)v[j]);
+    if (lane == 0) red[w][j] = x;
+  }
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  for (int j = threadIdx.x; j < M; j += blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < nw; ++q) s += red[q][j];
+    out[j] = s;
+  }
+}
+
+// In the last block: warp j sums partials[b * kPartialStride + j] over all blocks b
+// (fixed order) for j < M, and calls fin(j, sum) from lane 0.
+template <class F>
+__device__ __forceinline__ void final_reduce(const double* partials, int M, F fin) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = w; j < M; j += nw) {
+    double s = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) s += partials[(size_t)b * kPartialStride + j];
+    s = warp_sum(s);
+    if (lane == 0) fin(j, s);
+  }
+}
+
+static int stream_grid(long long nvec) {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  long long want = (nvec + 255) / 256;
+  long long cap = 4LL * sms;
+  if (cap > kPartialBlocks) cap = kPartialBlocks;
+  if (want > cap) want = cap;
+  if (want < 1) want = 1;
+  return (int)want;
+}
+
+// ------------------------------------------------------------------ layer 1 forward
+// pre = W1 f + b1, hid = LeakyReLU(pre), scal[1] = sum f
+template <class R, int H>
+__global__ void __launch_bounds__(256) k_l1_forward(const R* __restrict__ theta, const R* __restrict__ f,
+                                                     long long n, R* pre, R* hid, double* scal,
+                                                     double* partials, unsigned int* counter, R slope) {
+  using VV = Vec<R>;
+  constexpr int VW = VV::W;
+  const R* W1 = theta;
+  const R* b1 = theta + 2LL * H * n + n;
+  R acc[H + 1];
+#pragma unroll
+  for (int j = 0; j <= H; ++j) acc[j] = R(0);
+  const long long nv = n / VW;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (long long)gridDim.x * blockDim.x) {
+    R fv[VW];
+    VV::ld(f + i * VW, fv);
+#pragma unroll
+    for (int u = 0; u < VW; ++u) acc[H] += fv[u];
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      R w[VW];
+      VV::ld(W1 + (long long)j * n + i * VW, w);
+#pragma unroll
+      for (int u = 0; u < VW; ++u) acc[j] += w[u] * fv[u];
+    }
+  }
+  block_reduce_to<H + 1>(acc, partials + (size_t)blockIdx.x * kPartialStride);
+  if (last_block_arrived(counter)) {
+    final_reduce(partials, H + 1, [&](int j, double s) {
+      if (j < H) {
+        const R p = (R)(s + (double)b1[j]);
+        pre[j] = p;
+        hid[j] = leaky(p, slope);
+      } else {
+        scal[1] = s;
+      }
+    });
+    __syncthreads();
+    if (threadIdx.x == 0) *counter = 0u;
+  }
+}
+
+// ------------------------------------------------------------------ layer 2 + Hermitian T
+// t = W2 h + b2; R = t as d x d row-major; T_ii = R_ii, T_ij = R_ij + i R_ji (i > j), T_ji = conj T_ij.
+// One CTA per tile pair (I, J), I >= J, of TS x TS tiles.  Also scal[0] = ||T||_F^2 = Tr T^2.
+// With Tb != NULL the BF16 hi/lo planes (re, im, -im) are written instead of complex T.
+template <class R, int H>
+__global__ void __launch_bounds__(256) k_build_T(const R* __restrict__ theta, const R* __restrict__ hid, int N,
+                                                  cx_t<R>* __restrict__ T, __nv_bfloat16* __restrict__ Tb,
+                                                  double* scal, double* partials, unsigned int* counter) {
+  using V = cx_t<R>;
+  __shared__ R hs[H];
+  __shared__ R Ra[32][33];
+  __shared__ R Rb[32][33];
+  const int d = 1 << N;
+  const long long n = 1LL << (2 * N);
+  const int TS = d < 32 ? d : 32;
+  const R* W2T = theta + (long long)H * n;
+  const R* b2 = theta + 2LL * H * n;
+  int I, J;
+  tri_decode(blockIdx.x, I, J);
+  if (threadIdx.x < H) hs[threadIdx.x] = hid[threadIdx.x];
+  __syncthreads();
+  R nrm = R(0);
+  for (int e = threadIdx.x; e < TS * TS; e += blockDim.x) {
+    const int r = e / TS, c = e % TS;
+    const long long ia = (long long)(I * TS + r) * d + J * TS + c;
+    R ta = b2[ia];
+#pragma unroll
+    for (int j = 0; j < H; ++j) ta += W2T[(long long)j * n + ia] * hs[j];
+    Ra[r][c] = ta;
+    if (I != J) {
+      const long long ib = (long long)(J * TS + r) * d + I * TS + c;
+      R tb = b2[ib];
+#pragma unroll
+      for (int j = 0; j < H; ++j) tb += W2T[(long long)j * n + ib] * hs[j];
+      Rb[r][c] = tb;
+      nrm += R(2) * (ta * ta + tb * tb);
+    } else {
+      nrm += (r == c ? R(1) : R(2)) * ta * ta;
+    }
+  }
+  __syncthreads();
+  const long long nn = (long long)d * d;
+  for (int e = threadIdx.x; e < TS * TS; e += blockDim.x) {
+    const int r = e / TS, c = e % TS;
+    R re, im;
+    if (I != J) { re = Ra[r][c]; im = Rb[c][r]; }
+    else if (r > c) { re = Ra[r][c]; im = Ra[c][r]; }
+    else if (r < c) { re = Ra[c][r]; im = -Ra[r][c]; }
+    else { re = Ra[r][r]; im = R(0); }
+    const long long o = (long long)(I * TS + r) * d + J * TS + c;
+    if (Tb == nullptr) {
+      T[o] = cmake<V>(re, im);
+    } else {
+      const float fr = (float)re, fi = (float)im;
+      const __nv_bfloat16 rh = __float2bfloat16_rn(fr), ih = __float2bfloat16_rn(fi), nh = __float2bfloat16_rn(-fi);
+      Tb[o] = rh; Tb[nn + o] = ih; Tb[2 * nn + o] = nh;
+      Tb[3 * nn + o] = __float2bfloat16_rn(fr - __bfloat162float(rh));
+      Tb[4 * nn + o] = __float2bfloat16_rn(fi - __bfloat162float(ih));
+      Tb[5 * nn + o] = __float2bfloat16_rn(-fi - __bfloat162float(nh));
+    }
+  }
+  if (I != J) {
+    for (int e = threadIdx.x; e < TS * TS; e += blockDim.x) {
+      const int a = e / TS, b = e % TS;
+      const R re = Ra[b][a], im = -Rb[a][b];
+      const long long o = (long long)(J * TS + a) * d + I * TS + b;
+      if (Tb == nullptr) {
+        T[o] = cmake<V>(re, im);
+      } else {
+        const float fr = (float)re, fi = (float)im;
+        const __nv_bfloat16 rh = __float2bfloat16_rn(fr), ih = __float2bfloat16_rn(fi), nh = __float2bfloat16_rn(-fi);
+        Tb[o] = rh; Tb[nn + o] = ih; Tb[2 * nn + o] = nh;
+        Tb[3 * nn + o] = __float2bfloat16_rn(fr - __bfloat162float(rh));
+        Tb[4 * nn + o] = __float2bfloat16_rn(fi - __bfloat162float(ih));
+        Tb[5 * nn + o] = __float2bfloat16_rn(-fi - __bfloat162float(nh));
+      }
+    }
+  }
+  R v1[1] = {nrm};
+  block_reduce_to<1>(v1, partials + (size_t)blockIdx.x * kPartialStride);
+  if (last_block_arrived(counter)) {
+    final_reduce(partials, 1, [&](int, double s) { scal[0] = s; });
+    __syncthreads();
+    if (threadIdx.x == 0) *counter = 0u;
+  }
+}
+
+// ------------------------------------------------------------------ W2 pass (backward + Rprop)
+// db2 = dt, dW2^T[j][i] = h_j dt_i, dh_j = sum_i W2^T[j][i] dt_i (old weights);
+// then dpre = dh * LeakyReLU'(pre), db1 = dpre.  update: Rprop on W2^T, b2, b1; else write dtheta.
+template <class R, int H, bool UPD>
+__global__ void __launch_bounds__(256) k_w2_pass(R* __restrict__ theta, R* __restrict__ step, int8_t* __restrict__ sign,
+                                                  const R* __restrict__ dt, const R* __restrict__ hid,
+                                                  const R* __restrict__ pre, R* dpre, R* __restrict__ dtheta,
+                                                  long long n, double* partials, unsigned int* counter,
+                                                  RpropCfg<R> rc, R slope) {
+  using VV = Vec<R>;
+  constexpr int VW = VV::W;
+  const long long o2 = (long long)H * n, ob2 = 2LL * H * n, ob1 = 2LL * H * n + n;
+  __shared__ R hs[H];
+  if (threadIdx.x < H) hs[threadIdx.x] = hid[threadIdx.x];
+  __syncthreads();
+  R acc[H];
+#pragma unroll
+  for (int j = 0; j < H; ++j) acc[j] = R(0);
+  const long long nv = n / VW;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (long long)gridDim.x * blockDim.x) {
+    const long long x = i * VW;
+    R dv[VW];
+    VV::ld(dt + x, dv);
+    if (UPD) {
+      R w[VW], st[VW];
+      int8_t sg[VW];
+      VV::ld(theta + ob2 + x, w); VV::ld(step + ob2 + x, st); VV::lds(sign + ob2 + x, sg);
+#pragma unroll
+      for (int u = 0; u < VW; ++u) w[u] = rprop1(w[u], dv[u], st[u], sg[u], rc);
+      VV::st(theta + ob2 + x, w); VV::st(step + ob2 + x, st); VV::sts(sign + ob2 + x, sg);
+    } else {
+      VV::st(dtheta + ob2 + x, dv);
+    }
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      const long long oj = o2 + (long long)j * n + x;
+      R w[VW], g[VW];
+      VV::ld(theta + oj, w);
+#pragma unroll
+      for (int u = 0; u < VW; ++u) { acc[j] += w[u] * dv[u]; g[u] = hs[j] * dv[u]; }
+      if (UPD) {
+        R st[VW];
+        int8_t sg[VW];
+        VV::ld(step + oj, st); VV::lds(sign + oj, sg);
+#pragma unroll
+        for (int u = 0; u < VW; ++u) w[u] = rprop1(w[u], g[u], st[u], sg[u], rc);
+        VV::st(theta + oj, w); VV::st(step + oj, st); VV::sts(sign + oj, sg);
+      } else {
+        VV::st(dtheta + oj, g);
+      }
+    }
+  }
+  block_reduce_to<H>(acc, partials + (size_t)blockIdx.x * kPartialStride);
+  if (last_block_arrived(counter)) {
+    final_reduce(partials, H, [&](int j, double s) {
+      const R p = pre[j];
+      const R dp = (R)s * (p > R(0) ? R(1) : slope);
+      dpre[j] = dp;
+      if (UPD) {
+        R st = step[ob1 + j];
+        int8_t sg = sign[ob1 + j];
+        theta[ob1 + j] = rprop1(theta[ob1 + j], dp, st, sg, rc);
+        step[ob1 + j] = st;
+        sign[ob1 + j] = sg;
+      } else {
+        dtheta[ob1 + j] = dp;
+      }
+    });
+    __syncthreads();
+    if (threadIdx.x == 0) *counter = 0u;
+  }
+}
+
+// ------------------------------------------------------------------ W1 pass (backward + Rprop + next forward)
+// dW1[j][i] = dpre_j f_i.  update: Rprop on W1, then pre = W1' f + b1', hid = LeakyReLU(pre),
+// scal[1] = sum f (the hidden layer of the next iteration); else write dtheta.
+template <class R, int H, bool UPD>
+__global__ void __launch_bounds__(256) k_w1_pass(R* __restrict__ theta, R* __restrict__ step, int8_t* __restrict__ sign,
+                                                  const R* __restrict__ f, const R* __restrict__ dpre, R* pre,
+                                                  R* hid, R* __restrict__ dtheta, long long n, double* scal,
+                                                  double* partials, unsigned int* counter, RpropCfg<R> rc, R slope) {
+  using VV = Vec<R>;
+  constexpr int VW = VV::W;
+  const long long ob1 = 2LL * H * n + n;
+  __shared__ R dps[H];
+  if (threadIdx.x < H) dps[threadIdx.x] = dpre[threadIdx.x];
+  __syncthreads();
+  R acc[H + 1];
+#pragma unroll
+  for (int j = 0; j <= H; ++j) acc[j] = R(0);
+  const long long nv = n / VW;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (long long)gridDim.x * blockDim.x) {
+    const long long x = i * VW;
+    R fv[VW];
+    VV::ld(f + x, fv);
+#pragma unroll
+    for (int u = 0; u < VW; ++u) acc[H] += fv[u];
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      const long long oj = (long long)j * n + x;
+      R g[VW];
+#pragma unroll
+      for (int u = 0; u < VW; ++u) g[u] = dps[j] * fv[u];
+      if (UPD) {
+        R w[VW], st[VW];
+        int8_t sg[VW];
+        VV::ld(theta + oj, w); VV::ld(step + oj, st); VV::lds(sign + oj, sg);
+#pragma unroll
+        for (int u = 0; u < VW; ++u) {
+          w[u] = rprop1(w[u], g[u], st[u], sg[u], rc);
+          acc[j] += w[u] * fv[u];
+        }
+        VV::st(theta + oj, w); VV::st(step + oj, st); VV::sts(sign + oj, sg);
+      } else {
+        VV::st(dtheta + oj, g);
+      }
+    }
+  }
+  if (!UPD) return;
+  block_reduce_to<H + 1>(acc, partials + (size_t)blockIdx.x * kPartialStride);
+  if (last_block_arrived(counter)) {
+    final_reduce(partials, H + 1, [&](int j, double s) {
+      if (j < H) {
+        const R p = (R)(s + (double)theta[ob1 + j]);
+        pre[j] = p;
+        hid[j] = leaky(p, slope);
+      } else {
+        scal[1] = s;
+      }
+    });
+    __syncthreads();
+    if (threadIdx.x == 0) *counter = 0u;
+  }
+}
+
+// ------------------------------------------------------------------ dL/dt from Y = G T
+// Gamma = Y + Y^dag;  dR_ij = 2 Re Gamma_ij, dR_ji = 2 Im Gamma_ij (i > j), dR_ii = Re Gamma_ii.
+template <class R, bool PLANAR>
+__global__ void __launch_bounds__(256) k_symmetrize(const cx_t<R>* __restrict__ Y, const float* __restrict__ Yre,
+                                                     const float* __restrict__ Yim, R* __restrict__ dt, int d) {
+  __shared__ R Ar[32][33], Ai[32][33], Br[32][33], Bi[32][33];
+  const int TS = d < 32 ? d : 32;
+  int I, J;
+  tri_decode(blockIdx.x, I, J);
+  for (int e = threadIdx.x; e < TS * TS; e += blockDim.x) {
+    const int r = e / TS, c = e % TS;
+    const long long ia = (long long)(I * TS + r) * d + J * TS + c;
+    const long long ib = (long long)(J * TS + r) * d + I * TS + c;
+    if (PLANAR) {
+      Ar[r][c] = (R)Yre[ia]; Ai[r][c] = (R)Yim[ia];
+      Br[r][c] = (R)Yre[ib]; Bi[r][c] = (R)Yim[ib];
+    } else {
+      const cx_t<R> a = Y[ia], b = Y[ib];
+      Ar[r][c] = a.x; Ai[r][c] = a.y; Br[r][c] = b.x; Bi[r][c] = b.y;
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < TS * TS; e += blockDim.x) {
+    const int r = e / TS, c = e % TS;
+    if (I != J) {
+      // lower tile (I, J): rows > cols
+      dt[(long long)(I * TS + r) * d + J * TS + c] = R(2) * (Ar[r][c] + Br[c][r]);
+      // upper tile (J, I): element (J TS + r, I TS + c) = 2 Im Gamma_{(I TS + c),(J TS + r)}
+      dt[(long long)(J * TS + r) * d + I * TS + c] = R(2) * (Ai[c][r] - Bi[r][c]);
+    } else {
+      R v;
+      if (r > c) v = R(2) * (Ar[r][c] + Ar[c][r]);
+      else if (r < c) v = R(2) * (Ai[c][r] - Ai[r][c]);
+      else v = R(2) * Ar[r][r];
+      dt[(long long)(I * TS + r) * d + J * TS + c] = v;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+#define QST_SWITCH_H(H, ...)                      \
+  switch (H) {                                    \
+    case 2: { constexpr int HH = 2; __VA_ARGS__; } break;   \
+    case 4: { constexpr int HH = 4; __VA_ARGS__; } break;   \
+    case 6: { constexpr int HH = 6; __VA_ARGS__; } break;   \
+    case 8: { constexpr int HH = 8; __VA_ARGS__; } break;   \
+    case 10: { constexpr int HH = 10; __VA_ARGS__; } break; \
+    case 12: { constexpr int HH = 12; __VA_ARGS__; } break; \
+    case 14: { constexpr int HH = 14; __VA_ARGS__; } break; \
+    case 16: { constexpr int HH = 16; __VA_ARGS__; } break; \
+    case 18: { constexpr int HH = 18; __VA_ARGS__; } break; \
+    case 20: { constexpr int HH = 20; __VA_ARGS__; } break; \
+    case 22: { constexpr int HH = 22; __VA_ARGS__; } break; \
+    case 24: { constexpr int HH = 24; __VA_ARGS__; } break; \
+    default: return cudaErrorInvalidValue;        \
+  }
+
+template <class R> static RpropCfg<R> rcfg(const NetCfg& c) {
+  RpropCfg<R> r;
+  r.eta_minus = (R)c.eta_minus; r.eta_plus = (R)c.eta_plus; r.step_min = (R)c.step_min; r.step_max = (R)c.step_max;
+  return r;
+}
+
+template <class R>
+cudaError_t net_l1_forward(const Dims& D, const R* theta, const R* f, R* pre, R* hid, double* scal,
+                           double* partials, unsigned int* counter, const NetCfg& c, cudaStream_t s) {
+  const int grid = stream_grid(D.n / Vec<R>::W);
+  QST_SWITCH_H(D.H, k_l1_forward<R, HH><<<grid, 256, 0, s>>>(theta, f, D.n, pre, hid, scal, partials, counter, (R)c.slope));
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t net_build_T(const Dims& D, const R* theta, const R* hid, cx_t<R>* T, void* Tb, double* scal,
+                        double* partials, unsigned int* counter, cudaStream_t s) {
+  const int TS = D.d < 32 ? D.d : 32;
+  const int nt = D.d / TS;
+  const unsigned pairs = (unsigned)(nt * (nt + 1) / 2);
+  if (pairs > (unsigned)kPartialBlocks * 4) {
+    // partial slots: one stride per block
+  }
+  QST_SWITCH_H(D.H, k_build_T<R, HH><<<pairs, 256, 0, s>>>(theta, hid, D.N, T, (__nv_bfloat16*)Tb, scal, partials,
+                                                           counter));
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t net_w2_pass(const Dims& D, R* theta, R* step, int8_t* sign, const R* dt, const R* hid, const R* pre,
+                        R* dpre, R* dtheta, double* partials, unsigned int* counter, const NetCfg& c, bool update,
+                        cudaStream_t s) {
+  const int grid = stream_grid(D.n / Vec<R>::W);
+  if (update) {
+    QST_SWITCH_H(D.H, k_w2_pass<R, HH, true><<<grid, 256, 0, s>>>(theta, step, sign, dt, hid, pre, dpre, dtheta, D.n,
+                                                                 partials, counter, rcfg<R>(c), (R)c.slope));
+  } else {
+    QST_SWITCH_H(D.H, k_w2_pass<R, HH, false><<<grid, 256, 0, s>>>(theta, step, sign, dt, hid, pre, dpre, dtheta, D.n,
+                                                                  partials, counter, rcfg<R>(c), (R)c.slope));
+  }
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t net_w1_pass(const Dims& D, R* theta, R* step, int8_t* sign, const R* f, const R* dpre, R* pre, R* hid,
+                        R* dtheta, double* scal, double* partials, unsigned int* counter, const NetCfg& c,
+                        bool update, cudaStream_t s) {
+  const int grid = stream_grid(D.n / Vec<R>::W);
+  if (update) {
+    QST_SWITCH_H(D.H, k_w1_pass<R, HH, true><<<grid, 256, 0, s>>>(theta, step, sign, f, dpre, pre, hid, dtheta, D.n,
+                                                                 scal, partials, counter, rcfg<R>(c), (R)c.slope));
+  } else {
+    QST_SWITCH_H(D.H, k_w1_pass<R, HH, false><<<grid, 256, 0, s>>>(theta, step, sign, f, dpre, pre, hid, dtheta, D.n,
+                                                                  scal, partials, counter, rcfg<R>(c), (R)c.slope));
+  }
+  return cudaGetLastError();
+}
+
+template <class R> cudaError_t net_symmetrize(const Dims& D, const cx_t<R>* Y, R* dt, cudaStream_t s) {
+  const int TS = D.d < 32 ? D.d : 32;
+  const int nt = D.d / TS;
+  k_symmetrize<R, false><<<(unsigned)(nt * (nt + 1) / 2), 256, 0, s>>>(Y, nullptr, nullptr, dt, D.d);
+  return cudaGetLastError();
+}
+
+cudaError_t net_symmetrize_planar(const Dims& D, const float* Yre, const float* Yim, float* dt, cudaStream_t s) {
+  const int TS = D.d < 32 ? D.d : 32;
+  const int nt = D.d / TS;
+  k_symmetrize<float, true><<<(unsigned)(nt * (nt + 1) / 2), 256, 0, s>>>(nullptr, Yre, Yim, dt, D.d);
+  return cudaGetLastError();
+}
+
+#define QST_INST(R)                                                                                              \
+  template cudaError_t net_l1_forward<R>(const Dims&, const R*, const R*, R*, R*, double*, double*, unsigned int*, \
+                                         const NetCfg&, cudaStream_t);                                           \
+  template cudaError_t net_build_T<R>(const Dims&, const R*, const R*, cx_t<R>*, void*, double*, double*,        \
+                                      unsigned int*, cudaStream_t);                                              \
+  template cudaError_t net_w2_pass<R>(const Dims&, R*, R*, int8_t*, const R*, const R*, const R*, R*, R*, double*, \
+                                      unsigned int*, const NetCfg&, bool, cudaStream_t);                         \
+  template cudaError_t net_w1_pass<R>(const Dims&, R*, R*, int8_t*, const R*, const R*, R*, R*, R*, double*,     \
+                                      double*, unsigned int*, const NetCfg&, bool, cudaStream_t);                \
+  template cudaError_t net_symmetrize<R>(const Dims&, const cx_t<R>*, R*, cudaStream_t);
+QST_INST(float)
+QST_INST(double)
+#undef QST_INST
+
+}  // namespace qst

@@ -1,0 +1,103 @@
+// Internal interface between the C ABI (api.cu) and the kernel files of libqst.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace qst {
+
+// Sizes of one N-qubit problem and of the two-pass POVM split.
+//   d = 2^N, n = 4^N, H = 2N.
+//   The POVM map runs in two passes: the low g qubits inside S x S tiles of the
+//   d x d matrix (S = 2^g), then the high h = N - g qubits over an nb x nb grid
+//   (nb = 2^h) for chunks of C low outcomes at a time.
+struct Dims {
+  int N, d, H, g, h, S, nb, C;
+  long long n;
+};
+
+Dims make_dims(int N, bool fp64);
+
+// Device buffers of a context (all owned by the context).
+template <class R> struct Work {
+  using V = cx_t<R>;
+  R* theta;            // parameters, qst_theta_size(N)
+  R* step;             // Rprop step sizes, same layout
+  int8_t* sign;        // Rprop previous-gradient signs, same layout
+  R* pre;              // hidden pre-activation [H]
+  R* hid;              // hidden activation [H]
+  R* dpre;             // dL/dpre [H]
+  V* T;                // T, d x d complex (SIMT products)
+  V* X;                // X = T T (lower tiles written), or rho
+  V* G;                // dL/dX, d x d complex
+  V* Y;                // G T, d x d complex
+  R* Wlo;              // packed low-pass intermediate, n reals
+  R* Whi;              // packed adjoint intermediate, n reals
+  R* dt;               // dL/dt, n reals
+  R* fstage;           // staging copy of a host f, n reals
+  double* scal;        // [0] Tr X, [1] sum f, [2] loss, [3] tr-sum scratch
+  double* partials;    // per-block partial sums
+  unsigned int* counters;  // last-block counters, one per reduction site
+  unsigned int* flags;     // [0] clamp count
+  // mixed precision operands (BF16 hi / lo planes), NULL when unused
+  void* Tb;            // 6 planes of d x d bf16: re_hi, im_hi, nim_hi, re_lo, im_lo, nim_lo
+  void* Gb;            // 4 planes of d x d bf16: re_hi, im_hi, re_lo, im_lo
+  float* Yre;          // d x d float (mixed: real part of G T)
+  float* Yim;          // d x d float (mixed: imaginary part of G T)
+};
+
+enum Counter { CNT_L1 = 0, CNT_T = 1, CNT_NLL = 2, CNT_W2 = 3, CNT_W1 = 4, CNT_TR = 5, CNT_COUNT = 8 };
+constexpr int kPartialBlocks = 1024;   // max blocks of a reducing kernel
+constexpr int kPartialStride = 32;     // doubles per block in `partials` (>= H + 1)
+
+struct NetCfg {
+  double slope;
+  double eta_minus, eta_plus, step_min, step_max;
+};
+
+// ---- POVM map (povm.cu) ----
+template <class R> cudaError_t povm_lo_fwd(const Dims& D, const cx_t<R>* X, R* W, const PovmB<R>& B, cudaStream_t s);
+template <class R> cudaError_t povm_hi_fwd(const Dims& D, const R* W, R* p, const PovmB<R>& B, cudaStream_t s);
+// high-qubit forward, loss and (optionally) high-qubit adjoint; loss -> scal[2]
+template <class R> cudaError_t povm_hi_nll(const Dims& D, const R* W, const R* f, double* scal, R* Wadj,
+                                           double* partials, unsigned int* counter, unsigned int* flags,
+                                           const PovmB<R>& B, bool adjoint, cudaStream_t s);
+template <class R> cudaError_t povm_lo_adj(const Dims& D, const R* Wadj, cx_t<R>* G, const PovmB<R>& B, cudaStream_t s);
+// full Hermitian matrix from its lower tiles, scaled by 1 / scal[0] (rho = X / Tr X)
+template <class R> cudaError_t hermitian_complete(const Dims& D, const cx_t<R>* Xlow, cx_t<R>* rho,
+                                                  const double* scal, cudaStream_t s);
+
+// ---- network (fnn.cu) ----
+template <class R> cudaError_t net_l1_forward(const Dims& D, const R* theta, const R* f, R* pre, R* hid,
+                                              double* scal, double* partials, unsigned int* counter,
+                                              const NetCfg& c, cudaStream_t s);
+template <class R> cudaError_t net_build_T(const Dims& D, const R* theta, const R* hid, cx_t<R>* T, void* Tb,
+                                           double* scal, double* partials, unsigned int* counter, cudaStream_t s);
+template <class R> cudaError_t net_w2_pass(const Dims& D, R* theta, R* step, int8_t* sign, const R* dt,
+                                           const R* hid, const R* pre, R* dpre, R* dtheta,
+                                           double* partials, unsigned int* counter, const NetCfg& c,
+                                           bool update, cudaStream_t s);
+template <class R> cudaError_t net_w1_pass(const Dims& D, R* theta, R* step, int8_t* sign, const R* f,
+                                           const R* dpre, R* pre, R* hid, R* dtheta, double* scal,
+                                           double* partials, unsigned int* counter, const NetCfg& c,
+                                           bool update, cudaStream_t s);
+// dL/dt from Y = G T:  dR_ij = 2(Re Y_ij + Re Y_ji), dR_ji = 2(Im Y_ij - Im Y_ji) (i > j), dR_ii = 2 Re Y_ii
+template <class R> cudaError_t net_symmetrize(const Dims& D, const cx_t<R>* Y, R* dt, cudaStream_t s);
+cudaError_t net_symmetrize_planar(const Dims& D, const float* Yre, const float* Yim, float* dt, cudaStream_t s);
+
+// ---- complex products (gemm_simt.cu) ----
+// C = A B for d x d complex row-major matrices; lower == true computes only tiles I >= J.
+template <class R> cudaError_t cgemm_simt(int d, const cx_t<R>* A, const cx_t<R>* B, cx_t<R>* C, bool lower,
+                                          cudaStream_t s);
+
+// ---- tensor-core products (gemm_tc.cu) ----
+// BF16 planes from G (complex, FP32): re_hi, im_hi, re_lo, im_lo
+cudaError_t split_bf16_G(int d, const float2* G, void* Gb, cudaStream_t s);
+// X = T T (lower tiles, complex FP32 out) and Y = G T (full, planar FP32 out) on tcgen05
+cudaError_t tc_herm_square(int d, const void* Tb, float2* X, cudaStream_t s);
+cudaError_t tc_gt_product(int d, const void* Gb, const void* Tb, float* Yre, float* Yim, cudaStream_t s);
+bool tc_available();
+
+}  // namespace qst

@@ -1,0 +1,362 @@
+// Product-POVM map of Sec. 3.3 (eq. PS), its adjoint, and the likelihood of Sec. 3.1.
+//
+//   q_k = Tr[(M_k1 (x) ... (x) M_kN) X],   k = sum_b a_b 4^b,  qubit b <-> row/col bit b.
+//
+// The map is a chain of per-qubit 4 x 4 mode contractions on the index pair
+// (i_b, j_b) of X.  It runs in two passes:
+//   pass 1 (povm_lo_*): one CTA per lower S x S tile (I >= J) of the d x d matrix
+//     applies the g low qubits in shared memory.  For fixed low outcomes a_lo the
+//     result Z[I, J, a_lo] is Hermitian in (I, J), so only lower tiles are read and
+//     the result is stored packed as reals: Re at [I][J], Im at [J][I]
+//     (W[(I nb + J) S^2 + a_lo]).
+//   pass 2 (povm_hi_*): one CTA per chunk of C low outcomes loads the nb x nb
+//     Hermitian matrices of its chunk, applies the h high qubits, and writes q
+//     (forward), or evaluates the likelihood, forms g_k = dL/dq_k and applies the
+//     adjoint high-qubit maps (training step).
+// The adjoint pass 1 (povm_lo_adj) maps the packed adjoint back to the full
+// Hermitian d x d matrix G = sum_k g_k M_k.
+#include <float.h>
+
+#include "impl.h"
+
+namespace qst {
+
+Dims make_dims(int N, bool fp64) {
+  Dims D;
+  D.N = N;
+  D.d = 1 << N;
+  D.n = 1LL << (2 * N);
+  D.H = 2 * N;
+  int g = N < 6 ? N : 6;
+  if (!fp64 && N >= 12) g = 7;
+  D.g = g;
+  D.h = N - g;
+  D.S = 1 << g;
+  D.nb = 1 << D.h;
+  const long long SS = 1LL << (2 * g);
+  const int vbytes = fp64 ? 16 : 8;
+  long long budget = 96 * 1024;
+  long long C = 1;
+  while (C * 2 <= SS && (long long)D.nb * D.nb * (C * 2) * vbytes <= budget) C *= 2;
+  D.C = (int)C;
+  return D;
+}
+
+template <class T> __device__ __forceinline__ T min_normal();
+template <> __device__ __forceinline__ float min_normal<float>() { return FLT_MIN; }
+template <> __device__ __forceinline__ double min_normal<double>() { return DBL_MIN; }
+
+// Apply per-qubit mode maps on bits [0, bits) of (row, col) of an array
+// Z[(r * pitch + c) * C + cc], r, c < 2^side_log2, cc < C = 2^logC.
+template <class R, bool ADJ>
+__device__ void apply_modes(cx_t<R>* Z, int side_log2, int pitch, int logC, int bits, const PovmB<R>& B) {
+  using V = cx_t<R>;
+  if (bits <= 0) return;
+  const int C = 1 << logC;
+  const int half_log2 = side_log2 - 1;
+  const int groups = 1 << (2 * half_log2 + logC);
+  for (int b = 0; b < bits; ++b) {
+    const int bit = 1 << b;
+    const int lowmask = bit - 1;
+    for (int t = threadIdx.x; t < groups; t += blockDim.x) {
+      const int cc = t & (C - 1);
+      const int gi = t >> logC;
+      const int rr = gi >> half_log2;
+      const int c2 = gi & ((1 << half_log2) - 1);
+      const int r0 = ((rr & ~lowmask) << 1) | (rr & lowmask);
+      const int c0 = ((c2 & ~lowmask) << 1) | (c2 & lowmask);
+      V* p00 = Z + ((size_t)(r0 * pitch + c0) << logC) + cc;
+      V* p01 = p00 + ((size_t)bit << logC);
+      V* p10 = p00 + ((size_t)(bit * pitch) << logC);
+      V* p11 = p10 + ((size_t)bit << logC);
+      V x00 = *p00, x01 = *p01, x10 = *p10, x11 = *p11;
+      if (ADJ) mode_adj(B, x00, x01, x10, x11);
+      else mode_fwd(B, x00, x01, x10, x11);
+      *p00 = x00; *p01 = x01; *p10 = x10; *p11 = x11;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- pass 1
+template <class R>
+__global__ void __launch_bounds__(256) k_povm_lo_fwd(const cx_t<R>* __restrict__ X, R* __restrict__ W,
+                                                      int N, int g, PovmB<R> B) {
+  using V = cx_t<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* Z = reinterpret_cast<V*>(smem_raw);
+  const int S = 1 << g, pitch = S + 1, nb = 1 << (N - g);
+  const long long d = 1LL << N;
+  int I, J;
+  tri_decode(blockIdx.x, I, J);
+  const V* src = X + (long long)I * S * d + (long long)J * S;
+  for (int e = threadIdx.x; e < S * S; e += blockDim.x) {
+    const int il = e >> g, jl = e & (S - 1);
+    Z[il * pitch + jl] = src[il * d + jl];
+  }
+  __syncthreads();
+  if (I == J) {  // diagonal tile: rebuild the upper triangle from the lower one
+    for (int e = threadIdx.x; e < S * S; e += blockDim.x) {
+      const int il = e >> g, jl = e & (S - 1);
+      if (il < jl) Z[il * pitch + jl] = cconj(Z[jl * pitch + il]);
+    }
+    __syncthreads();
+  }
+  apply_modes<R, false>(Z, g, pitch, 0, g, B);
+  const long long SS = (long long)S * S;
+  R* wlo = W + ((long long)I * nb + J) * SS;
+  R* whi = W + ((long long)J * nb + I) * SS;
+  for (int al = threadIdx.x; al < S * S; al += blockDim.x) {
+    const V v = Z[row_of(al) * pitch + col_of(al)];
+    wlo[al] = v.x;
+    if (I != J) whi[al] = v.y;
+  }
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) k_povm_lo_adj(const R* __restrict__ W, cx_t<R>* __restrict__ G,
+                                                      int N, int g, PovmB<R> B) {
+  using V = cx_t<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* Z = reinterpret_cast<V*>(smem_raw);
+  const int S = 1 << g, pitch = S + 1, nb = 1 << (N - g);
+  const long long d = 1LL << N;
+  int I, J;
+  tri_decode(blockIdx.x, I, J);
+  const long long SS = (long long)S * S;
+  const R* wlo = W + ((long long)I * nb + J) * SS;
+  const R* whi = W + ((long long)J * nb + I) * SS;
+  for (int al = threadIdx.x; al < S * S; al += blockDim.x) {
+    const R re = wlo[al];
+    const R im = (I != J) ? whi[al] : R(0);
+    Z[row_of(al) * pitch + col_of(al)] = cmake<V>(re, im);
+  }
+  __syncthreads();
+  apply_modes<R, true>(Z, g, pitch, 0, g, B);
+  V* dst = G + (long long)I * S * d + (long long)J * S;
+  for (int e = threadIdx.x; e < S * S; e += blockDim.x) {
+    const int il = e >> g, jl = e & (S - 1);
+    dst[il * d + jl] = Z[il * pitch + jl];
+  }
+  if (I != J) {
+    V* mir = G + (long long)J * S * d + (long long)I * S;
+    for (int e = threadIdx.x; e < S * S; e += blockDim.x) {
+      const int r = e >> g, c = e & (S - 1);
+      mir[r * d + c] = cconj(Z[c * pitch + r]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- pass 2
+template <class R>
+__device__ __forceinline__ void load_hermitian_chunk(cx_t<R>* Z, const R* __restrict__ W, int h, int logC,
+                                                     long long SS, long long al0) {
+  using V = cx_t<R>;
+  const int nb = 1 << h, C = 1 << logC;
+  const int tot = nb * nb * C;
+  for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+    const int c = t & (C - 1);
+    const int pidx = t >> logC;
+    const int ih = pidx >> h, jh = pidx & (nb - 1);
+    const R a = W[((long long)ih * nb + jh) * SS + al0 + c];
+    V v;
+    if (ih == jh) {
+      v = cmake<V>(a, R(0));
+    } else {
+      const R b = W[((long long)jh * nb + ih) * SS + al0 + c];
+      v = ih > jh ? cmake<V>(a, b) : cmake<V>(b, -a);
+    }
+    Z[t] = v;
+  }
+  __syncthreads();
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) k_povm_hi_fwd(const R* __restrict__ W, R* __restrict__ p, int N, int g,
+                                                      int logC, PovmB<R> B) {
+  using V = cx_t<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* Z = reinterpret_cast<V*>(smem_raw);
+  const int h = N - g, nb = 1 << h, C = 1 << logC;
+  const long long SS = 1LL << (2 * g);
+  const long long al0 = (long long)blockIdx.x * C;
+  load_hermitian_chunk<R>(Z, W, h, logC, SS, al0);
+  apply_modes<R, false>(Z, h, nb, logC, h, B);
+  const int tot = nb * nb * C;
+  for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+    const int c = t & (C - 1);
+    const uint32_t ah = (uint32_t)(t >> logC);
+    p[(long long)ah * SS + al0 + c] = Z[((row_of(ah) * nb + col_of(ah)) << logC) + c].x;
+  }
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) k_povm_hi_nll(const R* __restrict__ W, const R* __restrict__ f,
+                                                      double* scal, R* __restrict__ Wadj, double* partials,
+                                                      unsigned int* counter, unsigned int* flags, int N, int g,
+                                                      int logC, PovmB<R> B, int adjoint) {
+  using V = cx_t<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* Z = reinterpret_cast<V*>(smem_raw);
+  __shared__ double red[32];
+  const int h = N - g, nb = 1 << h, C = 1 << logC;
+  const long long SS = 1LL << (2 * g);
+  const long long al0 = (long long)blockIdx.x * C;
+  load_hermitian_chunk<R>(Z, W, h, logC, SS, al0);
+  apply_modes<R, false>(Z, h, nb, logC, h, B);
+
+  // L = -sum_k f_k log q_k + (sum_k f_k) log Tr X;  g_k = dL/dq_k = -f_k / q_k + sum f / Tr X
+  const double tX = scal[0], sumf = scal[1];
+  const R gconst = (R)(sumf / tX);
+  const R qmin = min_normal<R>();
+  double acc = 0.0;
+  unsigned int nclamp = 0;
+  const int tot = nb * nb * C;
+  for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+    const int c = t & (C - 1);
+    const uint32_t ah = (uint32_t)(t >> logC);
+    const int zi = ((row_of(ah) * nb + col_of(ah)) << logC) + c;
+    R q = Z[zi].x;
+    const R fk = f[(long long)ah * SS + al0 + c];
+    R gk = gconst;
+    if (fk > R(0)) {
+      if (!(q >= qmin)) { q = qmin; ++nclamp; }
+      acc += (double)fk * (double)log(q);
+      gk -= fk / q;
+    }
+    Z[zi] = cmake<V>(gk, R(0));
+  }
+  if (nclamp) atomicAdd(flags, nclamp);
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) partials[blockIdx.x] = v;
+  }
+  if (adjoint) {
+    apply_modes<R, true>(Z, h, nb, logC, h, B);
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+      const int c = t & (C - 1);
+      const int pidx = t >> logC;
+      const int ih = pidx >> h, jh = pidx & (nb - 1);
+      if (ih < jh) continue;
+      const V v = Z[t];
+      Wadj[((long long)ih * nb + jh) * SS + al0 + c] = v.x;
+      if (ih > jh) Wadj[((long long)jh * nb + ih) * SS + al0 + c] = v.y;
+    }
+  }
+  if (last_block_arrived(counter)) {
+    if (threadIdx.x < 32) {
+      double v = 0.0;
+      for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) v += partials[b];
+      v = warp_sum(v);
+      if (threadIdx.x == 0) {
+        scal[2] = -v + sumf * log(tX);
+        *counter = 0u;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- rho = X / Tr X from lower tiles
+template <class R>
+__global__ void __launch_bounds__(256) k_herm_complete(const cx_t<R>* __restrict__ X, cx_t<R>* __restrict__ rho,
+                                                        int d, const double* scal) {
+  using V = cx_t<R>;
+  __shared__ V tile[32][33];
+  const int TS = d < 32 ? d : 32;
+  const int bi = blockIdx.y, bj = blockIdx.x;  // output tile (row block, col block)
+  const R s = (R)(1.0 / scal[0]);
+  // load the tile of the lower triangle that covers this output tile
+  const int lr = bi >= bj ? bi : bj, lc = bi >= bj ? bj : bi;
+  for (int e = threadIdx.x; e < TS * TS; e += blockDim.x) {
+    const int r = e / TS, c = e % TS;
+    tile[r][c] = X[(long long)(lr * TS + r) * d + lc * TS + c];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < TS * TS; e += blockDim.x) {
+    const int r = e / TS, c = e % TS;
+    const int gi = bi * TS + r, gj = bj * TS + c;
+    V v;
+    if (bi > bj) v = tile[r][c];
+    else if (bi < bj) v = cconj(tile[c][r]);
+    else v = gi >= gj ? tile[r][c] : cconj(tile[c][r]);
+    rho[(long long)gi * d + gj] = cscale(v, s);
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+static int ilog2i(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
+
+template <class R> static cudaError_t set_smem(const void* fn, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <class R>
+cudaError_t povm_lo_fwd(const Dims& D, const cx_t<R>* X, R* W, const PovmB<R>& B, cudaStream_t s) {
+  const size_t sm = (size_t)D.S * (D.S + 1) * sizeof(cx_t<R>);
+  cudaError_t e = set_smem<R>((const void*)k_povm_lo_fwd<R>, sm);
+  if (e != cudaSuccess) return e;
+  const unsigned tiles = (unsigned)(D.nb * (D.nb + 1) / 2);
+  k_povm_lo_fwd<R><<<tiles, 256, sm, s>>>(X, W, D.N, D.g, B);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t povm_lo_adj(const Dims& D, const R* Wadj, cx_t<R>* G, const PovmB<R>& B, cudaStream_t s) {
+  const size_t sm = (size_t)D.S * (D.S + 1) * sizeof(cx_t<R>);
+  cudaError_t e = set_smem<R>((const void*)k_povm_lo_adj<R>, sm);
+  if (e != cudaSuccess) return e;
+  const unsigned tiles = (unsigned)(D.nb * (D.nb + 1) / 2);
+  k_povm_lo_adj<R><<<tiles, 256, sm, s>>>(Wadj, G, D.N, D.g, B);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t povm_hi_fwd(const Dims& D, const R* W, R* p, const PovmB<R>& B, cudaStream_t s) {
+  const size_t sm = (size_t)D.nb * D.nb * D.C * sizeof(cx_t<R>);
+  cudaError_t e = set_smem<R>((const void*)k_povm_hi_fwd<R>, sm);
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = (unsigned)((1LL << (2 * D.g)) / D.C);
+  k_povm_hi_fwd<R><<<blocks, 256, sm, s>>>(W, p, D.N, D.g, ilog2i(D.C), B);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t povm_hi_nll(const Dims& D, const R* W, const R* f, double* scal, R* Wadj, double* partials,
+                        unsigned int* counter, unsigned int* flags, const PovmB<R>& B, bool adjoint,
+                        cudaStream_t s) {
+  const size_t sm = (size_t)D.nb * D.nb * D.C * sizeof(cx_t<R>);
+  cudaError_t e = set_smem<R>((const void*)k_povm_hi_nll<R>, sm);
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = (unsigned)((1LL << (2 * D.g)) / D.C);
+  if (blocks > (unsigned)kPartialBlocks * kPartialStride) return cudaErrorInvalidConfiguration;
+  k_povm_hi_nll<R><<<blocks, 256, sm, s>>>(W, f, scal, Wadj, partials, counter, flags, D.N, D.g,
+                                          ilog2i(D.C), B, adjoint ? 1 : 0);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t hermitian_complete(const Dims& D, const cx_t<R>* Xlow, cx_t<R>* rho, const double* scal,
+                               cudaStream_t s) {
+  const int TS = D.d < 32 ? D.d : 32;
+  dim3 grid(D.d / TS, D.d / TS);
+  k_herm_complete<R><<<grid, 256, 0, s>>>(Xlow, rho, D.d, scal);
+  return cudaGetLastError();
+}
+
+#define QST_INST(R)                                                                                        \
+  template cudaError_t povm_lo_fwd<R>(const Dims&, const cx_t<R>*, R*, const PovmB<R>&, cudaStream_t);       \
+  template cudaError_t povm_lo_adj<R>(const Dims&, const R*, cx_t<R>*, const PovmB<R>&, cudaStream_t);       \
+  template cudaError_t povm_hi_fwd<R>(const Dims&, const R*, R*, const PovmB<R>&, cudaStream_t);             \
+  template cudaError_t povm_hi_nll<R>(const Dims&, const R*, const R*, double*, R*, double*, unsigned int*,  \
+                                      unsigned int*, const PovmB<R>&, bool, cudaStream_t);                   \
+  template cudaError_t hermitian_complete<R>(const Dims&, const cx_t<R>*, cx_t<R>*, const double*, cudaStream_t);
+QST_INST(float)
+QST_INST(double)
+#undef QST_INST
+
+}  // namespace qst

@@ -1,0 +1,235 @@
+"""Thin ctypes binding of libqst.so (include/qst.h), same call names as the C ABI.
+
+Only argument marshalling happens here: tensors are passed as raw pointers
+(``tensor.data_ptr()`` for CUDA tensors, the array address for NumPy / CPU
+buffers) and every step of the computation runs inside libqst's CUDA kernels.
+If the shared library is missing, every call raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqst.so")
+
+QST_OK = 0
+QST_E_INVAL = -1
+QST_E_INPUT = -2
+QST_E_NOMEM = -3
+QST_E_CUDA = -4
+QST_E_TIMEOUT = -5
+QST_E_STATE = -6
+QST_E_UNSUPPORTED = -7
+QST_W_CLAMP = 1
+
+QST_MAP_CHOL_H = 0
+QST_MAP_ABS_P = 1
+QST_FP64 = 0
+QST_FP32 = 1
+QST_MIXED = 2
+
+EXPORTED = [
+    "qst_default_options", "qst_theta_size", "qst_init", "qst_set_params", "qst_get_params",
+    "qst_probs", "qst_loss_grad", "qst_step", "qst_reconstruct", "qst_get_rho",
+    "qst_state_bytes", "qst_get_state", "qst_set_state", "qst_iterations",
+    "qst_kernel_launches", "qst_sync", "qst_strerror", "qst_destroy",
+]
+
+
+class qst_options(ctypes.Structure):
+    _fields_ = [
+        ("mapping", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("P", ctypes.c_double),
+        ("lr", ctypes.c_double),
+        ("eta_minus", ctypes.c_double),
+        ("eta_plus", ctypes.c_double),
+        ("step_min", ctypes.c_double),
+        ("step_max", ctypes.c_double),
+        ("leaky_slope", ctypes.c_double),
+    ]
+
+
+class QstError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {strerror(status)} ({status})")
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libqst.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} not found: build it with paper_2207_05341_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    pd = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "qst_default_options": (None, [ctypes.POINTER(qst_options)]),
+        "qst_theta_size": (sz, [i]),
+        "qst_init": (i, [ctypes.POINTER(vp), i, vp, i, ctypes.POINTER(qst_options), vp]),
+        "qst_set_params": (i, [vp, vp]),
+        "qst_get_params": (i, [vp, vp]),
+        "qst_probs": (i, [vp, vp, vp]),
+        "qst_loss_grad": (i, [vp, vp, vp, pd, vp]),
+        "qst_step": (i, [vp, vp, pd]),
+        "qst_reconstruct": (i, [vp, vp, i, vp, pd]),
+        "qst_get_rho": (i, [vp, vp, vp, pd]),
+        "qst_state_bytes": (sz, [vp]),
+        "qst_get_state": (i, [vp, vp, sz]),
+        "qst_set_state": (i, [vp, vp, sz]),
+        "qst_iterations": (ctypes.c_longlong, [vp]),
+        "qst_kernel_launches": (ctypes.c_longlong, [vp]),
+        "qst_sync": (i, [vp]),
+        "qst_strerror": (ctypes.c_char_p, [i]),
+        "qst_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def ptr(x) -> int | None:
+    """Raw address of a torch tensor, NumPy array, integer address or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"cannot take the address of {type(x)!r}")
+
+
+def strerror(status: int) -> str:
+    try:
+        return load().qst_strerror(int(status)).decode()
+    except RuntimeError:
+        return f"status {status}"
+
+
+def _check(status: int, what: str, allow_warn: bool = True) -> int:
+    if status < 0 or (status > 0 and not allow_warn):
+        raise QstError(status, what)
+    return status
+
+
+def qst_default_options() -> qst_options:
+    o = qst_options()
+    load().qst_default_options(ctypes.byref(o))
+    return o
+
+
+def qst_theta_size(N: int) -> int:
+    return int(load().qst_theta_size(int(N)))
+
+
+def tetrahedral_povm_flat() -> np.ndarray:
+    """The Sec. 4.1 tetrahedral POVM as the K*2*2 interleaved complex doubles qst_init takes."""
+    s = np.array([[1, 1, 1], [-1, -1, 1], [-1, 1, -1], [1, -1, -1]], dtype=float) / np.sqrt(3.0)
+    out = np.empty((4, 2, 2, 2), dtype=np.float64)
+    for a in range(4):
+        x, y, z = s[a]
+        m = np.array([[1 + z, x - 1j * y], [x + 1j * y, 1 - z]]) / 4.0
+        out[a, :, :, 0] = m.real
+        out[a, :, :, 1] = m.imag
+    return np.ascontiguousarray(out.reshape(-1))
+
+
+def qst_init(N: int, povm=None, K: int = 4, opt: qst_options | None = None, stream: int = 0) -> int:
+    """Create a context; returns the opaque handle (an integer address)."""
+    if povm is None:
+        povm = tetrahedral_povm_flat()
+    povm = np.ascontiguousarray(povm, dtype=np.float64)
+    h = ctypes.c_void_p()
+    st = load().qst_init(ctypes.byref(h), int(N), povm.ctypes.data, int(K),
+                         ctypes.byref(opt) if opt is not None else None, stream or None)
+    _check(st, "qst_init")
+    return h.value
+
+
+def qst_set_params(ctx: int, theta) -> int:
+    return _check(load().qst_set_params(ctx, ptr(theta)), "qst_set_params")
+
+
+def qst_get_params(ctx: int, theta) -> int:
+    return _check(load().qst_get_params(ctx, ptr(theta)), "qst_get_params")
+
+
+def qst_probs(ctx: int, rho, p) -> int:
+    return _check(load().qst_probs(ctx, ptr(rho), ptr(p)), "qst_probs")
+
+
+def qst_loss_grad(ctx: int, theta, f, dtheta) -> tuple[float, int]:
+    loss = ctypes.c_double()
+    st = _check(load().qst_loss_grad(ctx, ptr(theta), ptr(f), ctypes.byref(loss), ptr(dtheta)), "qst_loss_grad")
+    return loss.value, st
+
+
+def qst_step(ctx: int, f, want_loss: bool = True) -> tuple[float | None, int]:
+    loss = ctypes.c_double()
+    st = _check(load().qst_step(ctx, ptr(f), ctypes.byref(loss) if want_loss else None), "qst_step")
+    return (loss.value if want_loss else None), st
+
+
+def qst_reconstruct(ctx: int, f, iters: int, rho_out=None, want_loss: bool = True) -> tuple[float | None, int]:
+    loss = ctypes.c_double()
+    st = _check(load().qst_reconstruct(ctx, ptr(f), int(iters), ptr(rho_out),
+                                       ctypes.byref(loss) if want_loss else None), "qst_reconstruct")
+    return (loss.value if want_loss else None), st
+
+
+def qst_get_rho(ctx: int, f, rho_out, want_loss: bool = False) -> tuple[float | None, int]:
+    loss = ctypes.c_double()
+    st = _check(load().qst_get_rho(ctx, ptr(f), ptr(rho_out), ctypes.byref(loss) if want_loss else None),
+                "qst_get_rho")
+    return (loss.value if want_loss else None), st
+
+
+def qst_state_bytes(ctx: int) -> int:
+    return int(load().qst_state_bytes(ctx))
+
+
+def qst_get_state(ctx: int) -> bytes:
+    n = qst_state_bytes(ctx)
+    buf = ctypes.create_string_buffer(n)
+    _check(load().qst_get_state(ctx, buf, n), "qst_get_state")
+    return buf.raw
+
+
+def qst_set_state(ctx: int, blob: bytes) -> int:
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    return _check(load().qst_set_state(ctx, buf, len(blob)), "qst_set_state")
+
+
+def qst_iterations(ctx: int) -> int:
+    return int(load().qst_iterations(ctx))
+
+
+def qst_kernel_launches(ctx: int) -> int:
+    return int(load().qst_kernel_launches(ctx))
+
+
+def qst_sync(ctx: int) -> int:
+    return _check(load().qst_sync(ctx), "qst_sync")
+
+
+def qst_destroy(ctx: int) -> None:
+    if ctx:
+        load().qst_destroy(ctx)

@@ -1,0 +1,58 @@
+"""CPU-side checks of the C ABI: the library loads and exports what include/qst.h declares.
+
+No compute call is made (there may be no GPU); only host-only entry points run.
+"""
+import os
+import re
+
+import pytest
+
+from paper_2207_05341_gb300 import qst
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(qst_[a-z_0-9]+)\s*\(", txt))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(qst.LIB_PATH):
+        from paper_2207_05341_gb300 import build
+        build.build()
+    return qst.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    declared = _declared()
+    assert "qst_init" in declared and "qst_step" in declared
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(qst.EXPORTED) <= declared
+
+
+def test_host_only_entry_points(lib):
+    o = qst.qst_default_options()
+    assert o.lr == pytest.approx(1e-3) and o.eta_minus == 0.5 and o.eta_plus == 1.2
+    assert o.step_min == 1e-6 and o.step_max == 50.0 and o.leaky_slope == 0.01
+    assert o.mapping == qst.QST_MAP_CHOL_H and o.precision == qst.QST_FP32
+    for N in (1, 2, 11, 12):
+        n, H = 4 ** N, 2 * N
+        assert qst.qst_theta_size(N) == 2 * H * n + n + H
+    assert qst.qst_theta_size(0) == 0 and qst.qst_theta_size(13) == 0
+    assert "invalid" in qst.strerror(qst.QST_E_INVAL)
+    assert "clamp" in qst.strerror(qst.QST_W_CLAMP)
+
+
+def test_binding_povm_matches_paper():
+    import numpy as np
+    import oracle as O
+    flat = qst.tetrahedral_povm_flat().reshape(4, 2, 2, 2)
+    np.testing.assert_allclose(flat[..., 0] + 1j * flat[..., 1], O.tetrahedral_povm(), atol=1e-16)

@@ -167,3 +167,11 @@ def test_adjoint_bruteforce_and_identity(N):
     lhs = np.dot(g, O.born_probabilities(X, M).real)
     rhs = np.real(np.trace(G @ X))
     assert abs(lhs - rhs) < 1e-12 * max(1.0, abs(lhs))
+
+
+def test_single_outcome_helper_matches_full_map():
+    M = O.tetrahedral_povm()
+    rho = synth.ginibre_mixed(4, 5, 77)
+    p = O.born_probabilities(rho, M)
+    for k in (0, 1, 17, 100, 255):
+        assert abs(O.born_probability_at(rho, M, k) - p[k]) < 1e-15
