@@ -161,17 +161,33 @@ def test_gradient_central_fd_n8(rank):
     try:
         L, g, _ = _gpu_loss_grad(N, theta, f, qst.QST_FP32, ctx)
         rng = np.random.default_rng(rank)
-        dirs = [g / np.linalg.norm(g)]
+        gn = np.linalg.norm(g)
+        # steepest direction, two directions correlated with g (v_i = g_i u_i, u_i ~ U(0.5, 1.5)),
+        # and one unstructured direction; unit length, so |dL/dv| <= ||g||
+        dirs = [g / gn]
         for _ in range(2):
-            v = rng.standard_normal(theta.size) * np.abs(g).clip(1e-12)
+            v = g * rng.uniform(0.5, 1.5, theta.size)
             dirs.append(v / np.linalg.norm(v))
+        v = rng.standard_normal(theta.size)
+        dirs.append(v / np.linalg.norm(v))
         h = 1e-3
+        th64 = theta.astype(np.float32).astype(np.float64)
+        f64 = f.astype(np.float32).astype(np.float64)
+        _, g64, _ = O.loss_and_grad(th64, f64, M, N)
         for v in dirs:
             Lp = _gpu_loss_grad(N, theta + h * v, f, qst.QST_FP32, ctx)[0]
             Lm = _gpu_loss_grad(N, theta - h * v, f, qst.QST_FP32, ctx)[0]
             fd = (Lp - Lm) / (2 * h)
             an = float(np.dot(g, v))
-            assert abs(fd - an) <= 1e-3 * abs(an) + 1e-6, (fd, an)
+            # the central difference's own O(h^2) error, measured noise-free by the FP64 oracle
+            Lp64 = O.loss_and_grad(th64 + h * v, f64, M, N)[0]
+            Lm64 = O.loss_and_grad(th64 - h * v, f64, M, N)[0]
+            fd64 = (Lp64 - Lm64) / (2 * h)
+            trunc = abs(fd64 - float(np.dot(g64, v)))
+            # FP32 rounding of the two losses, measured against the FP64 oracle at the same points
+            noise = (abs(Lp - Lp64) + abs(Lm - Lm64)) / (2 * h)
+            assert abs(fd - an) <= 1e-3 * max(abs(an), 0.5 * gn) + trunc + noise, (fd, an, gn, trunc, noise)
+            assert abs(fd - fd64) <= noise + 1e-4 * abs(fd64) + 1e-12
     finally:
         qst.qst_destroy(ctx)
     L_ref, g_ref, _ = O.loss_and_grad(theta.astype(np.float32).astype(np.float64),
