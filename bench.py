@@ -1,0 +1,491 @@
+"""Benchmark of the NN-QST maximum-likelihood iteration on one GB300 (N = 11 qubits).
+
+One step = one full iteration of the hot path (network forward, Hermitian T,
+X = T T, POVM map, likelihood, adjoint, G T, backward, Rprop) through the C ABI
+(qst_step).  Prints ONE JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload (synthetic, seeded): N = 11, a Haar-random pure state mixed with
+depolarising noise, 10^7 multinomial shots of the tetrahedral product POVM, the
+3-layer network (4^11 -> 22 -> 4^11) from a seeded default initialisation.
+Under torchrun (N > 1 GPUs) every rank runs its own independent tomography
+(replicas; there is no collective in the method's data path).
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "11-qubit QST MLE iters/s & time-to-fidelity 0.99: mixed vs plain FP32, 1 GB300"
+UNIT = "iters/s"
+NQ = 11
+SHOTS = 10**7
+LAMBDAS = (0.0, 0.1, 0.2)
+STATE_SEEDS = (20, 21, 22)
+THETA_SEED = 23
+COUNT_SEED = 24
+FID_TARGET = 0.99
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+
+
+def workload_name(lam):
+    return (f"N=11 qubits (rho 2048x2048, 4^11 outcomes), Haar pure state + depolarizing lambda={lam}, "
+            f"10^7 shots, Chol_H, FNN 4^11->22->4^11, Rprop")
+
+
+# ------------------------------------------------------------------ helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks sampled every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            out = {}
+            for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained"):
+                for kk, vv in d.items():
+                    if kk.startswith(k) and isinstance(vv, (int, float)):
+                        out.setdefault(k, float(vv))
+            if "hbm_gbs" in out:
+                return out, "measured"
+        except Exception:
+            pass
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+def kernel_sources_hash():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2207_05341_gb300", "csrc", "*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(phase, prec_name):
+    """DRAM traffic per launch from the committed ncu summary, if it matches the current sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    if d.get("sources_sha") != kernel_sources_hash():
+        return None
+    return d.get("per_launch_bytes", {}).get(f"{prec_name}:{phase}")
+
+
+# ------------------------------------------------------------------ algorithmic work per phase (N = 11)
+def phase_work(phase, N, mixed):
+    """(bound, algorithmic amount per launch, unit) of each phase, as stated in the design notes."""
+    n = 4 ** N
+    d = 2 ** N
+    H = 2 * N
+    if phase == "build_T":
+        return "hbm", (H + 1) * 4 * n + (12 if mixed else 8) * n, "B"
+    if phase == "x_fwd":
+        return ("tensor" if mixed else "alu"), 4 * d ** 3, "FLOP"
+    if phase == "gt":
+        return ("tensor" if mixed else "alu"), 8 * d ** 3, "FLOP"
+    if phase == "povm_lo":
+        return "hbm", 4 * n + 4 * n, "B"
+    if phase == "povm_hi":
+        return "hbm", 4 * n + 4 * n + 4 * n, "B"
+    if phase == "povm_adj":
+        return "hbm", 4 * n + 8 * n, "B"
+    if phase == "sym":
+        return "hbm", 8 * n + 4 * n, "B"
+    if phase == "w2":
+        return "hbm", 18 * H * n + 22 * n, "B"
+    if phase == "w1":
+        return "hbm", 18 * H * n + 4 * n, "B"
+    if phase == "hidden":
+        return "hbm", 4 * H * n + 4 * n, "B"
+    return "hbm", 0, "B"
+
+
+# ------------------------------------------------------------------ evaluation (off the clock)
+def fidelity_depolarized(torch, rho_hat, psi, lam):
+    """F_q of Sec. 2.3 between rho_hat and (1-lam)|psi><psi| + lam I/d, evaluated on the GPU.
+
+    sqrt(rho) = b I + (sqrt(1 - lam + lam/d) - b)|psi><psi| with b = sqrt(lam/d), then
+    F = (sum_i sqrt(w_i))^2 over the eigenvalues w of sqrt(rho) rho_hat sqrt(rho).
+    Measurement harness only (not part of the hot path).
+    """
+    d = rho_hat.shape[0]
+    if lam == 0.0:
+        return float(torch.real(torch.vdot(psi, rho_hat @ psi)))
+    b = (lam / d) ** 0.5
+    a = (1 - lam + lam / d) ** 0.5 - b
+    S = a * torch.outer(psi, psi.conj())
+    S.diagonal().add_(b)
+    Mx = S @ rho_hat @ S
+    Mx = 0.5 * (Mx + Mx.conj().T)
+    w = torch.linalg.eigvalsh(Mx).clamp_min(0)
+    return float(torch.sqrt(w).sum() ** 2)
+
+
+# ------------------------------------------------------------------ our arm
+def make_inputs(torch, qst, synth, dev, lam, seed):
+    """Target state, exact probabilities (by the library's own POVM map) and seeded counts."""
+    psi = synth.haar_pure(NQ, seed)
+    rho = synth.depolarized(psi, lam)
+    ctx = qst.qst_init(NQ)
+    try:
+        rho_t = torch.from_numpy(rho.astype(np.complex64)).to(dev)
+        P = torch.empty(4 ** NQ, device=dev)
+        qst.qst_probs(ctx, rho_t, P)
+        P = P.double().cpu().numpy()
+    finally:
+        qst.qst_destroy(ctx)
+    f = synth.frequencies(synth.multinomial_counts(P, SHOTS, COUNT_SEED + seed), np.float32)
+    return psi, f
+
+
+def time_steps(torch, qst, ctx, f_dev, K, stream):
+    l0 = qst.qst_kernel_launches(ctx)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        qst.qst_step(ctx, f_dev, want_loss=False)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1), qst.qst_kernel_launches(ctx) - l0
+
+
+def run_precision(torch, qst, synth, dev, stream, prec, theta0, f, K, W, dist):
+    opt = qst.qst_default_options()
+    opt.precision = prec
+    ctx = qst.qst_init(NQ, opt=opt, stream=stream.cuda_stream)
+    try:
+        qst.qst_set_params(ctx, theta0)
+        f_dev = torch.from_numpy(f).to(dev)
+        for _ in range(W):
+            qst.qst_step(ctx, f_dev, want_loss=False)
+        qst.qst_timing_enable(ctx, K + 1)
+        torch.cuda.synchronize()
+        dist.barrier()
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            ms, launches = time_steps(torch, qst, ctx, f_dev, K, stream)
+        phases = qst.qst_timing_read(ctx)
+        qst.qst_timing_enable(ctx, 0)
+        # end to end: pinned host f copied in and the loss read back every step
+        f_pin = torch.from_numpy(f).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            qst.qst_step(ctx, f_pin, want_loss=True)
+        e2e_s = time.perf_counter() - t0
+        return {"ms": ms, "launches": launches, "phases": phases, "clocks": clk.summary(), "e2e_s": e2e_s}
+    finally:
+        qst.qst_destroy(ctx)
+
+
+def time_to_fidelity(torch, qst, dev, stream, prec, theta0, f, psi, lam, max_iters, every):
+    opt = qst.qst_default_options()
+    opt.precision = prec
+    ctx = qst.qst_init(NQ, opt=opt, stream=stream.cuda_stream)
+    d = 2 ** NQ
+    try:
+        qst.qst_set_params(ctx, theta0)
+        f_dev = torch.from_numpy(f).to(dev)
+        psi_t = torch.from_numpy(psi.astype(np.complex64)).to(dev)
+        rho = torch.empty((d, d), dtype=torch.complex64, device=dev)
+        gpu_ms = 0.0
+        it = 0
+        F = None
+        while it < max_iters:
+            ms, _ = time_steps(torch, qst, ctx, f_dev, every, stream)
+            gpu_ms += ms
+            it += every
+            qst.qst_get_rho(ctx, f_dev, rho)
+            F = fidelity_depolarized(torch, rho, psi_t, lam)
+            if F >= FID_TARGET:
+                return {"lambda": lam, "reached": True, "iters": it, "seconds": gpu_ms / 1e3, "F": F}
+        return {"lambda": lam, "reached": False, "iters": it, "seconds": gpu_ms / 1e3, "F": F}
+    finally:
+        qst.qst_destroy(ctx)
+
+
+def cpu_baseline(f, theta0, seconds=12.0):
+    """The FP64 oracle, as it stands, on the host cores: full N = 11 iterations."""
+    import oracle as O
+    M = O.tetrahedral_povm()
+    theta = theta0.astype(np.float64)
+    f64 = f.astype(np.float64)
+    st = O.RpropState(theta.size)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        _, g, _ = O.loss_and_grad(theta, f64, M, NQ)
+        theta = O.rprop_update(theta, g, st)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or n >= 8:
+            break
+    return {"value": n / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n} full N=11 iterations (loss, analytic gradient, Rprop) in FP64 NumPy, {el:.1f} s"}
+
+
+class _NoDist:
+    def barrier(self):
+        pass
+
+
+def profile_only(args):
+    """Short, fixed launch sequence for ncu: inputs, then a few steps of each available path."""
+    import torch
+
+    from paper_2207_05341_gb300 import qst, synth
+    qst.load()
+    dev = torch.device("cuda", 0)
+    psi, f = make_inputs(torch, qst, synth, dev, LAMBDAS[1], STATE_SEEDS[1])
+    theta0 = synth.init_theta(NQ, THETA_SEED).astype(np.float32)
+    f_dev = torch.from_numpy(f).to(dev)
+    for prec in (qst.QST_FP32, qst.QST_MIXED):
+        o = qst.qst_default_options()
+        o.precision = prec
+        try:
+            ctx = qst.qst_init(NQ, opt=o)
+        except qst.QstError:
+            continue
+        try:
+            qst.qst_set_params(ctx, theta0)
+            for _ in range(args.profile_steps):
+                qst.qst_step(ctx, f_dev, want_loss=False)
+            qst.qst_sync(ctx)
+        finally:
+            qst.qst_destroy(ctx)
+    torch.cuda.synchronize()
+
+
+def main_ours(args):
+    import torch
+
+    from paper_2207_05341_gb300 import qst, synth
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = _NoDist()
+    if ws > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("gloo")
+        dist = tdist
+    qst.load()
+    stream = torch.cuda.Stream(device=dev)
+    lam = LAMBDAS[1]
+    psi, f = make_inputs(torch, qst, synth, dev, lam, STATE_SEEDS[1])
+    theta0 = synth.init_theta(NQ, THETA_SEED).astype(np.float32)
+
+    mixed_ok = True
+    try:
+        o = qst.qst_default_options(); o.precision = qst.QST_MIXED
+        c = qst.qst_init(NQ, opt=o); qst.qst_destroy(c)
+    except qst.QstError:
+        mixed_ok = False
+    precs = [("plain_fp32", qst.QST_FP32)] + ([("mixed_bf16x3", qst.QST_MIXED)] if mixed_ok else [])
+    res = {}
+    with torch.cuda.stream(stream):
+        for name, prec in precs:
+            res[name] = run_precision(torch, qst, synth, dev, stream, prec, theta0, f, args.steps, args.warmup, dist)
+
+    head = "mixed_bf16x3" if mixed_ok else "plain_fp32"
+    # max over ranks of the timed region
+    ms_local = res[head]["ms"]
+    ms_max = ms_local
+    if ws > 1:
+        t = torch.tensor([ms_local], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = ws * args.steps / (ms_max / 1e3)
+
+    ttf = {}
+    if args.ttf and rank == 0:
+        with torch.cuda.stream(stream):
+            for name, prec in precs:
+                ttf[name] = []
+                for lam_i, seed in zip(LAMBDAS, STATE_SEEDS):
+                    psi_i, f_i = (psi, f) if lam_i == lam else make_inputs(torch, qst, synth, dev, lam_i, seed)
+                    ttf[name].append(time_to_fidelity(torch, qst, dev, stream, prec, theta0, f_i, psi_i, lam_i,
+                                                      args.max_iters, args.fid_every))
+    if ws > 1:
+        dist.barrier()
+    if rank != 0:
+        return
+
+    peaks, peak_src = load_peaks()
+    r = res[head]
+    per = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in r["phases"].items()}
+    dom = max((k for k in per if per[k] > 0), key=lambda k: per[k])
+    bound, amount, unit = phase_work(dom, NQ, head == "mixed_bf16x3")
+    sec = per[dom] / 1e3
+    clk = r["clocks"]
+    if bound == "hbm":
+        achieved, peak, runit = amount / sec / 1e9, peaks["hbm_gbs"], "GB/s"
+    elif bound == "tensor":
+        achieved, peak, runit = amount / sec / 1e12, peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]), "TFLOP/s"
+    else:
+        mhz = clk.get("sm_max_mhz") or 2070.0
+        achieved = amount / sec / 1e12
+        peak = NUM_SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+        runit = "TFLOP/s"
+    e2e_rate = args.steps / res[head]["e2e_s"]
+    n = 4 ** NQ
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x3+f32" if head == "mixed_bf16x3" else "f32", "data": "synthetic",
+        "config": {"workload": workload_name(lam), "path": head, "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": "inputs larger than L2: 1.7 GB of parameters and Rprop state streamed per step, no flush"},
+        "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"), "reasons": clk.get("reasons")},
+        "e2e": {"value": ws * e2e_rate, "unit": UNIT, "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 12},
+        "gpu_launches": int(res[head]["launches"]),
+        "roofline": {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": runit,
+                     "frac": achieved / peak, "peak_source": peak_src if bound != "alu" else "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                     "traffic": recorded_traffic(dom, head)},
+        "paths": {name: {"iters_per_s": ws * args.steps / (v["ms"] / 1e3), "ms_per_step": v["ms"] / args.steps,
+                         "phase_ms": {k: round(pm[0] / pm[1], 4) for k, pm in v["phases"].items() if pm[1]}}
+                  for name, v in res.items()},
+        "time_to_fidelity": ttf if ttf else None,
+        "paper_context": "11-qubit tomography within 2 minutes on a laptop (GTX 1070); not this metric's baseline",
+    }
+    if args.cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(f, theta0, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+
+
+def main_reference(args):
+    """The reference arm: the FP64 NumPy oracle on the host cores, same metric and workload."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2207_05341_gb300 import synth
+    import oracle as O
+    lam = LAMBDAS[1]
+    psi = synth.haar_pure(NQ, STATE_SEEDS[1])
+    rho = synth.depolarized(psi, lam)
+    M = O.tetrahedral_povm()
+    P = O.born_probabilities(rho, M).real
+    f = synth.frequencies(synth.multinomial_counts(P, SHOTS, COUNT_SEED + STATE_SEEDS[1]), np.float32)
+    theta = synth.init_theta(NQ, THETA_SEED).astype(np.float32).astype(np.float64)
+    f64 = f.astype(np.float64)
+    st = O.RpropState(theta.size)
+    for _ in range(args.warmup):
+        _, g, _ = O.loss_and_grad(theta, f64, M, NQ)
+        theta = O.rprop_update(theta, g, st)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _, g, _ = O.loss_and_grad(theta, f64, M, NQ)
+        theta = O.rprop_update(theta, g, st)
+    el = time.perf_counter() - t0
+    v = args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(lam), "path": "oracle (FP64 NumPy, host)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{args.steps} full N=11 iterations after {args.warmup} warm-up"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-ttf", dest="ttf", action="store_false")
+    ap.add_argument("--max-iters", type=int, default=1000)
+    ap.add_argument("--fid-every", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="profiling aid: only run this many plain and mixed steps at N=11 and exit (no JSON line)")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        main_reference(args)
+    elif args.profile_steps > 0:
+        profile_only(args)
+    else:
+        main_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -149,6 +149,28 @@ long long qst_iterations(const qst_ctx* ctx);
  * replays count every kernel node). */
 long long qst_kernel_launches(const qst_ctx* ctx);
 
+/* Per-phase timing of qst_step (instrumentation; the paper has no counterpart).
+ * With timing enabled, every qst_step records a CUDA event on the context's
+ * stream after each phase below; qst_timing_read synchronises, adds the
+ * elapsed times per phase over all steps recorded since the last read, writes
+ * the totals (milliseconds) and step counts, and starts a new window.
+ * max_steps bounds the window (extra steps are not recorded); 0 disables. */
+enum {
+    QST_PH_HIDDEN = 0,   /* layer-1 forward (only when the input changed) */
+    QST_PH_BUILD_T = 1,  /* layer 2 + Hermitian T (+ Tr T^2) */
+    QST_PH_XFWD = 2,     /* X = T T */
+    QST_PH_POVM_LO = 3,  /* POVM map, low qubits */
+    QST_PH_POVM_HI = 4,  /* POVM map high qubits + likelihood + adjoint high qubits */
+    QST_PH_POVM_ADJ = 5, /* adjoint low qubits -> G */
+    QST_PH_GT = 6,       /* Y = G T (incl. operand conversion) */
+    QST_PH_SYM = 7,      /* dL/dt from Y */
+    QST_PH_W2 = 8,       /* layer-2 backward + Rprop */
+    QST_PH_W1 = 9,       /* layer-1 backward + Rprop + next hidden layer */
+    QST_NPHASE = 10
+};
+qst_status qst_timing_enable(qst_ctx* ctx, int max_steps);
+qst_status qst_timing_read(qst_ctx* ctx, double* phase_ms, long long* phase_count, int nphase);
+
 /* Wait for all work enqueued on the context's stream. */
 qst_status qst_sync(qst_ctx* ctx);
 

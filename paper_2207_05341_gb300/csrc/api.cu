@@ -49,6 +49,10 @@ struct qst_ctx {
   double* h_scal = nullptr;     // pinned host mirror of scal[0..4]
   unsigned int* h_flags = nullptr;
   size_t partial_doubles = 0;
+  // per-phase timing (qst_timing_enable)
+  std::vector<cudaEvent_t> tev;   // max_steps * (QST_NPHASE + 1) events
+  std::vector<unsigned int> tmask;
+  int tmax = 0, tcount = 0, tslot = -1;
 };
 
 namespace {
@@ -64,6 +68,20 @@ qst_status cuda_status(cudaError_t e) {
     cudaError_t _e = (expr);                       \
     if (_e != cudaSuccess) return cuda_status(_e); \
   } while (0)
+
+// Timing marks: slot `tslot` holds a start event and one event per phase.
+void tmark_begin(qst_ctx* c) {
+  c->tslot = -1;
+  if (c->tmax <= 0 || c->tcount >= c->tmax) return;
+  c->tslot = c->tcount++;
+  c->tmask[c->tslot] = 0u;
+  cudaEventRecord(c->tev[(size_t)c->tslot * (QST_NPHASE + 1)], c->stream);
+}
+void tmark(qst_ctx* c, int phase) {
+  if (c->tslot < 0) return;
+  cudaEventRecord(c->tev[(size_t)c->tslot * (QST_NPHASE + 1) + 1 + phase], c->stream);
+  c->tmask[c->tslot] |= 1u << phase;
+}
 
 template <class T> cudaError_t dalloc(qst_ctx* c, T** p, size_t count) {
   void* q = nullptr;
@@ -175,12 +193,14 @@ template <class R> struct Engine {
     QST_CU(net_build_T<R>(D, theta, w->hid, w->T, mixed ? w->Tb : nullptr, w->scal, w->partials,
                           w->counters + CNT_T, c->stream));
     c->launches += 1;
+    tmark(c, QST_PH_BUILD_T);
     if (mixed) {
       QST_CU(tc_herm_square(D.d, w->Tb, reinterpret_cast<float2*>(w->X), c->stream));
     } else {
       QST_CU(cgemm_simt<R>(D.d, w->T, w->T, w->X, true, c->stream));
     }
     c->launches += 1;
+    tmark(c, QST_PH_XFWD);
     return QST_OK;
   }
 
@@ -190,12 +210,15 @@ template <class R> struct Engine {
     const Dims& D = c->D;
     const PovmB<R>& B = povmB<R>(c);
     QST_CU(povm_lo_fwd<R>(D, w->X, w->Wlo, B, c->stream));
+    tmark(c, QST_PH_POVM_LO);
     QST_CU(povm_hi_nll<R>(D, w->Wlo, f, w->scal, w->Whi, w->partials, w->counters + CNT_NLL, w->flags, B,
                           backward, c->stream));
+    tmark(c, QST_PH_POVM_HI);
     c->launches += 2;
     if (backward) {
       QST_CU(povm_lo_adj<R>(D, w->Whi, w->G, B, c->stream));
       c->launches += 1;
+      tmark(c, QST_PH_POVM_ADJ);
     }
     return QST_OK;
   }
@@ -207,11 +230,15 @@ template <class R> struct Engine {
     if (c->prec == QST_MIXED) {
       QST_CU(split_bf16_G(D.d, reinterpret_cast<const float2*>(w->G), w->Gb, c->stream));
       QST_CU(tc_gt_product(D.d, w->Gb, w->Tb, w->Yre, w->Yim, c->stream));
+      tmark(c, QST_PH_GT);
       QST_CU(net_symmetrize_planar(D, w->Yre, w->Yim, reinterpret_cast<float*>(w->dt), c->stream));
+      tmark(c, QST_PH_SYM);
       c->launches += 3;
     } else {
       QST_CU(cgemm_simt<R>(D.d, w->G, w->T, w->Y, false, c->stream));
+      tmark(c, QST_PH_GT);
       QST_CU(net_symmetrize<R>(D, w->Y, w->dt, c->stream));
+      tmark(c, QST_PH_SYM);
       c->launches += 2;
     }
     return QST_OK;
@@ -222,6 +249,7 @@ template <class R> struct Engine {
     QST_CU(net_l1_forward<R>(c->D, theta, f, w->pre, w->hid, w->scal, w->partials, w->counters + CNT_L1, c->net,
                              c->stream));
     c->launches += 1;
+    tmark(c, QST_PH_HIDDEN);
     return QST_OK;
   }
 
@@ -248,6 +276,9 @@ template <class R> struct Engine {
     if (new_f) {
       st = validate_f<R>(c, f);
       if (st != QST_OK) return st;
+    }
+    tmark_begin(c);
+    if (new_f) {
       if ((st = hidden(c, w->theta, f)) != QST_OK) return st;
     }
     if ((st = forward_state(c, w->theta)) != QST_OK) return st;
@@ -255,8 +286,11 @@ template <class R> struct Engine {
     if ((st = backward_state(c)) != QST_OK) return st;
     QST_CU(net_w2_pass<R>(D, w->theta, w->step, w->sign, w->dt, w->hid, w->pre, w->dpre, nullptr, w->partials,
                           w->counters + CNT_W2, c->net, true, c->stream));
+    tmark(c, QST_PH_W2);
     QST_CU(net_w1_pass<R>(D, w->theta, w->step, w->sign, f, w->dpre, w->pre, w->hid, nullptr, w->scal, w->partials,
                           w->counters + CNT_W1, c->net, true, c->stream));
+    tmark(c, QST_PH_W1);
+    c->tslot = -1;
     c->launches += 2;
     c->hidden_valid = true;
     c->f_last = f_user;
@@ -546,6 +580,42 @@ qst_status qst_set_state(qst_ctx* c, const void* host_buf, size_t bytes) {
 long long qst_iterations(const qst_ctx* c) { return c ? c->iters : -1; }
 long long qst_kernel_launches(const qst_ctx* c) { return c ? c->launches : -1; }
 
+qst_status qst_timing_enable(qst_ctx* c, int max_steps) {
+  if (!c || max_steps < 0) return QST_E_INVAL;
+  for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
+  c->tev.clear();
+  c->tmask.clear();
+  c->tmax = 0;
+  c->tcount = 0;
+  c->tslot = -1;
+  if (max_steps == 0) return QST_OK;
+  const size_t ne = (size_t)max_steps * (QST_NPHASE + 1);
+  c->tev.resize(ne);
+  for (size_t i = 0; i < ne; ++i) QST_CU(cudaEventCreate(&c->tev[i]));
+  c->tmask.assign((size_t)max_steps, 0u);
+  c->tmax = max_steps;
+  return QST_OK;
+}
+
+qst_status qst_timing_read(qst_ctx* c, double* phase_ms, long long* phase_count, int nphase) {
+  if (!c || !phase_ms || !phase_count || nphase < 1) return QST_E_INVAL;
+  QST_CU(cudaStreamSynchronize(c->stream));
+  for (int p = 0; p < nphase; ++p) { phase_ms[p] = 0.0; phase_count[p] = 0; }
+  for (int s = 0; s < c->tcount; ++s) {
+    cudaEvent_t prev = c->tev[(size_t)s * (QST_NPHASE + 1)];
+    for (int p = 0; p < QST_NPHASE; ++p) {
+      if (!(c->tmask[s] & (1u << p))) continue;
+      cudaEvent_t e = c->tev[(size_t)s * (QST_NPHASE + 1) + 1 + p];
+      float ms = 0.f;
+      QST_CU(cudaEventElapsedTime(&ms, prev, e));
+      if (p < nphase) { phase_ms[p] += ms; phase_count[p] += 1; }
+      prev = e;
+    }
+  }
+  c->tcount = 0;
+  return QST_OK;
+}
+
 qst_status qst_sync(qst_ctx* c) {
   if (!c) return QST_E_INVAL;
   QST_CU(cudaStreamSynchronize(c->stream));
@@ -571,6 +641,7 @@ void qst_destroy(qst_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
+  for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
   if (c->work) {
     if (c->prec == QST_FP64) free_work<double>(c);

@@ -36,7 +36,10 @@ EXPORTED = [
     "qst_probs", "qst_loss_grad", "qst_step", "qst_reconstruct", "qst_get_rho",
     "qst_state_bytes", "qst_get_state", "qst_set_state", "qst_iterations",
     "qst_kernel_launches", "qst_sync", "qst_strerror", "qst_destroy",
+    "qst_timing_enable", "qst_timing_read",
 ]
+
+PHASES = ["hidden", "build_T", "x_fwd", "povm_lo", "povm_hi", "povm_adj", "gt", "sym", "w2", "w1"]
 
 
 class qst_options(ctypes.Structure):
@@ -91,6 +94,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "qst_sync": (i, [vp]),
         "qst_strerror": (ctypes.c_char_p, [i]),
         "qst_destroy": (None, [vp]),
+        "qst_timing_enable": (i, [vp, i]),
+        "qst_timing_read": (i, [vp, pd, ctypes.POINTER(ctypes.c_longlong), i]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -233,3 +238,16 @@ def qst_sync(ctx: int) -> int:
 def qst_destroy(ctx: int) -> None:
     if ctx:
         load().qst_destroy(ctx)
+
+
+def qst_timing_enable(ctx: int, max_steps: int) -> int:
+    return _check(load().qst_timing_enable(ctx, int(max_steps)), "qst_timing_enable")
+
+
+def qst_timing_read(ctx: int) -> dict:
+    """Per-phase (total ms, count) over the steps recorded since the last read."""
+    n = len(PHASES)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_longlong * n)()
+    _check(load().qst_timing_read(ctx, ms, cnt, n), "qst_timing_read")
+    return {PHASES[p]: (ms[p], int(cnt[p])) for p in range(n)}
