@@ -110,6 +110,28 @@ qst_status qst_get_params(qst_ctx* ctx, void* theta);
  *   p    device, n reals (written).  No normalisation is applied. */
 qst_status qst_probs(qst_ctx* ctx, const void* rho, void* p);
 
+/* Allocation-free variant of qst_probs, for callers that cannot call cudaMalloc
+ * (a framework whose own pool allocator owns the device memory, a latency-bound
+ * loop that must avoid the synchronisation allocation can cause, or a one-off
+ * evaluation without a context, which qst_init would allocate).  The paper has
+ * no counterpart; this is an interface convenience.
+ *   N       1 <= N <= 10 (larger N returns QST_E_INVAL): the packed intermediate
+ *           lives in a fixed 4 MiB device array (4^10 floats) inside libqst,
+ *           which every GPU that loads the library holds until the process exits.
+ *   povm    as for qst_init (host, K = 4, Hermitian, summing to I).
+ *   rho, p  device, FP32: d x d complex rho (lower triangle read, as qst_probs)
+ *           and n reals written.
+ *   stream  cudaStream_t (as void*), may be NULL.
+ * The first call on a device looks up the array's device address (set-up, once
+ * per device, with that device current); make that first call before any
+ * stream capture.  All calls share the one array: calls whose work overlaps on
+ * the GPU (different streams, or different host threads on one device) race
+ * and must be serialised by the caller.  The array keeps the previous call's
+ * contents; every entry a call reads is first written by the same call, so
+ * nothing needs clearing.  Calls no cudaMalloc, cudaFree or allocating
+ * library routine. */
+qst_status qst_probs_static(int N, const double* povm, int K, const void* rho, void* p, void* stream);
+
 /* Loss and gradient of Sec. 3.1 for externally held parameters, no update.
  *   theta  device, qst_theta_size(N) reals (read only).
  *   f      device or host, n reals: measured frequencies (Sec. 2.1), f >= 0, sum 1.

@@ -36,7 +36,7 @@ EXPORTED = [
     "qst_probs", "qst_loss_grad", "qst_step", "qst_reconstruct", "qst_get_rho",
     "qst_state_bytes", "qst_get_state", "qst_set_state", "qst_iterations",
     "qst_kernel_launches", "qst_sync", "qst_strerror", "qst_destroy",
-    "qst_timing_enable", "qst_timing_read",
+    "qst_timing_enable", "qst_timing_read", "qst_probs_static",
 ]
 
 PHASES = ["hidden", "build_T", "x_fwd", "povm_lo", "povm_hi", "povm_adj", "gt", "sym", "w2", "w1"]
@@ -96,6 +96,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "qst_destroy": (None, [vp]),
         "qst_timing_enable": (i, [vp, i]),
         "qst_timing_read": (i, [vp, pd, ctypes.POINTER(ctypes.c_longlong), i]),
+        "qst_probs_static": (i, [i, vp, i, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -251,3 +252,12 @@ def qst_timing_read(ctx: int) -> dict:
     cnt = (ctypes.c_longlong * n)()
     _check(load().qst_timing_read(ctx, ms, cnt, n), "qst_timing_read")
     return {PHASES[p]: (ms[p], int(cnt[p])) for p in range(n)}
+
+
+def qst_probs_static(N: int, rho, p, povm=None, K: int = 4, stream: int = 0) -> int:
+    """Allocation-free POVM map (FP32, N <= 10): see qst_probs_static in include/qst.h."""
+    if povm is None:
+        povm = tetrahedral_povm_flat()
+    povm = np.ascontiguousarray(povm, dtype=np.float64)
+    return _check(load().qst_probs_static(int(N), povm.ctypes.data, int(K), ptr(rho), ptr(p), stream or None),
+                  "qst_probs_static")
