@@ -148,8 +148,6 @@ template <class R> qst_status alloc_work(qst_ctx* c) {
     unsigned short* gb = nullptr;
     QST_CU(dalloc(c, &gb, 4 * nn));
     w->Gb = gb;
-    QST_CU(dalloc(c, &w->Yre, nn));
-    QST_CU(dalloc(c, &w->Yim, nn));
   }
   return QST_OK;
 }
@@ -195,7 +193,7 @@ template <class R> struct Engine {
     c->launches += 1;
     tmark(c, QST_PH_BUILD_T);
     if (mixed) {
-      QST_CU(tc_herm_square(D.d, w->Tb, reinterpret_cast<float2*>(w->X), c->stream));
+      QST_CU(tc_herm_square(D.d, w->Tb, reinterpret_cast<float2*>(w->X), w->flags + 1, c->stream));
     } else {
       QST_CU(cgemm_simt<R>(D.d, w->T, w->T, w->X, true, c->stream));
     }
@@ -229,9 +227,9 @@ template <class R> struct Engine {
     const Dims& D = c->D;
     if (c->prec == QST_MIXED) {
       QST_CU(split_bf16_G(D.d, reinterpret_cast<const float2*>(w->G), w->Gb, c->stream));
-      QST_CU(tc_gt_product(D.d, w->Gb, w->Tb, w->Yre, w->Yim, c->stream));
+      QST_CU(tc_gt_product(D.d, w->Gb, w->Tb, reinterpret_cast<float2*>(w->Y), w->flags + 1, c->stream));
       tmark(c, QST_PH_GT);
-      QST_CU(net_symmetrize_planar(D, w->Yre, w->Yim, reinterpret_cast<float*>(w->dt), c->stream));
+      QST_CU(net_symmetrize<R>(D, w->Y, w->dt, c->stream));
       tmark(c, QST_PH_SYM);
       c->launches += 3;
     } else {
@@ -256,9 +254,13 @@ template <class R> struct Engine {
   static qst_status read_loss(qst_ctx* c, double* loss) {
     Work<R>* w = W<R>(c);
     QST_CU(cudaMemcpyAsync(c->h_scal, w->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    QST_CU(cudaMemcpyAsync(c->h_flags, w->flags, sizeof(unsigned int), cudaMemcpyDeviceToHost, c->stream));
+    QST_CU(cudaMemcpyAsync(c->h_flags, w->flags, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost, c->stream));
     QST_CU(cudaStreamSynchronize(c->stream));
     *loss = c->h_scal[2];
+    if (c->h_flags[1] != 0u) {
+      QST_CU(cudaMemsetAsync(w->flags + 1, 0, sizeof(unsigned int), c->stream));
+      return QST_E_TIMEOUT;
+    }
     if (c->h_flags[0] != 0u) {
       QST_CU(cudaMemsetAsync(w->flags, 0, sizeof(unsigned int), c->stream));
       return QST_W_CLAMP;

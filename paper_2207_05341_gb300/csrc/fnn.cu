@@ -340,9 +340,8 @@ __global__ void __launch_bounds__(256) k_w1_pass(R* __restrict__ theta, R* __res
 
 // ------------------------------------------------------------------ dL/dt from Y = G T
 // Gamma = Y + Y^dag;  dR_ij = 2 Re Gamma_ij, dR_ji = 2 Im Gamma_ij (i > j), dR_ii = Re Gamma_ii.
-template <class R, bool PLANAR>
-__global__ void __launch_bounds__(256) k_symmetrize(const cx_t<R>* __restrict__ Y, const float* __restrict__ Yre,
-                                                     const float* __restrict__ Yim, R* __restrict__ dt, int d) {
+template <class R>
+__global__ void __launch_bounds__(256) k_symmetrize(const cx_t<R>* __restrict__ Y, R* __restrict__ dt, int d) {
   __shared__ R Ar[32][33], Ai[32][33], Br[32][33], Bi[32][33];
   const int TS = d < 32 ? d : 32;
   int I, J;
@@ -351,13 +350,8 @@ __global__ void __launch_bounds__(256) k_symmetrize(const cx_t<R>* __restrict__ 
     const int r = e / TS, c = e % TS;
     const long long ia = (long long)(I * TS + r) * d + J * TS + c;
     const long long ib = (long long)(J * TS + r) * d + I * TS + c;
-    if (PLANAR) {
-      Ar[r][c] = (R)Yre[ia]; Ai[r][c] = (R)Yim[ia];
-      Br[r][c] = (R)Yre[ib]; Bi[r][c] = (R)Yim[ib];
-    } else {
-      const cx_t<R> a = Y[ia], b = Y[ib];
-      Ar[r][c] = a.x; Ai[r][c] = a.y; Br[r][c] = b.x; Bi[r][c] = b.y;
-    }
+    const cx_t<R> a = Y[ia], b = Y[ib];
+    Ar[r][c] = a.x; Ai[r][c] = a.y; Br[r][c] = b.x; Bi[r][c] = b.y;
   }
   __syncthreads();
   for (int e = threadIdx.x; e < TS * TS; e += blockDim.x) {
@@ -456,14 +450,7 @@ cudaError_t net_w1_pass(const Dims& D, R* theta, R* step, int8_t* sign, const R*
 template <class R> cudaError_t net_symmetrize(const Dims& D, const cx_t<R>* Y, R* dt, cudaStream_t s) {
   const int TS = D.d < 32 ? D.d : 32;
   const int nt = D.d / TS;
-  k_symmetrize<R, false><<<(unsigned)(nt * (nt + 1) / 2), 256, 0, s>>>(Y, nullptr, nullptr, dt, D.d);
-  return cudaGetLastError();
-}
-
-cudaError_t net_symmetrize_planar(const Dims& D, const float* Yre, const float* Yim, float* dt, cudaStream_t s) {
-  const int TS = D.d < 32 ? D.d : 32;
-  const int nt = D.d / TS;
-  k_symmetrize<float, true><<<(unsigned)(nt * (nt + 1) / 2), 256, 0, s>>>(nullptr, Yre, Yim, dt, D.d);
+  k_symmetrize<R><<<(unsigned)(nt * (nt + 1) / 2), 256, 0, s>>>(Y, dt, D.d);
   return cudaGetLastError();
 }
 

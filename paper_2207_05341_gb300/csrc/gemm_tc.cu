@@ -1,12 +1,372 @@
-// Tensor-core (tcgen05) complex products for the mixed-precision path.
+// Tensor-core (tcgen05) complex products of the mixed-precision path:
+//   X = T T   (Sec. 3.2 eq. unified_DP; lower 128 x 128 tiles only, X is Hermitian)
+//   Y = G T   (backward of X = T T)
+//
+// A complex product is run as one real GEMM with the K axis doubled and the N
+// axis doubled.  With T Hermitian (T_re symmetric, T_im antisymmetric) and the
+// row-major planes P_re = T_re, P_im = T_im, P_nim = -T_im:
+//   Re(A T)[m, n] = sum_k A_re[m,k] P_re[n,k] + A_im[m,k] P_im[n,k]
+//   Im(A T)[m, n] = sum_k A_re[m,k] P_nim[n,k] + A_im[m,k] P_re[n,k]
+// so both outputs are A' B'^T with A' = [A_re | A_im] (K = 2d) and, stacked along
+// N, B1 = [P_re | P_im] and B2 = [P_nim | P_re]; every operand is K-major.  A = T
+// for the forward, A = G for the backward.
+//
+// Precision: each FP32 operand is split into BF16 hi + lo (lo = bf16(x - hi));
+// the product keeps hi*hi + hi*lo + lo*hi with FP32 accumulation in TMEM.
+//
+// Kernel: one CTA (4 warps) per 128 x 128 complex output tile; accumulator
+// 128 lanes x 256 FP32 columns (Re | Im) in TMEM.  Warp 0 lane 0 streams
+// operands with TMA (128B swizzle) into a 2-stage ring (96 KB per stage:
+// A_hi, A_lo, B_hi = [B1_hi; B2_hi], B_lo), warp 1 lane 0 issues tcgen05.mma
+// (M = 128, N = 256, K = 16) and commits each stage back to the producer; all
+// four warps then read TMEM (tcgen05.ld 32x32b) and store the tile.  Every
+// mbarrier wait is bounded: on timeout the kernel raises an error flag, drains
+// what it issued (bounded), frees TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
 #include "impl.h"
 
 namespace qst {
 
-bool tc_available() { return false; }
+namespace {
 
-cudaError_t split_bf16_G(int, const float2*, void*, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t tc_herm_square(int, const void*, float2*, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t tc_gt_product(int, const void*, const void*, float*, float*, cudaStream_t) { return cudaErrorNotSupported; }
+constexpr int kBM = 128;              // output rows per tile
+constexpr int kBN = 128;              // complex output columns per tile (N = 256 reals)
+constexpr int kBK = 64;               // K elements per stage (128 bytes of BF16)
+constexpr int kStages = 2;
+constexpr int kTileBytes = 128 * kBK * 2;        // one 128-row x 64-col BF16 box: 16 KB
+constexpr int kStageBytes = 6 * kTileBytes;      // 96 KB
+constexpr int kTmemCols = 256;
+constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
+constexpr unsigned long long kWaitCycles = 4000000000ULL;  // ~2 s at 2 GHz
+
+struct TcMaps {
+  CUtensorMap a[4];  // A planes: re_hi, im_hi, re_lo, im_lo
+  CUtensorMap b[6];  // T planes: re_hi, im_hi, nim_hi, re_lo, im_lo, nim_lo
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false after ~kWaitCycles.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = clock64();
+  while (!mbar_try(bar, parity)) {
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of 1024 bytes.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);        // start address
+  d |= (uint64_t)1 << 16;                           // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset: one 8-row atom
+  d |= (uint64_t)1 << 46;                           // descriptor version
+  d |= (uint64_t)2 << 61;                           // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, M = 128, N = 256.
+constexpr uint32_t kIdesc =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(2 * kBN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accum) {
+  asm volatile(
+      "{\n.reg .pred p;\n"
+      "setp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(128, 1) k_tc_cgemm(const __grid_constant__ TcMaps maps, float2* __restrict__ C,
+                                                      int d, int lower, unsigned int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+  const uint32_t full0 = smem_u32(bars);                  // full[s]  = bars[s]
+  const uint32_t empty0 = smem_u32(bars + kStages);       // empty[s] = bars[kStages + s]
+  const uint32_t done = smem_u32(bars + 2 * kStages);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 1);
+  __shared__ int s_fail;
+
+  int I, J;
+  if (lower) tri_decode(blockIdx.x, I, J);
+  else { I = blockIdx.y; J = blockIdx.x; }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const int nkb = 2 * d / kBK;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    int issued = 0;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % kStages, it = kb / kStages;
+      if (kb >= kStages && !mbar_wait(empty0 + 8 * s, (uint32_t)((it - 1) & 1))) {
+        s_fail = 1;
+        atomicOr(err, 1u);
+        break;
+      }
+      const uint32_t fb = full0 + 8 * s;
+      mbar_expect_tx(fb, kStageBytes);
+      const int part = (kb * kBK) < d ? 0 : 1;
+      const int col = kb * kBK - part * d;
+      const CUtensorMap* a_hi = &maps.a[part == 0 ? 0 : 1];
+      const CUtensorMap* a_lo = &maps.a[part == 0 ? 2 : 3];
+      const CUtensorMap* b1_hi = &maps.b[part == 0 ? 0 : 1];
+      const CUtensorMap* b1_lo = &maps.b[part == 0 ? 3 : 4];
+      const CUtensorMap* b2_hi = &maps.b[part == 0 ? 2 : 0];
+      const CUtensorMap* b2_lo = &maps.b[part == 0 ? 5 : 3];
+      const uint32_t base = smem_u32(smem + s * kStageBytes);
+      tma_load_2d(base + 0 * kTileBytes, a_hi, col, I * kBM, fb);
+      tma_load_2d(base + 1 * kTileBytes, a_lo, col, I * kBM, fb);
+      tma_load_2d(base + 2 * kTileBytes, b1_hi, col, J * kBN, fb);
+      tma_load_2d(base + 3 * kTileBytes, b2_hi, col, J * kBN, fb);
+      tma_load_2d(base + 4 * kTileBytes, b1_lo, col, J * kBN, fb);
+      tma_load_2d(base + 5 * kTileBytes, b2_lo, col, J * kBN, fb);
+      ++issued;
+    }
+    // drain: every stage issued must have landed before the CTA may exit
+    for (int kb = (issued > kStages ? issued - kStages : 0); kb < issued; ++kb) {
+      const int s = kb % kStages, it = kb / kStages;
+      if (!mbar_wait(full0 + 8 * s, (uint32_t)(it & 1))) {
+        s_fail = 1;
+        atomicOr(err, 1u);
+        break;
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    bool ok = true;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % kStages, it = kb / kStages;
+      if (!mbar_wait(full0 + 8 * s, (uint32_t)(it & 1))) { ok = false; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t base = smem_u32(smem + s * kStageBytes);
+#pragma unroll
+      for (int kk = 0; kk < kBK / 16; ++kk) {
+        const uint64_t ah = smem_desc(base + 0 * kTileBytes + kk * 32);
+        const uint64_t al = smem_desc(base + 1 * kTileBytes + kk * 32);
+        const uint64_t bh = smem_desc(base + 2 * kTileBytes + kk * 32);
+        const uint64_t bl = smem_desc(base + 4 * kTileBytes + kk * 32);
+        mma_bf16(tmem, ah, bh, (kb > 0 || kk > 0) ? 1u : 0u);
+        mma_bf16(tmem, ah, bl, 1u);
+        mma_bf16(tmem, al, bh, 1u);
+      }
+      mma_commit(empty0 + 8 * s);
+    }
+    if (!ok) {
+      s_fail = 1;
+      atomicOr(err, 2u);
+    }
+    mma_commit(done);  // arrives once all MMAs issued so far have completed
+  }
+  __syncwarp();
+
+  // ---------------- epilogue: TMEM -> registers -> global
+  const bool ready = mbar_wait(done, 0u);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ready && !s_fail) {
+    const int row = I * kBM + warp * 32 + lane;
+    float2* out = C + (long long)row * d + (long long)J * kBN;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int c = 0; c < kBN; c += 16) {
+      uint32_t re[16], im[16];
+      tmem_ld16(lane_base + (uint32_t)c, re);
+      tmem_ld16(lane_base + (uint32_t)(kBN + c), im);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int u = 0; u < 16; u += 2) {
+        float4 v = make_float4(__uint_as_float(re[u]), __uint_as_float(im[u]), __uint_as_float(re[u + 1]),
+                               __uint_as_float(im[u + 1]));
+        *reinterpret_cast<float4*>(out + c + u) = v;
+      }
+    }
+  }
+  if (!ready || s_fail) {
+    if (threadIdx.x == 0) atomicOr(err, 1u);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+// FP32 complex G -> BF16 planes re_hi, im_hi, re_lo, im_lo.
+__global__ void __launch_bounds__(256) k_split_G(const float2* __restrict__ G, __nv_bfloat16* __restrict__ Gb,
+                                                  long long nn) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (long long)gridDim.x * blockDim.x) {
+    const float2 g = G[i];
+    const __nv_bfloat16 rh = __float2bfloat16_rn(g.x), ih = __float2bfloat16_rn(g.y);
+    Gb[i] = rh;
+    Gb[nn + i] = ih;
+    Gb[2 * nn + i] = __float2bfloat16_rn(g.x - __bfloat162float(rh));
+    Gb[3 * nn + i] = __float2bfloat16_rn(g.y - __bfloat162float(ih));
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 2-D map over one d x d BF16 plane, box 64 columns x 128 rows, 128-byte swizzle.
+bool make_plane_map(CUtensorMap* m, const void* plane, int d) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)d};
+  cuuint64_t strides[1] = {(cuuint64_t)d * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kBK, 128u};
+  cuuint32_t estr[2] = {1u, 1u};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(plane), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+cudaError_t build_maps(TcMaps* M, int d, const void* Ab, int a_planes_are_T, const void* Tb) {
+  const size_t nn = (size_t)d * d;
+  const __nv_bfloat16* t = static_cast<const __nv_bfloat16*>(Tb);
+  for (int p = 0; p < 6; ++p)
+    if (!make_plane_map(&M->b[p], t + p * nn, d)) return cudaErrorInvalidValue;
+  const __nv_bfloat16* a = static_cast<const __nv_bfloat16*>(Ab);
+  // A planes in the order re_hi, im_hi, re_lo, im_lo
+  const int tidx[4] = {0, 1, 3, 4};
+  for (int p = 0; p < 4; ++p) {
+    const __nv_bfloat16* src = a_planes_are_T ? t + tidx[p] * nn : a + p * nn;
+    if (!make_plane_map(&M->a[p], src, d)) return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_tc(const TcMaps& M, float2* C, int d, bool lower, unsigned int* err, cudaStream_t s) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_cgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int nt = d / kBM;
+  if (lower) {
+    k_tc_cgemm<<<(unsigned)(nt * (nt + 1) / 2), 128, kSmemBytes, s>>>(M, C, d, 1, err);
+  } else {
+    k_tc_cgemm<<<dim3(nt, nt), 128, kSmemBytes, s>>>(M, C, d, 0, err);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_available() {
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  if (major != 10 || minor != 3) return false;
+  return encode_fn() != nullptr;
+}
+
+cudaError_t split_bf16_G(int d, const float2* G, void* Gb, cudaStream_t s) {
+  const long long nn = (long long)d * d;
+  long long blocks = (nn + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  k_split_G<<<(unsigned)blocks, 256, 0, s>>>(G, static_cast<__nv_bfloat16*>(Gb), nn);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_herm_square(int d, const void* Tb, float2* X, unsigned int* err, cudaStream_t s) {
+  if (d < 128 || d % 128) return cudaErrorInvalidValue;
+  TcMaps M;
+  cudaError_t e = build_maps(&M, d, Tb, 1, Tb);
+  if (e != cudaSuccess) return e;
+  return launch_tc(M, X, d, true, err, s);
+}
+
+cudaError_t tc_gt_product(int d, const void* Gb, const void* Tb, float2* Y, unsigned int* err, cudaStream_t s) {
+  if (d < 128 || d % 128) return cudaErrorInvalidValue;
+  TcMaps M;
+  cudaError_t e = build_maps(&M, d, Gb, 0, Tb);
+  if (e != cudaSuccess) return e;
+  return launch_tc(M, Y, d, false, err, s);
+}
 
 }  // namespace qst

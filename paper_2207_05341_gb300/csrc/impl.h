@@ -37,15 +37,13 @@ template <class R> struct Work {
   R* Whi;              // packed adjoint intermediate, n reals
   R* dt;               // dL/dt, n reals
   R* fstage;           // staging copy of a host f, n reals
-  double* scal;        // [0] Tr X, [1] sum f, [2] loss, [3] tr-sum scratch
+  double* scal;        // [0] Tr X, [1] sum f, [2] loss
   double* partials;    // per-block partial sums
   unsigned int* counters;  // last-block counters, one per reduction site
-  unsigned int* flags;     // [0] clamp count
+  unsigned int* flags;     // [0] clamp count, [1] device-side wait timeouts
   // mixed precision operands (BF16 hi / lo planes), NULL when unused
   void* Tb;            // 6 planes of d x d bf16: re_hi, im_hi, nim_hi, re_lo, im_lo, nim_lo
   void* Gb;            // 4 planes of d x d bf16: re_hi, im_hi, re_lo, im_lo
-  float* Yre;          // d x d float (mixed: real part of G T)
-  float* Yim;          // d x d float (mixed: imaginary part of G T)
 };
 
 enum Counter { CNT_L1 = 0, CNT_T = 1, CNT_NLL = 2, CNT_W2 = 3, CNT_W1 = 4, CNT_TR = 5, CNT_COUNT = 8 };
@@ -85,7 +83,6 @@ template <class R> cudaError_t net_w1_pass(const Dims& D, R* theta, R* step, int
                                            bool update, cudaStream_t s);
 // dL/dt from Y = G T:  dR_ij = 2(Re Y_ij + Re Y_ji), dR_ji = 2(Im Y_ij - Im Y_ji) (i > j), dR_ii = 2 Re Y_ii
 template <class R> cudaError_t net_symmetrize(const Dims& D, const cx_t<R>* Y, R* dt, cudaStream_t s);
-cudaError_t net_symmetrize_planar(const Dims& D, const float* Yre, const float* Yim, float* dt, cudaStream_t s);
 
 // ---- complex products (gemm_simt.cu) ----
 // C = A B for d x d complex row-major matrices; lower == true computes only tiles I >= J.
@@ -95,9 +92,10 @@ template <class R> cudaError_t cgemm_simt(int d, const cx_t<R>* A, const cx_t<R>
 // ---- tensor-core products (gemm_tc.cu) ----
 // BF16 planes from G (complex, FP32): re_hi, im_hi, re_lo, im_lo
 cudaError_t split_bf16_G(int d, const float2* G, void* Gb, cudaStream_t s);
-// X = T T (lower tiles, complex FP32 out) and Y = G T (full, planar FP32 out) on tcgen05
-cudaError_t tc_herm_square(int d, const void* Tb, float2* X, cudaStream_t s);
-cudaError_t tc_gt_product(int d, const void* Gb, const void* Tb, float* Yre, float* Yim, cudaStream_t s);
+// X = T T (lower 128 x 128 tiles) and Y = G T (full) on tcgen05, complex FP32 out;
+// a device-side wait that runs out sets *err != 0.
+cudaError_t tc_herm_square(int d, const void* Tb, float2* X, unsigned int* err, cudaStream_t s);
+cudaError_t tc_gt_product(int d, const void* Gb, const void* Tb, float2* Y, unsigned int* err, cudaStream_t s);
 bool tc_available();
 
 }  // namespace qst

@@ -1,0 +1,107 @@
+"""GPU parity of the mixed-precision path (tcgen05 BF16 hi+lo products, FP32 accumulation).
+
+Tolerance from the arithmetic: each operand is carried as BF16 hi + lo
+(~16 significant bits, relative error <= 2^-17 per entry), the product keeps
+hi*hi + hi*lo + lo*hi (the dropped lo*lo term is <= 2^-16 of each product
+term) and accumulates in FP32.  rho then differs from the FP32 path by a few
+1e-5 relative; the bar is 1e-4 (normwise) on rho and the loss and 1e-3
+(normwise) on the gradient, where the backward product adds its own split.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2207_05341_gb300 import qst, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+M = O.tetrahedral_povm()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import os
+    if not os.path.exists(qst.LIB_PATH):
+        from paper_2207_05341_gb300 import build
+        build.build()
+    qst.load()
+
+
+def _ctx(N, prec):
+    o = qst.qst_default_options()
+    o.precision = prec
+    return qst.qst_init(N, opt=o)
+
+
+def _problem(N, seed, shots=10**6):
+    rho = synth.ginibre_mixed(N, max(1, (1 << N) // 4), 700 + seed)
+    P = O.born_probabilities(rho, M).real
+    f = synth.frequencies(synth.multinomial_counts(P, shots, 800 + seed))
+    return rho, f, synth.init_theta(N, 900 + seed)
+
+
+@pytest.mark.parametrize("N", [7, 8, 9, 10, 11])
+def test_mixed_rho_matches_fp32_path(N):
+    _, f, theta = _problem(N, N)
+    th = torch.from_numpy(theta.astype(np.float32)).cuda()
+    fd = torch.from_numpy(f.astype(np.float32)).cuda()
+    out = {}
+    for prec in (qst.QST_FP32, qst.QST_MIXED):
+        ctx = _ctx(N, prec)
+        try:
+            qst.qst_set_params(ctx, th)
+            rho = torch.empty((1 << N, 1 << N), dtype=torch.complex64, device="cuda")
+            L, st = qst.qst_get_rho(ctx, fd, rho, want_loss=True)
+            assert st == qst.QST_OK
+            out[prec] = (rho.cpu().numpy().astype(np.complex128), L)
+        finally:
+            qst.qst_destroy(ctx)
+    (r32, L32), (rmx, Lmx) = out[qst.QST_FP32], out[qst.QST_MIXED]
+    assert np.linalg.norm(rmx - r32) / np.linalg.norm(r32) < 1e-4
+    assert np.abs(rmx - r32).max() < 1e-4 * np.abs(r32).max()
+    assert abs(Lmx - L32) < 1e-4 * abs(L32)
+
+
+@pytest.mark.parametrize("N", [7, 9, 11])
+def test_mixed_loss_grad_vs_oracle(N):
+    _, f, theta = _problem(N, 20 + N)
+    th64 = theta.astype(np.float32).astype(np.float64)
+    f64 = f.astype(np.float32).astype(np.float64)
+    L_ref, g_ref, _ = O.loss_and_grad(th64, f64, M, N)
+    ctx = _ctx(N, qst.QST_MIXED)
+    try:
+        th = torch.from_numpy(theta.astype(np.float32)).cuda()
+        g = torch.empty_like(th)
+        L, st = qst.qst_loss_grad(ctx, th, torch.from_numpy(f.astype(np.float32)).cuda(), g)
+        g = g.cpu().numpy().astype(np.float64)
+    finally:
+        qst.qst_destroy(ctx)
+    assert st == qst.QST_OK
+    assert abs(L - L_ref) <= 1e-4 * abs(L_ref)
+    rel = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
+    assert rel < 1e-3, rel
+
+
+def test_mixed_reconstruction_reaches_oracle_fidelity():
+    """N = 8 from exact probabilities of a pure state: mixed and oracle reconstructions both reach F ~ 1."""
+    N = 8
+    psi = synth.haar_pure(N, 31)
+    f = O.born_probabilities(synth.pure_density(psi), M).real
+    theta = synth.init_theta(N, 32)
+    iters = 300
+    _, rho_ref, _ = O.reconstruct(theta.astype(np.float32).astype(np.float64),
+                                  f.astype(np.float32).astype(np.float64), M, N, iters)
+    F_ref = O.fidelity_pure(rho_ref, psi)
+    ctx = _ctx(N, qst.QST_MIXED)
+    try:
+        qst.qst_set_params(ctx, theta.astype(np.float32))
+        rho = np.empty((1 << N, 1 << N), dtype=np.complex64)
+        qst.qst_reconstruct(ctx, np.ascontiguousarray(f.astype(np.float32)), iters, rho)
+    finally:
+        qst.qst_destroy(ctx)
+    F = O.fidelity_pure(rho.astype(np.complex128), psi)
+    assert F_ref > 0.99
+    assert abs(F - F_ref) < 1e-3, (F, F_ref)
