@@ -66,11 +66,16 @@ typedef enum {
 } qst_status;
 
 enum { QST_MAP_CHOL_H = 0, QST_MAP_ABS_P = 1 };
-enum { QST_FP64 = 0, QST_FP32 = 1, QST_MIXED = 2 };
+/* Precisions.  QST_MIXED runs the two complex d x d products on tensor cores
+ * (tcgen05) with each FP32 operand split into FP16 hi + lo after a power-of-two
+ * scaling (about 2^-21 relative error); QST_MIXED_BF16 uses a BF16 hi + lo split
+ * without scaling (about 2^-16).  Everything else stays FP32 in both.  Mixed
+ * modes need N >= 7 (d a multiple of 128). */
+enum { QST_FP64 = 0, QST_FP32 = 1, QST_MIXED = 2, QST_MIXED_BF16 = 3 };
 
 typedef struct qst_options {
     int mapping;        /* QST_MAP_CHOL_H (paper default, Sec. 4.3) or QST_MAP_ABS_P (eq. abs_P) */
-    int precision;      /* QST_FP64, QST_FP32, or QST_MIXED (BF16 hi+lo tensor-core products, FP32 elsewhere) */
+    int precision;      /* QST_FP64, QST_FP32, QST_MIXED or QST_MIXED_BF16 (see above) */
     double P;           /* order of the absolute projection A_P; used when mapping == QST_MAP_ABS_P */
     double lr;          /* Rprop initial step (Sec. 4.1: 0.001) */
     double eta_minus;   /* Rprop shrink factor (0.5) */

@@ -103,6 +103,8 @@ size_t theta_size(int N) {
 }
 
 size_t rsize(const qst_ctx* c) { return c->prec == QST_FP64 ? sizeof(double) : sizeof(float); }
+bool is_mixed(const qst_ctx* c) { return c->prec == QST_MIXED || c->prec == QST_MIXED_BF16; }
+int tc_fmt(const qst_ctx* c) { return c->prec == QST_MIXED_BF16 ? TC_BF16 : TC_FP16_SCALED; }
 
 template <class R> qst_status alloc_work(qst_ctx* c) {
   Work<R>* w = new (std::nothrow) Work<R>();
@@ -141,7 +143,7 @@ template <class R> qst_status alloc_work(qst_ctx* c) {
   QST_CU(cudaMemsetAsync(w->counters, 0, CNT_COUNT * sizeof(unsigned int), c->stream));
   QST_CU(cudaMemsetAsync(w->flags, 0, 8 * sizeof(unsigned int), c->stream));
   QST_CU(cudaMemsetAsync(w->scal, 0, 16 * sizeof(double), c->stream));
-  if (c->prec == QST_MIXED) {
+  if (is_mixed(c)) {
     unsigned short* tb = nullptr;
     QST_CU(dalloc(c, &tb, 6 * nn));
     w->Tb = tb;
@@ -187,13 +189,18 @@ template <class R> struct Engine {
   static qst_status forward_state(qst_ctx* c, const R* theta) {
     Work<R>* w = W<R>(c);
     const Dims& D = c->D;
-    const bool mixed = c->prec == QST_MIXED;
-    QST_CU(net_build_T<R>(D, theta, w->hid, w->T, mixed ? w->Tb : nullptr, w->scal, w->partials,
-                          w->counters + CNT_T, c->stream));
+    const bool mixed = is_mixed(c);
+    QST_CU(net_build_T<R>(D, theta, w->hid, w->T, w->scal, w->partials, w->counters + CNT_T, c->stream));
     c->launches += 1;
+    if (mixed) {
+      QST_CU(tc_split_T(D.d, reinterpret_cast<const float2*>(w->T), w->Tb, tc_fmt(c), w->scal, w->partials,
+                        w->counters + CNT_MAXT, c->stream));
+      c->launches += tc_fmt(c) == TC_FP16_SCALED ? 2 : 1;
+    }
     tmark(c, QST_PH_BUILD_T);
     if (mixed) {
-      QST_CU(tc_herm_square(D.d, w->Tb, reinterpret_cast<float2*>(w->X), w->flags + 1, c->stream));
+      QST_CU(tc_herm_square(D.d, w->Tb, tc_fmt(c), w->scal, reinterpret_cast<float2*>(w->X), w->flags + 1,
+                            c->stream));
     } else {
       QST_CU(cgemm_simt<R>(D.d, w->T, w->T, w->X, true, c->stream));
     }
@@ -225,13 +232,15 @@ template <class R> struct Engine {
   static qst_status backward_state(qst_ctx* c) {
     Work<R>* w = W<R>(c);
     const Dims& D = c->D;
-    if (c->prec == QST_MIXED) {
-      QST_CU(split_bf16_G(D.d, reinterpret_cast<const float2*>(w->G), w->Gb, c->stream));
-      QST_CU(tc_gt_product(D.d, w->Gb, w->Tb, reinterpret_cast<float2*>(w->Y), w->flags + 1, c->stream));
+    if (is_mixed(c)) {
+      QST_CU(tc_split_G(D.d, reinterpret_cast<const float2*>(w->G), w->Gb, tc_fmt(c), w->scal, w->partials,
+                        w->counters + CNT_MAXG, c->stream));
+      QST_CU(tc_gt_product(D.d, w->Gb, w->Tb, tc_fmt(c), w->scal, reinterpret_cast<float2*>(w->Y), w->flags + 1,
+                           c->stream));
       tmark(c, QST_PH_GT);
       QST_CU(net_symmetrize<R>(D, w->Y, w->dt, c->stream));
       tmark(c, QST_PH_SYM);
-      c->launches += 3;
+      c->launches += tc_fmt(c) == TC_FP16_SCALED ? 4 : 3;
     } else {
       QST_CU(cgemm_simt<R>(D.d, w->G, w->T, w->Y, false, c->stream));
       tmark(c, QST_PH_GT);
@@ -428,7 +437,9 @@ qst_status qst_init(qst_ctx** out, int N, const double* povm, int K, const qst_o
   qst_options o;
   qst_default_options(&o);
   if (opt) o = *opt;
-  if (o.precision != QST_FP64 && o.precision != QST_FP32 && o.precision != QST_MIXED) return QST_E_INVAL;
+  if (o.precision != QST_FP64 && o.precision != QST_FP32 && o.precision != QST_MIXED &&
+      o.precision != QST_MIXED_BF16)
+    return QST_E_INVAL;
   if (N < 1 || N > (o.precision == QST_FP64 ? 10 : 12)) return QST_E_INVAL;
   if (o.mapping != QST_MAP_CHOL_H) return QST_E_UNSUPPORTED;
   if (!(o.lr > 0) || !(o.eta_minus > 0 && o.eta_minus < 1) || !(o.eta_plus > 1) || !(o.step_min > 0) ||
@@ -437,7 +448,7 @@ qst_status qst_init(qst_ctx** out, int N, const double* povm, int K, const qst_o
   PovmB<double> Bd;
   qst_status st = check_povm(povm, K, &Bd);
   if (st != QST_OK) return st;
-  if (o.precision == QST_MIXED) {
+  if (o.precision == QST_MIXED || o.precision == QST_MIXED_BF16) {
     if (N < 7) return QST_E_UNSUPPORTED;
     if (!tc_available()) return QST_E_UNSUPPORTED;
   }

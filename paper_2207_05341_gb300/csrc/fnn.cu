@@ -5,8 +5,6 @@
 // width H = 2N is a template parameter so that the H running sums live in
 // registers.  Sums over the 4^N axis are reduced per block and then by the last
 // block to arrive, in a fixed order (deterministic, no floating-point atomics).
-#include <cuda_bf16.h>
-
 #include "impl.h"
 
 namespace qst {
@@ -119,11 +117,10 @@ __global__ void __launch_bounds__(256) k_l1_forward(const R* __restrict__ theta,
 // ------------------------------------------------------------------ layer 2 + Hermitian T
 // t = W2 h + b2; R = t as d x d row-major; T_ii = R_ii, T_ij = R_ij + i R_ji (i > j), T_ji = conj T_ij.
 // One CTA per tile pair (I, J), I >= J, of TS x TS tiles.  Also scal[0] = ||T||_F^2 = Tr T^2.
-// With Tb != NULL the BF16 hi/lo planes (re, im, -im) are written instead of complex T.
 template <class R, int H>
 __global__ void __launch_bounds__(256) k_build_T(const R* __restrict__ theta, const R* __restrict__ hid, int N,
-                                                  cx_t<R>* __restrict__ T, __nv_bfloat16* __restrict__ Tb,
-                                                  double* scal, double* partials, unsigned int* counter) {
+                                                  cx_t<R>* __restrict__ T, double* scal, double* partials,
+                                                  unsigned int* counter) {
   using V = cx_t<R>;
   __shared__ R hs[H];
   __shared__ R Ra[32][33];
@@ -157,7 +154,6 @@ __global__ void __launch_bounds__(256) k_build_T(const R* __restrict__ theta, co
     }
   }
   __syncthreads();
-  const long long nn = (long long)d * d;
   for (int e = threadIdx.x; e < TS * TS; e += blockDim.x) {
     const int r = e / TS, c = e % TS;
     R re, im;
@@ -165,33 +161,12 @@ __global__ void __launch_bounds__(256) k_build_T(const R* __restrict__ theta, co
     else if (r > c) { re = Ra[r][c]; im = Ra[c][r]; }
     else if (r < c) { re = Ra[c][r]; im = -Ra[r][c]; }
     else { re = Ra[r][r]; im = R(0); }
-    const long long o = (long long)(I * TS + r) * d + J * TS + c;
-    if (Tb == nullptr) {
-      T[o] = cmake<V>(re, im);
-    } else {
-      const float fr = (float)re, fi = (float)im;
-      const __nv_bfloat16 rh = __float2bfloat16_rn(fr), ih = __float2bfloat16_rn(fi), nh = __float2bfloat16_rn(-fi);
-      Tb[o] = rh; Tb[nn + o] = ih; Tb[2 * nn + o] = nh;
-      Tb[3 * nn + o] = __float2bfloat16_rn(fr - __bfloat162float(rh));
-      Tb[4 * nn + o] = __float2bfloat16_rn(fi - __bfloat162float(ih));
-      Tb[5 * nn + o] = __float2bfloat16_rn(-fi - __bfloat162float(nh));
-    }
+    T[(long long)(I * TS + r) * d + J * TS + c] = cmake<V>(re, im);
   }
   if (I != J) {
     for (int e = threadIdx.x; e < TS * TS; e += blockDim.x) {
       const int a = e / TS, b = e % TS;
-      const R re = Ra[b][a], im = -Rb[a][b];
-      const long long o = (long long)(J * TS + a) * d + I * TS + b;
-      if (Tb == nullptr) {
-        T[o] = cmake<V>(re, im);
-      } else {
-        const float fr = (float)re, fi = (float)im;
-        const __nv_bfloat16 rh = __float2bfloat16_rn(fr), ih = __float2bfloat16_rn(fi), nh = __float2bfloat16_rn(-fi);
-        Tb[o] = rh; Tb[nn + o] = ih; Tb[2 * nn + o] = nh;
-        Tb[3 * nn + o] = __float2bfloat16_rn(fr - __bfloat162float(rh));
-        Tb[4 * nn + o] = __float2bfloat16_rn(fi - __bfloat162float(ih));
-        Tb[5 * nn + o] = __float2bfloat16_rn(-fi - __bfloat162float(nh));
-      }
+      T[(long long)(J * TS + a) * d + I * TS + b] = cmake<V>(Ra[b][a], -Rb[a][b]);
     }
   }
   R v1[1] = {nrm};
@@ -404,16 +379,12 @@ cudaError_t net_l1_forward(const Dims& D, const R* theta, const R* f, R* pre, R*
 }
 
 template <class R>
-cudaError_t net_build_T(const Dims& D, const R* theta, const R* hid, cx_t<R>* T, void* Tb, double* scal,
+cudaError_t net_build_T(const Dims& D, const R* theta, const R* hid, cx_t<R>* T, double* scal,
                         double* partials, unsigned int* counter, cudaStream_t s) {
   const int TS = D.d < 32 ? D.d : 32;
   const int nt = D.d / TS;
   const unsigned pairs = (unsigned)(nt * (nt + 1) / 2);
-  if (pairs > (unsigned)kPartialBlocks * 4) {
-    // partial slots: one stride per block
-  }
-  QST_SWITCH_H(D.H, k_build_T<R, HH><<<pairs, 256, 0, s>>>(theta, hid, D.N, T, (__nv_bfloat16*)Tb, scal, partials,
-                                                           counter));
+  QST_SWITCH_H(D.H, k_build_T<R, HH><<<pairs, 256, 0, s>>>(theta, hid, D.N, T, scal, partials, counter));
   return cudaGetLastError();
 }
 
@@ -457,7 +428,7 @@ template <class R> cudaError_t net_symmetrize(const Dims& D, const cx_t<R>* Y, R
 #define QST_INST(R)                                                                                              \
   template cudaError_t net_l1_forward<R>(const Dims&, const R*, const R*, R*, R*, double*, double*, unsigned int*, \
                                          const NetCfg&, cudaStream_t);                                           \
-  template cudaError_t net_build_T<R>(const Dims&, const R*, const R*, cx_t<R>*, void*, double*, double*,        \
+  template cudaError_t net_build_T<R>(const Dims&, const R*, const R*, cx_t<R>*, double*, double*,               \
                                       unsigned int*, cudaStream_t);                                              \
   template cudaError_t net_w2_pass<R>(const Dims&, R*, R*, int8_t*, const R*, const R*, const R*, R*, R*, double*, \
                                       unsigned int*, const NetCfg&, bool, cudaStream_t);                         \

@@ -11,8 +11,13 @@
 // N, B1 = [P_re | P_im] and B2 = [P_nim | P_re]; every operand is K-major.  A = T
 // for the forward, A = G for the backward.
 //
-// Precision: each FP32 operand is split into BF16 hi + lo (lo = bf16(x - hi));
-// the product keeps hi*hi + hi*lo + lo*hi with FP32 accumulation in TMEM.
+// Precision: each FP32 operand x is split into a 16-bit hi + lo pair (lo = x - hi
+// rounded again) and the product keeps hi*hi + hi*lo + lo*hi with FP32
+// accumulation in TMEM.  Two operand formats:
+//   FP16 (default): the operand is first scaled by a power of two s so that
+//     max |s x| lies in [1, 2); hi + lo then carry ~22 bits and the result is
+//     unscaled exactly in the epilogue (relative error ~2^-21).
+//   BF16: no scaling; hi + lo carry ~16 bits (relative error ~2^-16).
 //
 // Kernel: one CTA (4 warps) per 128 x 128 complex output tile; accumulator
 // 128 lanes x 256 FP32 columns (Re | Im) in TMEM.  Warp 0 lane 0 streams
@@ -24,6 +29,7 @@
 // what it issued (bounded), frees TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include "impl.h"
@@ -99,16 +105,18 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return d;
 }
 
-// Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, M = 128, N = 256.
-constexpr uint32_t kIdesc =
-    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(2 * kBN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+// Instruction descriptor, kind::f16: D FP32, A and B FP16 (fmt 0) or BF16 (fmt 1), both
+// K-major, M = 128, N = 256.
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(2 * kBN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accum) {
+__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
   asm volatile(
       "{\n.reg .pred p;\n"
       "setp.ne.b32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(accum)
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
       : "memory");
 }
 
@@ -126,7 +134,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 }
 
 __global__ void __launch_bounds__(128, 1) k_tc_cgemm(const __grid_constant__ TcMaps maps, float2* __restrict__ C,
-                                                      int d, int lower, unsigned int* err) {
+                                                      int d, int lower, uint32_t idesc, const double* sA,
+                                                      const double* sB, unsigned int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
@@ -214,9 +223,9 @@ __global__ void __launch_bounds__(128, 1) k_tc_cgemm(const __grid_constant__ TcM
         const uint64_t al = smem_desc(base + 1 * kTileBytes + kk * 32);
         const uint64_t bh = smem_desc(base + 2 * kTileBytes + kk * 32);
         const uint64_t bl = smem_desc(base + 4 * kTileBytes + kk * 32);
-        mma_bf16(tmem, ah, bh, (kb > 0 || kk > 0) ? 1u : 0u);
-        mma_bf16(tmem, ah, bl, 1u);
-        mma_bf16(tmem, al, bh, 1u);
+        mma_f16(tmem, ah, bh, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+        mma_f16(tmem, ah, bl, idesc, 1u);
+        mma_f16(tmem, al, bh, idesc, 1u);
       }
       mma_commit(empty0 + 8 * s);
     }
@@ -232,6 +241,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_cgemm(const __grid_constant__ TcM
   const bool ready = mbar_wait(done, 0u);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ready && !s_fail) {
+    const float unscale = (float)(1.0 / (*sA * *sB));  // exact: both scales are powers of two
     const int row = I * kBM + warp * 32 + lane;
     float2* out = C + (long long)row * d + (long long)J * kBN;
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
@@ -243,8 +253,8 @@ __global__ void __launch_bounds__(128, 1) k_tc_cgemm(const __grid_constant__ TcM
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
       for (int u = 0; u < 16; u += 2) {
-        float4 v = make_float4(__uint_as_float(re[u]), __uint_as_float(im[u]), __uint_as_float(re[u + 1]),
-                               __uint_as_float(im[u + 1]));
+        float4 v = make_float4(unscale * __uint_as_float(re[u]), unscale * __uint_as_float(im[u]),
+                               unscale * __uint_as_float(re[u + 1]), unscale * __uint_as_float(im[u + 1]));
         *reinterpret_cast<float4*>(out + c + u) = v;
       }
     }
@@ -259,16 +269,62 @@ __global__ void __launch_bounds__(128, 1) k_tc_cgemm(const __grid_constant__ TcM
   }
 }
 
-// FP32 complex G -> BF16 planes re_hi, im_hi, re_lo, im_lo.
-__global__ void __launch_bounds__(256) k_split_G(const float2* __restrict__ G, __nv_bfloat16* __restrict__ Gb,
-                                                  long long nn) {
+// Largest |entry| of a complex matrix (as 2 nn floats) -> *s_out = 2^-e with max in [2^e, 2^(e+1)),
+// i.e. the power of two that brings the largest entry into [1, 2).  Last-block reduction.
+__global__ void __launch_bounds__(256) k_absmax_scale(const float* __restrict__ x, long long cnt, double* partials,
+                                                       unsigned int* counter, double* s_out) {
+  float m = 0.f;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (long long)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(x[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ float red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float b = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = fmaxf(b, red[w]);
+    partials[blockIdx.x] = (double)b;
+  }
+  if (last_block_arrived(counter)) {
+    if (threadIdx.x == 0) {
+      double g = 0.0;
+      for (int b = 0; b < (int)gridDim.x; ++b) g = fmax(g, partials[b]);
+      *s_out = (g > 0.0 && isfinite(g)) ? ldexp(1.0, -ilogb(g)) : 1.0;
+      *counter = 0u;
+    }
+  }
+}
+
+template <class H> __device__ __forceinline__ H to16(float v);
+template <> __device__ __forceinline__ __half to16<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 to16<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+__device__ __forceinline__ float from16(__half v) { return __half2float(v); }
+__device__ __forceinline__ float from16(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// Complex FP32 matrix -> 16-bit hi / lo planes of s * x.  T (nplanes = 6): re, im, -im (hi), re, im, -im (lo);
+// G (nplanes = 4): re, im (hi), re, im (lo).
+// With s_read == NULL no scaling is applied and *s_unit is set to 1.
+template <class H, int NPL>
+__global__ void __launch_bounds__(256) k_split(const float2* __restrict__ A, H* __restrict__ P, long long nn,
+                                                const double* s_read, double* s_unit) {
+  const float sc = s_read ? (float)*s_read : 1.f;
+  if (s_read == nullptr && blockIdx.x == 0 && threadIdx.x == 0) *s_unit = 1.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (long long)gridDim.x * blockDim.x) {
-    const float2 g = G[i];
-    const __nv_bfloat16 rh = __float2bfloat16_rn(g.x), ih = __float2bfloat16_rn(g.y);
-    Gb[i] = rh;
-    Gb[nn + i] = ih;
-    Gb[2 * nn + i] = __float2bfloat16_rn(g.x - __bfloat162float(rh));
-    Gb[3 * nn + i] = __float2bfloat16_rn(g.y - __bfloat162float(ih));
+    const float2 a = A[i];
+    const float re = sc * a.x, im = sc * a.y;
+    const H rh = to16<H>(re), ih = to16<H>(im);
+    if (NPL == 6) {
+      const H nh = to16<H>(-im);
+      P[i] = rh; P[nn + i] = ih; P[2 * nn + i] = nh;
+      P[3 * nn + i] = to16<H>(re - from16(rh));
+      P[4 * nn + i] = to16<H>(im - from16(ih));
+      P[5 * nn + i] = to16<H>(-im - from16(nh));
+    } else {
+      P[i] = rh; P[nn + i] = ih;
+      P[2 * nn + i] = to16<H>(re - from16(rh));
+      P[3 * nn + i] = to16<H>(im - from16(ih));
+    }
   }
 }
 
@@ -291,34 +347,36 @@ EncodeTiledFn encode_fn() {
 }
 
 // 2-D map over one d x d BF16 plane, box 64 columns x 128 rows, 128-byte swizzle.
-bool make_plane_map(CUtensorMap* m, const void* plane, int d) {
+bool make_plane_map(CUtensorMap* m, const void* plane, int d, int fmt) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
   cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)d};
   cuuint64_t strides[1] = {(cuuint64_t)d * 2};
   cuuint32_t box[2] = {(cuuint32_t)kBK, 128u};
   cuuint32_t estr[2] = {1u, 1u};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(plane), dims, strides, box, estr,
+  return enc(m, fmt == TC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+             const_cast<void*>(plane), dims, strides, box, estr,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-cudaError_t build_maps(TcMaps* M, int d, const void* Ab, int a_planes_are_T, const void* Tb) {
+cudaError_t build_maps(TcMaps* M, int d, const void* Ab, int a_planes_are_T, const void* Tb, int fmt) {
   const size_t nn = (size_t)d * d;
-  const __nv_bfloat16* t = static_cast<const __nv_bfloat16*>(Tb);
+  const uint16_t* t = static_cast<const uint16_t*>(Tb);
   for (int p = 0; p < 6; ++p)
-    if (!make_plane_map(&M->b[p], t + p * nn, d)) return cudaErrorInvalidValue;
-  const __nv_bfloat16* a = static_cast<const __nv_bfloat16*>(Ab);
+    if (!make_plane_map(&M->b[p], t + p * nn, d, fmt)) return cudaErrorInvalidValue;
+  const uint16_t* a = static_cast<const uint16_t*>(Ab);
   // A planes in the order re_hi, im_hi, re_lo, im_lo
   const int tidx[4] = {0, 1, 3, 4};
   for (int p = 0; p < 4; ++p) {
-    const __nv_bfloat16* src = a_planes_are_T ? t + tidx[p] * nn : a + p * nn;
-    if (!make_plane_map(&M->a[p], src, d)) return cudaErrorInvalidValue;
+    const uint16_t* src = a_planes_are_T ? t + tidx[p] * nn : a + p * nn;
+    if (!make_plane_map(&M->a[p], src, d, fmt)) return cudaErrorInvalidValue;
   }
   return cudaSuccess;
 }
 
-cudaError_t launch_tc(const TcMaps& M, float2* C, int d, bool lower, unsigned int* err, cudaStream_t s) {
+cudaError_t launch_tc(const TcMaps& M, float2* C, int d, bool lower, int fmt, const double* sA, const double* sB,
+                      unsigned int* err, cudaStream_t s) {
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_tc_cgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
@@ -327,9 +385,9 @@ cudaError_t launch_tc(const TcMaps& M, float2* C, int d, bool lower, unsigned in
   }
   const int nt = d / kBM;
   if (lower) {
-    k_tc_cgemm<<<(unsigned)(nt * (nt + 1) / 2), 128, kSmemBytes, s>>>(M, C, d, 1, err);
+    k_tc_cgemm<<<(unsigned)(nt * (nt + 1) / 2), 128, kSmemBytes, s>>>(M, C, d, 1, make_idesc(fmt), sA, sB, err);
   } else {
-    k_tc_cgemm<<<dim3(nt, nt), 128, kSmemBytes, s>>>(M, C, d, 0, err);
+    k_tc_cgemm<<<dim3(nt, nt), 128, kSmemBytes, s>>>(M, C, d, 0, make_idesc(fmt), sA, sB, err);
   }
   return cudaGetLastError();
 }
@@ -345,28 +403,53 @@ bool tc_available() {
   return encode_fn() != nullptr;
 }
 
-cudaError_t split_bf16_G(int d, const float2* G, void* Gb, cudaStream_t s) {
+static cudaError_t split_any(int d, const float2* A, void* P, int nplanes, int fmt, double* s_slot, double* partials,
+                             unsigned int* counter, cudaStream_t s) {
   const long long nn = (long long)d * d;
   long long blocks = (nn + 255) / 256;
-  if (blocks > 4096) blocks = 4096;
-  k_split_G<<<(unsigned)blocks, 256, 0, s>>>(G, static_cast<__nv_bfloat16*>(Gb), nn);
+  if (blocks > 1024) blocks = 1024;
+  const double* sp = nullptr;
+  if (fmt == TC_FP16_SCALED) {
+    k_absmax_scale<<<(unsigned)blocks, 256, 0, s>>>(reinterpret_cast<const float*>(A), 2 * nn, partials, counter,
+                                                   s_slot);
+    sp = s_slot;
+  }
+  if (fmt == TC_BF16) {
+    if (nplanes == 6) k_split<__nv_bfloat16, 6><<<(unsigned)blocks, 256, 0, s>>>(A, (__nv_bfloat16*)P, nn, sp, s_slot);
+    else k_split<__nv_bfloat16, 4><<<(unsigned)blocks, 256, 0, s>>>(A, (__nv_bfloat16*)P, nn, sp, s_slot);
+  } else {
+    if (nplanes == 6) k_split<__half, 6><<<(unsigned)blocks, 256, 0, s>>>(A, (__half*)P, nn, sp, s_slot);
+    else k_split<__half, 4><<<(unsigned)blocks, 256, 0, s>>>(A, (__half*)P, nn, sp, s_slot);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t tc_herm_square(int d, const void* Tb, float2* X, unsigned int* err, cudaStream_t s) {
-  if (d < 128 || d % 128) return cudaErrorInvalidValue;
-  TcMaps M;
-  cudaError_t e = build_maps(&M, d, Tb, 1, Tb);
-  if (e != cudaSuccess) return e;
-  return launch_tc(M, X, d, true, err, s);
+cudaError_t tc_split_T(int d, const float2* T, void* Tb, int fmt, double* scal, double* partials,
+                       unsigned int* counter, cudaStream_t s) {
+  return split_any(d, T, Tb, 6, fmt, scal + kScaleT, partials, counter, s);
 }
 
-cudaError_t tc_gt_product(int d, const void* Gb, const void* Tb, float2* Y, unsigned int* err, cudaStream_t s) {
+cudaError_t tc_split_G(int d, const float2* G, void* Gb, int fmt, double* scal, double* partials,
+                       unsigned int* counter, cudaStream_t s) {
+  return split_any(d, G, Gb, 4, fmt, scal + kScaleG, partials, counter, s);
+}
+
+cudaError_t tc_herm_square(int d, const void* Tb, int fmt, const double* scal, float2* X, unsigned int* err,
+                           cudaStream_t s) {
   if (d < 128 || d % 128) return cudaErrorInvalidValue;
   TcMaps M;
-  cudaError_t e = build_maps(&M, d, Gb, 0, Tb);
+  cudaError_t e = build_maps(&M, d, Tb, 1, Tb, fmt);
   if (e != cudaSuccess) return e;
-  return launch_tc(M, Y, d, false, err, s);
+  return launch_tc(M, X, d, true, fmt, scal + kScaleT, scal + kScaleT, err, s);
+}
+
+cudaError_t tc_gt_product(int d, const void* Gb, const void* Tb, int fmt, const double* scal, float2* Y,
+                          unsigned int* err, cudaStream_t s) {
+  if (d < 128 || d % 128) return cudaErrorInvalidValue;
+  TcMaps M;
+  cudaError_t e = build_maps(&M, d, Gb, 0, Tb, fmt);
+  if (e != cudaSuccess) return e;
+  return launch_tc(M, Y, d, false, fmt, scal + kScaleG, scal + kScaleT, err, s);
 }
 
 }  // namespace qst

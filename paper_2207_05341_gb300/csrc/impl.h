@@ -37,7 +37,7 @@ template <class R> struct Work {
   R* Whi;              // packed adjoint intermediate, n reals
   R* dt;               // dL/dt, n reals
   R* fstage;           // staging copy of a host f, n reals
-  double* scal;        // [0] Tr X, [1] sum f, [2] loss
+  double* scal;        // [0] Tr X, [1] sum f, [2] loss, [3] scale of T, [4] scale of G
   double* partials;    // per-block partial sums
   unsigned int* counters;  // last-block counters, one per reduction site
   unsigned int* flags;     // [0] clamp count, [1] device-side wait timeouts
@@ -46,7 +46,9 @@ template <class R> struct Work {
   void* Gb;            // 4 planes of d x d bf16: re_hi, im_hi, re_lo, im_lo
 };
 
-enum Counter { CNT_L1 = 0, CNT_T = 1, CNT_NLL = 2, CNT_W2 = 3, CNT_W1 = 4, CNT_TR = 5, CNT_COUNT = 8 };
+enum Counter { CNT_L1 = 0, CNT_T = 1, CNT_NLL = 2, CNT_W2 = 3, CNT_W1 = 4, CNT_MAXT = 5, CNT_MAXG = 6, CNT_COUNT = 8 };
+constexpr int kScaleT = 3;  // scal slot of the power-of-two scale of T (mixed path)
+constexpr int kScaleG = 4;  // scal slot of the scale of G
 constexpr int kPartialBlocks = 1024;   // max blocks of a reducing kernel
 constexpr int kPartialStride = 32;     // doubles per block in `partials` (>= H + 1)
 
@@ -71,7 +73,7 @@ template <class R> cudaError_t hermitian_complete(const Dims& D, const cx_t<R>* 
 template <class R> cudaError_t net_l1_forward(const Dims& D, const R* theta, const R* f, R* pre, R* hid,
                                               double* scal, double* partials, unsigned int* counter,
                                               const NetCfg& c, cudaStream_t s);
-template <class R> cudaError_t net_build_T(const Dims& D, const R* theta, const R* hid, cx_t<R>* T, void* Tb,
+template <class R> cudaError_t net_build_T(const Dims& D, const R* theta, const R* hid, cx_t<R>* T,
                                            double* scal, double* partials, unsigned int* counter, cudaStream_t s);
 template <class R> cudaError_t net_w2_pass(const Dims& D, R* theta, R* step, int8_t* sign, const R* dt,
                                            const R* hid, const R* pre, R* dpre, R* dtheta,
@@ -90,12 +92,19 @@ template <class R> cudaError_t cgemm_simt(int d, const cx_t<R>* A, const cx_t<R>
                                           cudaStream_t s);
 
 // ---- tensor-core products (gemm_tc.cu) ----
-// BF16 planes from G (complex, FP32): re_hi, im_hi, re_lo, im_lo
-cudaError_t split_bf16_G(int d, const float2* G, void* Gb, cudaStream_t s);
-// X = T T (lower 128 x 128 tiles) and Y = G T (full) on tcgen05, complex FP32 out;
+enum TcFormat { TC_FP16_SCALED = 0, TC_BF16 = 1 };
+// 16-bit hi / lo operand planes of T (6 planes: re, im, -im; hi then lo) and G (4 planes: re, im; hi
+// then lo).  TC_FP16_SCALED first scales by a power of two (scal[kScaleT] / scal[kScaleG]).
+cudaError_t tc_split_T(int d, const float2* T, void* Tb, int fmt, double* scal, double* partials,
+                       unsigned int* counter, cudaStream_t s);
+cudaError_t tc_split_G(int d, const float2* G, void* Gb, int fmt, double* scal, double* partials,
+                       unsigned int* counter, cudaStream_t s);
+// X = T T (lower 128 x 128 tiles) and Y = G T (full) on tcgen05, complex FP32 out (unscaled);
 // a device-side wait that runs out sets *err != 0.
-cudaError_t tc_herm_square(int d, const void* Tb, float2* X, unsigned int* err, cudaStream_t s);
-cudaError_t tc_gt_product(int d, const void* Gb, const void* Tb, float2* Y, unsigned int* err, cudaStream_t s);
+cudaError_t tc_herm_square(int d, const void* Tb, int fmt, const double* scal, float2* X, unsigned int* err,
+                           cudaStream_t s);
+cudaError_t tc_gt_product(int d, const void* Gb, const void* Tb, int fmt, const double* scal, float2* Y,
+                          unsigned int* err, cudaStream_t s);
 bool tc_available();
 
 }  // namespace qst

@@ -30,6 +30,7 @@ QST_MAP_ABS_P = 1
 QST_FP64 = 0
 QST_FP32 = 1
 QST_MIXED = 2
+QST_MIXED_BF16 = 3
 
 EXPORTED = [
     "qst_default_options", "qst_theta_size", "qst_init", "qst_set_params", "qst_get_params",

@@ -1,11 +1,11 @@
-"""GPU parity of the mixed-precision path (tcgen05 BF16 hi+lo products, FP32 accumulation).
+"""GPU parity of the mixed-precision paths (tcgen05 products with 16-bit hi + lo operands).
 
-Tolerance from the arithmetic: each operand is carried as BF16 hi + lo
-(~16 significant bits, relative error <= 2^-17 per entry), the product keeps
-hi*hi + hi*lo + lo*hi (the dropped lo*lo term is <= 2^-16 of each product
-term) and accumulates in FP32.  rho then differs from the FP32 path by a few
-1e-5 relative; the bar is 1e-4 (normwise) on rho and the loss and 1e-3
-(normwise) on the gradient, where the backward product adds its own split.
+Tolerances from the arithmetic.  QST_MIXED (FP16 hi + lo after power-of-two
+scaling): ~22 significant bits per operand, dropped lo*lo term <= 2^-22 of a
+product term, FP32 accumulation: relative error ~2^-21 (5e-7), so rho, the loss
+and the gradient are held to 1e-5.  QST_MIXED_BF16 (BF16 hi + lo): ~16 bits,
+relative error ~2^-16 (1.5e-5): rho and the loss to 1e-4, the gradient to 1e-3
+(normwise; the backward product adds its own split).
 """
 import numpy as np
 import pytest
@@ -43,13 +43,17 @@ def _problem(N, seed, shots=10**6):
     return rho, f, synth.init_theta(N, 900 + seed)
 
 
+TOL = {qst.QST_MIXED: (1e-5, 1e-5, 1e-5), qst.QST_MIXED_BF16: (1e-4, 1e-4, 1e-3)}  # rho, loss, gradient
+
+
+@pytest.mark.parametrize("mode", [qst.QST_MIXED, qst.QST_MIXED_BF16])
 @pytest.mark.parametrize("N", [7, 8, 9, 10, 11])
-def test_mixed_rho_matches_fp32_path(N):
+def test_mixed_rho_matches_fp32_path(N, mode):
     _, f, theta = _problem(N, N)
     th = torch.from_numpy(theta.astype(np.float32)).cuda()
     fd = torch.from_numpy(f.astype(np.float32)).cuda()
     out = {}
-    for prec in (qst.QST_FP32, qst.QST_MIXED):
+    for prec in (qst.QST_FP32, mode):
         ctx = _ctx(N, prec)
         try:
             qst.qst_set_params(ctx, th)
@@ -59,19 +63,21 @@ def test_mixed_rho_matches_fp32_path(N):
             out[prec] = (rho.cpu().numpy().astype(np.complex128), L)
         finally:
             qst.qst_destroy(ctx)
-    (r32, L32), (rmx, Lmx) = out[qst.QST_FP32], out[qst.QST_MIXED]
-    assert np.linalg.norm(rmx - r32) / np.linalg.norm(r32) < 1e-4
-    assert np.abs(rmx - r32).max() < 1e-4 * np.abs(r32).max()
-    assert abs(Lmx - L32) < 1e-4 * abs(L32)
+    (r32, L32), (rmx, Lmx) = out[qst.QST_FP32], out[mode]
+    t_rho, t_loss, _ = TOL[mode]
+    assert np.linalg.norm(rmx - r32) / np.linalg.norm(r32) < t_rho
+    assert np.abs(rmx - r32).max() < t_rho * np.abs(r32).max()
+    assert abs(Lmx - L32) < t_loss * abs(L32)
 
 
+@pytest.mark.parametrize("mode", [qst.QST_MIXED, qst.QST_MIXED_BF16])
 @pytest.mark.parametrize("N", [7, 9, 11])
-def test_mixed_loss_grad_vs_oracle(N):
+def test_mixed_loss_grad_vs_oracle(N, mode):
     _, f, theta = _problem(N, 20 + N)
     th64 = theta.astype(np.float32).astype(np.float64)
     f64 = f.astype(np.float32).astype(np.float64)
     L_ref, g_ref, _ = O.loss_and_grad(th64, f64, M, N)
-    ctx = _ctx(N, qst.QST_MIXED)
+    ctx = _ctx(N, mode)
     try:
         th = torch.from_numpy(theta.astype(np.float32)).cuda()
         g = torch.empty_like(th)
@@ -80,9 +86,10 @@ def test_mixed_loss_grad_vs_oracle(N):
     finally:
         qst.qst_destroy(ctx)
     assert st == qst.QST_OK
-    assert abs(L - L_ref) <= 1e-4 * abs(L_ref)
+    _, t_loss, t_grad = TOL[mode]
+    assert abs(L - L_ref) <= t_loss * abs(L_ref)
     rel = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
-    assert rel < 1e-3, rel
+    assert rel < t_grad, rel
 
 
 def test_mixed_reconstruction_reaches_oracle_fidelity():
