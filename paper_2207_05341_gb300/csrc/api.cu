@@ -190,7 +190,7 @@ template <class R> struct Engine {
     Work<R>* w = W<R>(c);
     const Dims& D = c->D;
     const bool mixed = is_mixed(c);
-    QST_CU(net_build_T<R>(D, theta, w->hid, w->T, w->scal, w->partials, w->counters + CNT_T, c->stream));
+    QST_CU(net_build_T<R>(D, theta, w->hid, w->T, c->stream));
     c->launches += 1;
     if (mixed) {
       QST_CU(tc_split_T(D.d, reinterpret_cast<const float2*>(w->T), w->Tb, tc_fmt(c), w->scal, w->partials,
@@ -204,7 +204,8 @@ template <class R> struct Engine {
     } else {
       QST_CU(cgemm_simt<R>(D.d, w->T, w->T, w->X, true, c->stream));
     }
-    c->launches += 1;
+    QST_CU(trace_X<R>(D, w->X, w->scal, c->stream));
+    c->launches += 2;
     tmark(c, QST_PH_XFWD);
     return QST_OK;
   }

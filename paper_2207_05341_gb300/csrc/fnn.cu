@@ -116,11 +116,10 @@ __global__ void __launch_bounds__(256) k_l1_forward(const R* __restrict__ theta,
 
 // ------------------------------------------------------------------ layer 2 + Hermitian T
 // t = W2 h + b2; R = t as d x d row-major; T_ii = R_ii, T_ij = R_ij + i R_ji (i > j), T_ji = conj T_ij.
-// One CTA per tile pair (I, J), I >= J, of TS x TS tiles.  Also scal[0] = ||T||_F^2 = Tr T^2.
+// One CTA per tile pair (I, J), I >= J, of TS x TS tiles.
 template <class R, int H>
 __global__ void __launch_bounds__(256) k_build_T(const R* __restrict__ theta, const R* __restrict__ hid, int N,
-                                                  cx_t<R>* __restrict__ T, double* scal, double* partials,
-                                                  unsigned int* counter) {
+                                                  cx_t<R>* __restrict__ T) {
   using V = cx_t<R>;
   __shared__ R hs[H];
   __shared__ R Ra[32][33];
@@ -134,7 +133,6 @@ __global__ void __launch_bounds__(256) k_build_T(const R* __restrict__ theta, co
   tri_decode(blockIdx.x, I, J);
   if (threadIdx.x < H) hs[threadIdx.x] = hid[threadIdx.x];
   __syncthreads();
-  R nrm = R(0);
   for (int e = threadIdx.x; e < TS * TS; e += blockDim.x) {
     const int r = e / TS, c = e % TS;
     const long long ia = (long long)(I * TS + r) * d + J * TS + c;
@@ -148,9 +146,6 @@ __global__ void __launch_bounds__(256) k_build_T(const R* __restrict__ theta, co
 #pragma unroll
       for (int j = 0; j < H; ++j) tb += W2T[(long long)j * n + ib] * hs[j];
       Rb[r][c] = tb;
-      nrm += R(2) * (ta * ta + tb * tb);
-    } else {
-      nrm += (r == c ? R(1) : R(2)) * ta * ta;
     }
   }
   __syncthreads();
@@ -168,13 +163,6 @@ __global__ void __launch_bounds__(256) k_build_T(const R* __restrict__ theta, co
       const int a = e / TS, b = e % TS;
       T[(long long)(J * TS + a) * d + I * TS + b] = cmake<V>(Ra[b][a], -Rb[a][b]);
     }
-  }
-  R v1[1] = {nrm};
-  block_reduce_to<1>(v1, partials + (size_t)blockIdx.x * kPartialStride);
-  if (last_block_arrived(counter)) {
-    final_reduce(partials, 1, [&](int, double s) { scal[0] = s; });
-    __syncthreads();
-    if (threadIdx.x == 0) *counter = 0u;
   }
 }
 
@@ -379,12 +367,11 @@ cudaError_t net_l1_forward(const Dims& D, const R* theta, const R* f, R* pre, R*
 }
 
 template <class R>
-cudaError_t net_build_T(const Dims& D, const R* theta, const R* hid, cx_t<R>* T, double* scal,
-                        double* partials, unsigned int* counter, cudaStream_t s) {
+cudaError_t net_build_T(const Dims& D, const R* theta, const R* hid, cx_t<R>* T, cudaStream_t s) {
   const int TS = D.d < 32 ? D.d : 32;
   const int nt = D.d / TS;
   const unsigned pairs = (unsigned)(nt * (nt + 1) / 2);
-  QST_SWITCH_H(D.H, k_build_T<R, HH><<<pairs, 256, 0, s>>>(theta, hid, D.N, T, scal, partials, counter));
+  QST_SWITCH_H(D.H, k_build_T<R, HH><<<pairs, 256, 0, s>>>(theta, hid, D.N, T));
   return cudaGetLastError();
 }
 
@@ -428,8 +415,7 @@ template <class R> cudaError_t net_symmetrize(const Dims& D, const cx_t<R>* Y, R
 #define QST_INST(R)                                                                                              \
   template cudaError_t net_l1_forward<R>(const Dims&, const R*, const R*, R*, R*, double*, double*, unsigned int*, \
                                          const NetCfg&, cudaStream_t);                                           \
-  template cudaError_t net_build_T<R>(const Dims&, const R*, const R*, cx_t<R>*, double*, double*,               \
-                                      unsigned int*, cudaStream_t);                                              \
+  template cudaError_t net_build_T<R>(const Dims&, const R*, const R*, cx_t<R>*, cudaStream_t);                 \
   template cudaError_t net_w2_pass<R>(const Dims&, R*, R*, int8_t*, const R*, const R*, const R*, R*, R*, double*, \
                                       unsigned int*, const NetCfg&, bool, cudaStream_t);                         \
   template cudaError_t net_w1_pass<R>(const Dims&, R*, R*, int8_t*, const R*, const R*, R*, R*, R*, double*,     \

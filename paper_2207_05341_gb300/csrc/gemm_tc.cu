@@ -19,8 +19,11 @@
 //     unscaled exactly in the epilogue (relative error ~2^-21).
 //   BF16: no scaling; hi + lo carry ~16 bits (relative error ~2^-16).
 //
-// Kernel: one CTA (4 warps) per 128 x 128 complex output tile; accumulator
-// 128 lanes x 256 FP32 columns (Re | Im) in TMEM.  Warp 0 lane 0 streams
+// Kernel: one CTA (4 warps) per 128 x 128 complex output tile; two accumulators
+// of 128 lanes x 256 FP32 columns (Re | Im) in TMEM, one for hi*hi and one for
+// the small cross terms, so that the cross terms are not added into the large
+// running sum (the tensor core's FP32 accumulation truncates; keeping the chains
+// apart keeps that error on the large sum to the hi*hi steps alone).  Warp 0 lane 0 streams
 // operands with TMA (128B swizzle) into a 2-stage ring (96 KB per stage:
 // A_hi, A_lo, B_hi = [B1_hi; B2_hi], B_lo), warp 1 lane 0 issues tcgen05.mma
 // (M = 128, N = 256, K = 16) and commits each stage back to the producer; all
@@ -44,7 +47,7 @@ constexpr int kBK = 64;               // K elements per stage (128 bytes of BF16
 constexpr int kStages = 2;
 constexpr int kTileBytes = 128 * kBK * 2;        // one 128-row x 64-col BF16 box: 16 KB
 constexpr int kStageBytes = 6 * kTileBytes;      // 96 KB
-constexpr int kTmemCols = 256;
+constexpr int kTmemCols = 512;   // two 128 x 256 FP32 accumulators: hi*hi, and hi*lo + lo*hi
 constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
 constexpr unsigned long long kWaitCycles = 4000000000ULL;  // ~2 s at 2 GHz
 
@@ -223,9 +226,10 @@ __global__ void __launch_bounds__(128, 1) k_tc_cgemm(const __grid_constant__ TcM
         const uint64_t al = smem_desc(base + 1 * kTileBytes + kk * 32);
         const uint64_t bh = smem_desc(base + 2 * kTileBytes + kk * 32);
         const uint64_t bl = smem_desc(base + 4 * kTileBytes + kk * 32);
-        mma_f16(tmem, ah, bh, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
-        mma_f16(tmem, ah, bl, idesc, 1u);
-        mma_f16(tmem, al, bh, idesc, 1u);
+        const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+        mma_f16(tmem, ah, bh, idesc, acc);
+        mma_f16(tmem + 256, ah, bl, idesc, acc);
+        mma_f16(tmem + 256, al, bh, idesc, 1u);
       }
       mma_commit(empty0 + 8 * s);
     }
@@ -247,14 +251,19 @@ __global__ void __launch_bounds__(128, 1) k_tc_cgemm(const __grid_constant__ TcM
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
     for (int c = 0; c < kBN; c += 16) {
-      uint32_t re[16], im[16];
+      uint32_t re[16], im[16], re2[16], im2[16];
       tmem_ld16(lane_base + (uint32_t)c, re);
       tmem_ld16(lane_base + (uint32_t)(kBN + c), im);
+      tmem_ld16(lane_base + 256u + (uint32_t)c, re2);
+      tmem_ld16(lane_base + 256u + (uint32_t)(kBN + c), im2);
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
       for (int u = 0; u < 16; u += 2) {
-        float4 v = make_float4(unscale * __uint_as_float(re[u]), unscale * __uint_as_float(im[u]),
-                               unscale * __uint_as_float(re[u + 1]), unscale * __uint_as_float(im[u + 1]));
+        const float r0 = __uint_as_float(re[u]) + __uint_as_float(re2[u]);
+        const float i0 = __uint_as_float(im[u]) + __uint_as_float(im2[u]);
+        const float r1 = __uint_as_float(re[u + 1]) + __uint_as_float(re2[u + 1]);
+        const float i1 = __uint_as_float(im[u + 1]) + __uint_as_float(im2[u + 1]);
+        float4 v = make_float4(unscale * r0, unscale * i0, unscale * r1, unscale * i1);
         *reinterpret_cast<float4*>(out + c + u) = v;
       }
     }

@@ -65,6 +65,8 @@ template <class R> cudaError_t povm_hi_nll(const Dims& D, const R* W, const R* f
                                            double* partials, unsigned int* counter, unsigned int* flags,
                                            const PovmB<R>& B, bool adjoint, cudaStream_t s);
 template <class R> cudaError_t povm_lo_adj(const Dims& D, const R* Wadj, cx_t<R>* G, const PovmB<R>& B, cudaStream_t s);
+// scal[0] = Tr X = sum_i Re X_ii of the computed X (fixed-order FP64 sum)
+template <class R> cudaError_t trace_X(const Dims& D, const cx_t<R>* X, double* scal, cudaStream_t s);
 // full Hermitian matrix from its lower tiles, scaled by 1 / scal[0] (rho = X / Tr X)
 template <class R> cudaError_t hermitian_complete(const Dims& D, const cx_t<R>* Xlow, cx_t<R>* rho,
                                                   const double* scal, cudaStream_t s);
@@ -73,8 +75,7 @@ template <class R> cudaError_t hermitian_complete(const Dims& D, const cx_t<R>* 
 template <class R> cudaError_t net_l1_forward(const Dims& D, const R* theta, const R* f, R* pre, R* hid,
                                               double* scal, double* partials, unsigned int* counter,
                                               const NetCfg& c, cudaStream_t s);
-template <class R> cudaError_t net_build_T(const Dims& D, const R* theta, const R* hid, cx_t<R>* T,
-                                           double* scal, double* partials, unsigned int* counter, cudaStream_t s);
+template <class R> cudaError_t net_build_T(const Dims& D, const R* theta, const R* hid, cx_t<R>* T, cudaStream_t s);
 template <class R> cudaError_t net_w2_pass(const Dims& D, R* theta, R* step, int8_t* sign, const R* dt,
                                            const R* hid, const R* pre, R* dpre, R* dtheta,
                                            double* partials, unsigned int* counter, const NetCfg& c,

@@ -260,6 +260,24 @@ __global__ void __launch_bounds__(256) k_povm_hi_nll(const R* __restrict__ W, co
   }
 }
 
+// ---------------------------------------------------------------- Tr X of the computed X
+// The likelihood and rho = X / Tr X use the trace of X as computed (not ||T||_F^2), so the
+// normalisation carries the same rounding as q and the loss stays invariant to the scale of T.
+template <class R>
+__global__ void __launch_bounds__(256) k_trace(const cx_t<R>* __restrict__ X, int d, double* scal) {
+  __shared__ double red[8];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < d; i += blockDim.x) acc += (double)X[(long long)i * d + i].x;
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    scal[0] = t;
+  }
+}
+
 // ---------------------------------------------------------------- rho = X / Tr X from lower tiles
 template <class R>
 __global__ void __launch_bounds__(256) k_herm_complete(const cx_t<R>* __restrict__ X, cx_t<R>* __restrict__ rho,
@@ -339,6 +357,11 @@ cudaError_t povm_hi_nll(const Dims& D, const R* W, const R* f, double* scal, R* 
   return cudaGetLastError();
 }
 
+template <class R> cudaError_t trace_X(const Dims& D, const cx_t<R>* X, double* scal, cudaStream_t s) {
+  k_trace<R><<<1, 256, 0, s>>>(X, D.d, scal);
+  return cudaGetLastError();
+}
+
 template <class R>
 cudaError_t hermitian_complete(const Dims& D, const cx_t<R>* Xlow, cx_t<R>* rho, const double* scal,
                                cudaStream_t s) {
@@ -354,7 +377,8 @@ cudaError_t hermitian_complete(const Dims& D, const cx_t<R>* Xlow, cx_t<R>* rho,
   template cudaError_t povm_hi_fwd<R>(const Dims&, const R*, R*, const PovmB<R>&, cudaStream_t);             \
   template cudaError_t povm_hi_nll<R>(const Dims&, const R*, const R*, double*, R*, double*, unsigned int*,  \
                                       unsigned int*, const PovmB<R>&, bool, cudaStream_t);                   \
-  template cudaError_t hermitian_complete<R>(const Dims&, const cx_t<R>*, cx_t<R>*, const double*, cudaStream_t);
+  template cudaError_t hermitian_complete<R>(const Dims&, const cx_t<R>*, cx_t<R>*, const double*, cudaStream_t); \
+  template cudaError_t trace_X<R>(const Dims&, const cx_t<R>*, double*, cudaStream_t);
 QST_INST(float)
 QST_INST(double)
 #undef QST_INST

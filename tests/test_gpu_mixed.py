@@ -1,11 +1,12 @@
 """GPU parity of the mixed-precision paths (tcgen05 products with 16-bit hi + lo operands).
 
 Tolerances from the arithmetic.  QST_MIXED (FP16 hi + lo after power-of-two
-scaling): ~22 significant bits per operand, dropped lo*lo term <= 2^-22 of a
-product term, FP32 accumulation: relative error ~2^-21 (5e-7), so rho, the loss
-and the gradient are held to 1e-5.  QST_MIXED_BF16 (BF16 hi + lo): ~16 bits,
-relative error ~2^-16 (1.5e-5): rho and the loss to 1e-4, the gradient to 1e-3
-(normwise; the backward product adds its own split).
+scaling): ~22 significant bits per operand and a dropped lo*lo term <= 2^-22 of
+a product term (together ~2^-21); the tensor core's FP32 accumulation then adds
+up to one truncation (2^-23 relative) per K = 16 step, i.e. (2d / 16) 2^-23 for
+K = 2d.  The bar is 1e-5 + (2d / 16) 2^-23 (4e-5 at d = 2048) on rho, the loss
+and the gradient.  QST_MIXED_BF16 (BF16 hi + lo, ~16 bits): 1e-4 on rho and the
+loss and 1e-3 on the gradient (normwise; the backward product adds its own split).
 """
 import numpy as np
 import pytest
@@ -43,7 +44,12 @@ def _problem(N, seed, shots=10**6):
     return rho, f, synth.init_theta(N, 900 + seed)
 
 
-TOL = {qst.QST_MIXED: (1e-5, 1e-5, 1e-5), qst.QST_MIXED_BF16: (1e-4, 1e-4, 1e-3)}  # rho, loss, gradient
+def TOLS(mode, N):
+    """(rho, loss, gradient) tolerances; see the module docstring."""
+    if mode == qst.QST_MIXED:
+        t = 1e-5 + (2 * (1 << N) / 16) * 2.0 ** -23
+        return t, t, t
+    return 1e-4, 1e-4, 1e-3
 
 
 @pytest.mark.parametrize("mode", [qst.QST_MIXED, qst.QST_MIXED_BF16])
@@ -64,7 +70,7 @@ def test_mixed_rho_matches_fp32_path(N, mode):
         finally:
             qst.qst_destroy(ctx)
     (r32, L32), (rmx, Lmx) = out[qst.QST_FP32], out[mode]
-    t_rho, t_loss, _ = TOL[mode]
+    t_rho, t_loss, _ = TOLS(mode, N)
     assert np.linalg.norm(rmx - r32) / np.linalg.norm(r32) < t_rho
     assert np.abs(rmx - r32).max() < t_rho * np.abs(r32).max()
     assert abs(Lmx - L32) < t_loss * abs(L32)
@@ -86,7 +92,7 @@ def test_mixed_loss_grad_vs_oracle(N, mode):
     finally:
         qst.qst_destroy(ctx)
     assert st == qst.QST_OK
-    _, t_loss, t_grad = TOL[mode]
+    _, t_loss, t_grad = TOLS(mode, N)
     assert abs(L - L_ref) <= t_loss * abs(L_ref)
     rel = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
     assert rel < t_grad, rel
@@ -110,5 +116,23 @@ def test_mixed_reconstruction_reaches_oracle_fidelity():
     finally:
         qst.qst_destroy(ctx)
     F = O.fidelity_pure(rho.astype(np.complex128), psi)
+    print(f"N=8 reconstruction: F mixed {F:.6f}, oracle {F_ref:.6f}")
     assert F_ref > 0.99
-    assert abs(F - F_ref) < 1e-3, (F, F_ref)
+    assert abs(F - F_ref) < 1e-4, (F, F_ref)
+
+
+def test_mixed_trajectory_tracks_fp32_n10():
+    """N = 10, 10^6 shots, 60 Rprop steps: the mixed path follows the FP32 path's loss trajectory."""
+    N = 10
+    _, f, theta = _problem(N, 40, shots=10**6)
+    fd = torch.from_numpy(f.astype(np.float32)).cuda()
+    traj = {}
+    for prec in (qst.QST_FP32, qst.QST_MIXED):
+        ctx = _ctx(N, prec)
+        try:
+            qst.qst_set_params(ctx, theta.astype(np.float32))
+            traj[prec] = np.array([qst.qst_step(ctx, fd)[0] for _ in range(60)])
+        finally:
+            qst.qst_destroy(ctx)
+    rel = np.abs(traj[qst.QST_MIXED] - traj[qst.QST_FP32]) / np.abs(traj[qst.QST_FP32])
+    assert rel.max() < 1e-5, rel.max()
