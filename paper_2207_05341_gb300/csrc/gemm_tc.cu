@@ -296,11 +296,15 @@ __global__ void __launch_bounds__(256) k_absmax_scale(const float* __restrict__ 
     partials[blockIdx.x] = (double)b;
   }
   if (last_block_arrived(counter)) {
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
       double g = 0.0;
-      for (int b = 0; b < (int)gridDim.x; ++b) g = fmax(g, partials[b]);
-      *s_out = (g > 0.0 && isfinite(g)) ? ldexp(1.0, -ilogb(g)) : 1.0;
-      *counter = 0u;
+      for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) g = fmax(g, partials[b]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) g = fmax(g, __shfl_xor_sync(0xffffffffu, g, o));
+      if (threadIdx.x == 0) {
+        *s_out = (g > 0.0 && isfinite(g)) ? ldexp(1.0, -ilogb(g)) : 1.0;
+        *counter = 0u;
+      }
     }
   }
 }
