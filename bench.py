@@ -210,7 +210,9 @@ def make_inputs(torch, qst, synth, dev, lam, seed, exact=False):
     """
     psi = synth.haar_pure(NQ, seed)
     rho = synth.depolarized(psi, lam)
-    ctx = qst.qst_init(NQ)
+    # the library works on the stream it is given: use torch's current stream so that the
+    # copies below are ordered after qst_probs (torch streams do not sync with the legacy one)
+    ctx = qst.qst_init(NQ, stream=torch.cuda.current_stream(dev).cuda_stream)
     try:
         rho_t = torch.from_numpy(rho.astype(np.complex64)).to(dev)
         P = torch.empty(4 ** NQ, device=dev)
@@ -507,7 +509,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-ttf", dest="ttf", action="store_false")
-    ap.add_argument("--max-iters", type=int, default=1000)
+    ap.add_argument("--max-iters", type=int, default=2000)
     ap.add_argument("--shots-iters", type=int, default=200)
     ap.add_argument("--fid-every", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
