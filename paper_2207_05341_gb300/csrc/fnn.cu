@@ -27,6 +27,10 @@ template <> struct Vec<double> {
 
 template <class R> __device__ __forceinline__ R leaky(R x, R slope) { return x > R(0) ? x : slope * x; }
 
+// Parameter rows of a weight pass whose loads are issued together before their
+// Rprop updates and stores (keeps enough bytes in flight to stream at HBM rate).
+constexpr int kRowBatch = 4;
+
 // Reduce M per-thread values over the block; thread 0 writes them (as double) to out[0..M).
 template <int M, class R>
 __device__ __forceinline__ void block_reduce_to(const R (&v)[M], double* out) {
@@ -133,19 +137,55 @@ __global__ void __launch_bounds__(256) k_build_T(const R* __restrict__ theta, co
   tri_decode(blockIdx.x, I, J);
   if (threadIdx.x < H) hs[threadIdx.x] = hid[threadIdx.x];
   __syncthreads();
-  for (int e = threadIdx.x; e < TS * TS; e += blockDim.x) {
-    const int r = e / TS, c = e % TS;
-    const long long ia = (long long)(I * TS + r) * d + J * TS + c;
-    R ta = b2[ia];
+  using VV = Vec<R>;
+  constexpr int VW = VV::W;
+  if (TS % VW == 0) {
+    // VW consecutive columns per thread, 16-byte loads of every W2^T row
+    const int gpr = TS / VW;
+    for (int e = threadIdx.x; e < TS * gpr; e += blockDim.x) {
+      const int r = e / gpr, c = (e % gpr) * VW;
+      const long long ia = (long long)(I * TS + r) * d + J * TS + c;
+      R ta[VW];
+      VV::ld(b2 + ia, ta);
 #pragma unroll
-    for (int j = 0; j < H; ++j) ta += W2T[(long long)j * n + ia] * hs[j];
-    Ra[r][c] = ta;
-    if (I != J) {
-      const long long ib = (long long)(J * TS + r) * d + I * TS + c;
-      R tb = b2[ib];
+      for (int j = 0; j < H; ++j) {
+        R w[VW];
+        VV::ld(W2T + (long long)j * n + ia, w);
 #pragma unroll
-      for (int j = 0; j < H; ++j) tb += W2T[(long long)j * n + ib] * hs[j];
-      Rb[r][c] = tb;
+        for (int u = 0; u < VW; ++u) ta[u] += w[u] * hs[j];
+      }
+#pragma unroll
+      for (int u = 0; u < VW; ++u) Ra[r][c + u] = ta[u];
+      if (I != J) {
+        const long long ib = (long long)(J * TS + r) * d + I * TS + c;
+        R tb[VW];
+        VV::ld(b2 + ib, tb);
+#pragma unroll
+        for (int j = 0; j < H; ++j) {
+          R w[VW];
+          VV::ld(W2T + (long long)j * n + ib, w);
+#pragma unroll
+          for (int u = 0; u < VW; ++u) tb[u] += w[u] * hs[j];
+        }
+#pragma unroll
+        for (int u = 0; u < VW; ++u) Rb[r][c + u] = tb[u];
+      }
+    }
+  } else {
+    for (int e = threadIdx.x; e < TS * TS; e += blockDim.x) {
+      const int r = e / TS, c = e % TS;
+      const long long ia = (long long)(I * TS + r) * d + J * TS + c;
+      R ta = b2[ia];
+#pragma unroll
+      for (int j = 0; j < H; ++j) ta += W2T[(long long)j * n + ia] * hs[j];
+      Ra[r][c] = ta;
+      if (I != J) {
+        const long long ib = (long long)(J * TS + r) * d + I * TS + c;
+        R tb = b2[ib];
+#pragma unroll
+        for (int j = 0; j < H; ++j) tb += W2T[(long long)j * n + ib] * hs[j];
+        Rb[r][c] = tb;
+      }
     }
   }
   __syncthreads();
@@ -170,13 +210,14 @@ __global__ void __launch_bounds__(256) k_build_T(const R* __restrict__ theta, co
 // db2 = dt, dW2^T[j][i] = h_j dt_i, dh_j = sum_i W2^T[j][i] dt_i (old weights);
 // then dpre = dh * LeakyReLU'(pre), db1 = dpre.  update: Rprop on W2^T, b2, b1; else write dtheta.
 template <class R, int H, bool UPD>
-__global__ void __launch_bounds__(256) k_w2_pass(R* __restrict__ theta, R* __restrict__ step, int8_t* __restrict__ sign,
+__global__ void __launch_bounds__(256, 2) k_w2_pass(R* __restrict__ theta, R* __restrict__ step, int8_t* __restrict__ sign,
                                                   const R* __restrict__ dt, const R* __restrict__ hid,
                                                   const R* __restrict__ pre, R* dpre, R* __restrict__ dtheta,
                                                   long long n, double* partials, unsigned int* counter,
                                                   RpropCfg<R> rc, R slope) {
   using VV = Vec<R>;
   constexpr int VW = VV::W;
+  constexpr int JB = kRowBatch;  // rows whose loads are issued together, ahead of their updates
   const long long o2 = (long long)H * n, ob2 = 2LL * H * n, ob1 = 2LL * H * n + n;
   __shared__ R hs[H];
   if (threadIdx.x < H) hs[threadIdx.x] = hid[threadIdx.x];
@@ -200,21 +241,33 @@ __global__ void __launch_bounds__(256) k_w2_pass(R* __restrict__ theta, R* __res
       VV::st(dtheta + ob2 + x, dv);
     }
 #pragma unroll
-    for (int j = 0; j < H; ++j) {
-      const long long oj = o2 + (long long)j * n + x;
-      R w[VW], g[VW];
-      VV::ld(theta + oj, w);
+    for (int j0 = 0; j0 < H; j0 += JB) {
+      R w[JB][VW], st[JB][VW];
+      int8_t sg[JB][VW];
 #pragma unroll
-      for (int u = 0; u < VW; ++u) { acc[j] += w[u] * dv[u]; g[u] = hs[j] * dv[u]; }
-      if (UPD) {
-        R st[VW];
-        int8_t sg[VW];
-        VV::ld(step + oj, st); VV::lds(sign + oj, sg);
+      for (int jj = 0; jj < JB; ++jj) {
+        if (j0 + jj < H) {
+          const long long oj = o2 + (long long)(j0 + jj) * n + x;
+          VV::ld(theta + oj, w[jj]);
+          if (UPD) { VV::ld(step + oj, st[jj]); VV::lds(sign + oj, sg[jj]); }
+        }
+      }
 #pragma unroll
-        for (int u = 0; u < VW; ++u) w[u] = rprop1(w[u], g[u], st[u], sg[u], rc);
-        VV::st(theta + oj, w); VV::st(step + oj, st); VV::sts(sign + oj, sg);
-      } else {
-        VV::st(dtheta + oj, g);
+      for (int jj = 0; jj < JB; ++jj) {
+        if (j0 + jj < H) {
+          const int j = j0 + jj;
+          const long long oj = o2 + (long long)j * n + x;
+          R g[VW];
+#pragma unroll
+          for (int u = 0; u < VW; ++u) { acc[j] += w[jj][u] * dv[u]; g[u] = hs[j] * dv[u]; }
+          if (UPD) {
+#pragma unroll
+            for (int u = 0; u < VW; ++u) w[jj][u] = rprop1(w[jj][u], g[u], st[jj][u], sg[jj][u], rc);
+            VV::st(theta + oj, w[jj]); VV::st(step + oj, st[jj]); VV::sts(sign + oj, sg[jj]);
+          } else {
+            VV::st(dtheta + oj, g);
+          }
+        }
       }
     }
   }
@@ -243,7 +296,7 @@ __global__ void __launch_bounds__(256) k_w2_pass(R* __restrict__ theta, R* __res
 // dW1[j][i] = dpre_j f_i.  update: Rprop on W1, then pre = W1' f + b1', hid = LeakyReLU(pre),
 // scal[1] = sum f (the hidden layer of the next iteration); else write dtheta.
 template <class R, int H, bool UPD>
-__global__ void __launch_bounds__(256) k_w1_pass(R* __restrict__ theta, R* __restrict__ step, int8_t* __restrict__ sign,
+__global__ void __launch_bounds__(256, 2) k_w1_pass(R* __restrict__ theta, R* __restrict__ step, int8_t* __restrict__ sign,
                                                   const R* __restrict__ f, const R* __restrict__ dpre, R* pre,
                                                   R* hid, R* __restrict__ dtheta, long long n, double* scal,
                                                   double* partials, unsigned int* counter, RpropCfg<R> rc, R slope) {
@@ -256,6 +309,7 @@ __global__ void __launch_bounds__(256) k_w1_pass(R* __restrict__ theta, R* __res
   R acc[H + 1];
 #pragma unroll
   for (int j = 0; j <= H; ++j) acc[j] = R(0);
+  constexpr int JB = kRowBatch;
   const long long nv = n / VW;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (long long)gridDim.x * blockDim.x) {
     const long long x = i * VW;
@@ -264,23 +318,37 @@ __global__ void __launch_bounds__(256) k_w1_pass(R* __restrict__ theta, R* __res
 #pragma unroll
     for (int u = 0; u < VW; ++u) acc[H] += fv[u];
 #pragma unroll
-    for (int j = 0; j < H; ++j) {
-      const long long oj = (long long)j * n + x;
-      R g[VW];
-#pragma unroll
-      for (int u = 0; u < VW; ++u) g[u] = dps[j] * fv[u];
+    for (int j0 = 0; j0 < H; j0 += JB) {
+      R w[JB][VW], st[JB][VW];
+      int8_t sg[JB][VW];
       if (UPD) {
-        R w[VW], st[VW];
-        int8_t sg[VW];
-        VV::ld(theta + oj, w); VV::ld(step + oj, st); VV::lds(sign + oj, sg);
 #pragma unroll
-        for (int u = 0; u < VW; ++u) {
-          w[u] = rprop1(w[u], g[u], st[u], sg[u], rc);
-          acc[j] += w[u] * fv[u];
+        for (int jj = 0; jj < JB; ++jj) {
+          if (j0 + jj < H) {
+            const long long oj = (long long)(j0 + jj) * n + x;
+            VV::ld(theta + oj, w[jj]); VV::ld(step + oj, st[jj]); VV::lds(sign + oj, sg[jj]);
+          }
         }
-        VV::st(theta + oj, w); VV::st(step + oj, st); VV::sts(sign + oj, sg);
-      } else {
-        VV::st(dtheta + oj, g);
+      }
+#pragma unroll
+      for (int jj = 0; jj < JB; ++jj) {
+        if (j0 + jj < H) {
+          const int j = j0 + jj;
+          const long long oj = (long long)j * n + x;
+          R g[VW];
+#pragma unroll
+          for (int u = 0; u < VW; ++u) g[u] = dps[j] * fv[u];
+          if (UPD) {
+#pragma unroll
+            for (int u = 0; u < VW; ++u) {
+              w[jj][u] = rprop1(w[jj][u], g[u], st[jj][u], sg[jj][u], rc);
+              acc[j] += w[jj][u] * fv[u];
+            }
+            VV::st(theta + oj, w[jj]); VV::st(step + oj, st[jj]); VV::sts(sign + oj, sg[jj]);
+          } else {
+            VV::st(dtheta + oj, g);
+          }
+        }
       }
     }
   }
