@@ -198,8 +198,41 @@ enum {
 qst_status qst_timing_enable(qst_ctx* ctx, int max_steps);
 qst_status qst_timing_read(qst_ctx* ctx, double* phase_ms, long long* phase_count, int nphase);
 
+/* Capture the steady-state iteration of qst_step into a CUDA graph and replay it
+ * (enable != 0), or go back to launching kernel by kernel (0).  Needs a context
+ * created with a non-NULL stream (QST_E_UNSUPPORTED otherwise).  The graph is
+ * captured on the first qst_step whose device input f was also given to the
+ * previous step (the hidden layer is then known) and is re-captured when f's
+ * pointer changes; host inputs and enabled per-phase timing use the launch-by-
+ * launch path.  Instrumentation of the library, not part of the method. */
+qst_status qst_graph_enable(qst_ctx* ctx, int enable);
+
 /* Wait for all work enqueued on the context's stream. */
 qst_status qst_sync(qst_ctx* ctx);
+
+/* ---- batches of independent tomographies (one graph launch per iteration) ----
+ * B tomographies of possibly different qubit counts Ns[b], each with its own
+ * context (parameters, Rprop state, scratch) and stream.  From the second
+ * qst_batch_step with the same inputs on, one iteration of all B is a single
+ * cudaGraphLaunch on `stream` whose graph forks to one kernel chain per
+ * tomography and joins them.  QST_MIXED / QST_MIXED_BF16 apply to the
+ * tomographies with N >= 7; smaller ones run FP32.  The tomographies share
+ * nothing, so this is the method applied B times (Sec. 4 runs many states). */
+typedef struct qst_batch qst_batch;
+qst_status qst_batch_init(qst_batch** out, int B, const int* Ns, const double* povm, int K,
+                          const qst_options* opt, void* stream);
+/* Context of tomography b (for qst_get_params, qst_get_rho, ...); owned by the batch. */
+qst_ctx* qst_batch_context(qst_batch* batch, int b);
+qst_status qst_batch_set_params(qst_batch* batch, int b, const void* theta);
+/* One iteration of every tomography.  f: host array of B device pointers (n_b reals
+ * each).  losses: host array of B doubles or NULL (synchronises). */
+qst_status qst_batch_step(qst_batch* batch, const void* const* f, double* losses);
+/* iters iterations, then each rho_out[b] (device or host, or rho_out NULL) and final loss. */
+qst_status qst_batch_reconstruct(qst_batch* batch, const void* const* f, int iters, void* const* rho_out,
+                                 double* final_losses);
+long long qst_batch_kernel_launches(const qst_batch* batch);
+qst_status qst_batch_sync(qst_batch* batch);
+void qst_batch_destroy(qst_batch* batch);
 
 const char* qst_strerror(qst_status s);
 

@@ -53,6 +53,11 @@ struct qst_ctx {
   std::vector<cudaEvent_t> tev;   // max_steps * (QST_NPHASE + 1) events
   std::vector<unsigned int> tmask;
   int tmax = 0, tcount = 0, tslot = -1;
+  // CUDA graph of one steady-state qst_step (qst_graph_enable)
+  bool graph_on = false;
+  cudaGraphExec_t gexec = nullptr;
+  const void* gf = nullptr;
+  long long gnodes = 0;
 };
 
 namespace {
@@ -278,21 +283,13 @@ template <class R> struct Engine {
     return QST_OK;
   }
 
-  static qst_status step(qst_ctx* c, const void* f_user, double* loss) {
+  // The steady-state iteration after the hidden layer is known: forward, likelihood,
+  // backward, Rprop on W2 / b2 / b1, Rprop on W1 with the next hidden layer.  Stream
+  // work only (no host synchronisation), so that it can be captured into a graph.
+  static qst_status step_body(qst_ctx* c, const R* f) {
     Work<R>* w = W<R>(c);
     const Dims& D = c->D;
     qst_status st;
-    const R* f = (const R*)stage_input(c, f_user, (size_t)D.n * sizeof(R), w->fstage, &st);
-    if (st != QST_OK) return st;
-    const bool new_f = !c->hidden_valid || f_user != c->f_last;
-    if (new_f) {
-      st = validate_f<R>(c, f);
-      if (st != QST_OK) return st;
-    }
-    tmark_begin(c);
-    if (new_f) {
-      if ((st = hidden(c, w->theta, f)) != QST_OK) return st;
-    }
     if ((st = forward_state(c, w->theta)) != QST_OK) return st;
     if ((st = povm_likelihood(c, f, true)) != QST_OK) return st;
     if ((st = backward_state(c)) != QST_OK) return st;
@@ -302,8 +299,58 @@ template <class R> struct Engine {
     QST_CU(net_w1_pass<R>(D, w->theta, w->step, w->sign, f, w->dpre, w->pre, w->hid, nullptr, w->scal, w->partials,
                           w->counters + CNT_W1, c->net, true, c->stream));
     tmark(c, QST_PH_W1);
-    c->tslot = -1;
     c->launches += 2;
+    return QST_OK;
+  }
+
+  // Capture step_body for input f into c->gexec (replaces an earlier graph).
+  static qst_status capture(qst_ctx* c, const void* f_user) {
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    const long long l0 = c->launches;
+    QST_CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    const qst_status st = step_body(c, (const R*)f_user);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    c->launches = l0;
+    if (st != QST_OK) { if (g) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) return cuda_status(e);
+    const cudaError_t e2 = cudaGraphInstantiate(&c->gexec, g, 0);
+    size_t nodes = 0;
+    cudaGraphGetNodes(g, nullptr, &nodes);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) { c->gexec = nullptr; return cuda_status(e2); }
+    c->gnodes = (long long)nodes;
+    c->gf = f_user;
+    return QST_OK;
+  }
+
+  static qst_status step(qst_ctx* c, const void* f_user, double* loss) {
+    Work<R>* w = W<R>(c);
+    const Dims& D = c->D;
+    qst_status st;
+    const bool graphable = c->graph_on && c->tmax == 0 && is_device_ptr(f_user);
+    const R* f = graphable ? (const R*)f_user
+                           : (const R*)stage_input(c, f_user, (size_t)D.n * sizeof(R), w->fstage, &st);
+    if (!graphable && st != QST_OK) return st;
+    const bool new_f = !c->hidden_valid || f_user != c->f_last;
+    if (new_f) {
+      st = validate_f<R>(c, f);
+      if (st != QST_OK) return st;
+    }
+    if (graphable && !new_f) {
+      if (!c->gexec || c->gf != f_user) {
+        if ((st = capture(c, f_user)) != QST_OK) return st;
+      }
+      QST_CU(cudaGraphLaunch(c->gexec, c->stream));
+      c->launches += c->gnodes;
+    } else {
+      tmark_begin(c);
+      if (new_f) {
+        if ((st = hidden(c, w->theta, f)) != QST_OK) return st;
+      }
+      if ((st = step_body(c, f)) != QST_OK) return st;
+      c->tslot = -1;
+    }
     c->hidden_valid = true;
     c->f_last = f_user;
     c->iters += 1;
@@ -406,6 +453,69 @@ template <class R> qst_status reset_rprop(qst_ctx* c) {
   QST_CU(cudaMemcpyAsync(w->step, h.data(), P * sizeof(R), cudaMemcpyHostToDevice, c->stream));
   QST_CU(cudaMemsetAsync(w->sign, 0, P, c->stream));
   QST_CU(cudaStreamSynchronize(c->stream));
+  return QST_OK;
+}
+
+double* ctx_scal(qst_ctx* c) {
+  return c->prec == QST_FP64 ? W<double>(c)->scal : W<float>(c)->scal;
+}
+
+__global__ void k_gather_losses(double* const* scal, double* out, int B) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) out[b] = scal[b][2];
+}
+
+}  // namespace
+
+struct qst_batch {
+  int B = 0;
+  std::vector<qst_ctx*> ctx;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> done;
+  cudaEvent_t fork = nullptr;
+  cudaStream_t root = nullptr;
+  bool own_root = false;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<const void*> gf;
+  long long gnodes = 0;
+  long long launches = 0;
+  double** d_scal = nullptr;
+  double* d_losses = nullptr;
+  double* h_losses = nullptr;
+};
+
+namespace {
+
+// One iteration of every tomography of the batch, captured once into a single graph:
+// the root stream forks to one stream per tomography and joins them again.
+qst_status batch_capture(qst_batch* bt, const void* const* f) {
+  if (bt->gexec) { cudaGraphExecDestroy(bt->gexec); bt->gexec = nullptr; }
+  QST_CU(cudaStreamBeginCapture(bt->root, cudaStreamCaptureModeThreadLocal));
+  qst_status st = QST_OK;
+  cudaError_t e = cudaEventRecord(bt->fork, bt->root);
+  for (int b = 0; b < bt->B && st == QST_OK && e == cudaSuccess; ++b) {
+    qst_ctx* c = bt->ctx[b];
+    e = cudaStreamWaitEvent(c->stream, bt->fork, 0);
+    if (e != cudaSuccess) break;
+    const long long l0 = c->launches;
+    st = c->prec == QST_FP64 ? Engine<double>::step_body(c, (const double*)f[b])
+                             : Engine<float>::step_body(c, (const float*)f[b]);
+    c->launches = l0;
+    if (st != QST_OK) break;
+    e = cudaEventRecord(bt->done[b], c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(bt->root, bt->done[b], 0);
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(bt->root, &g);
+  if (st != QST_OK) { if (g) cudaGraphDestroy(g); return st; }
+  if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_status(e); }
+  if (e2 != cudaSuccess) return cuda_status(e2);
+  size_t nodes = 0;
+  cudaGraphGetNodes(g, nullptr, &nodes);
+  const cudaError_t e3 = cudaGraphInstantiate(&bt->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e3 != cudaSuccess) { bt->gexec = nullptr; return cuda_status(e3); }
+  bt->gnodes = (long long)nodes;
+  bt->gf.assign(f, f + bt->B);
   return QST_OK;
 }
 
@@ -630,6 +740,18 @@ qst_status qst_timing_read(qst_ctx* c, double* phase_ms, long long* phase_count,
   return QST_OK;
 }
 
+qst_status qst_graph_enable(qst_ctx* c, int enable) {
+  if (!c) return QST_E_INVAL;
+  if (enable && c->stream == nullptr) return QST_E_UNSUPPORTED;  // the legacy stream cannot be captured
+  c->graph_on = enable != 0;
+  if (!c->graph_on && c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->gf = nullptr;
+  }
+  return QST_OK;
+}
+
 qst_status qst_sync(qst_ctx* c) {
   if (!c) return QST_E_INVAL;
   QST_CU(cudaStreamSynchronize(c->stream));
@@ -656,6 +778,7 @@ void qst_destroy(qst_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
   for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
   for (void* p : c->allocs) cudaFree(p);
   if (c->work) {
     if (c->prec == QST_FP64) free_work<double>(c);
@@ -664,6 +787,147 @@ void qst_destroy(qst_ctx* c) {
   if (c->h_scal) cudaFreeHost(c->h_scal);
   if (c->h_flags) cudaFreeHost(c->h_flags);
   delete c;
+}
+
+}  // extern "C"
+
+// =============================================================================== batches of tomographies
+extern "C" {
+
+qst_status qst_batch_init(qst_batch** out, int B, const int* Ns, const double* povm, int K, const qst_options* opt,
+                          void* stream) {
+  if (!out || B < 1 || !Ns) return QST_E_INVAL;
+  *out = nullptr;
+  qst_batch* bt = new (std::nothrow) qst_batch();
+  if (!bt) return QST_E_NOMEM;
+  bt->B = B;
+  auto fail = [&](qst_status st) { qst_batch_destroy(bt); return st; };
+  if (stream) {
+    bt->root = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&bt->root, cudaStreamNonBlocking) != cudaSuccess) return fail(QST_E_CUDA);
+    bt->own_root = true;
+  }
+  if (cudaEventCreateWithFlags(&bt->fork, cudaEventDisableTiming) != cudaSuccess) return fail(QST_E_CUDA);
+  qst_options o;
+  qst_default_options(&o);
+  if (opt) o = *opt;
+  bt->ctx.assign(B, nullptr);
+  bt->streams.assign(B, nullptr);
+  bt->done.assign(B, nullptr);
+  std::vector<double*> scal(B);
+  for (int b = 0; b < B; ++b) {
+    if (cudaStreamCreateWithFlags(&bt->streams[b], cudaStreamNonBlocking) != cudaSuccess) return fail(QST_E_CUDA);
+    if (cudaEventCreateWithFlags(&bt->done[b], cudaEventDisableTiming) != cudaSuccess) return fail(QST_E_CUDA);
+    qst_options ob = o;
+    if ((ob.precision == QST_MIXED || ob.precision == QST_MIXED_BF16) && Ns[b] < 7) ob.precision = QST_FP32;
+    const qst_status st = qst_init(&bt->ctx[b], Ns[b], povm, K, &ob, bt->streams[b]);
+    if (st != QST_OK) return fail(st);
+    scal[b] = ctx_scal(bt->ctx[b]);
+  }
+  if (cudaMalloc(&bt->d_scal, B * sizeof(double*)) != cudaSuccess) return fail(QST_E_NOMEM);
+  if (cudaMalloc(&bt->d_losses, B * sizeof(double)) != cudaSuccess) return fail(QST_E_NOMEM);
+  if (cudaMallocHost(&bt->h_losses, B * sizeof(double)) != cudaSuccess) return fail(QST_E_NOMEM);
+  if (cudaMemcpy(bt->d_scal, scal.data(), B * sizeof(double*), cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(QST_E_CUDA);
+  *out = bt;
+  return QST_OK;
+}
+
+qst_ctx* qst_batch_context(qst_batch* bt, int b) {
+  if (!bt || b < 0 || b >= bt->B) return nullptr;
+  return bt->ctx[b];
+}
+
+qst_status qst_batch_set_params(qst_batch* bt, int b, const void* theta) {
+  if (!bt || b < 0 || b >= bt->B) return QST_E_INVAL;
+  return qst_set_params(bt->ctx[b], theta);
+}
+
+qst_status qst_batch_step(qst_batch* bt, const void* const* f, double* losses) {
+  if (!bt || !f) return QST_E_INVAL;
+  bool steady = true;
+  for (int b = 0; b < bt->B; ++b) {
+    qst_ctx* c = bt->ctx[b];
+    if (!f[b] || !is_device_ptr(f[b])) return QST_E_INVAL;
+    if (!c->params_set) return QST_E_STATE;
+    if (!c->hidden_valid || c->f_last != f[b]) steady = false;
+  }
+  if (!steady) {
+    // first iteration for these inputs: validate them and build each hidden layer (not captured)
+    QST_CU(cudaEventRecord(bt->fork, bt->root));
+    for (int b = 0; b < bt->B; ++b) {
+      qst_ctx* c = bt->ctx[b];
+      QST_CU(cudaStreamWaitEvent(c->stream, bt->fork, 0));
+      const long long l0 = c->launches;
+      const qst_status st = qst_step(c, f[b], nullptr);
+      if (st < 0) return st;
+      bt->launches += c->launches - l0;
+      QST_CU(cudaEventRecord(bt->done[b], c->stream));
+      QST_CU(cudaStreamWaitEvent(bt->root, bt->done[b], 0));
+    }
+  } else {
+    bool same = bt->gexec != nullptr && (int)bt->gf.size() == bt->B;
+    for (int b = 0; same && b < bt->B; ++b) same = bt->gf[b] == f[b];
+    if (!same) {
+      const qst_status st = batch_capture(bt, f);
+      if (st != QST_OK) return st;
+    }
+    QST_CU(cudaGraphLaunch(bt->gexec, bt->root));
+    bt->launches += bt->gnodes;
+    for (int b = 0; b < bt->B; ++b) bt->ctx[b]->iters += 1;
+  }
+  if (losses) {
+    k_gather_losses<<<(bt->B + 255) / 256, 256, 0, bt->root>>>(bt->d_scal, bt->d_losses, bt->B);
+    QST_CU(cudaGetLastError());
+    QST_CU(cudaMemcpyAsync(bt->h_losses, bt->d_losses, bt->B * sizeof(double), cudaMemcpyDeviceToHost, bt->root));
+    QST_CU(cudaStreamSynchronize(bt->root));
+    memcpy(losses, bt->h_losses, bt->B * sizeof(double));
+  }
+  return QST_OK;
+}
+
+qst_status qst_batch_reconstruct(qst_batch* bt, const void* const* f, int iters, void* const* rho_out,
+                                 double* final_losses) {
+  if (!bt || !f || iters < 0) return QST_E_INVAL;
+  for (int i = 0; i < iters; ++i) {
+    const qst_status st = qst_batch_step(bt, f, nullptr);
+    if (st < 0) return st;
+  }
+  QST_CU(cudaStreamSynchronize(bt->root));
+  for (int b = 0; b < bt->B; ++b) {
+    if (!rho_out && !final_losses) break;
+    const qst_status st = qst_get_rho(bt->ctx[b], f[b], rho_out ? rho_out[b] : nullptr,
+                                      final_losses ? final_losses + b : nullptr);
+    if (st < 0) return st;
+  }
+  return QST_OK;
+}
+
+long long qst_batch_kernel_launches(const qst_batch* bt) { return bt ? bt->launches : -1; }
+
+qst_status qst_batch_sync(qst_batch* bt) {
+  if (!bt) return QST_E_INVAL;
+  QST_CU(cudaStreamSynchronize(bt->root));
+  return QST_OK;
+}
+
+void qst_batch_destroy(qst_batch* bt) {
+  if (!bt) return;
+  if (bt->root) cudaStreamSynchronize(bt->root);
+  if (bt->gexec) cudaGraphExecDestroy(bt->gexec);
+  for (qst_ctx* c : bt->ctx)
+    if (c) qst_destroy(c);
+  for (cudaStream_t s : bt->streams)
+    if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : bt->done)
+    if (e) cudaEventDestroy(e);
+  if (bt->fork) cudaEventDestroy(bt->fork);
+  if (bt->d_scal) cudaFree(bt->d_scal);
+  if (bt->d_losses) cudaFree(bt->d_losses);
+  if (bt->h_losses) cudaFreeHost(bt->h_losses);
+  if (bt->own_root && bt->root) cudaStreamDestroy(bt->root);
+  delete bt;
 }
 
 }  // extern "C"

@@ -37,7 +37,9 @@ EXPORTED = [
     "qst_probs", "qst_loss_grad", "qst_step", "qst_reconstruct", "qst_get_rho",
     "qst_state_bytes", "qst_get_state", "qst_set_state", "qst_iterations",
     "qst_kernel_launches", "qst_sync", "qst_strerror", "qst_destroy",
-    "qst_timing_enable", "qst_timing_read", "qst_probs_static",
+    "qst_timing_enable", "qst_timing_read", "qst_probs_static", "qst_graph_enable",
+    "qst_batch_init", "qst_batch_context", "qst_batch_set_params", "qst_batch_step",
+    "qst_batch_reconstruct", "qst_batch_kernel_launches", "qst_batch_sync", "qst_batch_destroy",
 ]
 
 PHASES = ["hidden", "build_T", "x_fwd", "povm_lo", "povm_hi", "povm_adj", "gt", "sym", "w2", "w1"]
@@ -98,6 +100,16 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "qst_timing_enable": (i, [vp, i]),
         "qst_timing_read": (i, [vp, pd, ctypes.POINTER(ctypes.c_longlong), i]),
         "qst_probs_static": (i, [i, vp, i, vp, vp, vp]),
+        "qst_graph_enable": (i, [vp, i]),
+        "qst_batch_init": (i, [ctypes.POINTER(vp), i, ctypes.POINTER(ctypes.c_int), vp, i,
+                               ctypes.POINTER(qst_options), vp]),
+        "qst_batch_context": (vp, [vp, i]),
+        "qst_batch_set_params": (i, [vp, i, vp]),
+        "qst_batch_step": (i, [vp, ctypes.POINTER(vp), pd]),
+        "qst_batch_reconstruct": (i, [vp, ctypes.POINTER(vp), i, ctypes.POINTER(vp), pd]),
+        "qst_batch_kernel_launches": (ctypes.c_longlong, [vp]),
+        "qst_batch_sync": (i, [vp]),
+        "qst_batch_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -262,3 +274,63 @@ def qst_probs_static(N: int, rho, p, povm=None, K: int = 4, stream: int = 0) -> 
     povm = np.ascontiguousarray(povm, dtype=np.float64)
     return _check(load().qst_probs_static(int(N), povm.ctypes.data, int(K), ptr(rho), ptr(p), stream or None),
                   "qst_probs_static")
+
+
+def qst_graph_enable(ctx: int, enable: bool = True) -> int:
+    return _check(load().qst_graph_enable(ctx, 1 if enable else 0), "qst_graph_enable")
+
+
+def _ptr_array(xs):
+    arr = (ctypes.c_void_p * len(xs))()
+    for k, x in enumerate(xs):
+        arr[k] = ptr(x)
+    return arr
+
+
+def qst_batch_init(Ns, povm=None, K: int = 4, opt: qst_options | None = None, stream: int = 0) -> int:
+    """Create a batch of len(Ns) independent tomographies; returns the handle."""
+    if povm is None:
+        povm = tetrahedral_povm_flat()
+    povm = np.ascontiguousarray(povm, dtype=np.float64)
+    ns = (ctypes.c_int * len(Ns))(*[int(x) for x in Ns])
+    h = ctypes.c_void_p()
+    st = load().qst_batch_init(ctypes.byref(h), len(Ns), ns, povm.ctypes.data, int(K),
+                               ctypes.byref(opt) if opt is not None else None, stream or None)
+    _check(st, "qst_batch_init")
+    return h.value
+
+
+def qst_batch_context(batch: int, b: int) -> int:
+    return load().qst_batch_context(batch, int(b))
+
+
+def qst_batch_set_params(batch: int, b: int, theta) -> int:
+    return _check(load().qst_batch_set_params(batch, int(b), ptr(theta)), "qst_batch_set_params")
+
+
+def qst_batch_step(batch: int, fs, want_losses: bool = False):
+    arr = _ptr_array(fs)
+    losses = (ctypes.c_double * len(fs))() if want_losses else None
+    _check(load().qst_batch_step(batch, arr, losses), "qst_batch_step")
+    return list(losses) if want_losses else None
+
+
+def qst_batch_reconstruct(batch: int, fs, iters: int, rhos=None, want_losses: bool = True):
+    arr = _ptr_array(fs)
+    rarr = _ptr_array(rhos) if rhos is not None else None
+    losses = (ctypes.c_double * len(fs))() if want_losses else None
+    _check(load().qst_batch_reconstruct(batch, arr, int(iters), rarr, losses), "qst_batch_reconstruct")
+    return list(losses) if want_losses else None
+
+
+def qst_batch_kernel_launches(batch: int) -> int:
+    return int(load().qst_batch_kernel_launches(batch))
+
+
+def qst_batch_sync(batch: int) -> int:
+    return _check(load().qst_batch_sync(batch), "qst_batch_sync")
+
+
+def qst_batch_destroy(batch: int) -> None:
+    if batch:
+        load().qst_batch_destroy(batch)

@@ -1,0 +1,92 @@
+"""CUDA-graph replay of qst_step and batches of tomographies: both must reproduce the
+launch-by-launch path bit for bit (all reductions in the library have a fixed order)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2207_05341_gb300 import qst, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import os
+    if not os.path.exists(qst.LIB_PATH):
+        from paper_2207_05341_gb300 import build
+        build.build()
+    qst.load()
+
+
+def _inputs(N, seed):
+    M = O.tetrahedral_povm()
+    rho = synth.ginibre_mixed(N, max(1, (1 << N) // 3), 40 + seed)
+    f = synth.frequencies(synth.multinomial_counts(O.born_probabilities(rho, M).real, 10**5 * N, 50 + seed))
+    return f.astype(np.float32), synth.init_theta(N, 60 + seed).astype(np.float32)
+
+
+def _run(N, f, theta, steps, prec, graph):
+    stream = torch.cuda.Stream()
+    o = qst.qst_default_options()
+    o.precision = prec
+    ctx = qst.qst_init(N, opt=o, stream=stream.cuda_stream)
+    try:
+        if graph:
+            qst.qst_graph_enable(ctx, True)
+        qst.qst_set_params(ctx, theta)
+        fd = torch.from_numpy(f).cuda()
+        torch.cuda.synchronize()
+        losses = [qst.qst_step(ctx, fd)[0] for _ in range(steps)]
+        out = torch.empty(theta.size, device="cuda")
+        qst.qst_get_params(ctx, out)
+        qst.qst_sync(ctx)
+        return losses, out.cpu().numpy(), qst.qst_iterations(ctx)
+    finally:
+        qst.qst_destroy(ctx)
+
+
+@pytest.mark.parametrize("N,prec", [(5, qst.QST_FP32), (8, qst.QST_MIXED)])
+def test_graph_replay_is_bit_identical(N, prec):
+    f, theta = _inputs(N, N)
+    la, ta, ia = _run(N, f, theta, 6, prec, graph=False)
+    lb, tb, ib = _run(N, f, theta, 6, prec, graph=True)
+    assert la == lb and ia == ib == 6
+    assert np.array_equal(ta, tb)
+
+
+def test_graph_needs_a_stream():
+    ctx = qst.qst_init(3)
+    try:
+        with pytest.raises(qst.QstError) as e:
+            qst.qst_graph_enable(ctx, True)
+        assert e.value.status == qst.QST_E_UNSUPPORTED
+    finally:
+        qst.qst_destroy(ctx)
+
+
+def test_batch_matches_individual_contexts():
+    Ns = [3, 5, 7, 4, 6, 8, 3]
+    data = [_inputs(N, 10 + b) for b, N in enumerate(Ns)]
+    steps = 5
+    want = [_run(N, f, th, steps, qst.QST_FP32, graph=False) for N, (f, th) in zip(Ns, data)]
+    stream = torch.cuda.Stream()
+    bt = qst.qst_batch_init(Ns, stream=stream.cuda_stream)
+    try:
+        fds = [torch.from_numpy(f).cuda() for f, _ in data]
+        for b, (_, th) in enumerate(data):
+            qst.qst_batch_set_params(bt, b, th)
+        torch.cuda.synchronize()
+        losses = [qst.qst_batch_step(bt, fds, want_losses=True) for _ in range(steps)]
+        for b, N in enumerate(Ns):
+            out = torch.empty(data[b][1].size, device="cuda")
+            qst.qst_get_params(qst.qst_batch_context(bt, b), out)
+            qst.qst_batch_sync(bt)
+            torch.cuda.synchronize()
+            assert [l[b] for l in losses] == want[b][0], b
+            assert np.array_equal(out.cpu().numpy(), want[b][1]), b
+        assert qst.qst_batch_kernel_launches(bt) > 0
+    finally:
+        qst.qst_batch_destroy(bt)
