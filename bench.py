@@ -326,6 +326,54 @@ def cpu_baseline(f, theta0, seconds=12.0):
             "sample": f"{n} full N=11 iterations (loss, analytic gradient, Rprop) in FP64 NumPy, {el:.1f} s"}
 
 
+def batch_c4(torch, qst, synth, dev, steps, warmup, seed=30, B=512):
+    """512 independent tomographies, N ~ U{3..9}, rank-r Ginibre states (r ~ U{1..2^N}),
+    10^5 N shots each; one graph launch per iteration of all of them."""
+    rng = np.random.default_rng(seed)
+    Ns = [int(x) for x in rng.integers(3, 10, B)]
+    stream = torch.cuda.Stream(device=dev)
+    bt = qst.qst_batch_init(Ns, stream=stream.cuda_stream)
+    try:
+        fds = []
+        with torch.cuda.stream(stream):
+            for b, N in enumerate(Ns):
+                r = int(rng.integers(1, 2 ** N + 1))
+                rho = synth.ginibre_mixed(N, r, seed * 100000 + b)
+                rho_t = torch.from_numpy(rho.astype(np.complex64)).to(dev)
+                P = torch.empty(4 ** N, device=dev)
+                cb = qst.qst_batch_context(bt, b)
+                torch.cuda.current_stream(dev).synchronize()
+                qst.qst_probs(cb, rho_t, P)
+                qst.qst_sync(cb)  # the context runs on its own stream
+                P = P.double().cpu().numpy()
+                f = synth.frequencies(synth.multinomial_counts(P, 10**5 * N, seed * 100000 + B + b), np.float32)
+                fds.append(torch.from_numpy(f).to(dev))
+                qst.qst_batch_set_params(bt, b, synth.init_theta(N, seed * 100000 + 2 * B + b).astype(np.float32))
+            for _ in range(max(warmup, 2)):
+                qst.qst_batch_step(bt, fds)
+            torch.cuda.synchronize()
+            l0 = qst.qst_batch_kernel_launches(bt)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                qst.qst_batch_step(bt, fds)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            launches = qst.qst_batch_kernel_launches(bt) - l0
+            losses = qst.qst_batch_step(bt, fds, want_losses=True)
+        it_s = B * steps / (ms / 1e3)
+        return {"workload": "512 tomographies, N ~ U{3..9}, rank-r Ginibre (r ~ U{1..2^N}), 10^5 N shots, FP32",
+                "Ns_hist": {str(k): Ns.count(k) for k in range(3, 10)},
+                "ms_per_batch_iteration": ms / steps, "aggregate_iters_per_s": it_s,
+                "tomographies_per_s_at_1000_iters": it_s / 1000.0,
+                "graph_nodes_per_iteration": launches // max(steps, 1),
+                "all_losses_finite": bool(np.all(np.isfinite(losses)))}
+    finally:
+        qst.qst_batch_destroy(bt)
+
+
 class _NoDist:
     def barrier(self):
         pass
@@ -462,6 +510,8 @@ def main_ours(args):
                               **ttf} if ttf else None),
         "paper_context": "11-qubit tomography within 2 minutes on a laptop (GTX 1070); not this metric's baseline",
     }
+    if args.batch:
+        line["batch_c4"] = batch_c4(torch, qst, synth, dev, args.steps, args.warmup)
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(f, theta0, args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -513,6 +563,7 @@ def main():
     ap.add_argument("--shots-iters", type=int, default=200)
     ap.add_argument("--fid-every", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-batch", dest="batch", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="profiling aid: only run this many plain and mixed steps at N=11 and exit (no JSON line)")
