@@ -65,6 +65,9 @@ typedef enum {
     QST_W_CLAMP = 1
 } qst_status;
 
+/* State maps of Sec. 3.2.  QST_MAP_ABS_P (eq. abs_P, any P > 0) diagonalises T every
+ * iteration with a cyclic Jacobi method on the GPU (FP32 / FP64 contexts; the mixed
+ * modes support QST_MAP_CHOL_H only). */
 enum { QST_MAP_CHOL_H = 0, QST_MAP_ABS_P = 1 };
 /* Precisions.  QST_MIXED runs the two complex d x d products on tensor cores
  * (tcgen05) with each FP32 operand split into FP16 hi + lo after a power-of-two
@@ -83,6 +86,8 @@ typedef struct qst_options {
     double step_min;    /* Rprop step lower bound (1e-6) */
     double step_max;    /* Rprop step upper bound (50) */
     double leaky_slope; /* LeakyReLU negative slope (0.01) */
+    int eig_sweeps;     /* QST_MAP_ABS_P: Jacobi sweeps of the eigendecomposition of T per iteration
+                           (0 = default, 10) */
 } qst_options;
 
 /* Fill *opt with the paper's settings (Sec. 4.1) and the defaults stated above. */

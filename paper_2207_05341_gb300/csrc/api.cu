@@ -53,6 +53,8 @@ struct qst_ctx {
   std::vector<cudaEvent_t> tev;   // max_steps * (QST_NPHASE + 1) events
   std::vector<unsigned int> tmask;
   int tmax = 0, tcount = 0, tslot = -1;
+  void* apw = nullptr;  // AbsPWork<R> (QST_MAP_ABS_P)
+  int sweeps = 10;
   // CUDA graph of one steady-state qst_step (qst_graph_enable)
   bool graph_on = false;
   cudaGraphExec_t gexec = nullptr;
@@ -148,6 +150,22 @@ template <class R> qst_status alloc_work(qst_ctx* c) {
   QST_CU(cudaMemsetAsync(w->counters, 0, CNT_COUNT * sizeof(unsigned int), c->stream));
   QST_CU(cudaMemsetAsync(w->flags, 0, 8 * sizeof(unsigned int), c->stream));
   QST_CU(cudaMemsetAsync(w->scal, 0, 16 * sizeof(double), c->stream));
+  if (c->opt.mapping == QST_MAP_ABS_P) {
+    AbsPWork<R>* ap = new (std::nothrow) AbsPWork<R>();
+    if (!ap) return QST_E_NOMEM;
+    memset(ap, 0, sizeof(*ap));
+    c->apw = ap;
+    QST_CU(dalloc(c, &ap->A0, nn));
+    QST_CU(dalloc(c, &ap->A1, nn));
+    QST_CU(dalloc(c, &ap->V0, nn));
+    QST_CU(dalloc(c, &ap->V1, nn));
+    QST_CU(dalloc(c, &ap->W, nn));
+    QST_CU(dalloc(c, &ap->Qh, nn));
+    QST_CU(dalloc(c, &ap->lam, (size_t)D.d));
+    QST_CU(dalloc(c, &ap->s, (size_t)D.d));
+    QST_CU(dalloc(c, &ap->sp, (size_t)D.d));
+    c->sweeps = c->opt.eig_sweeps > 0 ? c->opt.eig_sweeps : 10;
+  }
   if (is_mixed(c)) {
     unsigned short* tb = nullptr;
     QST_CU(dalloc(c, &tb, 6 * nn));
@@ -159,7 +177,10 @@ template <class R> qst_status alloc_work(qst_ctx* c) {
   return QST_OK;
 }
 
-template <class R> void free_work(qst_ctx* c) { delete W<R>(c); }
+template <class R> void free_work(qst_ctx* c) {
+  delete W<R>(c);
+  delete reinterpret_cast<AbsPWork<R>*>(c->apw);
+}
 
 // ---- stream helpers
 const void* stage_input(qst_ctx* c, const void* f, size_t bytes, void* stage, qst_status* st) {
@@ -203,7 +224,11 @@ template <class R> struct Engine {
       c->launches += tc_fmt(c) == TC_FP16_SCALED ? 2 : 1;
     }
     tmark(c, QST_PH_BUILD_T);
-    if (mixed) {
+    if (c->opt.mapping == QST_MAP_ABS_P) {
+      QST_CU(abs_p_forward<R>(D.d, w->T, *reinterpret_cast<AbsPWork<R>*>(c->apw), c->sweeps, c->opt.P, w->X,
+                              c->stream));
+      c->launches += 4 + (long long)c->sweeps * (D.d - 1);
+    } else if (mixed) {
       QST_CU(tc_herm_square(D.d, w->Tb, tc_fmt(c), w->scal, reinterpret_cast<float2*>(w->X), w->flags + 1,
                             c->stream));
     } else {
@@ -247,6 +272,13 @@ template <class R> struct Engine {
       QST_CU(net_symmetrize<R>(D, w->Y, w->dt, c->stream));
       tmark(c, QST_PH_SYM);
       c->launches += tc_fmt(c) == TC_FP16_SCALED ? 4 : 3;
+    } else if (c->opt.mapping == QST_MAP_ABS_P) {
+      QST_CU(abs_p_backward<R>(D.d, w->G, *reinterpret_cast<AbsPWork<R>*>(c->apw), w->Y, c->stream));
+      c->launches += 4;
+      tmark(c, QST_PH_GT);
+      QST_CU(net_symmetrize<R>(D, w->Y, w->dt, c->stream));
+      tmark(c, QST_PH_SYM);
+      c->launches += 2;
     } else {
       QST_CU(cgemm_simt<R>(D.d, w->G, w->T, w->Y, false, c->stream));
       tmark(c, QST_PH_GT);
@@ -535,6 +567,7 @@ void qst_default_options(qst_options* o) {
   o->step_min = 1e-6;
   o->step_max = 50.0;
   o->leaky_slope = 0.01;
+  o->eig_sweeps = 0;
 }
 
 size_t qst_theta_size(int N) {
@@ -552,7 +585,11 @@ qst_status qst_init(qst_ctx** out, int N, const double* povm, int K, const qst_o
       o.precision != QST_MIXED_BF16)
     return QST_E_INVAL;
   if (N < 1 || N > (o.precision == QST_FP64 ? 10 : 12)) return QST_E_INVAL;
-  if (o.mapping != QST_MAP_CHOL_H) return QST_E_UNSUPPORTED;
+  if (o.mapping != QST_MAP_CHOL_H && o.mapping != QST_MAP_ABS_P) return QST_E_INVAL;
+  if (o.mapping == QST_MAP_ABS_P) {
+    if (!(o.P > 0.0) || !isfinite(o.P) || o.eig_sweeps < 0) return QST_E_INVAL;
+    if (o.precision == QST_MIXED || o.precision == QST_MIXED_BF16) return QST_E_UNSUPPORTED;
+  }
   if (!(o.lr > 0) || !(o.eta_minus > 0 && o.eta_minus < 1) || !(o.eta_plus > 1) || !(o.step_min > 0) ||
       !(o.step_max >= o.step_min) || !(o.leaky_slope >= 0))
     return QST_E_INVAL;

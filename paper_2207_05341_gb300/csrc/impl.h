@@ -87,6 +87,19 @@ template <class R> cudaError_t net_w1_pass(const Dims& D, R* theta, R* step, int
 // dL/dt from Y = G T:  dR_ij = 2(Re Y_ij + Re Y_ji), dR_ji = 2(Im Y_ij - Im Y_ji) (i > j), dR_ii = 2 Re Y_ii
 template <class R> cudaError_t net_symmetrize(const Dims& D, const cx_t<R>* Y, R* dt, cudaStream_t s);
 
+// ---- P-order absolute projection (eigh.cu) ----
+template <class R> struct AbsPWork {
+  cx_t<R> *A0, *A1, *V0, *V1;  // Jacobi double buffers (matrix, eigenvectors)
+  cx_t<R> *W, *Qh;             // scratch, Q^dag
+  R *lam, *s, *sp;             // eigenvalues, |lambda|^P, derivative
+  cx_t<R> *A, *Q;              // set by abs_p_forward: diagonalised matrix, eigenvectors
+};
+// X = Q |Lambda|^P Q^dag (lower tiles) from T via `sweeps` Jacobi sweeps
+template <class R> cudaError_t abs_p_forward(int d, const cx_t<R>* T, AbsPWork<R>& w, int sweeps, double P,
+                                             cx_t<R>* X, cudaStream_t s);
+// Y with Y + Y^dag = dL/dT = Q (D o (Q^dag G Q)) Q^dag, from G = dL/dX
+template <class R> cudaError_t abs_p_backward(int d, const cx_t<R>* G, AbsPWork<R>& w, cx_t<R>* Y, cudaStream_t s);
+
 // ---- complex products (gemm_simt.cu) ----
 // C = A B for d x d complex row-major matrices; lower == true computes only tiles I >= J.
 template <class R> cudaError_t cgemm_simt(int d, const cx_t<R>* A, const cx_t<R>* B, cx_t<R>* C, bool lower,

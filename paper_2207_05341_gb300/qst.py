@@ -56,6 +56,7 @@ class qst_options(ctypes.Structure):
         ("step_min", ctypes.c_double),
         ("step_max", ctypes.c_double),
         ("leaky_slope", ctypes.c_double),
+        ("eig_sweeps", ctypes.c_int),
     ]
 
 

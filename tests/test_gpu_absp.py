@@ -1,0 +1,106 @@
+"""GPU parity of the P-order absolute projection (Sec. 3.2 eq. abs_P) against the oracle.
+
+The eigendecomposition is a Jacobi method run for a fixed number of sweeps; after
+10 sweeps it has converged to rounding level for these sizes, so the FP64 path
+is held to 1e-8 and the FP32 path to 1e-4 on the loss and 2e-3 (normwise) on
+the gradient, whose Daleckii-Krein factors divide by eigenvalue gaps.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2207_05341_gb300 import qst, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+M = O.tetrahedral_povm()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import os
+    if not os.path.exists(qst.LIB_PATH):
+        from paper_2207_05341_gb300 import build
+        build.build()
+    qst.load()
+
+
+def _opt(prec, mapping=qst.QST_MAP_ABS_P, P=2.0):
+    o = qst.qst_default_options()
+    o.precision = prec
+    o.mapping = mapping
+    o.P = P
+    return o
+
+
+def _problem(N, seed):
+    rho = synth.ginibre_mixed(N, max(1, (1 << N) // 2), 1000 + seed)
+    f = synth.frequencies(synth.multinomial_counts(O.born_probabilities(rho, M).real, 10**5, 1100 + seed))
+    return f, synth.init_theta(N, 1200 + seed)
+
+
+def _gpu(N, theta, f, opt):
+    dt = np.float64 if opt.precision == qst.QST_FP64 else np.float32
+    ctx = qst.qst_init(N, opt=opt)
+    try:
+        th = torch.from_numpy(theta.astype(dt)).cuda()
+        g = torch.empty_like(th)
+        L, _ = qst.qst_loss_grad(ctx, th, torch.from_numpy(f.astype(dt)).cuda(), g)
+        return L, g.cpu().numpy().astype(np.float64)
+    finally:
+        qst.qst_destroy(ctx)
+
+
+CASES = [(qst.QST_FP64, N, P) for N in (1, 2, 4, 6) for P in (0.5, 1.5, 2.0, 4.0)] + \
+        [(qst.QST_FP32, N, P) for N in (3, 6) for P in (1.0, 2.0, 3.0)]
+
+
+@pytest.mark.parametrize("prec,N,P", CASES)
+def test_abs_p_loss_grad_parity(prec, N, P):
+    f, theta = _problem(N, N + int(10 * P))
+    dt = np.float64 if prec == qst.QST_FP64 else np.float32
+    L_ref, g_ref, _ = O.loss_and_grad(theta.astype(dt).astype(np.float64), f.astype(dt).astype(np.float64), M, N,
+                                      mapping="abs_p", P=P)
+    L, g = _gpu(N, theta, f, _opt(prec, P=P))
+    tl, tg = (1e-8, 1e-8) if prec == qst.QST_FP64 else (1e-4, 2e-3)
+    rl = abs(L - L_ref) / abs(L_ref)
+    rg = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
+    assert rl <= tl and rg < tg, (rl, rg)
+
+
+def test_abs_p2_equals_chol_h():
+    """Sec. 3.2: A_P with P = 2 is the unified Chol_H map."""
+    N = 5
+    f, theta = _problem(N, 77)
+    La, ga = _gpu(N, theta, f, _opt(qst.QST_FP64, qst.QST_MAP_ABS_P, 2.0))
+    Lc, gc = _gpu(N, theta, f, _opt(qst.QST_FP64, qst.QST_MAP_CHOL_H))
+    assert abs(La - Lc) < 1e-10 * abs(Lc)
+    assert np.linalg.norm(ga - gc) / np.linalg.norm(gc) < 1e-8
+
+
+def test_abs_p_reconstruction_matches_oracle():
+    N, P = 3, 1.5
+    psi = synth.haar_pure(N, 5)
+    rho_t = synth.depolarized(psi, 0.1)
+    f = np.ascontiguousarray(O.born_probabilities(rho_t, M).real)
+    theta = synth.init_theta(N, 6)
+    _, rho_ref, _ = O.reconstruct(theta, f, M, N, 300, mapping="abs_p", P=P)
+    ctx = qst.qst_init(N, opt=_opt(qst.QST_FP64, P=P))
+    try:
+        qst.qst_set_params(ctx, theta)
+        rho = np.empty((8, 8), dtype=np.complex128)
+        qst.qst_reconstruct(ctx, f, 300, rho)
+    finally:
+        qst.qst_destroy(ctx)
+    F, F_ref = O.fidelity(rho, rho_t), O.fidelity(rho_ref, rho_t)
+    assert F_ref > 0.99
+    assert abs(F - F_ref) < 1e-6, (F, F_ref)
+
+
+def test_abs_p_rejected_for_mixed_precision():
+    with pytest.raises(qst.QstError) as e:
+        qst.qst_init(8, opt=_opt(qst.QST_MIXED, P=1.5))
+    assert e.value.status == qst.QST_E_UNSUPPORTED

@@ -95,7 +95,7 @@ def test_gradient_central_fd_chol_h_n3_sampled():
     _fd_check(3, "chol_h", 2.0, idx=idx, seed=3)
 
 
-@pytest.mark.parametrize("P", [1.5, 2.0, 3.0])
+@pytest.mark.parametrize("P", [0.5, 1.0, 1.5, 2.0, 3.0])
 def test_gradient_central_fd_abs_p(P):
     _fd_check(2, "abs_p", P, seed=int(P * 10))
 
