@@ -86,8 +86,10 @@ typedef struct qst_options {
     double step_min;    /* Rprop step lower bound (1e-6) */
     double step_max;    /* Rprop step upper bound (50) */
     double leaky_slope; /* LeakyReLU negative slope (0.01) */
-    int eig_sweeps;     /* QST_MAP_ABS_P: Jacobi sweeps of the eigendecomposition of T per iteration
-                           (0 = default, 10) */
+    int eig_sweeps;     /* QST_MAP_ABS_P: Jacobi sweeps from a cold start (0 = default 10; rounded up
+                           to even) */
+    int eig_warm_sweeps;/* QST_MAP_ABS_P: sweeps when qst_step starts from the previous iteration's
+                           eigenvectors (0 = default 2; -1 = always cold; rounded up to even) */
 } qst_options;
 
 /* Fill *opt with the paper's settings (Sec. 4.1) and the defaults stated above. */
@@ -167,9 +169,10 @@ qst_status qst_reconstruct(qst_ctx* ctx, const void* f, int iters, void* rho_out
  * (device or host, d x d complex), and its loss if loss != NULL. */
 qst_status qst_get_rho(qst_ctx* ctx, const void* f, void* rho_out, double* loss);
 
-/* Checkpoint of parameters, Rprop state and iteration count, as an opaque host
- * byte buffer of qst_state_bytes(ctx) bytes.  Restoring it into a context with
- * the same N, precision and options resumes bit-identically. */
+/* Checkpoint of parameters, Rprop state and iteration count (and, for
+ * QST_MAP_ABS_P, the eigenvectors that warm-start the next eigendecomposition),
+ * as an opaque host byte buffer of qst_state_bytes(ctx) bytes.  Restoring it
+ * into a context with the same N, precision and options resumes bit-identically. */
 size_t qst_state_bytes(const qst_ctx* ctx);
 qst_status qst_get_state(qst_ctx* ctx, void* host_buf, size_t bytes);
 qst_status qst_set_state(qst_ctx* ctx, const void* host_buf, size_t bytes);

@@ -54,7 +54,9 @@ struct qst_ctx {
   std::vector<unsigned int> tmask;
   int tmax = 0, tcount = 0, tslot = -1;
   void* apw = nullptr;  // AbsPWork<R> (QST_MAP_ABS_P)
-  int sweeps = 10;
+  int sweeps = 10;       // cold-start Jacobi sweeps
+  int warm_sweeps = 2;   // warm-start sweeps (0: never warm-start)
+  bool warm_valid = false;
   // CUDA graph of one steady-state qst_step (qst_graph_enable)
   bool graph_on = false;
   cudaGraphExec_t gexec = nullptr;
@@ -165,6 +167,9 @@ template <class R> qst_status alloc_work(qst_ctx* c) {
     QST_CU(dalloc(c, &ap->s, (size_t)D.d));
     QST_CU(dalloc(c, &ap->sp, (size_t)D.d));
     c->sweeps = c->opt.eig_sweeps > 0 ? c->opt.eig_sweeps : 10;
+    c->sweeps += c->sweeps & 1;
+    c->warm_sweeps = c->opt.eig_warm_sweeps < 0 ? 0 : (c->opt.eig_warm_sweeps > 0 ? c->opt.eig_warm_sweeps : 2);
+    c->warm_sweeps += c->warm_sweeps & 1;
   }
   if (is_mixed(c)) {
     unsigned short* tb = nullptr;
@@ -212,7 +217,7 @@ template <class R> struct Engine {
   using V = cx_t<R>;
 
   // X = T T (lower tiles) from the hidden activation already in w->hid; Tr X -> scal[0]
-  static qst_status forward_state(qst_ctx* c, const R* theta) {
+  static qst_status forward_state(qst_ctx* c, const R* theta, bool own_params = true) {
     Work<R>* w = W<R>(c);
     const Dims& D = c->D;
     const bool mixed = is_mixed(c);
@@ -225,9 +230,13 @@ template <class R> struct Engine {
     }
     tmark(c, QST_PH_BUILD_T);
     if (c->opt.mapping == QST_MAP_ABS_P) {
-      QST_CU(abs_p_forward<R>(D.d, w->T, *reinterpret_cast<AbsPWork<R>*>(c->apw), c->sweeps, c->opt.P, w->X,
+      // the context's own parameters change slowly: start from the last eigenvectors
+      const bool warm = own_params && c->warm_valid && c->warm_sweeps > 0;
+      const int sw = warm ? c->warm_sweeps : c->sweeps;
+      QST_CU(abs_p_forward<R>(D.d, w->T, *reinterpret_cast<AbsPWork<R>*>(c->apw), sw, warm, c->opt.P, w->X,
                               c->stream));
-      c->launches += 4 + (long long)c->sweeps * (D.d - 1);
+      c->warm_valid = own_params;
+      c->launches += 4 + (long long)sw * (D.d - 1);
     } else if (mixed) {
       QST_CU(tc_herm_square(D.d, w->Tb, tc_fmt(c), w->scal, reinterpret_cast<float2*>(w->X), w->flags + 1,
                             c->stream));
@@ -401,7 +410,7 @@ template <class R> struct Engine {
     if ((st = validate_f<R>(c, f)) != QST_OK) return st;
     c->hidden_valid = false;  // the hidden buffers now hold the external parameters' activation
     if ((st = hidden(c, theta, f)) != QST_OK) return st;
-    if ((st = forward_state(c, theta)) != QST_OK) return st;
+    if ((st = forward_state(c, theta, false)) != QST_OK) return st;
     if ((st = povm_likelihood(c, f, true)) != QST_OK) return st;
     if ((st = backward_state(c)) != QST_OK) return st;
     QST_CU(net_w2_pass<R>(D, theta, nullptr, nullptr, w->dt, w->hid, w->pre, w->dpre, dtheta, w->partials,
@@ -568,6 +577,7 @@ void qst_default_options(qst_options* o) {
   o->step_max = 50.0;
   o->leaky_slope = 0.01;
   o->eig_sweeps = 0;
+  o->eig_warm_sweeps = 0;
 }
 
 size_t qst_theta_size(int N) {
@@ -640,6 +650,7 @@ qst_status qst_set_params(qst_ctx* c, const void* theta) {
   if (st != QST_OK) return st;
   c->params_set = true;
   c->hidden_valid = false;
+  c->warm_valid = false;
   c->iters = 0;
   return QST_OK;
 }
@@ -689,10 +700,21 @@ qst_status qst_reconstruct(qst_ctx* c, const void* f, int iters, void* rho_out, 
   return QST_OK;
 }
 
+// Warm-start eigenvectors in a checkpoint (QST_MAP_ABS_P): a flag word, then d x d complex.
+size_t warm_bytes(const qst_ctx* c) {
+  if (c->opt.mapping != QST_MAP_ABS_P) return 0;
+  return sizeof(unsigned long long) + (size_t)c->D.d * c->D.d * 2 * rsize(c);
+}
+
+void* warm_q(qst_ctx* c) {
+  return c->prec == QST_FP64 ? (void*)reinterpret_cast<AbsPWork<double>*>(c->apw)->V0
+                             : (void*)reinterpret_cast<AbsPWork<float>*>(c->apw)->V0;
+}
+
 size_t qst_state_bytes(const qst_ctx* c) {
   if (!c) return 0;
   const size_t P = theta_size(c->N);
-  return 4 * sizeof(unsigned long long) + 2 * P * rsize(c) + P;
+  return 4 * sizeof(unsigned long long) + 2 * P * rsize(c) + P + warm_bytes(c);
 }
 
 qst_status qst_get_state(qst_ctx* c, void* host_buf, size_t bytes) {
@@ -712,6 +734,13 @@ qst_status qst_get_state(qst_ctx* c, void* host_buf, size_t bytes) {
   QST_CU(cudaMemcpyAsync(p, th, P * rs, cudaMemcpyDeviceToHost, c->stream));
   QST_CU(cudaMemcpyAsync(p + P * rs, stp, P * rs, cudaMemcpyDeviceToHost, c->stream));
   QST_CU(cudaMemcpyAsync(p + 2 * P * rs, sg, P, cudaMemcpyDeviceToHost, c->stream));
+  if (warm_bytes(c)) {
+    char* q = p + 2 * P * rs + P;
+    *(unsigned long long*)q = c->warm_valid ? 1ULL : 0ULL;
+    if (c->warm_valid)
+      QST_CU(cudaMemcpyAsync(q + sizeof(unsigned long long), warm_q(c), warm_bytes(c) - sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, c->stream));
+  }
   QST_CU(cudaStreamSynchronize(c->stream));
   return QST_OK;
 }
@@ -731,6 +760,19 @@ qst_status qst_set_state(qst_ctx* c, const void* host_buf, size_t bytes) {
   QST_CU(cudaMemcpyAsync(th, p, P * rs, cudaMemcpyHostToDevice, c->stream));
   QST_CU(cudaMemcpyAsync(stp, p + P * rs, P * rs, cudaMemcpyHostToDevice, c->stream));
   QST_CU(cudaMemcpyAsync(sg, p + 2 * P * rs, P, cudaMemcpyHostToDevice, c->stream));
+  c->warm_valid = false;
+  if (warm_bytes(c)) {
+    const char* q = p + 2 * P * rs + P;
+    if (*(const unsigned long long*)q) {
+      QST_CU(cudaMemcpyAsync(warm_q(c), q + sizeof(unsigned long long), warm_bytes(c) - sizeof(unsigned long long),
+                             cudaMemcpyHostToDevice, c->stream));
+      if (c->prec == QST_FP64)
+        QST_CU(abs_p_restore_q<double>(c->D.d, *reinterpret_cast<AbsPWork<double>*>(c->apw), c->stream));
+      else
+        QST_CU(abs_p_restore_q<float>(c->D.d, *reinterpret_cast<AbsPWork<float>*>(c->apw), c->stream));
+      c->warm_valid = true;
+    }
+  }
   QST_CU(cudaStreamSynchronize(c->stream));
   c->params_set = true;
   c->hidden_valid = false;

@@ -192,13 +192,20 @@ int blocks_for(long long n) {
 }  // namespace
 
 template <class R>
-cudaError_t abs_p_forward(int d, const cx_t<R>* T, AbsPWork<R>& w, int sweeps, double P, cx_t<R>* X,
+cudaError_t abs_p_forward(int d, const cx_t<R>* T, AbsPWork<R>& w, int sweeps, bool warm, double P, cx_t<R>* X,
                           cudaStream_t s) {
   using V = cx_t<R>;
   const long long nn = (long long)d * d;
-  cudaError_t e = cudaMemcpyAsync(w.A0, T, nn * sizeof(V), cudaMemcpyDeviceToDevice, s);
-  if (e != cudaSuccess) return e;
-  k_identity<R><<<blocks_for(nn), 256, 0, s>>>(w.V0, d);
+  cudaError_t e;
+  if (warm) {
+    // previous eigenvectors Q (in V0) and Q^dag (in Qh): start from Q^dag T Q, nearly diagonal
+    if ((e = cgemm_simt<R>(d, w.Qh, T, w.W, false, s)) != cudaSuccess) return e;
+    if ((e = cgemm_simt<R>(d, w.W, w.V0, w.A0, false, s)) != cudaSuccess) return e;
+  } else {
+    if ((e = cudaMemcpyAsync(w.A0, T, nn * sizeof(V), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+    k_identity<R><<<blocks_for(nn), 256, 0, s>>>(w.V0, d);
+  }
+  // an even number of sweeps of d - 1 (odd) rounds brings both ping-pong pairs back to A0 / V0
   V *Ain = w.A0, *Aout = w.A1, *Vin = w.V0, *Vout = w.V1;
   const dim3 grid((d + 15) / 16, (d + 15) / 16);
   for (int sw = 0; sw < sweeps; ++sw) {
@@ -208,8 +215,8 @@ cudaError_t abs_p_forward(int d, const cx_t<R>* T, AbsPWork<R>& w, int sweeps, d
       t = Vin; Vin = Vout; Vout = t;
     }
   }
-  w.A = Ain;  // diagonalised
-  w.Q = Vin;  // eigenvectors (columns)
+  w.A = Ain;  // diagonalised (A0)
+  w.Q = Vin;  // eigenvectors in columns (V0)
   k_absp_spectrum<R><<<1, 1024, 0, s>>>(w.A, w.lam, w.s, w.sp, d, P, sizeof(R) == 4 ? 1e-7 : 1e-15);
   k_scale_cols<R><<<blocks_for(nn), 256, 0, s>>>(w.Q, w.s, w.W, d);
   const int TS = d < 32 ? d : 32;
@@ -218,6 +225,13 @@ cudaError_t abs_p_forward(int d, const cx_t<R>* T, AbsPWork<R>& w, int sweeps, d
   if (e != cudaSuccess) return e;
   // X = (Q diag(s)) Q^dag, lower tiles
   return cgemm_simt<R>(d, w.W, w.Qh, X, true, s);
+}
+
+template <class R> cudaError_t abs_p_restore_q(int d, AbsPWork<R>& w, cudaStream_t s) {
+  const int TS = d < 32 ? d : 32;
+  k_conj_transpose<R><<<dim3(d / TS, d / TS), 256, 0, s>>>(w.V0, w.Qh, d);
+  w.Q = w.V0;
+  return cudaGetLastError();
 }
 
 template <class R>
@@ -235,8 +249,12 @@ cudaError_t abs_p_backward(int d, const cx_t<R>* G, AbsPWork<R>& w, cx_t<R>* Y, 
   return cgemm_simt<R>(d, w.W, w.Qh, Y, false, s);
 }
 
-template cudaError_t abs_p_forward<float>(int, const float2*, AbsPWork<float>&, int, double, float2*, cudaStream_t);
-template cudaError_t abs_p_forward<double>(int, const double2*, AbsPWork<double>&, int, double, double2*, cudaStream_t);
+template cudaError_t abs_p_forward<float>(int, const float2*, AbsPWork<float>&, int, bool, double, float2*,
+                                          cudaStream_t);
+template cudaError_t abs_p_forward<double>(int, const double2*, AbsPWork<double>&, int, bool, double, double2*,
+                                           cudaStream_t);
+template cudaError_t abs_p_restore_q<float>(int, AbsPWork<float>&, cudaStream_t);
+template cudaError_t abs_p_restore_q<double>(int, AbsPWork<double>&, cudaStream_t);
 template cudaError_t abs_p_backward<float>(int, const float2*, AbsPWork<float>&, float2*, cudaStream_t);
 template cudaError_t abs_p_backward<double>(int, const double2*, AbsPWork<double>&, double2*, cudaStream_t);
 

@@ -94,9 +94,12 @@ template <class R> struct AbsPWork {
   R *lam, *s, *sp;             // eigenvalues, |lambda|^P, derivative
   cx_t<R> *A, *Q;              // set by abs_p_forward: diagonalised matrix, eigenvectors
 };
-// X = Q |Lambda|^P Q^dag (lower tiles) from T via `sweeps` Jacobi sweeps
-template <class R> cudaError_t abs_p_forward(int d, const cx_t<R>* T, AbsPWork<R>& w, int sweeps, double P,
-                                             cx_t<R>* X, cudaStream_t s);
+// X = Q |Lambda|^P Q^dag (lower tiles) from T via `sweeps` (even) Jacobi sweeps; warm == true starts
+// from the previous eigenvectors (V0, with Q^dag in Qh).  Leaves Q in V0 and Q^dag in Qh.
+template <class R> cudaError_t abs_p_forward(int d, const cx_t<R>* T, AbsPWork<R>& w, int sweeps, bool warm,
+                                             double P, cx_t<R>* X, cudaStream_t s);
+// After restoring Q into V0 (checkpoint), recompute Q^dag.
+template <class R> cudaError_t abs_p_restore_q(int d, AbsPWork<R>& w, cudaStream_t s);
 // Y with Y + Y^dag = dL/dT = Q (D o (Q^dag G Q)) Q^dag, from G = dL/dX
 template <class R> cudaError_t abs_p_backward(int d, const cx_t<R>* G, AbsPWork<R>& w, cx_t<R>* Y, cudaStream_t s);
 

@@ -57,6 +57,7 @@ class qst_options(ctypes.Structure):
         ("step_max", ctypes.c_double),
         ("leaky_slope", ctypes.c_double),
         ("eig_sweeps", ctypes.c_int),
+        ("eig_warm_sweeps", ctypes.c_int),
     ]
 
 

@@ -104,3 +104,46 @@ def test_abs_p_rejected_for_mixed_precision():
     with pytest.raises(qst.QstError) as e:
         qst.qst_init(8, opt=_opt(qst.QST_MIXED, P=1.5))
     assert e.value.status == qst.QST_E_UNSUPPORTED
+
+
+def _steps(N, theta, f, opt, k):
+    ctx = qst.qst_init(N, opt=opt)
+    try:
+        qst.qst_set_params(ctx, theta)
+        return [qst.qst_step(ctx, np.ascontiguousarray(f))[0] for _ in range(k)]
+    finally:
+        qst.qst_destroy(ctx)
+
+
+def test_warm_start_follows_cold_start_trajectory():
+    """Warm-started eigendecompositions (2 sweeps from the last eigenvectors) give the same
+    iteration as a cold start every step (10 sweeps)."""
+    N, P = 5, 1.5
+    f, theta = _problem(N, 91)
+    warm = _opt(qst.QST_FP64, P=P)
+    cold = _opt(qst.QST_FP64, P=P)
+    cold.eig_warm_sweeps = -1
+    lw = np.array(_steps(N, theta, f, warm, 10))
+    lc = np.array(_steps(N, theta, f, cold, 10))
+    # both eigendecompositions are exact to rounding; Rprop's sign decisions can then differ only on
+    # gradients at rounding level, so the losses agree far below any step's change
+    rel = np.abs(lw - lc) / np.abs(lc)
+    assert rel.max() < 1e-7, rel
+
+
+def test_abs_p_checkpoint_resume_bit_identical():
+    N, P = 4, 1.5
+    f, theta = _problem(N, 92)
+    f = np.ascontiguousarray(f)
+    ctx = qst.qst_init(N, opt=_opt(qst.QST_FP64, P=P))
+    try:
+        qst.qst_set_params(ctx, theta)
+        for _ in range(3):
+            qst.qst_step(ctx, f)
+        blob = qst.qst_get_state(ctx)
+        la = [qst.qst_step(ctx, f)[0] for _ in range(4)]
+        qst.qst_set_state(ctx, blob)
+        lb = [qst.qst_step(ctx, f)[0] for _ in range(4)]
+        assert la == lb
+    finally:
+        qst.qst_destroy(ctx)
