@@ -374,6 +374,56 @@ def batch_c4(torch, qst, synth, dev, steps, warmup, seed=30, B=512):
         qst.qst_batch_destroy(bt)
 
 
+def c5_leg(torch, qst, synth, dev, steps, seed=40):
+    """N = 12 (rho 4096 x 4096, 4^12 outcomes), 10^8 shots, depolarised rank-r Ginibre state:
+    Chol_H (= A_2, Sec. 3.2) on the mixed tensor-core path, and A_P with P = 1.5 through the
+    Jacobi eigensolver (cold first step, then warm-started steps)."""
+    N = 12
+    rng = np.random.default_rng(seed)
+    r = int(np.exp(rng.uniform(0, np.log(64))))
+    lam = float(rng.uniform(0, 0.3))
+    g = synth.ginibre_mixed(N, r, seed)
+    rho = (1 - lam) * g + lam * np.eye(2 ** N) / 2 ** N
+    stream = torch.cuda.Stream(device=dev)
+    out = {"workload": f"N=12, rank-{r} Ginibre mixed with depolarizing lambda={lam:.3f}, 10^8 shots"}
+    with torch.cuda.stream(stream):
+        ctx = qst.qst_init(N, stream=stream.cuda_stream)
+        try:
+            P = torch.empty(4 ** N, device=dev)
+            qst.qst_probs(ctx, torch.from_numpy(rho.astype(np.complex64)).to(dev), P)
+            P = P.double().cpu().numpy()
+        finally:
+            qst.qst_destroy(ctx)
+        del rho, g
+        f = torch.from_numpy(synth.frequencies(synth.multinomial_counts(P, 10**8, seed + 1), np.float32)).to(dev)
+        theta = synth.init_theta(N, seed + 2).astype(np.float32)
+        for name, prec, mapping, p_ord in (("chol_h_mixed_fp16x3", qst.QST_MIXED, qst.QST_MAP_CHOL_H, 2.0),
+                                           ("abs_p1.5_fp32_jacobi", qst.QST_FP32, qst.QST_MAP_ABS_P, 1.5)):
+            o = qst.qst_default_options()
+            o.precision, o.mapping, o.P = prec, mapping, p_ord
+            ctx = qst.qst_init(N, opt=o, stream=stream.cuda_stream)
+            try:
+                qst.qst_set_params(ctx, theta)
+                L0, _ = qst.qst_step(ctx, f)  # first step: input validation, hidden layer, cold eigensolver
+                k = steps if mapping == qst.QST_MAP_CHOL_H else 2
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(k):
+                    qst.qst_step(ctx, f, want_loss=False)
+                e1.record(stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1) / k
+                L1, _ = qst.qst_step(ctx, f)
+                out[name] = {"ms_per_iter": ms, "iters_per_s": 1e3 / ms, "steps_timed": k,
+                             "loss_first": L0, "loss_after": L1}
+            finally:
+                qst.qst_destroy(ctx)
+    out["note"] = "A_P with P = 2 is Chol_H (Sec. 3.2), so the P = 2 runs of this config use the T T path"
+    return out
+
+
 class _NoDist:
     def barrier(self):
         pass
@@ -512,6 +562,8 @@ def main_ours(args):
     }
     if args.batch:
         line["batch_c4"] = batch_c4(torch, qst, synth, dev, args.steps, args.warmup)
+    if args.c5:
+        line["n12_c5"] = c5_leg(torch, qst, synth, dev, min(args.steps, 10))
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(f, theta0, args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -564,6 +616,7 @@ def main():
     ap.add_argument("--fid-every", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-batch", dest="batch", action="store_false")
+    ap.add_argument("--no-c5", dest="c5", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="profiling aid: only run this many plain and mixed steps at N=11 and exit (no JSON line)")

@@ -10,8 +10,9 @@
 // with c = A_pq = |c| e^{i phi}, the 2 x 2 block is first made real by
 // diag(1, e^{-i phi}) and then zeroed by the real rotation of Golub and Van
 // Loan (tan theta = sign(tau) / (|tau| + sqrt(1 + tau^2)), tau = (a_qq - a_pp) / 2|c|).
-// One kernel per round updates every entry of A from the four entries it
-// depends on (double-buffered) and accumulates the eigenvectors V <- V R.
+// One kernel per round: each thread owns the 2 x 2 block (rows of one pair) x
+// (columns of another pair) of A and of V, so every entry is read and written
+// once per round (double-buffered), and V accumulates the rotations, V <- V R.
 #include <float.h>
 
 #include "impl.h"
@@ -69,39 +70,66 @@ __device__ __forceinline__ void rot_coeffs(const cx_t<R>* A, int d, int x, int p
 template <class V> __device__ __forceinline__ V cmul(V a, V b) { return cmake<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 template <class V> __device__ __forceinline__ V cmulc(V a, V b) { return cmake<V>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x); }  // conj(a) b
 
+// Rotation of pair k of round r: indices p < q and the 2 x 2 block R = [[cs, sn], [-e^{-i phi} sn, e^{-i phi} cs]]
+// (rows / columns in the order p, q), from the current A.
+template <class R> struct PairRot {
+  int p, q;
+  cx_t<R> r_pp, r_pq, r_qp, r_qq;
+};
+
+template <class R>
+__device__ __forceinline__ PairRot<R> pair_rotation(const cx_t<R>* A, int d, int k, int r) {
+  using V = cx_t<R>;
+  const int x = player_at(k, r, d), y = player_at(d - 1 - k, r, d);
+  PairRot<R> pr;
+  pr.p = x < y ? x : y;
+  pr.q = x < y ? y : x;
+  V alpha, beta;
+  rot_coeffs<R>(A, d, pr.p, pr.q, alpha, beta);  // column p: R[p][p] = alpha, R[q][p] = beta
+  pr.r_pp = alpha;
+  pr.r_qp = beta;
+  rot_coeffs<R>(A, d, pr.q, pr.p, alpha, beta);  // column q: R[q][q] = alpha, R[p][q] = beta
+  pr.r_qq = alpha;
+  pr.r_pq = beta;
+  return pr;
+}
+
+// One round: every thread owns the 2 x 2 block (rows of pair k) x (columns of pair l) of A and of V,
+// so each entry is read and written once: A' = R^dag A R on the block, V' = V R on rows {p_k, q_k}.
 template <class R>
 __global__ void __launch_bounds__(256) k_jacobi_round(const cx_t<R>* __restrict__ A, cx_t<R>* __restrict__ Ao,
                                                        const cx_t<R>* __restrict__ Vi, cx_t<R>* __restrict__ Vo,
                                                        int d, int r) {
   using V = cx_t<R>;
-  constexpr int TS = 16;
-  __shared__ V ra[TS], rb[TS], ca[TS], cb[TS];
-  __shared__ int rp[TS], cp[TS];
-  const int i0 = blockIdx.y * TS, j0 = blockIdx.x * TS;
+  constexpr int TP = 16;
+  __shared__ PairRot<R> rk[TP], rl[TP];
+  const int half = d >> 1;
+  const int k0 = blockIdx.y * TP, l0 = blockIdx.x * TP;
   const int t = threadIdx.x;
-  if (t < TS && i0 + t < d) {
-    const int x = i0 + t, px = partner_of(x, r, d);
-    rp[t] = px;
-    rot_coeffs<R>(A, d, x, px, ra[t], rb[t]);
-  } else if (t >= 32 && t < 32 + TS && j0 + t - 32 < d) {
-    const int x = j0 + t - 32, px = partner_of(x, r, d);
-    cp[t - 32] = px;
-    rot_coeffs<R>(A, d, x, px, ca[t - 32], cb[t - 32]);
-  }
+  if (t < TP && k0 + t < half) rk[t] = pair_rotation<R>(A, d, k0 + t, r);
+  else if (t >= 32 && t < 32 + TP && l0 + t - 32 < half) rl[t - 32] = pair_rotation<R>(A, d, l0 + t - 32, r);
   __syncthreads();
-  const int li = t / TS, lj = t % TS;
-  const int i = i0 + li, j = j0 + lj;
-  if (i >= d || j >= d) return;
-  const int pi = rp[li], pj = cp[lj];
-  const V ai = ra[li], bi = rb[li], aj = ca[lj], bj = cb[lj];
-  const V a_ij = A[(long long)i * d + j], a_ipj = A[(long long)i * d + pj];
-  const V a_pij = A[(long long)pi * d + j], a_pipj = A[(long long)pi * d + pj];
-  // A'_ij = conj(ai) (aj A_ij + bj A_i,pj) + conj(bi) (aj A_pi,j + bj A_pi,pj)
-  const V u = cadd(cmul(aj, a_ij), cmul(bj, a_ipj));
-  const V w = cadd(cmul(aj, a_pij), cmul(bj, a_pipj));
-  Ao[(long long)i * d + j] = cadd(cmulc(ai, u), cmulc(bi, w));
-  // V' = V R
-  Vo[(long long)i * d + j] = cadd(cmul(aj, Vi[(long long)i * d + j]), cmul(bj, Vi[(long long)i * d + pj]));
+  const int k = k0 + t / TP, l = l0 + t % TP;
+  if (k >= half || l >= half) return;
+  const PairRot<R> a = rk[t / TP], b = rl[t % TP];
+  const long long rp = (long long)a.p * d, rq = (long long)a.q * d;
+  const V m_pp = A[rp + b.p], m_pq = A[rp + b.q], m_qp = A[rq + b.p], m_qq = A[rq + b.q];
+  // M R_l (columns p_l, q_l)
+  const V u_pp = cadd(cmul(m_pp, b.r_pp), cmul(m_pq, b.r_qp));
+  const V u_pq = cadd(cmul(m_pp, b.r_pq), cmul(m_pq, b.r_qq));
+  const V u_qp = cadd(cmul(m_qp, b.r_pp), cmul(m_qq, b.r_qp));
+  const V u_qq = cadd(cmul(m_qp, b.r_pq), cmul(m_qq, b.r_qq));
+  // R_k^dag (M R_l): row p' = conj(R[p][p]) row p + conj(R[q][p]) row q; row q' = conj(R[p][q]) row p + conj(R[q][q]) row q
+  Ao[rp + b.p] = cadd(cmulc(a.r_pp, u_pp), cmulc(a.r_qp, u_qp));
+  Ao[rp + b.q] = cadd(cmulc(a.r_pp, u_pq), cmulc(a.r_qp, u_qq));
+  Ao[rq + b.p] = cadd(cmulc(a.r_pq, u_pp), cmulc(a.r_qq, u_qp));
+  Ao[rq + b.q] = cadd(cmulc(a.r_pq, u_pq), cmulc(a.r_qq, u_qq));
+  // V' = V R on rows p_k, q_k, columns p_l, q_l
+  const V v_pp = Vi[rp + b.p], v_pq = Vi[rp + b.q], v_qp = Vi[rq + b.p], v_qq = Vi[rq + b.q];
+  Vo[rp + b.p] = cadd(cmul(v_pp, b.r_pp), cmul(v_pq, b.r_qp));
+  Vo[rp + b.q] = cadd(cmul(v_pp, b.r_pq), cmul(v_pq, b.r_qq));
+  Vo[rq + b.p] = cadd(cmul(v_qp, b.r_pp), cmul(v_qq, b.r_qp));
+  Vo[rq + b.q] = cadd(cmul(v_qp, b.r_pq), cmul(v_qq, b.r_qq));
 }
 
 template <class R>
@@ -207,7 +235,7 @@ cudaError_t abs_p_forward(int d, const cx_t<R>* T, AbsPWork<R>& w, int sweeps, b
   }
   // an even number of sweeps of d - 1 (odd) rounds brings both ping-pong pairs back to A0 / V0
   V *Ain = w.A0, *Aout = w.A1, *Vin = w.V0, *Vout = w.V1;
-  const dim3 grid((d + 15) / 16, (d + 15) / 16);
+  const dim3 grid((d / 2 + 15) / 16, (d / 2 + 15) / 16);
   for (int sw = 0; sw < sweeps; ++sw) {
     for (int r = 0; r < d - 1; ++r) {
       k_jacobi_round<R><<<grid, 256, 0, s>>>(Ain, Aout, Vin, Vout, d, r);
