@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/qst.h"
@@ -57,6 +58,7 @@ struct qst_ctx {
   int sweeps = 10;       // cold-start Jacobi sweeps
   int warm_sweeps = 2;   // warm-start sweeps (0: never warm-start)
   bool warm_valid = false;
+  bool bulk_passes = true;  // FP32 weight passes with bulk-copy staging (fnn_bulk.cu)
   // CUDA graph of one steady-state qst_step (qst_graph_enable)
   bool graph_on = false;
   cudaGraphExec_t gexec = nullptr;
@@ -298,10 +300,26 @@ template <class R> struct Engine {
     return QST_OK;
   }
 
+  // The bulk weight passes apply to FP32 contexts with H >= 8 and a 16-byte aligned f.
+  static bool use_bulk(qst_ctx* c, const R* f) {
+    if constexpr (std::is_same<R, float>::value)
+      return c->bulk_passes && wpass_bulk_ok(c->D.H, c->D.n) && ((uintptr_t)f & 15u) == 0;
+    return false;
+  }
+
   static qst_status hidden(qst_ctx* c, const R* theta, const R* f) {
     Work<R>* w = W<R>(c);
-    QST_CU(net_l1_forward<R>(c->D, theta, f, w->pre, w->hid, w->scal, w->partials, w->counters + CNT_L1, c->net,
-                             c->stream));
+    bool done = false;
+    if constexpr (std::is_same<R, float>::value) {
+      if (use_bulk(c, f)) {
+        QST_CU(l1_forward_bulk(c->D, theta, f, w->pre, w->hid, w->scal, w->partials, w->counters + CNT_L1, c->net,
+                               c->stream));
+        done = true;
+      }
+    }
+    if (!done)
+      QST_CU(net_l1_forward<R>(c->D, theta, f, w->pre, w->hid, w->scal, w->partials, w->counters + CNT_L1, c->net,
+                               c->stream));
     c->launches += 1;
     tmark(c, QST_PH_HIDDEN);
     return QST_OK;
@@ -334,12 +352,23 @@ template <class R> struct Engine {
     if ((st = forward_state(c, w->theta)) != QST_OK) return st;
     if ((st = povm_likelihood(c, f, true)) != QST_OK) return st;
     if ((st = backward_state(c)) != QST_OK) return st;
-    QST_CU(net_w2_pass<R>(D, w->theta, w->step, w->sign, w->dt, w->hid, w->pre, w->dpre, nullptr, w->partials,
-                          w->counters + CNT_W2, c->net, true, c->stream));
-    tmark(c, QST_PH_W2);
-    QST_CU(net_w1_pass<R>(D, w->theta, w->step, w->sign, f, w->dpre, w->pre, w->hid, nullptr, w->scal, w->partials,
-                          w->counters + CNT_W1, c->net, true, c->stream));
-    tmark(c, QST_PH_W1);
+    if (use_bulk(c, f)) {
+      if constexpr (std::is_same<R, float>::value) {
+        QST_CU(w2_pass_bulk(D, w->theta, w->step, w->sign, w->dt, w->hid, w->pre, w->dpre, w->partials,
+                            w->counters + CNT_W2, w->flags + 1, c->net, c->stream));
+        tmark(c, QST_PH_W2);
+        QST_CU(w1_pass_bulk(D, w->theta, w->step, w->sign, f, w->dpre, w->pre, w->hid, w->scal, w->partials,
+                            w->counters + CNT_W1, w->flags + 1, c->net, c->stream));
+        tmark(c, QST_PH_W1);
+      }
+    } else {
+      QST_CU(net_w2_pass<R>(D, w->theta, w->step, w->sign, w->dt, w->hid, w->pre, w->dpre, nullptr, w->partials,
+                            w->counters + CNT_W2, c->net, true, c->stream));
+      tmark(c, QST_PH_W2);
+      QST_CU(net_w1_pass<R>(D, w->theta, w->step, w->sign, f, w->dpre, w->pre, w->hid, nullptr, w->scal,
+                            w->partials, w->counters + CNT_W1, c->net, true, c->stream));
+      tmark(c, QST_PH_W1);
+    }
     c->launches += 2;
     return QST_OK;
   }

@@ -84,6 +84,18 @@ template <class R> cudaError_t net_w1_pass(const Dims& D, R* theta, R* step, int
                                            const R* dpre, R* pre, R* hid, R* dtheta, double* scal,
                                            double* partials, unsigned int* counter, const NetCfg& c,
                                            bool update, cudaStream_t s);
+// FP32 in-place weight passes with bulk-copy staging (fnn_bulk.cu); usable when wpass_bulk_ok(H, n)
+// and every streamed array is 16-byte aligned.  flags: a timed-out wait ORs 4 into *flags.
+bool wpass_bulk_ok(int H, long long n);
+cudaError_t w2_pass_bulk(const Dims& D, float* theta, float* step, int8_t* sign, const float* dt, const float* hid,
+                         const float* pre, float* dpre, double* partials, unsigned int* counter, unsigned int* flags,
+                         const NetCfg& c, cudaStream_t s);
+// layer-1 forward with the same summation partition as w1_pass_bulk
+cudaError_t l1_forward_bulk(const Dims& D, const float* theta, const float* f, float* pre, float* hid, double* scal,
+                            double* partials, unsigned int* counter, const NetCfg& c, cudaStream_t s);
+cudaError_t w1_pass_bulk(const Dims& D, float* theta, float* step, int8_t* sign, const float* f, float* dpre,
+                         float* pre, float* hid, double* scal, double* partials, unsigned int* counter,
+                         unsigned int* flags, const NetCfg& c, cudaStream_t s);
 // dL/dt from Y = G T:  dR_ij = 2(Re Y_ij + Re Y_ji), dR_ji = 2(Im Y_ij - Im Y_ji) (i > j), dR_ii = 2 Re Y_ii
 template <class R> cudaError_t net_symmetrize(const Dims& D, const cx_t<R>* Y, R* dt, cudaStream_t s);
 
