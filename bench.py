@@ -240,29 +240,51 @@ def time_steps(torch, qst, ctx, f_dev, K, stream):
 
 
 def run_precision(torch, qst, synth, dev, stream, prec, theta0, f, K, W, dist):
+    """K timed iterations replayed from the captured CUDA graph (the headline), the same
+    K launched kernel by kernel, per-phase device times from timed graph replays, and the
+    end-to-end rate through qst_step with a page-locked host f and the loss read back."""
     opt = qst.qst_default_options()
     opt.precision = prec
     ctx = qst.qst_init(NQ, opt=opt, stream=stream.cuda_stream)
     try:
         qst.qst_set_params(ctx, theta0)
         f_dev = torch.from_numpy(f).to(dev)
-        for _ in range(W):
+        qst.qst_graph_enable(ctx, True)
+        for _ in range(max(W, 3)):
             qst.qst_step(ctx, f_dev, want_loss=False)
-        qst.qst_timing_enable(ctx, K + 1)
         torch.cuda.synchronize()
         dist.barrier()
         with ClockSampler(torch.cuda.current_device()) as clk:
             ms, launches = time_steps(torch, qst, ctx, f_dev, K, stream)
-        phases = qst.qst_timing_read(ctx)
+        # launch by launch, for comparison (same kernels, host launch gaps included)
+        qst.qst_graph_enable(ctx, False)
+        for _ in range(2):
+            qst.qst_step(ctx, f_dev, want_loss=False)
+        ms_nograph, _ = time_steps(torch, qst, ctx, f_dev, K, stream)
+        # per phase: events captured in the graph, read after each replay
+        qst.qst_graph_enable(ctx, True)
+        qst.qst_timing_enable(ctx, 1)
+        qst.qst_step(ctx, f_dev, want_loss=False)
+        reps = min(K, 20)
+        acc = {p: [0.0, 0] for p in qst.PHASES}
+        for _ in range(reps):
+            qst.qst_step(ctx, f_dev, want_loss=False)
+            for p, (t, n) in qst.qst_timing_read(ctx).items():
+                acc[p][0] += t
+                acc[p][1] += n
+        phases = {p: (t, n) for p, (t, n) in acc.items()}
         qst.qst_timing_enable(ctx, 0)
-        # end to end: pinned host f copied in and the loss read back every step
+        # end to end: page-locked host f copied in (a node of the graph) and the loss read back every step
         f_pin = torch.from_numpy(f).pin_memory()
+        qst.qst_step(ctx, f_pin, want_loss=True)
+        qst.qst_step(ctx, f_pin, want_loss=True)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(K):
             qst.qst_step(ctx, f_pin, want_loss=True)
         e2e_s = time.perf_counter() - t0
-        return {"ms": ms, "launches": launches, "phases": phases, "clocks": clk.summary(), "e2e_s": e2e_s}
+        return {"ms": ms, "ms_nograph": ms_nograph, "launches": launches, "phases": phases,
+                "clocks": clk.summary(), "e2e_s": e2e_s}
     finally:
         qst.qst_destroy(ctx)
 
@@ -279,6 +301,7 @@ def fidelity_run(torch, qst, dev, stream, prec, theta0, f, psi, lam, max_iters, 
     d = 2 ** NQ
     try:
         qst.qst_set_params(ctx, theta0)
+        qst.qst_graph_enable(ctx, True)
         f_dev = torch.from_numpy(f).to(dev)
         psi_t = torch.from_numpy(psi.astype(np.complex64)).to(dev)
         rho = torch.empty((d, d), dtype=torch.complex64, device=dev)
@@ -544,6 +567,7 @@ def main_ours(args):
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "fp16x3+f32" if head == "mixed_fp16x3" else "f32", "data": "synthetic",
         "config": {"workload": workload_name(lam), "path": head, "parallelism": "replicas" if ws > 1 else "single",
+                   "launch": "one CUDA graph replay per iteration (qst_graph_enable)",
                    "l2": "inputs larger than L2: 1.7 GB of parameters and Rprop state streamed per step, no flush"},
         "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"), "reasons": clk.get("reasons")},
         "e2e": {"value": ws * e2e_rate, "unit": UNIT, "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 12},
@@ -552,6 +576,7 @@ def main_ours(args):
                      "frac": achieved / peak, "peak_source": peak_src if bound != "alu" else "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
                      "traffic": recorded_traffic(dom, head)},
         "paths": {name: {"iters_per_s": ws * args.steps / (v["ms"] / 1e3), "ms_per_step": v["ms"] / args.steps,
+                         "ms_per_step_launch_by_launch": v["ms_nograph"] / args.steps,
                          "phase_ms": {k: round(pm[0] / pm[1], 4) for k, pm in v["phases"].items() if pm[1]}}
                   for name, v in res.items()},
         "time_to_fidelity": ({"target": FID_TARGET, "note": "GPU time of the steps only; F evaluated off the clock every "

@@ -189,7 +189,9 @@ long long qst_kernel_launches(const qst_ctx* ctx);
  * stream after each phase below; qst_timing_read synchronises, adds the
  * elapsed times per phase over all steps recorded since the last read, writes
  * the totals (milliseconds) and step counts, and starts a new window.
- * max_steps bounds the window (extra steps are not recorded); 0 disables. */
+ * max_steps bounds the window (extra steps are not recorded); 0 disables.
+ * With qst_graph_enable on, the events are nodes of the captured graph and
+ * qst_timing_read returns the phases of the latest replay only (one step). */
 enum {
     QST_PH_HIDDEN = 0,   /* layer-1 forward (only when the input changed) */
     QST_PH_BUILD_T = 1,  /* layer 2 + Hermitian T (+ Tr T^2) */
@@ -209,10 +211,12 @@ qst_status qst_timing_read(qst_ctx* ctx, double* phase_ms, long long* phase_coun
 /* Capture the steady-state iteration of qst_step into a CUDA graph and replay it
  * (enable != 0), or go back to launching kernel by kernel (0).  Needs a context
  * created with a non-NULL stream (QST_E_UNSUPPORTED otherwise).  The graph is
- * captured on the first qst_step whose device input f was also given to the
- * previous step (the hidden layer is then known) and is re-captured when f's
- * pointer changes; host inputs and enabled per-phase timing use the launch-by-
- * launch path.  Instrumentation of the library, not part of the method. */
+ * captured on the first qst_step whose input f was also given to the previous
+ * step (the hidden layer is then known) and is re-captured when f's pointer
+ * changes.  f may be device memory or page-locked host memory (then a copy node
+ * of the graph stages it on every replay); pageable host inputs use the
+ * launch-by-launch path.  A replay has no host work between kernels.
+ * Instrumentation of the library, not part of the method. */
 qst_status qst_graph_enable(qst_ctx* ctx, int enable);
 
 /* Wait for all work enqueued on the context's stream. */

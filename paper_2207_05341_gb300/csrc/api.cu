@@ -18,15 +18,18 @@ namespace {
 
 constexpr unsigned long long kStateMagic = 0x5153545354415445ULL;  // "QSTSTATE"
 
-bool is_device_ptr(const void* p) {
-  if (p == nullptr) return false;
+// 0: pageable or unknown host memory, 1: page-locked host memory, 2: device or managed memory.
+int ptr_kind(const void* p) {
+  if (p == nullptr) return 0;
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return 0;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return 2;
+  return a.type == cudaMemoryTypeHost ? 1 : 0;
 }
+bool is_device_ptr(const void* p) { return ptr_kind(p) == 2; }
 
 }  // namespace
 
@@ -61,9 +64,11 @@ struct qst_ctx {
   bool bulk_passes = true;  // FP32 weight passes with bulk-copy staging (fnn_bulk.cu)
   // CUDA graph of one steady-state qst_step (qst_graph_enable)
   bool graph_on = false;
+  bool graph_timed = false;  // the captured graph records the phase events into slot 0
   cudaGraphExec_t gexec = nullptr;
   const void* gf = nullptr;
-  long long gnodes = 0;
+  long long gnodes = 0;  // kernel launches in one replay of gexec
+  bool capturing = false;
 };
 
 namespace {
@@ -80,17 +85,24 @@ qst_status cuda_status(cudaError_t e) {
     if (_e != cudaSuccess) return cuda_status(_e); \
   } while (0)
 
+// Under stream capture an event record becomes a graph node only with cudaEventRecordExternal.
+void record_mark(qst_ctx* c, cudaEvent_t e) {
+  if (c->capturing)
+    cudaEventRecordWithFlags(e, c->stream, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, c->stream);
+}
 // Timing marks: slot `tslot` holds a start event and one event per phase.
 void tmark_begin(qst_ctx* c) {
   c->tslot = -1;
   if (c->tmax <= 0 || c->tcount >= c->tmax) return;
   c->tslot = c->tcount++;
   c->tmask[c->tslot] = 0u;
-  cudaEventRecord(c->tev[(size_t)c->tslot * (QST_NPHASE + 1)], c->stream);
+  record_mark(c, c->tev[(size_t)c->tslot * (QST_NPHASE + 1)]);
 }
 void tmark(qst_ctx* c, int phase) {
   if (c->tslot < 0) return;
-  cudaEventRecord(c->tev[(size_t)c->tslot * (QST_NPHASE + 1) + 1 + phase], c->stream);
+  record_mark(c, c->tev[(size_t)c->tslot * (QST_NPHASE + 1) + 1 + phase]);
   c->tmask[c->tslot] |= 1u << phase;
 }
 
@@ -214,6 +226,12 @@ template <class R> qst_status validate_f(qst_ctx* c, const void* fdev) {
   return QST_OK;
 }
 
+// The producer-side max slot of the scaled FP16 split (NULL on the other paths).
+unsigned int* amax_slot(qst_ctx* c, int slot) {
+  if (!is_mixed(c) || tc_fmt(c) != TC_FP16_SCALED) return nullptr;
+  return (c->prec == QST_FP64 ? W<double>(c)->counters : W<float>(c)->counters) + slot;
+}
+
 // ---- the hot path ------------------------------------------------------------
 template <class R> struct Engine {
   using V = cx_t<R>;
@@ -223,13 +241,13 @@ template <class R> struct Engine {
     Work<R>* w = W<R>(c);
     const Dims& D = c->D;
     const bool mixed = is_mixed(c);
-    QST_CU(net_build_T<R>(D, theta, w->hid, w->T, c->stream));
-    c->launches += 1;
+    // t = W2 h + b2 in the dt buffer (free until the backward writes dL/dt), then T (or its 16-bit planes)
+    QST_CU(net_build_T<R>(D, theta, w->hid, w->dt, mixed ? nullptr : w->T, amax_slot(c, CNT_AMAXT), c->stream));
     if (mixed) {
-      QST_CU(tc_split_T(D.d, reinterpret_cast<const float2*>(w->T), w->Tb, tc_fmt(c), w->scal, w->partials,
-                        w->counters + CNT_MAXT, c->stream));
-      c->launches += tc_fmt(c) == TC_FP16_SCALED ? 2 : 1;
+      QST_CU(tc_planes_T(D.d, reinterpret_cast<const float*>(w->dt), w->Tb, tc_fmt(c), w->scal,
+                         amax_slot(c, CNT_AMAXT), c->stream));
     }
+    c->launches += 2;
     tmark(c, QST_PH_BUILD_T);
     if (c->opt.mapping == QST_MAP_ABS_P) {
       // the context's own parameters change slowly: start from the last eigenvectors
@@ -241,7 +259,7 @@ template <class R> struct Engine {
       c->launches += 4 + (long long)sw * (D.d - 1);
     } else if (mixed) {
       QST_CU(tc_herm_square(D.d, w->Tb, tc_fmt(c), w->scal, reinterpret_cast<float2*>(w->X), w->flags + 1,
-                            c->stream));
+                            amax_slot(c, CNT_AMAXT), c->stream));
     } else {
       QST_CU(cgemm_simt<R>(D.d, w->T, w->T, w->X, true, c->stream));
     }
@@ -263,7 +281,7 @@ template <class R> struct Engine {
     tmark(c, QST_PH_POVM_HI);
     c->launches += 2;
     if (backward) {
-      QST_CU(povm_lo_adj<R>(D, w->Whi, w->G, B, c->stream));
+      QST_CU(povm_lo_adj<R>(D, w->Whi, w->G, B, amax_slot(c, CNT_AMAXG), c->stream));
       c->launches += 1;
       tmark(c, QST_PH_POVM_ADJ);
     }
@@ -275,14 +293,14 @@ template <class R> struct Engine {
     Work<R>* w = W<R>(c);
     const Dims& D = c->D;
     if (is_mixed(c)) {
-      QST_CU(tc_split_G(D.d, reinterpret_cast<const float2*>(w->G), w->Gb, tc_fmt(c), w->scal, w->partials,
-                        w->counters + CNT_MAXG, c->stream));
+      QST_CU(tc_split_G(D.d, reinterpret_cast<const float2*>(w->G), w->Gb, tc_fmt(c), w->scal,
+                        amax_slot(c, CNT_AMAXG), c->stream));
       QST_CU(tc_gt_product(D.d, w->Gb, w->Tb, tc_fmt(c), w->scal, reinterpret_cast<float2*>(w->Y), w->flags + 1,
-                           c->stream));
+                           amax_slot(c, CNT_AMAXG), c->stream));
       tmark(c, QST_PH_GT);
       QST_CU(net_symmetrize<R>(D, w->Y, w->dt, c->stream));
       tmark(c, QST_PH_SYM);
-      c->launches += tc_fmt(c) == TC_FP16_SCALED ? 4 : 3;
+      c->launches += 3;
     } else if (c->opt.mapping == QST_MAP_ABS_P) {
       QST_CU(abs_p_backward<R>(D.d, w->G, *reinterpret_cast<AbsPWork<R>*>(c->apw), w->Y, c->stream));
       c->launches += 4;
@@ -373,23 +391,39 @@ template <class R> struct Engine {
     return QST_OK;
   }
 
-  // Capture step_body for input f into c->gexec (replaces an earlier graph).
-  static qst_status capture(qst_ctx* c, const void* f_user) {
+  // Capture step_body for input f into c->gexec (replaces an earlier graph).  A
+  // page-locked host f is copied into the staging buffer by a node of the graph.
+  static qst_status capture(qst_ctx* c, const void* f_user, bool host_f) {
     if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    Work<R>* w = W<R>(c);
     const long long l0 = c->launches;
+    const bool timed = c->tmax > 0;
     QST_CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    const qst_status st = step_body(c, (const R*)f_user);
+    c->capturing = true;
+    const R* f = (const R*)f_user;
+    cudaError_t ec = cudaSuccess;
+    if (host_f) {
+      ec = cudaMemcpyAsync(w->fstage, f_user, (size_t)c->D.n * sizeof(R), cudaMemcpyHostToDevice, c->stream);
+      f = (const R*)w->fstage;
+    }
+    if (timed) {  // the phase events become nodes of the graph; every replay re-records them (slot 0)
+      c->tcount = 0;
+      tmark_begin(c);
+    }
+    const qst_status st = ec == cudaSuccess ? step_body(c, f) : cuda_status(ec);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    c->capturing = false;
+    c->tslot = -1;
+    c->graph_timed = timed;
+    const long long kernels = c->launches - l0;
     c->launches = l0;
     if (st != QST_OK) { if (g) cudaGraphDestroy(g); return st; }
     if (e != cudaSuccess) return cuda_status(e);
     const cudaError_t e2 = cudaGraphInstantiate(&c->gexec, g, 0);
-    size_t nodes = 0;
-    cudaGraphGetNodes(g, nullptr, &nodes);
     cudaGraphDestroy(g);
     if (e2 != cudaSuccess) { c->gexec = nullptr; return cuda_status(e2); }
-    c->gnodes = (long long)nodes;
+    c->gnodes = kernels;
     c->gf = f_user;
     return QST_OK;
   }
@@ -398,22 +432,19 @@ template <class R> struct Engine {
     Work<R>* w = W<R>(c);
     const Dims& D = c->D;
     qst_status st;
-    const bool graphable = c->graph_on && c->tmax == 0 && is_device_ptr(f_user);
-    const R* f = graphable ? (const R*)f_user
-                           : (const R*)stage_input(c, f_user, (size_t)D.n * sizeof(R), w->fstage, &st);
-    if (!graphable && st != QST_OK) return st;
+    const int kind = ptr_kind(f_user);
     const bool new_f = !c->hidden_valid || f_user != c->f_last;
-    if (new_f) {
-      st = validate_f<R>(c, f);
-      if (st != QST_OK) return st;
-    }
-    if (graphable && !new_f) {
+    if (c->graph_on && kind != 0 && !new_f) {
       if (!c->gexec || c->gf != f_user) {
-        if ((st = capture(c, f_user)) != QST_OK) return st;
+        if ((st = capture(c, f_user, kind == 1)) != QST_OK) return st;
       }
       QST_CU(cudaGraphLaunch(c->gexec, c->stream));
       c->launches += c->gnodes;
     } else {
+      const R* f = kind == 2 ? (const R*)f_user
+                             : (const R*)stage_input(c, f_user, (size_t)D.n * sizeof(R), w->fstage, &st);
+      if (kind != 2 && st != QST_OK) return st;
+      if (new_f && (st = validate_f<R>(c, f)) != QST_OK) return st;
       tmark_begin(c);
       if (new_f) {
         if ((st = hidden(c, w->theta, f)) != QST_OK) return st;
@@ -561,6 +592,7 @@ qst_status batch_capture(qst_batch* bt, const void* const* f) {
   if (bt->gexec) { cudaGraphExecDestroy(bt->gexec); bt->gexec = nullptr; }
   QST_CU(cudaStreamBeginCapture(bt->root, cudaStreamCaptureModeThreadLocal));
   qst_status st = QST_OK;
+  long long kernels = 0;
   cudaError_t e = cudaEventRecord(bt->fork, bt->root);
   for (int b = 0; b < bt->B && st == QST_OK && e == cudaSuccess; ++b) {
     qst_ctx* c = bt->ctx[b];
@@ -569,6 +601,7 @@ qst_status batch_capture(qst_batch* bt, const void* const* f) {
     const long long l0 = c->launches;
     st = c->prec == QST_FP64 ? Engine<double>::step_body(c, (const double*)f[b])
                              : Engine<float>::step_body(c, (const float*)f[b]);
+    kernels += c->launches - l0;
     c->launches = l0;
     if (st != QST_OK) break;
     e = cudaEventRecord(bt->done[b], c->stream);
@@ -579,12 +612,10 @@ qst_status batch_capture(qst_batch* bt, const void* const* f) {
   if (st != QST_OK) { if (g) cudaGraphDestroy(g); return st; }
   if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_status(e); }
   if (e2 != cudaSuccess) return cuda_status(e2);
-  size_t nodes = 0;
-  cudaGraphGetNodes(g, nullptr, &nodes);
   const cudaError_t e3 = cudaGraphInstantiate(&bt->gexec, g, 0);
   cudaGraphDestroy(g);
   if (e3 != cudaSuccess) { bt->gexec = nullptr; return cuda_status(e3); }
-  bt->gnodes = (long long)nodes;
+  bt->gnodes = kernels;
   bt->gf.assign(f, f + bt->B);
   return QST_OK;
 }
@@ -814,6 +845,13 @@ long long qst_kernel_launches(const qst_ctx* c) { return c ? c->launches : -1; }
 
 qst_status qst_timing_enable(qst_ctx* c, int max_steps) {
   if (!c || max_steps < 0) return QST_E_INVAL;
+  QST_CU(cudaStreamSynchronize(c->stream));
+  if (c->gexec) {  // recaptured on the next step, with or without the phase events
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->gf = nullptr;
+  }
+  c->graph_timed = false;
   for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
   c->tev.clear();
   c->tmask.clear();
@@ -833,7 +871,9 @@ qst_status qst_timing_read(qst_ctx* c, double* phase_ms, long long* phase_count,
   if (!c || !phase_ms || !phase_count || nphase < 1) return QST_E_INVAL;
   QST_CU(cudaStreamSynchronize(c->stream));
   for (int p = 0; p < nphase; ++p) { phase_ms[p] = 0.0; phase_count[p] = 0; }
-  for (int s = 0; s < c->tcount; ++s) {
+  // With a timed graph, slot 0 holds the events of the latest replay (if any replay ran).
+  const int slots = c->graph_timed ? (c->gexec && c->iters > 0 ? 1 : 0) : c->tcount;
+  for (int s = 0; s < slots; ++s) {
     cudaEvent_t prev = c->tev[(size_t)s * (QST_NPHASE + 1)];
     for (int p = 0; p < QST_NPHASE; ++p) {
       if (!(c->tmask[s] & (1u << p))) continue;
@@ -844,7 +884,7 @@ qst_status qst_timing_read(qst_ctx* c, double* phase_ms, long long* phase_count,
       prev = e;
     }
   }
-  c->tcount = 0;
+  if (!c->graph_timed) c->tcount = 0;
   return QST_OK;
 }
 

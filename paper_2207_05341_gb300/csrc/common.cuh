@@ -132,4 +132,19 @@ __device__ __forceinline__ bool last_block_arrived(unsigned int* counter) {
   return s_last;
 }
 
+// Fold a block's largest magnitude m >= 0 into *amax (float bits: non-negative floats
+// order like their bit patterns).  Called by every thread of the block.
+__device__ __forceinline__ void block_absmax_to(float m, unsigned int* amax) {
+  __shared__ float s_red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float b = 0.f;
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) b = fmaxf(b, s_red[w]);
+    atomicMax(amax, __float_as_uint(b));
+  }
+}
+
 }  // namespace qst

@@ -119,74 +119,55 @@ __global__ void __launch_bounds__(256) k_l1_forward(const R* __restrict__ theta,
 }
 
 // ------------------------------------------------------------------ layer 2 + Hermitian T
-// t = W2 h + b2; R = t as d x d row-major; T_ii = R_ii, T_ij = R_ij + i R_ji (i > j), T_ji = conj T_ij.
-// One CTA per tile pair (I, J), I >= J, of TS x TS tiles.
+// t = W2 h + b2 (k_layer2: a streaming pass over W2^T, 4^N-contiguous, every row read once;
+// optionally folds max |t_i| into a max slot for the FP16 split of T);
+// R = t as d x d row-major; T_ii = R_ii, T_ij = R_ij + i R_ji (i > j), T_ji = conj T_ij
+// (k_hermitian_T: one CTA per tile pair (I, J), I >= J, of TS x TS tiles, t read from L2; the
+// mixed-precision path writes T's 16-bit planes from t instead, tc_planes_T in gemm_tc.cu).
 template <class R, int H>
-__global__ void __launch_bounds__(256) k_build_T(const R* __restrict__ theta, const R* __restrict__ hid, int N,
-                                                  cx_t<R>* __restrict__ T) {
-  using V = cx_t<R>;
+__global__ void __launch_bounds__(256) k_layer2(const R* __restrict__ theta, const R* __restrict__ hid, long long n,
+                                                 R* __restrict__ t, unsigned int* amax) {
   __shared__ R hs[H];
-  __shared__ R Ra[32][33];
-  __shared__ R Rb[32][33];
-  const int d = 1 << N;
-  const long long n = 1LL << (2 * N);
-  const int TS = d < 32 ? d : 32;
-  const R* W2T = theta + (long long)H * n;
-  const R* b2 = theta + 2LL * H * n;
-  int I, J;
-  tri_decode(blockIdx.x, I, J);
   if (threadIdx.x < H) hs[threadIdx.x] = hid[threadIdx.x];
   __syncthreads();
   using VV = Vec<R>;
   constexpr int VW = VV::W;
-  if (TS % VW == 0) {
-    // VW consecutive columns per thread, 16-byte loads of every W2^T row
-    const int gpr = TS / VW;
-    for (int e = threadIdx.x; e < TS * gpr; e += blockDim.x) {
-      const int r = e / gpr, c = (e % gpr) * VW;
-      const long long ia = (long long)(I * TS + r) * d + J * TS + c;
-      R ta[VW];
-      VV::ld(b2 + ia, ta);
+  const R* W2T = theta + (long long)H * n;
+  const R* b2 = theta + 2LL * H * n;
+  const long long nv = n / VW;
+  float m = 0.f;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv; v += (long long)gridDim.x * blockDim.x) {
+    const long long i = v * VW;
+    R w[H][VW];
 #pragma unroll
-      for (int j = 0; j < H; ++j) {
-        R w[VW];
-        VV::ld(W2T + (long long)j * n + ia, w);
+    for (int j = 0; j < H; ++j) VV::ld(W2T + (long long)j * n + i, w[j]);
+    R ta[VW];
+    VV::ld(b2 + i, ta);
 #pragma unroll
-        for (int u = 0; u < VW; ++u) ta[u] += w[u] * hs[j];
-      }
+    for (int j = 0; j < H; ++j) {
 #pragma unroll
-      for (int u = 0; u < VW; ++u) Ra[r][c + u] = ta[u];
-      if (I != J) {
-        const long long ib = (long long)(J * TS + r) * d + I * TS + c;
-        R tb[VW];
-        VV::ld(b2 + ib, tb);
-#pragma unroll
-        for (int j = 0; j < H; ++j) {
-          R w[VW];
-          VV::ld(W2T + (long long)j * n + ib, w);
-#pragma unroll
-          for (int u = 0; u < VW; ++u) tb[u] += w[u] * hs[j];
-        }
-#pragma unroll
-        for (int u = 0; u < VW; ++u) Rb[r][c + u] = tb[u];
-      }
+      for (int u = 0; u < VW; ++u) ta[u] += w[j][u] * hs[j];
     }
-  } else {
-    for (int e = threadIdx.x; e < TS * TS; e += blockDim.x) {
-      const int r = e / TS, c = e % TS;
-      const long long ia = (long long)(I * TS + r) * d + J * TS + c;
-      R ta = b2[ia];
+    VV::st(t + i, ta);
 #pragma unroll
-      for (int j = 0; j < H; ++j) ta += W2T[(long long)j * n + ia] * hs[j];
-      Ra[r][c] = ta;
-      if (I != J) {
-        const long long ib = (long long)(J * TS + r) * d + I * TS + c;
-        R tb = b2[ib];
-#pragma unroll
-        for (int j = 0; j < H; ++j) tb += W2T[(long long)j * n + ib] * hs[j];
-        Rb[r][c] = tb;
-      }
-    }
+    for (int u = 0; u < VW; ++u) m = fmaxf(m, fabsf((float)ta[u]));
+  }
+  if (amax) block_absmax_to(m, amax);
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) k_hermitian_T(const R* __restrict__ t, int N, cx_t<R>* __restrict__ T) {
+  using V = cx_t<R>;
+  __shared__ R Ra[32][33];
+  __shared__ R Rb[32][33];
+  const int d = 1 << N;
+  const int TS = d < 32 ? d : 32;
+  int I, J;
+  tri_decode(blockIdx.x, I, J);
+  for (int e = threadIdx.x; e < TS * TS; e += blockDim.x) {
+    const int r = e / TS, c = e % TS;
+    Ra[r][c] = t[(long long)(I * TS + r) * d + J * TS + c];
+    if (I != J) Rb[r][c] = t[(long long)(J * TS + r) * d + I * TS + c];
   }
   __syncthreads();
   for (int e = threadIdx.x; e < TS * TS; e += blockDim.x) {
@@ -435,11 +416,27 @@ cudaError_t net_l1_forward(const Dims& D, const R* theta, const R* f, R* pre, R*
 }
 
 template <class R>
-cudaError_t net_build_T(const Dims& D, const R* theta, const R* hid, cx_t<R>* T, cudaStream_t s) {
+cudaError_t net_build_T(const Dims& D, const R* theta, const R* hid, R* t, cx_t<R>* T, unsigned int* amax,
+                        cudaStream_t s) {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long nv = D.n / Vec<R>::W;
+  const long long want = (nv + 255) / 256;
+  QST_SWITCH_H(D.H, {
+    static const int per_sm = [] {  // resident CTAs per SM: one wave of grid-stride CTAs
+      int b = 1;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_layer2<R, HH>, 256, 0);
+      return b < 1 ? 1 : b;
+    }();
+    const long long grid = want < (long long)per_sm * sms ? want : (long long)per_sm * sms;
+    k_layer2<R, HH><<<(unsigned)grid, 256, 0, s>>>(theta, hid, D.n, t, amax);
+  });
+  if (!T) return cudaGetLastError();
   const int TS = D.d < 32 ? D.d : 32;
   const int nt = D.d / TS;
   const unsigned pairs = (unsigned)(nt * (nt + 1) / 2);
-  QST_SWITCH_H(D.H, k_build_T<R, HH><<<pairs, 256, 0, s>>>(theta, hid, D.N, T));
+  k_hermitian_T<R><<<pairs, 256, 0, s>>>(t, D.N, T);
   return cudaGetLastError();
 }
 
@@ -483,7 +480,7 @@ template <class R> cudaError_t net_symmetrize(const Dims& D, const cx_t<R>* Y, R
 #define QST_INST(R)                                                                                              \
   template cudaError_t net_l1_forward<R>(const Dims&, const R*, const R*, R*, R*, double*, double*, unsigned int*, \
                                          const NetCfg&, cudaStream_t);                                           \
-  template cudaError_t net_build_T<R>(const Dims&, const R*, const R*, cx_t<R>*, cudaStream_t);                 \
+  template cudaError_t net_build_T<R>(const Dims&, const R*, const R*, R*, cx_t<R>*, unsigned int*, cudaStream_t);                 \
   template cudaError_t net_w2_pass<R>(const Dims&, R*, R*, int8_t*, const R*, const R*, const R*, R*, R*, double*, \
                                       unsigned int*, const NetCfg&, bool, cudaStream_t);                         \
   template cudaError_t net_w1_pass<R>(const Dims&, R*, R*, int8_t*, const R*, const R*, R*, R*, R*, double*,     \

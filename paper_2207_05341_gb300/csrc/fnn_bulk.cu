@@ -1,26 +1,38 @@
 // Rprop weight passes of the Sec. 3.1 network (FP32, in-place update) with bulk-copy staging.
 //
-// Each CTA walks chunks of kCols consecutive columns of the 4^N axis.  For a chunk,
-// one thread issues 1-D bulk copies (cp.async.bulk, completion counted on an
-// mbarrier) of every parameter row segment (weights, Rprop steps, previous signs)
-// and of the chunk of dt (W2 pass) or f (W1 pass) into one of two shared-memory
-// stages; all threads then update the chunk in shared memory (one column per
-// thread, all H rows), and the same thread writes the rows back with bulk stores.
-// The next chunk's loads are in flight while a chunk is updated, so the pass
-// streams at HBM rate without depending on registers for bytes in flight.
+// Each CTA walks chunks of kCols consecutive columns of the 4^N axis (chunk c to CTA
+// c mod grid).  The CTA is warp-specialised: one producer thread issues, per chunk, one
+// 2-D tensor copy (cp.async.bulk.tensor, box kCols x H) of each parameter array
+// (weights, Rprop steps, previous signs: H rows n apart) and 1-D bulk copies of the
+// chunk of dt (W2 pass) or f (W1 pass) and of b2's state, all counted on the stage's
+// "full" mbarrier, into a ring of kStages shared-memory stages; kCols consumer threads
+// update a chunk in shared memory (one column per thread, all H rows) and arrive on the
+// stage's "empty" mbarrier (kGroups threads per column, each with about H / kGroups of the rows,
+// so that enough warps hide the latency of the update); the producer then writes the boxes back with tensor stores
+// and refills the stage once the stores have read it.  A handful of copies per chunk
+// keeps the copy engine's per-instruction cost off the critical path.  Loads run
+// about kStages - 2 chunks ahead of the consumers and nobody waits for a store to drain, so
+// the pass streams at HBM rate.
 //
 // The arithmetic is that of k_w2_pass / k_w1_pass in fnn.cu (same Rprop; the sums
 // over the 4^N axis are per-thread partials reduced in a fixed order, so the pass is
 // deterministic, though the partition of those sums differs from fnn.cu's kernel).
-// Every mbarrier wait is bounded; a timeout raises flags[1] and the kernel drains
-// what it issued (bounded) before returning.
+// Every mbarrier wait is bounded; a timeout raises flags bit 4 and the kernel drains
+// the loads it issued (bounded) before returning.
+#include <cuda.h>
+
 #include "impl.h"
 
 namespace qst {
 
 namespace {
 
-constexpr int kCols = 256;                  // columns per chunk = threads per CTA
+constexpr int kCols = 128;                  // columns per chunk
+constexpr int kConsumerWarps = kCols / 32;  // warps over the columns of one row group
+constexpr int kGroups = 4;                  // row groups: consumer threads per column
+constexpr int kConsumers = kCols * kGroups;
+constexpr int kThreads = kConsumers + 32;   // + one producer warp
+constexpr int kMaxStages = 4;
 constexpr unsigned long long kWait = 4000000000ULL;
 
 __device__ __forceinline__ uint32_t s_u32(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
@@ -57,12 +69,35 @@ __device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t 
   asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(s_u32(src)), "r"(bytes)
                : "memory");
 }
+__device__ __forceinline__ void tma_load_box(void* dst, const CUtensorMap* map, int x, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          s_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(0), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_box(const CUtensorMap* map, int x, const void* src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(0), "r"(s_u32(src))
+               : "memory");
+}
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all_but_1() {
+  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
+__device__ __forceinline__ void bar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Stage layout (bytes): w[H][kCols] f32 | st[H][kCols] f32 | sg[H][kCols] i8 | vec[kCols] f32 (dt or f)
+// Tensor maps of the H x n parameter rows of one pass (W1, or W2^T) in theta, step and sign.
+struct WMaps {
+  CUtensorMap w, st, sg;
+};
+
+// Stage layout (bytes, every part 128-byte aligned): w[H][kCols] f32 | st[H][kCols] f32 | sg[H][kCols] i8 | vec[kCols] f32 (dt or f)
 //                       | W2 pass only: b2 w, st [kCols] f32, sg [kCols] i8
 template <int H, bool W2> struct Stage {
   static constexpr int kW = 0;
@@ -74,23 +109,29 @@ template <int H, bool W2> struct Stage {
   static constexpr int kBsg = kBst + kCols * 4;
   static constexpr int kBytes = W2 ? kBsg + kCols : kBw;  // multiple of 16
   static constexpr uint32_t kTx = (uint32_t)kBytes;
+  // ring depth: 4 stages while two CTAs still fit on an SM (228 KB), else 3
+  static constexpr int kStages = 4 * kBytes <= 110 * 1024 ? 4 : 3;
 };
 
 template <class R> __device__ __forceinline__ R leaky_b(R x, R slope) { return x > R(0) ? x : slope * x; }
 
+// Sum v over the kConsumerWarps warps of consumer threads (fixed order) into out[0..M); every
+// thread of the block calls it (the producer warp contributes nothing).
 template <int M>
 __device__ __forceinline__ void block_sum_to(const float (&v)[M], double* out) {
-  __shared__ double red[8][M];
+  __shared__ double red[kConsumerWarps][M];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (w < kConsumerWarps) {
 #pragma unroll
-  for (int j = 0; j < M; ++j) {
-    double x = warp_sum((double)v[j]);
-    if (lane == 0) red[w][j] = x;
+    for (int j = 0; j < M; ++j) {
+      double x = warp_sum((double)v[j]);
+      if (lane == 0) red[w][j] = x;
+    }
   }
   __syncthreads();
   for (int j = threadIdx.x; j < M; j += blockDim.x) {
     double s = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q][j];
+    for (int q = 0; q < kConsumerWarps; ++q) s += red[q][j];
     out[j] = s;
   }
 }
@@ -108,140 +149,179 @@ __device__ __forceinline__ void final_sum(const double* partials, int M, F fin) 
 
 // W2 pass (W2 true) or W1 pass (W2 false); see k_w2_pass / k_w1_pass in fnn.cu for the arithmetic.
 template <int H, bool W2>
-__global__ void __launch_bounds__(kCols, 2) k_wpass_bulk(float* __restrict__ theta, float* __restrict__ step,
-                                                        int8_t* __restrict__ sign, const float* __restrict__ vec,
-                                                        const float* __restrict__ hidv, const float* __restrict__ pre,
-                                                        float* dpre_io, float* pre_out, float* hid_out, double* scal,
-                                                        long long n, double* partials, unsigned int* counter,
-                                                        unsigned int* flags, RpropCfg<float> rc, float slope) {
+__global__ void __launch_bounds__(kThreads, 2) k_wpass_bulk(const __grid_constant__ WMaps maps,
+                                                          float* __restrict__ theta, float* __restrict__ step,
+                                                          int8_t* __restrict__ sign, const float* __restrict__ vec,
+                                                          const float* __restrict__ hidv, const float* __restrict__ pre,
+                                                          float* dpre_io, float* pre_out, float* hid_out, double* scal,
+                                                          long long n, double* partials, unsigned int* counter,
+                                                          unsigned int* flags, RpropCfg<float> rc, float slope) {
   using S = Stage<H, W2>;
-  extern __shared__ __align__(128) uint8_t smem[];
-  __shared__ __align__(8) uint64_t bars[2];
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((128u - (s_u32(smem_raw) & 127u)) & 127u);  // 128-byte aligned ring
+  constexpr int kStages = S::kStages;
+  __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
   __shared__ float hs[H];
   __shared__ int s_fail;
-  const long long rowoff = W2 ? (long long)H * n : 0;  // W2^T or W1 rows
   const long long ob2 = 2LL * H * n, ob1 = 2LL * H * n + n;
   const long long nchunks = n / kCols;
-  const int tid = threadIdx.x;
+  const long long nk = blockIdx.x < nchunks ? (nchunks - 1 - blockIdx.x) / gridDim.x + 1 : 0;  // chunks of this CTA
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid < H) hs[tid] = W2 ? hidv[tid] : dpre_io[tid];  // W2: h; W1: dpre
   if (tid == 0) {
     s_fail = 0;
-    bar_init(s_u32(&bars[0]), 1);
-    bar_init(s_u32(&bars[1]), 1);
+    for (int q = 0; q < kStages; ++q) {
+      bar_init(s_u32(&full[q]), 1);
+      bar_init(s_u32(&empty[q]), kConsumers);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
 
-  auto issue_loads = [&](long long chunk, int s) {
-    uint8_t* st = smem + s * S::kBytes;
-    const long long c0 = chunk * kCols;
-    const uint32_t bar = s_u32(&bars[s]);
-    bar_expect(bar, S::kTx);
-    for (int j = 0; j < H; ++j) {
-      const long long o = rowoff + (long long)j * n + c0;
-      bulk_load(st + S::kW + j * kCols * 4, theta + o, kCols * 4, bar);
-      bulk_load(st + S::kSt + j * kCols * 4, step + o, kCols * 4, bar);
-      bulk_load(st + S::kSg + j * kCols, sign + o, kCols, bar);
-    }
-    bulk_load(st + S::kVec, vec + c0, kCols * 4, bar);
-    if (W2) {
-      bulk_load(st + S::kBw, theta + ob2 + c0, kCols * 4, bar);
-      bulk_load(st + S::kBst, step + ob2 + c0, kCols * 4, bar);
-      bulk_load(st + S::kBsg, sign + ob2 + c0, kCols, bar);
-    }
-  };
-  auto issue_stores = [&](long long chunk, int s) {
-    uint8_t* st = smem + s * S::kBytes;
-    const long long c0 = chunk * kCols;
-    for (int j = 0; j < H; ++j) {
-      const long long o = rowoff + (long long)j * n + c0;
-      bulk_store(theta + o, st + S::kW + j * kCols * 4, kCols * 4);
-      bulk_store(step + o, st + S::kSt + j * kCols * 4, kCols * 4);
-      bulk_store(sign + o, st + S::kSg + j * kCols, kCols);
-    }
-    if (W2) {
-      bulk_store(theta + ob2 + c0, st + S::kBw, kCols * 4);
-      bulk_store(step + ob2 + c0, st + S::kBst, kCols * 4);
-      bulk_store(sign + ob2 + c0, st + S::kBsg, kCols);
-    }
-    bulk_commit();
-  };
-
-  float acc[W2 ? H : H + 1];
+  constexpr int RPT = (H + kGroups - 1) / kGroups;  // rows per consumer thread
+  const int col = tid % kCols, rg = tid / kCols;      // column of a chunk, row group
+  float acc[RPT], accf = 0.f, hr[RPT];
 #pragma unroll
-  for (int j = 0; j < (W2 ? H : H + 1); ++j) acc[j] = 0.f;
-
-  long long chunk = blockIdx.x;
-  if (tid == 0 && chunk < nchunks) issue_loads(chunk, 0);
-  int k = 0;
-  for (; chunk < nchunks; chunk += gridDim.x, ++k) {
-    const int s = k & 1;
-    const long long next = chunk + gridDim.x;
-    if (tid == 0 && next < nchunks) {
-      bulk_wait_read_all();  // stage s^1 held chunk k - 1, whose stores must have left shared memory
-      issue_loads(next, s ^ 1);
-    }
-    if (!bar_wait(s_u32(&bars[s]), (uint32_t)((k >> 1) & 1))) {
-      if (tid == 0) atomicOr(flags, 4u);
-      s_fail = 1;
-    }
-    __syncthreads();
-    if (s_fail) break;
-    uint8_t* st = smem + s * S::kBytes;
-    float* w = reinterpret_cast<float*>(st + S::kW);
-    float* sp = reinterpret_cast<float*>(st + S::kSt);
-    int8_t* sg = reinterpret_cast<int8_t*>(st + S::kSg);
-    const float v = reinterpret_cast<const float*>(st + S::kVec)[tid];  // dt_i or f_i
-    if (W2) {
-      float* bw = reinterpret_cast<float*>(st + S::kBw);
-      float* bst = reinterpret_cast<float*>(st + S::kBst);
-      int8_t* bsg = reinterpret_cast<int8_t*>(st + S::kBsg);
-      float bs = bst[tid];
-      int8_t bg = bsg[tid];
-      bw[tid] = rprop1(bw[tid], v, bs, bg, rc);
-      bst[tid] = bs;
-      bsg[tid] = bg;
-    } else {
-      acc[H] += v;
-    }
-#pragma unroll
-    for (int j = 0; j < H; ++j) {
-      const int e = j * kCols + tid;
-      float wj = w[e];
-      float sj = sp[e];
-      int8_t gj = sg[e];
-      if (W2) {
-        acc[j] += wj * v;  // dh_j with the old weights
-        wj = rprop1(wj, hs[j] * v, sj, gj, rc);
-      } else {
-        wj = rprop1(wj, hs[j] * v, sj, gj, rc);
-        acc[j] += wj * v;  // next pre-activation with the new weights
+  for (int l = 0; l < RPT; ++l) {
+    acc[l] = 0.f;
+    hr[l] = rg * RPT + l < H ? hs[rg * RPT + l] : 0.f;  // W2: h_j; W1: dpre_j
+  }
+  if (warp == kConsumers / 32) {
+    // ---------------- producer
+    if (lane == 0) {
+      auto issue_loads = [&](long long k) {
+        const int q = (int)(k % kStages);
+        uint8_t* st = smem + q * S::kBytes;
+        const long long c0 = (blockIdx.x + k * gridDim.x) * kCols;
+        const uint32_t bar = s_u32(&full[q]);
+        bar_expect(bar, S::kTx);
+        tma_load_box(st + S::kW, &maps.w, (int)c0, bar);
+        tma_load_box(st + S::kSt, &maps.st, (int)c0, bar);
+        tma_load_box(st + S::kSg, &maps.sg, (int)c0, bar);
+        bulk_load(st + S::kVec, vec + c0, kCols * 4, bar);
+        if (W2) {
+          bulk_load(st + S::kBw, theta + ob2 + c0, kCols * 4, bar);
+          bulk_load(st + S::kBst, step + ob2 + c0, kCols * 4, bar);
+          bulk_load(st + S::kBsg, sign + ob2 + c0, kCols, bar);
+        }
+      };
+      auto issue_stores = [&](long long k) {
+        const int q = (int)(k % kStages);
+        uint8_t* st = smem + q * S::kBytes;
+        const long long c0 = (blockIdx.x + k * gridDim.x) * kCols;
+        tma_store_box(&maps.w, (int)c0, st + S::kW);
+        tma_store_box(&maps.st, (int)c0, st + S::kSt);
+        tma_store_box(&maps.sg, (int)c0, st + S::kSg);
+        if (W2) {
+          bulk_store(theta + ob2 + c0, st + S::kBw, kCols * 4);
+          bulk_store(step + ob2 + c0, st + S::kBst, kCols * 4);
+          bulk_store(sign + ob2 + c0, st + S::kBsg, kCols);
+        }
+        bulk_commit();
+      };
+      long long loaded = 0;  // chunks [0, loaded) have been issued
+      for (; loaded < nk && loaded < kStages; ++loaded) issue_loads(loaded);
+      for (long long k = 0; k < nk; ++k) {
+        if (!bar_wait(s_u32(&empty[k % kStages]), (uint32_t)((k / kStages) & 1))) {
+          atomicOr(flags, 4u);
+          s_fail = 1;
+          break;
+        }
+        issue_stores(k);
+        // refill the stage of chunk k - 1, whose stores were committed one chunk ago
+        if (k >= 1 && loaded < nk) {
+          bulk_wait_read_all_but_1();
+          issue_loads(loaded++);
+        }
       }
-      w[e] = wj;
-      sp[e] = sj;
-      sg[e] = gj;
+      bulk_wait_all();
+      if (s_fail) {  // drain: wait (bounded) for the last load issued into every stage
+        for (int q = 0; q < kStages; ++q) {
+          long long last = -1;
+          for (long long k = loaded - 1; k >= 0 && k >= loaded - kStages; --k)
+            if (k % kStages == q) last = k;
+          if (last >= 0) bar_wait(s_u32(&full[q]), (uint32_t)((last / kStages) & 1));
+        }
+      }
     }
-    fence_async_smem();
-    __syncthreads();
-    if (tid == 0) issue_stores(chunk, s);
-  }
-  if (tid == 0) bulk_wait_all();
-  if (s_fail) {
-    // drain: the other stage may still have loads in flight
-    if (tid == 0) bar_wait(s_u32(&bars[(k + 1) & 1]), (uint32_t)(((k + 1) >> 1) & 1));
-    return;
-  }
-
-  if (W2) {
-    float a2[H];
-#pragma unroll
-    for (int j = 0; j < H; ++j) a2[j] = acc[j];
-    block_sum_to<H>(a2, partials + (size_t)blockIdx.x * kPartialStride);
+    __syncwarp();
   } else {
-    float a1[H + 1];
+    // ---------------- consumers: column col, rows rg * RPT + l, of every chunk
+    for (long long k = 0; k < nk; ++k) {
+      const int q = (int)(k % kStages);
+      if (!bar_wait(s_u32(&full[q]), (uint32_t)((k / kStages) & 1))) {
+        if (tid == 0) atomicOr(flags, 4u);
+        s_fail = 1;
+        break;
+      }
+      uint8_t* st = smem + q * S::kBytes;
+      float* w = reinterpret_cast<float*>(st + S::kW);
+      float* sp = reinterpret_cast<float*>(st + S::kSt);
+      int8_t* sg = reinterpret_cast<int8_t*>(st + S::kSg);
+      const float v = reinterpret_cast<const float*>(st + S::kVec)[col];  // dt_i or f_i
+      if (rg == 0) {
+        if (W2) {
+          float* bw = reinterpret_cast<float*>(st + S::kBw);
+          float* bst = reinterpret_cast<float*>(st + S::kBst);
+          int8_t* bsg = reinterpret_cast<int8_t*>(st + S::kBsg);
+          float bs = bst[col];
+          int8_t bg = bsg[col];
+          bw[col] = rprop1(bw[col], v, bs, bg, rc);
+          bst[col] = bs;
+          bsg[col] = bg;
+        } else {
+          accf += v;
+        }
+      }
 #pragma unroll
-    for (int j = 0; j <= H; ++j) a1[j] = acc[j];
-    block_sum_to<H + 1>(a1, partials + (size_t)blockIdx.x * kPartialStride);
+      for (int l = 0; l < RPT; ++l) {
+        const int j = rg * RPT + l;
+        if (RPT * kGroups != H && j >= H) continue;
+        const int e = j * kCols + col;
+        float wj = w[e];
+        float sj = sp[e];
+        int8_t gj = sg[e];
+        if (W2) {
+          acc[l] += wj * v;  // dh_j with the old weights
+          wj = rprop1(wj, hr[l] * v, sj, gj, rc);
+        } else {
+          wj = rprop1(wj, hr[l] * v, sj, gj, rc);
+          acc[l] += wj * v;  // next pre-activation with the new weights
+        }
+        w[e] = wj;
+        sp[e] = sj;
+        sg[e] = gj;
+      }
+      fence_async_smem();  // the producer's tensor stores read what this thread wrote
+      bar_arrive(s_u32(&empty[q]));
+    }
+  }
+  __syncthreads();
+  if (s_fail) return;
+
+  // per row j: the thread partials of its group's kCols columns, summed per warp (FP64) and over the
+  // group's kConsumerWarps warps in order (the partition of k_l1_forward_cols)
+  {
+    __shared__ double red[kGroups * kConsumerWarps][RPT + 1];
+    if (warp < kConsumers / 32) {
+#pragma unroll
+      for (int l = 0; l < RPT; ++l) {
+        const double x = warp_sum((double)acc[l]);
+        if (lane == 0) red[warp][l] = x;
+      }
+      if (!W2 && rg == 0) {
+        const double x = warp_sum((double)accf);
+        if (lane == 0) red[warp][RPT] = x;
+      }
+    }
+    __syncthreads();
+    double* out = partials + (size_t)blockIdx.x * kPartialStride;
+    for (int j = tid; j < (W2 ? H : H + 1); j += blockDim.x) {
+      const int g = j < H ? j / RPT : 0, l = j < H ? j % RPT : RPT;
+      double sum = 0.0;
+      for (int q = 0; q < kConsumerWarps; ++q) sum += red[g * kConsumerWarps + q][l];
+      out[j] = sum;
+    }
   }
   if (last_block_arrived(counter)) {
     if (W2) {
@@ -318,28 +398,53 @@ long long bulk_grid(long long n) {
   return grid;
 }
 
+typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                             const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                             CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// H x n rows starting at base (row stride n elements), box kCols x H, no swizzle.
+bool make_rows_map(CUtensorMap* m, void* base, long long n, int H, bool bytes) {
+  EncodeFn enc = reinterpret_cast<EncodeFn>(tma_encoder());
+  if (!enc) return false;
+  const cuuint64_t es = bytes ? 1 : 4;
+  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)H};
+  cuuint64_t strides[1] = {(cuuint64_t)n * es};
+  cuuint32_t box[2] = {(cuuint32_t)kCols, (cuuint32_t)H};
+  cuuint32_t estr[2] = {1u, 1u};
+  return enc(m, bytes ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides,
+             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int H, bool W2> cudaError_t launch_bulk(float* theta, float* step, int8_t* sign, const float* vec,
                                                    const float* hid, const float* pre, float* dpre, float* pre_out,
                                                    float* hid_out, double* scal, long long n, double* partials,
                                                    unsigned int* counter, unsigned int* flags,
                                                    const RpropCfg<float>& rc, float slope, cudaStream_t s) {
   using S = Stage<H, W2>;
-  const int smem = 2 * S::kBytes;
+  const int smem = S::kStages * S::kBytes + 128;
   static bool set = false;
   if (!set) {
     cudaError_t e = cudaFuncSetAttribute(k_wpass_bulk<H, W2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     set = true;
   }
+  const long long rowoff = W2 ? (long long)H * n : 0;  // W2^T or W1 rows
+  WMaps maps;
+  if (!make_rows_map(&maps.w, theta + rowoff, n, H, false) || !make_rows_map(&maps.st, step + rowoff, n, H, false) ||
+      !make_rows_map(&maps.sg, sign + rowoff, n, H, true))
+    return cudaErrorInvalidValue;
   const long long grid = bulk_grid(n);
-  k_wpass_bulk<H, W2><<<(unsigned)grid, kCols, smem, s>>>(theta, step, sign, vec, hid, pre, dpre, pre_out, hid_out,
-                                                          scal, n, partials, counter, flags, rc, slope);
+  k_wpass_bulk<H, W2><<<(unsigned)grid, kThreads, smem, s>>>(maps, theta, step, sign, vec, hid, pre, dpre, pre_out,
+                                                             hid_out, scal, n, partials, counter, flags, rc, slope);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-bool wpass_bulk_ok(int H, long long n) { return H >= 8 && H <= 24 && n % kCols == 0 && n >= kCols; }
+bool wpass_bulk_ok(int H, long long n) {
+  return H >= 8 && H <= 24 && n % kCols == 0 && n >= kCols && tma_encoder() != nullptr;
+}
 
 #define QST_BULK_SWITCH(H, ...)                                 \
   switch (H) {                                                  \

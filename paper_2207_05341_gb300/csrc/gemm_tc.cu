@@ -138,7 +138,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 
 __global__ void __launch_bounds__(128, 1) k_tc_cgemm(const __grid_constant__ TcMaps maps, float2* __restrict__ C,
                                                       int d, int lower, uint32_t idesc, const double* sA,
-                                                      const double* sB, unsigned int* err) {
+                                                      const double* sB, unsigned int* err, unsigned int* clear) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
@@ -153,6 +153,8 @@ __global__ void __launch_bounds__(128, 1) k_tc_cgemm(const __grid_constant__ TcM
   else { I = blockIdx.y; J = blockIdx.x; }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
+  // the max slot behind this product's operand scale was read by the kernel that made the planes
+  if (clear && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *clear = 0u;
   if (threadIdx.x == 0) {
     s_fail = 0;
     for (int s = 0; s < kStages; ++s) {
@@ -278,36 +280,9 @@ __global__ void __launch_bounds__(128, 1) k_tc_cgemm(const __grid_constant__ TcM
   }
 }
 
-// Largest |entry| of a complex matrix (as 2 nn floats) -> *s_out = 2^-e with max in [2^e, 2^(e+1)),
-// i.e. the power of two that brings the largest entry into [1, 2).  Last-block reduction.
-__global__ void __launch_bounds__(256) k_absmax_scale(const float* __restrict__ x, long long cnt, double* partials,
-                                                       unsigned int* counter, double* s_out) {
-  float m = 0.f;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (long long)gridDim.x * blockDim.x)
-    m = fmaxf(m, fabsf(x[i]));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  __shared__ float red[8];
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float b = 0.f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = fmaxf(b, red[w]);
-    partials[blockIdx.x] = (double)b;
-  }
-  if (last_block_arrived(counter)) {
-    if (threadIdx.x < 32) {
-      double g = 0.0;
-      for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) g = fmax(g, partials[b]);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) g = fmax(g, __shfl_xor_sync(0xffffffffu, g, o));
-      if (threadIdx.x == 0) {
-        *s_out = (g > 0.0 && isfinite(g)) ? ldexp(1.0, -ilogb(g)) : 1.0;
-        *counter = 0u;
-      }
-    }
-  }
-}
+template <class H> struct Pair16;
+template <> struct Pair16<__half> { using T = __half2; };
+template <> struct Pair16<__nv_bfloat16> { using T = __nv_bfloat162; };
 
 template <class H> __device__ __forceinline__ H to16(float v);
 template <> __device__ __forceinline__ __half to16<__half>(float v) { return __float2half_rn(v); }
@@ -315,29 +290,88 @@ template <> __device__ __forceinline__ __nv_bfloat16 to16<__nv_bfloat16>(float v
 __device__ __forceinline__ float from16(__half v) { return __half2float(v); }
 __device__ __forceinline__ float from16(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-// Complex FP32 matrix -> 16-bit hi / lo planes of s * x.  T (nplanes = 6): re, im, -im (hi), re, im, -im (lo);
-// G (nplanes = 4): re, im (hi), re, im (lo).
-// With s_read == NULL no scaling is applied and *s_unit is set to 1.
-template <class H, int NPL>
+// Scale of the FP16 split: 2^-e for the largest |re|, |im| in [2^e, 2^(e+1)) (*amax, float bits, folded
+// in by the kernel that wrote the matrix), i.e. the power of two that brings it into [1, 2); 1 without amax.
+__device__ __forceinline__ double split_scale(const unsigned int* amax) {
+  if (!amax) return 1.0;
+  const double m = (double)__uint_as_float(*reinterpret_cast<const volatile unsigned int*>(amax));
+  return (m > 0.0 && isfinite(m)) ? ldexp(1.0, -ilogb(m)) : 1.0;
+}
+
+// hi = 16-bit rounding of v, lo = 16-bit rounding of the remainder
+template <class H> __device__ __forceinline__ void hi_lo(float v, H& hi, H& lo) {
+  hi = to16<H>(v);
+  lo = to16<H>(v - from16(hi));
+}
+
+// Complex FP32 matrix -> 16-bit hi / lo planes of s * x (G: re, im (hi), re, im (lo)); s = split_scale(amax),
+// written to *s_slot.
+template <class H>
 __global__ void __launch_bounds__(256) k_split(const float2* __restrict__ A, H* __restrict__ P, long long nn,
-                                                const double* s_read, double* s_unit) {
-  const float sc = s_read ? (float)*s_read : 1.f;
-  if (s_read == nullptr && blockIdx.x == 0 && threadIdx.x == 0) *s_unit = 1.0;
+                                                const unsigned int* amax, double* s_slot) {
+  const double sd = split_scale(amax);
+  const float sc = (float)sd;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *s_slot = sd;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (long long)gridDim.x * blockDim.x) {
     const float2 a = A[i];
-    const float re = sc * a.x, im = sc * a.y;
-    const H rh = to16<H>(re), ih = to16<H>(im);
-    if (NPL == 6) {
-      const H nh = to16<H>(-im);
-      P[i] = rh; P[nn + i] = ih; P[2 * nn + i] = nh;
-      P[3 * nn + i] = to16<H>(re - from16(rh));
-      P[4 * nn + i] = to16<H>(im - from16(ih));
-      P[5 * nn + i] = to16<H>(-im - from16(nh));
-    } else {
-      P[i] = rh; P[nn + i] = ih;
-      P[2 * nn + i] = to16<H>(re - from16(rh));
-      P[3 * nn + i] = to16<H>(im - from16(ih));
+    H rh, rl, ih, il;
+    hi_lo(sc * a.x, rh, rl);
+    hi_lo(sc * a.y, ih, il);
+    P[i] = rh; P[nn + i] = ih; P[2 * nn + i] = rl; P[3 * nn + i] = il;
+  }
+}
+
+// The Hermitian T of t (R = t as d x d row-major; T_ii = R_ii, T_ij = R_ij + i R_ji for i > j,
+// T_ji = conj T_ij), written straight into the 6 planes of s * T: re, im, -im (hi), then (lo);
+// s = split_scale(amax) (max |t| folded in by the kernel that wrote t), written to *s_slot.  One CTA
+// per 32 x 32 tile pair (I, J), I >= J; a thread writes 2 adjacent columns of every plane.
+template <class H>
+__global__ void __launch_bounds__(256) k_hermitian_planes(const float* __restrict__ t, int d, H* __restrict__ P,
+                                                           const unsigned int* amax, double* s_slot) {
+  __shared__ float Ra[32][33];
+  __shared__ float Rb[32][33];
+  const double sd = split_scale(amax);
+  const float sc = (float)sd;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *s_slot = sd;
+  const long long nn = (long long)d * d;
+  int I, J;
+  tri_decode(blockIdx.x, I, J);
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    const int r = e >> 5, c = e & 31;
+    Ra[r][c] = t[(long long)(I * 32 + r) * d + J * 32 + c];
+    if (I != J) Rb[r][c] = t[(long long)(J * 32 + r) * d + I * 32 + c];
+  }
+  __syncthreads();
+  auto put = [&](long long idx, float re0, float im0, float re1, float im1) {
+    H h[6][2];
+    hi_lo(sc * re0, h[0][0], h[3][0]);
+    hi_lo(sc * im0, h[1][0], h[4][0]);
+    hi_lo(-(sc * im0), h[2][0], h[5][0]);
+    hi_lo(sc * re1, h[0][1], h[3][1]);
+    hi_lo(sc * im1, h[1][1], h[4][1]);
+    hi_lo(-(sc * im1), h[2][1], h[5][1]);
+#pragma unroll
+    for (int p = 0; p < 6; ++p) {
+      typename Pair16<H>::T v;
+      v.x = h[p][0];
+      v.y = h[p][1];
+      *reinterpret_cast<typename Pair16<H>::T*>(P + p * nn + idx) = v;
     }
+  };
+  for (int e = threadIdx.x; e < 32 * 16; e += blockDim.x) {
+    const int r = e >> 4, c = (e & 15) * 2;
+    float re[2], im[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int cc = c + u;
+      if (I != J) { re[u] = Ra[r][cc]; im[u] = Rb[cc][r]; }
+      else if (r > cc) { re[u] = Ra[r][cc]; im[u] = Ra[cc][r]; }
+      else if (r < cc) { re[u] = Ra[cc][r]; im[u] = -Ra[r][cc]; }
+      else { re[u] = Ra[r][r]; im[u] = 0.f; }
+    }
+    put((long long)(I * 32 + r) * d + J * 32 + c, re[0], im[0], re[1], im[1]);
+    if (I != J)  // tile (J, I): T[J*32 + r][I*32 + c] = conj T[I*32 + c][J*32 + r]
+      put((long long)(J * 32 + r) * d + I * 32 + c, Ra[c][r], -Rb[r][c], Ra[c + 1][r], -Rb[r][c + 1]);
   }
 }
 
@@ -389,7 +423,7 @@ cudaError_t build_maps(TcMaps* M, int d, const void* Ab, int a_planes_are_T, con
 }
 
 cudaError_t launch_tc(const TcMaps& M, float2* C, int d, bool lower, int fmt, const double* sA, const double* sB,
-                      unsigned int* err, cudaStream_t s) {
+                      unsigned int* err, unsigned int* clear, cudaStream_t s) {
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_tc_cgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
@@ -398,14 +432,17 @@ cudaError_t launch_tc(const TcMaps& M, float2* C, int d, bool lower, int fmt, co
   }
   const int nt = d / kBM;
   if (lower) {
-    k_tc_cgemm<<<(unsigned)(nt * (nt + 1) / 2), 128, kSmemBytes, s>>>(M, C, d, 1, make_idesc(fmt), sA, sB, err);
+    k_tc_cgemm<<<(unsigned)(nt * (nt + 1) / 2), 128, kSmemBytes, s>>>(M, C, d, 1, make_idesc(fmt), sA, sB, err,
+                                                                       clear);
   } else {
-    k_tc_cgemm<<<dim3(nt, nt), 128, kSmemBytes, s>>>(M, C, d, 0, make_idesc(fmt), sA, sB, err);
+    k_tc_cgemm<<<dim3(nt, nt), 128, kSmemBytes, s>>>(M, C, d, 0, make_idesc(fmt), sA, sB, err, clear);
   }
   return cudaGetLastError();
 }
 
 }  // namespace
+
+void* tma_encoder() { return reinterpret_cast<void*>(encode_fn()); }
 
 bool tc_available() {
   int dev = 0, major = 0, minor = 0;
@@ -416,53 +453,46 @@ bool tc_available() {
   return encode_fn() != nullptr;
 }
 
-static cudaError_t split_any(int d, const float2* A, void* P, int nplanes, int fmt, double* s_slot, double* partials,
-                             unsigned int* counter, cudaStream_t s) {
-  const long long nn = (long long)d * d;
-  long long blocks = (nn + 255) / 256;
-  if (blocks > 1024) blocks = 1024;
-  const double* sp = nullptr;
-  if (fmt == TC_FP16_SCALED) {
-    k_absmax_scale<<<(unsigned)blocks, 256, 0, s>>>(reinterpret_cast<const float*>(A), 2 * nn, partials, counter,
-                                                   s_slot);
-    sp = s_slot;
-  }
-  if (fmt == TC_BF16) {
-    if (nplanes == 6) k_split<__nv_bfloat16, 6><<<(unsigned)blocks, 256, 0, s>>>(A, (__nv_bfloat16*)P, nn, sp, s_slot);
-    else k_split<__nv_bfloat16, 4><<<(unsigned)blocks, 256, 0, s>>>(A, (__nv_bfloat16*)P, nn, sp, s_slot);
-  } else {
-    if (nplanes == 6) k_split<__half, 6><<<(unsigned)blocks, 256, 0, s>>>(A, (__half*)P, nn, sp, s_slot);
-    else k_split<__half, 4><<<(unsigned)blocks, 256, 0, s>>>(A, (__half*)P, nn, sp, s_slot);
-  }
+cudaError_t tc_planes_T(int d, const float* t, void* Tb, int fmt, double* scal, const unsigned int* amax,
+                        cudaStream_t s) {
+  if (d < 32 || d % 32) return cudaErrorInvalidValue;
+  const int nt = d / 32;
+  const unsigned pairs = (unsigned)(nt * (nt + 1) / 2);
+  if (fmt == TC_BF16)
+    k_hermitian_planes<__nv_bfloat16><<<pairs, 256, 0, s>>>(t, d, (__nv_bfloat16*)Tb, nullptr, scal + kScaleT);
+  else
+    k_hermitian_planes<__half><<<pairs, 256, 0, s>>>(t, d, (__half*)Tb, amax, scal + kScaleT);
   return cudaGetLastError();
 }
 
-cudaError_t tc_split_T(int d, const float2* T, void* Tb, int fmt, double* scal, double* partials,
-                       unsigned int* counter, cudaStream_t s) {
-  return split_any(d, T, Tb, 6, fmt, scal + kScaleT, partials, counter, s);
-}
-
-cudaError_t tc_split_G(int d, const float2* G, void* Gb, int fmt, double* scal, double* partials,
-                       unsigned int* counter, cudaStream_t s) {
-  return split_any(d, G, Gb, 4, fmt, scal + kScaleG, partials, counter, s);
+cudaError_t tc_split_G(int d, const float2* G, void* Gb, int fmt, double* scal, const unsigned int* amax,
+                       cudaStream_t s) {
+  const long long nn = (long long)d * d;
+  long long blocks = (nn + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  if (fmt == TC_BF16)
+    k_split<__nv_bfloat16><<<(unsigned)blocks, 256, 0, s>>>(G, (__nv_bfloat16*)Gb, nn, nullptr, scal + kScaleG);
+  else
+    k_split<__half><<<(unsigned)blocks, 256, 0, s>>>(G, (__half*)Gb, nn, amax, scal + kScaleG);
+  return cudaGetLastError();
 }
 
 cudaError_t tc_herm_square(int d, const void* Tb, int fmt, const double* scal, float2* X, unsigned int* err,
-                           cudaStream_t s) {
+                           unsigned int* clear, cudaStream_t s) {
   if (d < 128 || d % 128) return cudaErrorInvalidValue;
   TcMaps M;
   cudaError_t e = build_maps(&M, d, Tb, 1, Tb, fmt);
   if (e != cudaSuccess) return e;
-  return launch_tc(M, X, d, true, fmt, scal + kScaleT, scal + kScaleT, err, s);
+  return launch_tc(M, X, d, true, fmt, scal + kScaleT, scal + kScaleT, err, clear, s);
 }
 
 cudaError_t tc_gt_product(int d, const void* Gb, const void* Tb, int fmt, const double* scal, float2* Y,
-                          unsigned int* err, cudaStream_t s) {
+                          unsigned int* err, unsigned int* clear, cudaStream_t s) {
   if (d < 128 || d % 128) return cudaErrorInvalidValue;
   TcMaps M;
   cudaError_t e = build_maps(&M, d, Gb, 0, Tb, fmt);
   if (e != cudaSuccess) return e;
-  return launch_tc(M, Y, d, false, fmt, scal + kScaleG, scal + kScaleT, err, s);
+  return launch_tc(M, Y, d, false, fmt, scal + kScaleG, scal + kScaleT, err, clear, s);
 }
 
 }  // namespace qst

@@ -20,6 +20,9 @@ struct Dims {
 
 Dims make_dims(int N, bool fp64);
 
+// Raise a kernel's dynamic shared-memory limit to `bytes` (cached: one attribute call per size).
+cudaError_t ensure_dynamic_smem(const void* fn, size_t bytes);
+
 // Device buffers of a context (all owned by the context).
 template <class R> struct Work {
   using V = cx_t<R>;
@@ -46,7 +49,13 @@ template <class R> struct Work {
   void* Gb;            // 4 planes of d x d bf16: re_hi, im_hi, re_lo, im_lo
 };
 
-enum Counter { CNT_L1 = 0, CNT_T = 1, CNT_NLL = 2, CNT_W2 = 3, CNT_W1 = 4, CNT_MAXT = 5, CNT_MAXG = 6, CNT_COUNT = 8 };
+enum Counter {
+  CNT_L1 = 0, CNT_T = 1, CNT_NLL = 2, CNT_W2 = 3, CNT_W1 = 4,
+  CNT_AMAXT = 8,  // max |re|, |im| of T as float bits: folded in by the producer of t, read by the plane
+                  // writer, cleared by the product that reads the planes
+  CNT_AMAXG = 9,  // the same for G
+  CNT_COUNT = 16
+};
 constexpr int kScaleT = 3;  // scal slot of the power-of-two scale of T (mixed path)
 constexpr int kScaleG = 4;  // scal slot of the scale of G
 constexpr int kPartialBlocks = 1024;   // max blocks of a reducing kernel
@@ -64,7 +73,16 @@ template <class R> cudaError_t povm_hi_fwd(const Dims& D, const R* W, R* p, cons
 template <class R> cudaError_t povm_hi_nll(const Dims& D, const R* W, const R* f, double* scal, R* Wadj,
                                            double* partials, unsigned int* counter, unsigned int* flags,
                                            const PovmB<R>& B, bool adjoint, cudaStream_t s);
-template <class R> cudaError_t povm_lo_adj(const Dims& D, const R* Wadj, cx_t<R>* G, const PovmB<R>& B, cudaStream_t s);
+// amax (may be NULL): the largest |re|, |im| of G is folded into *amax (float bits).
+template <class R>
+cudaError_t povm_lo_adj(const Dims& D, const R* Wadj, cx_t<R>* G, const PovmB<R>& B, unsigned int* amax,
+                        cudaStream_t s);
+// register-row implementations of the high pass (povm_reg.cu), used when povm_hi_reg_ok(D)
+bool povm_hi_reg_ok(const Dims& D);
+template <class R> cudaError_t povm_hi_fwd_reg(const Dims& D, const R* W, R* p, const PovmB<R>& B, cudaStream_t s);
+template <class R> cudaError_t povm_hi_nll_reg(const Dims& D, const R* W, const R* f, double* scal, R* Wadj,
+                                               double* partials, unsigned int* counter, unsigned int* flags,
+                                               const PovmB<R>& B, bool adjoint, cudaStream_t s);
 // scal[0] = Tr X = sum_i Re X_ii of the computed X (fixed-order FP64 sum)
 template <class R> cudaError_t trace_X(const Dims& D, const cx_t<R>* X, double* scal, cudaStream_t s);
 // full Hermitian matrix from its lower tiles, scaled by 1 / scal[0] (rho = X / Tr X)
@@ -75,7 +93,11 @@ template <class R> cudaError_t hermitian_complete(const Dims& D, const cx_t<R>* 
 template <class R> cudaError_t net_l1_forward(const Dims& D, const R* theta, const R* f, R* pre, R* hid,
                                               double* scal, double* partials, unsigned int* counter,
                                               const NetCfg& c, cudaStream_t s);
-template <class R> cudaError_t net_build_T(const Dims& D, const R* theta, const R* hid, cx_t<R>* T, cudaStream_t s);
+// t = W2 h + b2 into the scratch t (n reals); then, when T != NULL, the Hermitian T of t (a second
+// launch).  amax (may be NULL): max |t_i| (= the largest |re|, |im| of T) is folded into *amax (float bits).
+template <class R>
+cudaError_t net_build_T(const Dims& D, const R* theta, const R* hid, R* t, cx_t<R>* T, unsigned int* amax,
+                        cudaStream_t s);
 template <class R> cudaError_t net_w2_pass(const Dims& D, R* theta, R* step, int8_t* sign, const R* dt,
                                            const R* hid, const R* pre, R* dpre, R* dtheta,
                                            double* partials, unsigned int* counter, const NetCfg& c,
@@ -122,18 +144,23 @@ template <class R> cudaError_t cgemm_simt(int d, const cx_t<R>* A, const cx_t<R>
 
 // ---- tensor-core products (gemm_tc.cu) ----
 enum TcFormat { TC_FP16_SCALED = 0, TC_BF16 = 1 };
-// 16-bit hi / lo operand planes of T (6 planes: re, im, -im; hi then lo) and G (4 planes: re, im; hi
-// then lo).  TC_FP16_SCALED first scales by a power of two (scal[kScaleT] / scal[kScaleG]).
-cudaError_t tc_split_T(int d, const float2* T, void* Tb, int fmt, double* scal, double* partials,
-                       unsigned int* counter, cudaStream_t s);
-cudaError_t tc_split_G(int d, const float2* G, void* Gb, int fmt, double* scal, double* partials,
-                       unsigned int* counter, cudaStream_t s);
+// 16-bit hi / lo operand planes of T (6 planes: re, im, -im; hi then lo), made straight from t (T is the
+// Hermitian matrix of t, as in net_build_T), and of G (4 planes: re, im; hi then lo).  TC_FP16_SCALED first
+// scales by the power of two (written to scal[kScaleT] / scal[kScaleG]) that brings *amax, the largest
+// magnitude folded in by the producer of t or G, into [1, 2).
+cudaError_t tc_planes_T(int d, const float* t, void* Tb, int fmt, double* scal, const unsigned int* amax,
+                        cudaStream_t s);
+cudaError_t tc_split_G(int d, const float2* G, void* Gb, int fmt, double* scal, const unsigned int* amax,
+                       cudaStream_t s);
 // X = T T (lower 128 x 128 tiles) and Y = G T (full) on tcgen05, complex FP32 out (unscaled);
-// a device-side wait that runs out sets *err != 0.
+// a device-side wait that runs out sets *err != 0.  clear (may be NULL) is zeroed by the kernel: the max
+// slot of the operand planes it reads, ready for the next producer.
 cudaError_t tc_herm_square(int d, const void* Tb, int fmt, const double* scal, float2* X, unsigned int* err,
-                           cudaStream_t s);
+                           unsigned int* clear, cudaStream_t s);
 cudaError_t tc_gt_product(int d, const void* Gb, const void* Tb, int fmt, const double* scal, float2* Y,
-                          unsigned int* err, cudaStream_t s);
+                          unsigned int* err, unsigned int* clear, cudaStream_t s);
 bool tc_available();
+// cuTensorMapEncodeTiled from the driver (NULL when unavailable).
+void* tma_encoder();
 
 }  // namespace qst

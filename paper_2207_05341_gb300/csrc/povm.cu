@@ -17,9 +17,25 @@
 // Hermitian d x d matrix G = sum_k g_k M_k.
 #include <float.h>
 
+#include <mutex>
+#include <unordered_map>
+
 #include "impl.h"
 
 namespace qst {
+
+// cudaFuncSetAttribute once per kernel and size (host calls between launches leave the GPU idle).
+cudaError_t ensure_dynamic_smem(const void* fn, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  static std::mutex mu;
+  static std::unordered_map<const void*, size_t> done;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = done.find(fn);
+  if (it != done.end() && it->second >= bytes) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done[fn] = bytes;
+  return e;
+}
 
 Dims make_dims(int N, bool fp64) {
   Dims D;
@@ -115,7 +131,7 @@ __global__ void __launch_bounds__(256) k_povm_lo_fwd(const cx_t<R>* __restrict__
 
 template <class R>
 __global__ void __launch_bounds__(256) k_povm_lo_adj(const R* __restrict__ W, cx_t<R>* __restrict__ G,
-                                                      int N, int g, PovmB<R> B) {
+                                                      int N, int g, PovmB<R> B, unsigned int* amax) {
   using V = cx_t<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* Z = reinterpret_cast<V*>(smem_raw);
@@ -134,10 +150,14 @@ __global__ void __launch_bounds__(256) k_povm_lo_adj(const R* __restrict__ W, cx
   __syncthreads();
   apply_modes<R, true>(Z, g, pitch, 0, g, B);
   V* dst = G + (long long)I * S * d + (long long)J * S;
+  float m = 0.f;
   for (int e = threadIdx.x; e < S * S; e += blockDim.x) {
     const int il = e >> g, jl = e & (S - 1);
-    dst[il * d + jl] = Z[il * pitch + jl];
+    const V z = Z[il * pitch + jl];
+    dst[il * d + jl] = z;
+    m = fmaxf(m, fmaxf(fabsf((float)z.x), fabsf((float)z.y)));
   }
+  if (amax) block_absmax_to(m, amax);  // the mirrored tile holds the same magnitudes
   if (I != J) {
     V* mir = G + (long long)J * S * d + (long long)I * S;
     for (int e = threadIdx.x; e < S * S; e += blockDim.x) {
@@ -308,10 +328,7 @@ __global__ void __launch_bounds__(256) k_herm_complete(const cx_t<R>* __restrict
 // ---------------------------------------------------------------- launchers
 static int ilog2i(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
 
-template <class R> static cudaError_t set_smem(const void* fn, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
+template <class R> static cudaError_t set_smem(const void* fn, size_t bytes) { return ensure_dynamic_smem(fn, bytes); }
 
 template <class R>
 cudaError_t povm_lo_fwd(const Dims& D, const cx_t<R>* X, R* W, const PovmB<R>& B, cudaStream_t s) {
@@ -324,17 +341,19 @@ cudaError_t povm_lo_fwd(const Dims& D, const cx_t<R>* X, R* W, const PovmB<R>& B
 }
 
 template <class R>
-cudaError_t povm_lo_adj(const Dims& D, const R* Wadj, cx_t<R>* G, const PovmB<R>& B, cudaStream_t s) {
+cudaError_t povm_lo_adj(const Dims& D, const R* Wadj, cx_t<R>* G, const PovmB<R>& B, unsigned int* amax,
+                        cudaStream_t s) {
   const size_t sm = (size_t)D.S * (D.S + 1) * sizeof(cx_t<R>);
   cudaError_t e = set_smem<R>((const void*)k_povm_lo_adj<R>, sm);
   if (e != cudaSuccess) return e;
   const unsigned tiles = (unsigned)(D.nb * (D.nb + 1) / 2);
-  k_povm_lo_adj<R><<<tiles, 256, sm, s>>>(Wadj, G, D.N, D.g, B);
+  k_povm_lo_adj<R><<<tiles, 256, sm, s>>>(Wadj, G, D.N, D.g, B, amax);
   return cudaGetLastError();
 }
 
 template <class R>
 cudaError_t povm_hi_fwd(const Dims& D, const R* W, R* p, const PovmB<R>& B, cudaStream_t s) {
+  if (povm_hi_reg_ok(D)) return povm_hi_fwd_reg<R>(D, W, p, B, s);
   const size_t sm = (size_t)D.nb * D.nb * D.C * sizeof(cx_t<R>);
   cudaError_t e = set_smem<R>((const void*)k_povm_hi_fwd<R>, sm);
   if (e != cudaSuccess) return e;
@@ -347,6 +366,7 @@ template <class R>
 cudaError_t povm_hi_nll(const Dims& D, const R* W, const R* f, double* scal, R* Wadj, double* partials,
                         unsigned int* counter, unsigned int* flags, const PovmB<R>& B, bool adjoint,
                         cudaStream_t s) {
+  if (povm_hi_reg_ok(D)) return povm_hi_nll_reg<R>(D, W, f, scal, Wadj, partials, counter, flags, B, adjoint, s);
   const size_t sm = (size_t)D.nb * D.nb * D.C * sizeof(cx_t<R>);
   cudaError_t e = set_smem<R>((const void*)k_povm_hi_nll<R>, sm);
   if (e != cudaSuccess) return e;
@@ -373,7 +393,8 @@ cudaError_t hermitian_complete(const Dims& D, const cx_t<R>* Xlow, cx_t<R>* rho,
 
 #define QST_INST(R)                                                                                        \
   template cudaError_t povm_lo_fwd<R>(const Dims&, const cx_t<R>*, R*, const PovmB<R>&, cudaStream_t);       \
-  template cudaError_t povm_lo_adj<R>(const Dims&, const R*, cx_t<R>*, const PovmB<R>&, cudaStream_t);       \
+  template cudaError_t povm_lo_adj<R>(const Dims&, const R*, cx_t<R>*, const PovmB<R>&, unsigned int*,      \
+                                      cudaStream_t);                                                         \
   template cudaError_t povm_hi_fwd<R>(const Dims&, const R*, R*, const PovmB<R>&, cudaStream_t);             \
   template cudaError_t povm_hi_nll<R>(const Dims&, const R*, const R*, double*, R*, double*, unsigned int*,  \
                                       unsigned int*, const PovmB<R>&, bool, cudaStream_t);                   \

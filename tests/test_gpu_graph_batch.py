@@ -28,7 +28,7 @@ def _inputs(N, seed):
     return f.astype(np.float32), synth.init_theta(N, 60 + seed).astype(np.float32)
 
 
-def _run(N, f, theta, steps, prec, graph):
+def _run(N, f, theta, steps, prec, graph, timing=False, extra=None):
     stream = torch.cuda.Stream()
     o = qst.qst_default_options()
     o.precision = prec
@@ -36,6 +36,8 @@ def _run(N, f, theta, steps, prec, graph):
     try:
         if graph:
             qst.qst_graph_enable(ctx, True)
+        if timing:
+            qst.qst_timing_enable(ctx, steps)
         qst.qst_set_params(ctx, theta)
         fd = torch.from_numpy(f).cuda()
         torch.cuda.synchronize()
@@ -43,6 +45,10 @@ def _run(N, f, theta, steps, prec, graph):
         out = torch.empty(theta.size, device="cuda")
         qst.qst_get_params(ctx, out)
         qst.qst_sync(ctx)
+        if extra is not None:
+            extra["launches"] = qst.qst_kernel_launches(ctx)
+            if timing:
+                extra["timing"] = qst.qst_timing_read(ctx)
         return losses, out.cpu().numpy(), qst.qst_iterations(ctx)
     finally:
         qst.qst_destroy(ctx)
@@ -55,6 +61,26 @@ def test_graph_replay_is_bit_identical(N, prec):
     lb, tb, ib = _run(N, f, theta, 6, prec, graph=True)
     assert la == lb and ia == ib == 6
     assert np.array_equal(ta, tb)
+
+
+@pytest.mark.parametrize("prec", [qst.QST_FP32, qst.QST_MIXED])
+def test_timed_graph_replay(prec):
+    """Phase events captured as graph nodes: same results and launch count as the
+    launch-by-launch path, and every phase of the latest replay is timed once."""
+    N = 7
+    f, theta = _inputs(N, 3)
+    xa, xb = {}, {}
+    la, ta, _ = _run(N, f, theta, 5, prec, graph=False, timing=True, extra=xa)
+    lb, tb, _ = _run(N, f, theta, 5, prec, graph=True, timing=True, extra=xb)
+    assert la == lb and np.array_equal(ta, tb)
+    assert xa["launches"] == xb["launches"] > 0
+    tm = xb["timing"]
+    timed = [p for p in qst.PHASES if tm[p][1] > 0]
+    assert "hidden" not in timed  # a replay does not recompute the f-dependent activation
+    assert {"build_T", "povm_lo", "povm_hi", "w2", "w1"} <= set(timed)
+    assert all(tm[p][1] == 1 and tm[p][0] > 0 for p in timed)
+    # the launch-by-launch path recorded all five steps
+    assert xa["timing"]["w2"][1] == 5 and xa["timing"]["hidden"][1] == 1
 
 
 def test_graph_needs_a_stream():
