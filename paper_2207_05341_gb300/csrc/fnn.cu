@@ -63,12 +63,16 @@ __device__ __forceinline__ void final_reduce(const double* partials, int M, F fi
   }
 }
 
-static int stream_grid(long long nvec) {
-  int dev = 0, sms = 152;
+// Grid of a grid-stride streaming kernel: one wave of resident 256-thread CTAs (a CTA that had to wait
+// for a free slot would run its whole share after the others), at most one thread per vector.
+template <class K> static int stream_grid(K kernel, long long nvec) {
+  int dev = 0, sms = 152, per = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 256, 0);
+  if (per < 1) per = 1;
   long long want = (nvec + 255) / 256;
-  long long cap = 4LL * sms;
+  long long cap = (long long)per * sms;
   if (cap > kPartialBlocks) cap = kPartialBlocks;
   if (want > cap) want = cap;
   if (want < 1) want = 1;
@@ -410,8 +414,11 @@ template <class R> static RpropCfg<R> rcfg(const NetCfg& c) {
 template <class R>
 cudaError_t net_l1_forward(const Dims& D, const R* theta, const R* f, R* pre, R* hid, double* scal,
                            double* partials, unsigned int* counter, const NetCfg& c, cudaStream_t s) {
-  const int grid = stream_grid(D.n / Vec<R>::W);
-  QST_SWITCH_H(D.H, k_l1_forward<R, HH><<<grid, 256, 0, s>>>(theta, f, D.n, pre, hid, scal, partials, counter, (R)c.slope));
+  // the grid of the W1 pass, whose sums this forward must reproduce bit for bit
+  QST_SWITCH_H(D.H, {
+    const int grid = stream_grid(k_w1_pass<R, HH, true>, D.n / Vec<R>::W);
+    k_l1_forward<R, HH><<<grid, 256, 0, s>>>(theta, f, D.n, pre, hid, scal, partials, counter, (R)c.slope);
+  });
   return cudaGetLastError();
 }
 
@@ -444,13 +451,15 @@ template <class R>
 cudaError_t net_w2_pass(const Dims& D, R* theta, R* step, int8_t* sign, const R* dt, const R* hid, const R* pre,
                         R* dpre, R* dtheta, double* partials, unsigned int* counter, const NetCfg& c, bool update,
                         cudaStream_t s) {
-  const int grid = stream_grid(D.n / Vec<R>::W);
+  const long long nv = D.n / Vec<R>::W;
   if (update) {
-    QST_SWITCH_H(D.H, k_w2_pass<R, HH, true><<<grid, 256, 0, s>>>(theta, step, sign, dt, hid, pre, dpre, dtheta, D.n,
-                                                                 partials, counter, rcfg<R>(c), (R)c.slope));
+    QST_SWITCH_H(D.H, k_w2_pass<R, HH, true><<<stream_grid(k_w2_pass<R, HH, true>, nv), 256, 0, s>>>(
+                          theta, step, sign, dt, hid, pre, dpre, dtheta, D.n, partials, counter, rcfg<R>(c),
+                          (R)c.slope));
   } else {
-    QST_SWITCH_H(D.H, k_w2_pass<R, HH, false><<<grid, 256, 0, s>>>(theta, step, sign, dt, hid, pre, dpre, dtheta, D.n,
-                                                                  partials, counter, rcfg<R>(c), (R)c.slope));
+    QST_SWITCH_H(D.H, k_w2_pass<R, HH, false><<<stream_grid(k_w2_pass<R, HH, false>, nv), 256, 0, s>>>(
+                          theta, step, sign, dt, hid, pre, dpre, dtheta, D.n, partials, counter, rcfg<R>(c),
+                          (R)c.slope));
   }
   return cudaGetLastError();
 }
@@ -459,13 +468,16 @@ template <class R>
 cudaError_t net_w1_pass(const Dims& D, R* theta, R* step, int8_t* sign, const R* f, const R* dpre, R* pre, R* hid,
                         R* dtheta, double* scal, double* partials, unsigned int* counter, const NetCfg& c,
                         bool update, cudaStream_t s) {
-  const int grid = stream_grid(D.n / Vec<R>::W);
+  const long long nv = D.n / Vec<R>::W;
+  // both variants use the grid of the updating pass (the partition k_l1_forward reproduces)
   if (update) {
-    QST_SWITCH_H(D.H, k_w1_pass<R, HH, true><<<grid, 256, 0, s>>>(theta, step, sign, f, dpre, pre, hid, dtheta, D.n,
-                                                                 scal, partials, counter, rcfg<R>(c), (R)c.slope));
+    QST_SWITCH_H(D.H, k_w1_pass<R, HH, true><<<stream_grid(k_w1_pass<R, HH, true>, nv), 256, 0, s>>>(
+                          theta, step, sign, f, dpre, pre, hid, dtheta, D.n, scal, partials, counter, rcfg<R>(c),
+                          (R)c.slope));
   } else {
-    QST_SWITCH_H(D.H, k_w1_pass<R, HH, false><<<grid, 256, 0, s>>>(theta, step, sign, f, dpre, pre, hid, dtheta, D.n,
-                                                                  scal, partials, counter, rcfg<R>(c), (R)c.slope));
+    QST_SWITCH_H(D.H, k_w1_pass<R, HH, false><<<stream_grid(k_w1_pass<R, HH, true>, nv), 256, 0, s>>>(
+                          theta, step, sign, f, dpre, pre, hid, dtheta, D.n, scal, partials, counter, rcfg<R>(c),
+                          (R)c.slope));
   }
   return cudaGetLastError();
 }

@@ -1,18 +1,18 @@
 // Rprop weight passes of the Sec. 3.1 network (FP32, in-place update) with bulk-copy staging.
 //
 // Each CTA walks chunks of kCols consecutive columns of the 4^N axis (chunk c to CTA
-// c mod grid).  The CTA is warp-specialised: one producer thread issues, per chunk, one
-// 2-D tensor copy (cp.async.bulk.tensor, box kCols x H) of each parameter array
-// (weights, Rprop steps, previous signs: H rows n apart) and 1-D bulk copies of the
+// c mod grid, one CTA per SM).  The CTA is warp-specialised: one producer thread issues,
+// per chunk, one 2-D tensor copy (cp.async.bulk.tensor, box kCols x H) of each parameter
+// array (weights, Rprop steps, previous signs: H rows n apart) and 1-D bulk copies of the
 // chunk of dt (W2 pass) or f (W1 pass) and of b2's state, all counted on the stage's
-// "full" mbarrier, into a ring of kStages shared-memory stages; kCols consumer threads
-// update a chunk in shared memory (one column per thread, all H rows) and arrive on the
-// stage's "empty" mbarrier (kGroups threads per column, each with about H / kGroups of the rows,
-// so that enough warps hide the latency of the update); the producer then writes the boxes back with tensor stores
-// and refills the stage once the stores have read it.  A handful of copies per chunk
-// keeps the copy engine's per-instruction cost off the critical path.  Loads run
-// about kStages - 2 chunks ahead of the consumers and nobody waits for a store to drain, so
-// the pass streams at HBM rate.
+// "full" mbarrier, into a ring of kStages shared-memory stages.  The consumer threads
+// (kGroups per column, each with about H / kGroups of the rows, enough warps to hide the
+// latency of the update) update the chunk in shared memory and arrive on the stage's
+// "empty" mbarrier; the producer then writes the boxes back with tensor stores and
+// refills the stage once the stores have read it.  A handful of copies per chunk keeps
+// the copy engine's per-instruction cost off the critical path, and nobody waits for a
+// store to drain.  The shape (256 columns, 2 row groups, 3 stages, one CTA per SM) is
+// the fastest of a sweep over chunk width, row groups, ring depth and CTAs per SM.
 //
 // The arithmetic is that of k_w2_pass / k_w1_pass in fnn.cu (same Rprop; the sums
 // over the 4^N axis are per-thread partials reduced in a fixed order, so the pass is
@@ -27,12 +27,14 @@ namespace qst {
 
 namespace {
 
-constexpr int kCols = 128;                  // columns per chunk
+constexpr int kCols = 256;                  // columns per chunk
 constexpr int kConsumerWarps = kCols / 32;  // warps over the columns of one row group
-constexpr int kGroups = 4;                  // row groups: consumer threads per column
+constexpr int kGroups = 2;                  // row groups: consumer threads per column
 constexpr int kConsumers = kCols * kGroups;
 constexpr int kThreads = kConsumers + 32;   // + one producer warp
-constexpr int kMaxStages = 4;
+constexpr int kMaxStages = 3;
+constexpr int kCtasPerSm = 1;
+constexpr int kRingBytes = 220 * 1024;      // shared memory of one CTA's ring (228 KB per SM)
 constexpr unsigned long long kWait = 4000000000ULL;
 
 __device__ __forceinline__ uint32_t s_u32(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
@@ -107,10 +109,15 @@ template <int H, bool W2> struct Stage {
   static constexpr int kBw = kVec + kCols * 4;
   static constexpr int kBst = kBw + kCols * 4;
   static constexpr int kBsg = kBst + kCols * 4;
-  static constexpr int kBytes = W2 ? kBsg + kCols : kBw;  // multiple of 16
-  static constexpr uint32_t kTx = (uint32_t)kBytes;
-  // ring depth: 4 stages while two CTAs still fit on an SM (228 KB), else 3
-  static constexpr int kStages = 4 * kBytes <= 110 * 1024 ? 4 : 3;
+  static constexpr int kUsed = W2 ? kBsg + kCols : kBw;   // bytes the copies of one chunk bring in
+  static constexpr int kBytes = (kUsed + 127) / 128 * 128;  // stage pitch: every stage 128-byte aligned
+  static constexpr uint32_t kTx = (uint32_t)kUsed;
+  static_assert(kSt % 128 == 0 && kSg % 128 == 0 && kVec % 128 == 0 && kBw % 16 == 0 && kBst % 16 == 0 &&
+                    kBsg % 16 == 0 && kCols % 16 == 0 && kCols <= 256,
+                "tensor-copy destinations must be 128-byte aligned, bulk-copy ones 16-byte aligned");
+  // ring depth: as many stages as fit in kRingBytes, at most kMaxStages (a deeper ring measured slower)
+  static constexpr int kStages = kRingBytes / kBytes < kMaxStages ? kRingBytes / kBytes : kMaxStages;
+  static_assert(kStages >= 3, "the ring needs three stages");
 };
 
 template <class R> __device__ __forceinline__ R leaky_b(R x, R slope) { return x > R(0) ? x : slope * x; }
@@ -149,7 +156,7 @@ __device__ __forceinline__ void final_sum(const double* partials, int M, F fin) 
 
 // W2 pass (W2 true) or W1 pass (W2 false); see k_w2_pass / k_w1_pass in fnn.cu for the arithmetic.
 template <int H, bool W2>
-__global__ void __launch_bounds__(kThreads, 2) k_wpass_bulk(const __grid_constant__ WMaps maps,
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) k_wpass_bulk(const __grid_constant__ WMaps maps,
                                                           float* __restrict__ theta, float* __restrict__ step,
                                                           int8_t* __restrict__ sign, const float* __restrict__ vec,
                                                           const float* __restrict__ hidv, const float* __restrict__ pre,
@@ -391,7 +398,7 @@ long long bulk_grid(long long n) {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  long long grid = 2LL * sms;
+  long long grid = (long long)kCtasPerSm * sms;
   const long long nchunks = n / kCols;
   if (grid > nchunks) grid = nchunks;
   if (grid > kPartialBlocks) grid = kPartialBlocks;

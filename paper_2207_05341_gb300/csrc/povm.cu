@@ -286,8 +286,18 @@ __global__ void __launch_bounds__(256) k_povm_hi_nll(const R* __restrict__ W, co
 template <class R>
 __global__ void __launch_bounds__(256) k_trace(const cx_t<R>* __restrict__ X, int d, double* scal) {
   __shared__ double red[8];
+  // every diagonal load of a thread is issued before the first add (one memory latency, not d / 256)
+  constexpr int kPer = 16;  // d <= 4096 = 16 x 256
+  R v[kPer];
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int i = threadIdx.x + k * 256;
+    v[k] = i < d ? X[(long long)i * d + i].x : R(0);
+  }
   double acc = 0.0;
-  for (int i = threadIdx.x; i < d; i += blockDim.x) acc += (double)X[(long long)i * d + i].x;
+#pragma unroll
+  for (int k = 0; k < kPer; ++k)
+    if (threadIdx.x + k * 256 < d) acc += (double)v[k];
   acc = warp_sum(acc);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
@@ -378,6 +388,7 @@ cudaError_t povm_hi_nll(const Dims& D, const R* W, const R* f, double* scal, R* 
 }
 
 template <class R> cudaError_t trace_X(const Dims& D, const cx_t<R>* X, double* scal, cudaStream_t s) {
+  if (D.d > 4096) return cudaErrorInvalidValue;
   k_trace<R><<<1, 256, 0, s>>>(X, D.d, scal);
   return cudaGetLastError();
 }
