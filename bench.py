@@ -15,7 +15,6 @@ Under torchrun (N > 1 GPUs) every rank runs its own independent tomography
 from __future__ import annotations
 
 import argparse
-import glob
 import hashlib
 import json
 import os
@@ -127,25 +126,24 @@ def load_peaks():
     return dict(FALLBACK_PEAKS), "fallback"
 
 
-def kernel_sources_hash():
+def sources_hash(files):
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2207_05341_gb300", "csrc", "*"))):
-        h.update(open(f, "rb").read())
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_2207_05341_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(phase, prec_name):
-    """DRAM traffic per launch from the committed ncu summary, if it matches the current sources."""
+def recorded_traffic(phase):
+    """DRAM bytes per launch of the phase's kernel from the committed ncu summary (profiles/traffic.json),
+    or None once that kernel's sources have changed since the counters were taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(p):
-        return None
     try:
-        d = json.load(open(p))
+        e = json.load(open(p))["entries"][phase]
+        if sources_hash(e["sources"]) != e["sha"]:
+            return None
+        return e["bytes_per_launch"]
     except Exception:
         return None
-    if d.get("sources_sha") != kernel_sources_hash():
-        return None
-    return d.get("per_launch_bytes", {}).get(f"{prec_name}:{phase}")
 
 
 # ------------------------------------------------------------------ algorithmic work per phase (N = 11)
@@ -574,7 +572,7 @@ def main_ours(args):
         "gpu_launches": int(res[head]["launches"]),
         "roofline": {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": runit,
                      "frac": achieved / peak, "peak_source": peak_src if bound != "alu" else "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
-                     "traffic": recorded_traffic(dom, head)},
+                     "traffic": recorded_traffic(dom)},
         "paths": {name: {"iters_per_s": ws * args.steps / (v["ms"] / 1e3), "ms_per_step": v["ms"] / args.steps,
                          "ms_per_step_launch_by_launch": v["ms_nograph"] / args.steps,
                          "phase_ms": {k: round(pm[0] / pm[1], 4) for k, pm in v["phases"].items() if pm[1]}}
