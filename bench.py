@@ -167,9 +167,9 @@ def phase_work(phase, N, mixed):
     if phase == "sym":
         return "hbm", 8 * n + 4 * n, "B"
     if phase == "w2":
-        return "hbm", 18 * H * n + 22 * n, "B"
+        return "hbm", 16 * H * n + 20 * n, "B"
     if phase == "w1":
-        return "hbm", 18 * H * n + 4 * n, "B"
+        return "hbm", 16 * H * n + 4 * n, "B"
     if phase == "hidden":
         return "hbm", 4 * H * n + 4 * n, "B"
     return "hbm", 0, "B"
@@ -566,7 +566,7 @@ def main_ours(args):
         "dtype": "fp16x3+f32" if head == "mixed_fp16x3" else "f32", "data": "synthetic",
         "config": {"workload": workload_name(lam), "path": head, "parallelism": "replicas" if ws > 1 else "single",
                    "launch": "one CUDA graph replay per iteration (qst_graph_enable)",
-                   "l2": "inputs larger than L2: 1.7 GB of parameters and Rprop state streamed per step, no flush"},
+                   "l2": "inputs larger than L2: 1.5 GB of parameters and Rprop state (3.3 GB of traffic) per step, no flush"},
         "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"), "reasons": clk.get("reasons")},
         "e2e": {"value": ws * e2e_rate, "unit": UNIT, "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 12},
         "gpu_launches": int(res[head]["launches"]),

@@ -80,7 +80,9 @@ typedef struct qst_options {
     int mapping;        /* QST_MAP_CHOL_H (paper default, Sec. 4.3) or QST_MAP_ABS_P (eq. abs_P) */
     int precision;      /* QST_FP64, QST_FP32, QST_MIXED or QST_MIXED_BF16 (see above) */
     double P;           /* order of the absolute projection A_P; used when mapping == QST_MAP_ABS_P */
-    double lr;          /* Rprop initial step (Sec. 4.1: 0.001) */
+    double lr;          /* Rprop initial step (Sec. 4.1: 0.001); lr, step_min and step_max must lie in
+                           [2^-33, 2^30] (QST_E_INVAL otherwise): the library keeps each parameter's
+                           step and previous gradient sign in one word, exactly, within that range */
     double eta_minus;   /* Rprop shrink factor (0.5) */
     double eta_plus;    /* Rprop growth factor (1.2) */
     double step_min;    /* Rprop step lower bound (1e-6) */

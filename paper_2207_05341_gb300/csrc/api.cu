@@ -16,7 +16,7 @@ using namespace qst;
 
 namespace {
 
-constexpr unsigned long long kStateMagic = 0x5153545354415445ULL;  // "QSTSTATE"
+constexpr unsigned long long kStateMagic = 0x5153545354415432ULL;  // "QSTSTAT2": theta, Rprop state words
 
 // 0: pageable or unknown host memory, 1: page-locked host memory, 2: device or managed memory.
 int ptr_kind(const void* p) {
@@ -139,7 +139,6 @@ template <class R> qst_status alloc_work(qst_ctx* c) {
   const size_t nn = (size_t)D.d * D.d;
   QST_CU(dalloc(c, &w->theta, P));
   QST_CU(dalloc(c, &w->step, P));
-  QST_CU(dalloc(c, &w->sign, P));
   QST_CU(dalloc(c, &w->pre, 32));
   QST_CU(dalloc(c, &w->hid, 32));
   QST_CU(dalloc(c, &w->dpre, 32));
@@ -372,18 +371,18 @@ template <class R> struct Engine {
     if ((st = backward_state(c)) != QST_OK) return st;
     if (use_bulk(c, f)) {
       if constexpr (std::is_same<R, float>::value) {
-        QST_CU(w2_pass_bulk(D, w->theta, w->step, w->sign, w->dt, w->hid, w->pre, w->dpre, w->partials,
+        QST_CU(w2_pass_bulk(D, w->theta, w->step, w->dt, w->hid, w->pre, w->dpre, w->partials,
                             w->counters + CNT_W2, w->flags + 1, c->net, c->stream));
         tmark(c, QST_PH_W2);
-        QST_CU(w1_pass_bulk(D, w->theta, w->step, w->sign, f, w->dpre, w->pre, w->hid, w->scal, w->partials,
+        QST_CU(w1_pass_bulk(D, w->theta, w->step, f, w->dpre, w->pre, w->hid, w->scal, w->partials,
                             w->counters + CNT_W1, w->flags + 1, c->net, c->stream));
         tmark(c, QST_PH_W1);
       }
     } else {
-      QST_CU(net_w2_pass<R>(D, w->theta, w->step, w->sign, w->dt, w->hid, w->pre, w->dpre, nullptr, w->partials,
+      QST_CU(net_w2_pass<R>(D, w->theta, w->step, w->dt, w->hid, w->pre, w->dpre, nullptr, w->partials,
                             w->counters + CNT_W2, c->net, true, c->stream));
       tmark(c, QST_PH_W2);
-      QST_CU(net_w1_pass<R>(D, w->theta, w->step, w->sign, f, w->dpre, w->pre, w->hid, nullptr, w->scal,
+      QST_CU(net_w1_pass<R>(D, w->theta, w->step, f, w->dpre, w->pre, w->hid, nullptr, w->scal,
                             w->partials, w->counters + CNT_W1, c->net, true, c->stream));
       tmark(c, QST_PH_W1);
     }
@@ -473,9 +472,9 @@ template <class R> struct Engine {
     if ((st = forward_state(c, theta, false)) != QST_OK) return st;
     if ((st = povm_likelihood(c, f, true)) != QST_OK) return st;
     if ((st = backward_state(c)) != QST_OK) return st;
-    QST_CU(net_w2_pass<R>(D, theta, nullptr, nullptr, w->dt, w->hid, w->pre, w->dpre, dtheta, w->partials,
+    QST_CU(net_w2_pass<R>(D, theta, nullptr, w->dt, w->hid, w->pre, w->dpre, dtheta, w->partials,
                           w->counters + CNT_W2, c->net, false, c->stream));
-    QST_CU(net_w1_pass<R>(D, theta, nullptr, nullptr, f, w->dpre, w->pre, w->hid, dtheta, w->scal, w->partials,
+    QST_CU(net_w1_pass<R>(D, theta, nullptr, f, w->dpre, w->pre, w->hid, dtheta, w->scal, w->partials,
                           w->counters + CNT_W1, c->net, false, c->stream));
     c->launches += 2;
     return read_loss(c, loss);
@@ -550,9 +549,8 @@ qst_status check_povm(const double* povm, int K, PovmB<double>* Bd) {
 template <class R> qst_status reset_rprop(qst_ctx* c) {
   Work<R>* w = W<R>(c);
   const size_t P = theta_size(c->N);
-  std::vector<R> h(P, (R)c->opt.lr);
+  std::vector<R> h(P, rprop_encode((R)c->opt.lr, 0));  // step lr, previous sign 0
   QST_CU(cudaMemcpyAsync(w->step, h.data(), P * sizeof(R), cudaMemcpyHostToDevice, c->stream));
-  QST_CU(cudaMemsetAsync(w->sign, 0, P, c->stream));
   QST_CU(cudaStreamSynchronize(c->stream));
   return QST_OK;
 }
@@ -660,8 +658,10 @@ qst_status qst_init(qst_ctx** out, int N, const double* povm, int K, const qst_o
     if (!(o.P > 0.0) || !isfinite(o.P) || o.eig_sweeps < 0) return QST_E_INVAL;
     if (o.precision == QST_MIXED || o.precision == QST_MIXED_BF16) return QST_E_UNSUPPORTED;
   }
-  if (!(o.lr > 0) || !(o.eta_minus > 0 && o.eta_minus < 1) || !(o.eta_plus > 1) || !(o.step_min > 0) ||
-      !(o.step_max >= o.step_min) || !(o.leaky_slope >= 0))
+  // steps within [2^-33, 2^30]: the Rprop state word then holds the previous sign exactly (rprop_encode)
+  const double lo = ldexp(1.0, -33), hi = ldexp(1.0, 30);
+  if (!(o.lr >= lo && o.lr <= hi) || !(o.eta_minus > 0 && o.eta_minus < 1) || !(o.eta_plus > 1) ||
+      !(o.step_min >= lo) || !(o.step_max >= o.step_min && o.step_max <= hi) || !(o.leaky_slope >= 0))
     return QST_E_INVAL;
   PovmB<double> Bd;
   qst_status st = check_povm(povm, K, &Bd);
@@ -774,7 +774,7 @@ void* warm_q(qst_ctx* c) {
 size_t qst_state_bytes(const qst_ctx* c) {
   if (!c) return 0;
   const size_t P = theta_size(c->N);
-  return 4 * sizeof(unsigned long long) + 2 * P * rsize(c) + P + warm_bytes(c);
+  return 4 * sizeof(unsigned long long) + 2 * P * rsize(c) + warm_bytes(c);
 }
 
 qst_status qst_get_state(qst_ctx* c, void* host_buf, size_t bytes) {
@@ -788,14 +788,13 @@ qst_status qst_get_state(qst_ctx* c, void* host_buf, size_t bytes) {
   hdr[2] = (unsigned long long)c->iters;
   hdr[3] = (unsigned long long)P;
   char* p = (char*)host_buf + 4 * sizeof(unsigned long long);
-  const void *th, *stp, *sg;
-  if (c->prec == QST_FP64) { th = W<double>(c)->theta; stp = W<double>(c)->step; sg = W<double>(c)->sign; }
-  else { th = W<float>(c)->theta; stp = W<float>(c)->step; sg = W<float>(c)->sign; }
+  const void *th, *stp;
+  if (c->prec == QST_FP64) { th = W<double>(c)->theta; stp = W<double>(c)->step; }
+  else { th = W<float>(c)->theta; stp = W<float>(c)->step; }
   QST_CU(cudaMemcpyAsync(p, th, P * rs, cudaMemcpyDeviceToHost, c->stream));
   QST_CU(cudaMemcpyAsync(p + P * rs, stp, P * rs, cudaMemcpyDeviceToHost, c->stream));
-  QST_CU(cudaMemcpyAsync(p + 2 * P * rs, sg, P, cudaMemcpyDeviceToHost, c->stream));
   if (warm_bytes(c)) {
-    char* q = p + 2 * P * rs + P;
+    char* q = p + 2 * P * rs;
     *(unsigned long long*)q = c->warm_valid ? 1ULL : 0ULL;
     if (c->warm_valid)
       QST_CU(cudaMemcpyAsync(q + sizeof(unsigned long long), warm_q(c), warm_bytes(c) - sizeof(unsigned long long),
@@ -814,15 +813,14 @@ qst_status qst_set_state(qst_ctx* c, const void* host_buf, size_t bytes) {
       hdr[3] != (unsigned long long)P)
     return QST_E_INVAL;
   const char* p = (const char*)host_buf + 4 * sizeof(unsigned long long);
-  void *th, *stp, *sg;
-  if (c->prec == QST_FP64) { th = W<double>(c)->theta; stp = W<double>(c)->step; sg = W<double>(c)->sign; }
-  else { th = W<float>(c)->theta; stp = W<float>(c)->step; sg = W<float>(c)->sign; }
+  void *th, *stp;
+  if (c->prec == QST_FP64) { th = W<double>(c)->theta; stp = W<double>(c)->step; }
+  else { th = W<float>(c)->theta; stp = W<float>(c)->step; }
   QST_CU(cudaMemcpyAsync(th, p, P * rs, cudaMemcpyHostToDevice, c->stream));
   QST_CU(cudaMemcpyAsync(stp, p + P * rs, P * rs, cudaMemcpyHostToDevice, c->stream));
-  QST_CU(cudaMemcpyAsync(sg, p + 2 * P * rs, P, cudaMemcpyHostToDevice, c->stream));
   c->warm_valid = false;
   if (warm_bytes(c)) {
-    const char* q = p + 2 * P * rs + P;
+    const char* q = p + 2 * P * rs;
     if (*(const unsigned long long*)q) {
       QST_CU(cudaMemcpyAsync(warm_q(c), q + sizeof(unsigned long long), warm_bytes(c) - sizeof(unsigned long long),
                              cudaMemcpyHostToDevice, c->stream));

@@ -97,16 +97,34 @@ __device__ __forceinline__ void tri_decode(uint32_t t, int& I, int& J) {
 // the gradient counts as zero; the parameter moves by -sign(g) step.
 template <class R> struct RpropCfg { R eta_minus, eta_plus, step_min, step_max; };
 
+// One word of Rprop state per parameter holds the step and the previous gradient sign:
+// +step (sign +1), -step (sign -1), or step * 2^64 (sign 0).  Steps stay within [2^-33, 2^30]
+// (the options are checked), so |state| >= 2^31 marks sign 0, and the power-of-two scaling is
+// exact: the arithmetic is the same as with a separate sign array, with 2 fewer bytes to stream
+// per parameter and iteration.
+template <class R> struct RpropCode {
+  static constexpr R kZero = R(18446744073709551616.0);          // 2^64
+  static constexpr R kInvZero = R(5.42101086242752217003726e-20);  // 2^-64
+  static constexpr R kThreshold = R(2147483648.0);                 // 2^31
+};
+
+template <class R> __host__ __device__ __forceinline__ R rprop_encode(R step, int prev) {
+  return prev == 0 ? step * RpropCode<R>::kZero : (prev < 0 ? -step : step);
+}
+
 template <class R>
-__device__ __forceinline__ R rprop1(R w, R g, R& step, int8_t& prev, const RpropCfg<R>& c) {
+__device__ __forceinline__ R rprop1(R w, R g, R& state, const RpropCfg<R>& c) {
+  const R a = state < R(0) ? -state : state;
+  const bool zero = a >= RpropCode<R>::kThreshold;
+  const int prev = zero ? 0 : (state < R(0) ? -1 : 1);
+  const R step = zero ? a * RpropCode<R>::kInvZero : a;
   int s = (g > R(0)) - (g < R(0));
-  int cs = s * (int)prev;
+  int cs = s * prev;
   R fac = cs > 0 ? c.eta_plus : (cs < 0 ? c.eta_minus : R(1));
   R st = step * fac;
   st = st < c.step_min ? c.step_min : (st > c.step_max ? c.step_max : st);
-  step = st;
   if (cs < 0) s = 0;
-  prev = (int8_t)s;
+  state = rprop_encode(st, s);
   return s > 0 ? w - st : (s < 0 ? w + st : w);
 }
 

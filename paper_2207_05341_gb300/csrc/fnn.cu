@@ -14,15 +14,11 @@ template <> struct Vec<float> {
   static constexpr int W = 4;
   __device__ static void ld(const float* p, float* v) { float4 t = *reinterpret_cast<const float4*>(p); v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w; }
   __device__ static void st(float* p, const float* v) { *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]); }
-  __device__ static void lds(const int8_t* p, int8_t* v) { char4 t = *reinterpret_cast<const char4*>(p); v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w; }
-  __device__ static void sts(int8_t* p, const int8_t* v) { *reinterpret_cast<char4*>(p) = make_char4(v[0], v[1], v[2], v[3]); }
 };
 template <> struct Vec<double> {
   static constexpr int W = 2;
   __device__ static void ld(const double* p, double* v) { double2 t = *reinterpret_cast<const double2*>(p); v[0] = t.x; v[1] = t.y; }
   __device__ static void st(double* p, const double* v) { *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]); }
-  __device__ static void lds(const int8_t* p, int8_t* v) { char2 t = *reinterpret_cast<const char2*>(p); v[0] = t.x; v[1] = t.y; }
-  __device__ static void sts(int8_t* p, const int8_t* v) { *reinterpret_cast<char2*>(p) = make_char2(v[0], v[1]); }
 };
 
 template <class R> __device__ __forceinline__ R leaky(R x, R slope) { return x > R(0) ? x : slope * x; }
@@ -195,7 +191,7 @@ __global__ void __launch_bounds__(256) k_hermitian_T(const R* __restrict__ t, in
 // db2 = dt, dW2^T[j][i] = h_j dt_i, dh_j = sum_i W2^T[j][i] dt_i (old weights);
 // then dpre = dh * LeakyReLU'(pre), db1 = dpre.  update: Rprop on W2^T, b2, b1; else write dtheta.
 template <class R, int H, bool UPD>
-__global__ void __launch_bounds__(256, 2) k_w2_pass(R* __restrict__ theta, R* __restrict__ step, int8_t* __restrict__ sign,
+__global__ void __launch_bounds__(256, 2) k_w2_pass(R* __restrict__ theta, R* __restrict__ step,
                                                   const R* __restrict__ dt, const R* __restrict__ hid,
                                                   const R* __restrict__ pre, R* dpre, R* __restrict__ dtheta,
                                                   long long n, double* partials, unsigned int* counter,
@@ -217,24 +213,22 @@ __global__ void __launch_bounds__(256, 2) k_w2_pass(R* __restrict__ theta, R* __
     VV::ld(dt + x, dv);
     if (UPD) {
       R w[VW], st[VW];
-      int8_t sg[VW];
-      VV::ld(theta + ob2 + x, w); VV::ld(step + ob2 + x, st); VV::lds(sign + ob2 + x, sg);
+      VV::ld(theta + ob2 + x, w); VV::ld(step + ob2 + x, st);
 #pragma unroll
-      for (int u = 0; u < VW; ++u) w[u] = rprop1(w[u], dv[u], st[u], sg[u], rc);
-      VV::st(theta + ob2 + x, w); VV::st(step + ob2 + x, st); VV::sts(sign + ob2 + x, sg);
+      for (int u = 0; u < VW; ++u) w[u] = rprop1(w[u], dv[u], st[u], rc);
+      VV::st(theta + ob2 + x, w); VV::st(step + ob2 + x, st);
     } else {
       VV::st(dtheta + ob2 + x, dv);
     }
 #pragma unroll
     for (int j0 = 0; j0 < H; j0 += JB) {
       R w[JB][VW], st[JB][VW];
-      int8_t sg[JB][VW];
 #pragma unroll
       for (int jj = 0; jj < JB; ++jj) {
         if (j0 + jj < H) {
           const long long oj = o2 + (long long)(j0 + jj) * n + x;
           VV::ld(theta + oj, w[jj]);
-          if (UPD) { VV::ld(step + oj, st[jj]); VV::lds(sign + oj, sg[jj]); }
+          if (UPD) VV::ld(step + oj, st[jj]);
         }
       }
 #pragma unroll
@@ -247,8 +241,8 @@ __global__ void __launch_bounds__(256, 2) k_w2_pass(R* __restrict__ theta, R* __
           for (int u = 0; u < VW; ++u) { acc[j] += w[jj][u] * dv[u]; g[u] = hs[j] * dv[u]; }
           if (UPD) {
 #pragma unroll
-            for (int u = 0; u < VW; ++u) w[jj][u] = rprop1(w[jj][u], g[u], st[jj][u], sg[jj][u], rc);
-            VV::st(theta + oj, w[jj]); VV::st(step + oj, st[jj]); VV::sts(sign + oj, sg[jj]);
+            for (int u = 0; u < VW; ++u) w[jj][u] = rprop1(w[jj][u], g[u], st[jj][u], rc);
+            VV::st(theta + oj, w[jj]); VV::st(step + oj, st[jj]);
           } else {
             VV::st(dtheta + oj, g);
           }
@@ -264,10 +258,8 @@ __global__ void __launch_bounds__(256, 2) k_w2_pass(R* __restrict__ theta, R* __
       dpre[j] = dp;
       if (UPD) {
         R st = step[ob1 + j];
-        int8_t sg = sign[ob1 + j];
-        theta[ob1 + j] = rprop1(theta[ob1 + j], dp, st, sg, rc);
+        theta[ob1 + j] = rprop1(theta[ob1 + j], dp, st, rc);
         step[ob1 + j] = st;
-        sign[ob1 + j] = sg;
       } else {
         dtheta[ob1 + j] = dp;
       }
@@ -281,7 +273,7 @@ __global__ void __launch_bounds__(256, 2) k_w2_pass(R* __restrict__ theta, R* __
 // dW1[j][i] = dpre_j f_i.  update: Rprop on W1, then pre = W1' f + b1', hid = LeakyReLU(pre),
 // scal[1] = sum f (the hidden layer of the next iteration); else write dtheta.
 template <class R, int H, bool UPD>
-__global__ void __launch_bounds__(256, 2) k_w1_pass(R* __restrict__ theta, R* __restrict__ step, int8_t* __restrict__ sign,
+__global__ void __launch_bounds__(256, 2) k_w1_pass(R* __restrict__ theta, R* __restrict__ step,
                                                   const R* __restrict__ f, const R* __restrict__ dpre, R* pre,
                                                   R* hid, R* __restrict__ dtheta, long long n, double* scal,
                                                   double* partials, unsigned int* counter, RpropCfg<R> rc, R slope) {
@@ -305,13 +297,12 @@ __global__ void __launch_bounds__(256, 2) k_w1_pass(R* __restrict__ theta, R* __
 #pragma unroll
     for (int j0 = 0; j0 < H; j0 += JB) {
       R w[JB][VW], st[JB][VW];
-      int8_t sg[JB][VW];
       if (UPD) {
 #pragma unroll
         for (int jj = 0; jj < JB; ++jj) {
           if (j0 + jj < H) {
             const long long oj = (long long)(j0 + jj) * n + x;
-            VV::ld(theta + oj, w[jj]); VV::ld(step + oj, st[jj]); VV::lds(sign + oj, sg[jj]);
+            VV::ld(theta + oj, w[jj]); VV::ld(step + oj, st[jj]);
           }
         }
       }
@@ -326,10 +317,10 @@ __global__ void __launch_bounds__(256, 2) k_w1_pass(R* __restrict__ theta, R* __
           if (UPD) {
 #pragma unroll
             for (int u = 0; u < VW; ++u) {
-              w[jj][u] = rprop1(w[jj][u], g[u], st[jj][u], sg[jj][u], rc);
+              w[jj][u] = rprop1(w[jj][u], g[u], st[jj][u], rc);
               acc[j] += w[jj][u] * fv[u];
             }
-            VV::st(theta + oj, w[jj]); VV::st(step + oj, st[jj]); VV::sts(sign + oj, sg[jj]);
+            VV::st(theta + oj, w[jj]); VV::st(step + oj, st[jj]);
           } else {
             VV::st(dtheta + oj, g);
           }
@@ -448,35 +439,35 @@ cudaError_t net_build_T(const Dims& D, const R* theta, const R* hid, R* t, cx_t<
 }
 
 template <class R>
-cudaError_t net_w2_pass(const Dims& D, R* theta, R* step, int8_t* sign, const R* dt, const R* hid, const R* pre,
+cudaError_t net_w2_pass(const Dims& D, R* theta, R* step, const R* dt, const R* hid, const R* pre,
                         R* dpre, R* dtheta, double* partials, unsigned int* counter, const NetCfg& c, bool update,
                         cudaStream_t s) {
   const long long nv = D.n / Vec<R>::W;
   if (update) {
     QST_SWITCH_H(D.H, k_w2_pass<R, HH, true><<<stream_grid(k_w2_pass<R, HH, true>, nv), 256, 0, s>>>(
-                          theta, step, sign, dt, hid, pre, dpre, dtheta, D.n, partials, counter, rcfg<R>(c),
+                          theta, step, dt, hid, pre, dpre, dtheta, D.n, partials, counter, rcfg<R>(c),
                           (R)c.slope));
   } else {
     QST_SWITCH_H(D.H, k_w2_pass<R, HH, false><<<stream_grid(k_w2_pass<R, HH, false>, nv), 256, 0, s>>>(
-                          theta, step, sign, dt, hid, pre, dpre, dtheta, D.n, partials, counter, rcfg<R>(c),
+                          theta, step, dt, hid, pre, dpre, dtheta, D.n, partials, counter, rcfg<R>(c),
                           (R)c.slope));
   }
   return cudaGetLastError();
 }
 
 template <class R>
-cudaError_t net_w1_pass(const Dims& D, R* theta, R* step, int8_t* sign, const R* f, const R* dpre, R* pre, R* hid,
+cudaError_t net_w1_pass(const Dims& D, R* theta, R* step, const R* f, const R* dpre, R* pre, R* hid,
                         R* dtheta, double* scal, double* partials, unsigned int* counter, const NetCfg& c,
                         bool update, cudaStream_t s) {
   const long long nv = D.n / Vec<R>::W;
   // both variants use the grid of the updating pass (the partition k_l1_forward reproduces)
   if (update) {
     QST_SWITCH_H(D.H, k_w1_pass<R, HH, true><<<stream_grid(k_w1_pass<R, HH, true>, nv), 256, 0, s>>>(
-                          theta, step, sign, f, dpre, pre, hid, dtheta, D.n, scal, partials, counter, rcfg<R>(c),
+                          theta, step, f, dpre, pre, hid, dtheta, D.n, scal, partials, counter, rcfg<R>(c),
                           (R)c.slope));
   } else {
     QST_SWITCH_H(D.H, k_w1_pass<R, HH, false><<<stream_grid(k_w1_pass<R, HH, true>, nv), 256, 0, s>>>(
-                          theta, step, sign, f, dpre, pre, hid, dtheta, D.n, scal, partials, counter, rcfg<R>(c),
+                          theta, step, f, dpre, pre, hid, dtheta, D.n, scal, partials, counter, rcfg<R>(c),
                           (R)c.slope));
   }
   return cudaGetLastError();
@@ -493,9 +484,9 @@ template <class R> cudaError_t net_symmetrize(const Dims& D, const cx_t<R>* Y, R
   template cudaError_t net_l1_forward<R>(const Dims&, const R*, const R*, R*, R*, double*, double*, unsigned int*, \
                                          const NetCfg&, cudaStream_t);                                           \
   template cudaError_t net_build_T<R>(const Dims&, const R*, const R*, R*, cx_t<R>*, unsigned int*, cudaStream_t);                 \
-  template cudaError_t net_w2_pass<R>(const Dims&, R*, R*, int8_t*, const R*, const R*, const R*, R*, R*, double*, \
+  template cudaError_t net_w2_pass<R>(const Dims&, R*, R*, const R*, const R*, const R*, R*, R*, double*, \
                                       unsigned int*, const NetCfg&, bool, cudaStream_t);                         \
-  template cudaError_t net_w1_pass<R>(const Dims&, R*, R*, int8_t*, const R*, const R*, R*, R*, R*, double*,     \
+  template cudaError_t net_w1_pass<R>(const Dims&, R*, R*, const R*, const R*, R*, R*, R*, double*,     \
                                       double*, unsigned int*, const NetCfg&, bool, cudaStream_t);                \
   template cudaError_t net_symmetrize<R>(const Dims&, const cx_t<R>*, R*, cudaStream_t);
 QST_INST(float)

@@ -3,7 +3,7 @@
 // Each CTA walks chunks of kCols consecutive columns of the 4^N axis (chunk c to CTA
 // c mod grid, one CTA per SM).  The CTA is warp-specialised: one producer thread issues,
 // per chunk, one 2-D tensor copy (cp.async.bulk.tensor, box kCols x H) of each parameter
-// array (weights, Rprop steps, previous signs: H rows n apart) and 1-D bulk copies of the
+// array (weights, Rprop state words: H rows n apart) and 1-D bulk copies of the
 // chunk of dt (W2 pass) or f (W1 pass) and of b2's state, all counted on the stage's
 // "full" mbarrier, into a ring of kStages shared-memory stages.  The consumer threads
 // (kGroups per column, each with about H / kGroups of the rows, enough warps to hide the
@@ -94,26 +94,24 @@ __device__ __forceinline__ void bar_arrive(uint32_t bar) {
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Tensor maps of the H x n parameter rows of one pass (W1, or W2^T) in theta, step and sign.
+// Tensor maps of the H x n parameter rows of one pass (W1, or W2^T) in theta and in the Rprop state.
 struct WMaps {
-  CUtensorMap w, st, sg;
+  CUtensorMap w, st;
 };
 
-// Stage layout (bytes, every part 128-byte aligned): w[H][kCols] f32 | st[H][kCols] f32 | sg[H][kCols] i8 | vec[kCols] f32 (dt or f)
-//                       | W2 pass only: b2 w, st [kCols] f32, sg [kCols] i8
+// Stage layout (bytes, every part 128-byte aligned): w[H][kCols] f32 | st[H][kCols] f32 (Rprop state)
+//                       | vec[kCols] f32 (dt or f) | W2 pass only: b2 w, st [kCols] f32
 template <int H, bool W2> struct Stage {
   static constexpr int kW = 0;
   static constexpr int kSt = kW + H * kCols * 4;
-  static constexpr int kSg = kSt + H * kCols * 4;
-  static constexpr int kVec = kSg + H * kCols;
+  static constexpr int kVec = kSt + H * kCols * 4;
   static constexpr int kBw = kVec + kCols * 4;
   static constexpr int kBst = kBw + kCols * 4;
-  static constexpr int kBsg = kBst + kCols * 4;
-  static constexpr int kUsed = W2 ? kBsg + kCols : kBw;   // bytes the copies of one chunk bring in
+  static constexpr int kUsed = W2 ? kBst + kCols * 4 : kBw;  // bytes the copies of one chunk bring in
   static constexpr int kBytes = (kUsed + 127) / 128 * 128;  // stage pitch: every stage 128-byte aligned
   static constexpr uint32_t kTx = (uint32_t)kUsed;
-  static_assert(kSt % 128 == 0 && kSg % 128 == 0 && kVec % 128 == 0 && kBw % 16 == 0 && kBst % 16 == 0 &&
-                    kBsg % 16 == 0 && kCols % 16 == 0 && kCols <= 256,
+  static_assert(kSt % 128 == 0 && kVec % 128 == 0 && kBw % 16 == 0 && kBst % 16 == 0 && kCols % 16 == 0 &&
+                    kCols <= 256,
                 "tensor-copy destinations must be 128-byte aligned, bulk-copy ones 16-byte aligned");
   // ring depth: as many stages as fit in kRingBytes, at most kMaxStages (a deeper ring measured slower)
   static constexpr int kStages = kRingBytes / kBytes < kMaxStages ? kRingBytes / kBytes : kMaxStages;
@@ -158,7 +156,7 @@ __device__ __forceinline__ void final_sum(const double* partials, int M, F fin) 
 template <int H, bool W2>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_wpass_bulk(const __grid_constant__ WMaps maps,
                                                           float* __restrict__ theta, float* __restrict__ step,
-                                                          int8_t* __restrict__ sign, const float* __restrict__ vec,
+                                                          const float* __restrict__ vec,
                                                           const float* __restrict__ hidv, const float* __restrict__ pre,
                                                           float* dpre_io, float* pre_out, float* hid_out, double* scal,
                                                           long long n, double* partials, unsigned int* counter,
@@ -204,12 +202,10 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_wpass_bulk(const __gri
         bar_expect(bar, S::kTx);
         tma_load_box(st + S::kW, &maps.w, (int)c0, bar);
         tma_load_box(st + S::kSt, &maps.st, (int)c0, bar);
-        tma_load_box(st + S::kSg, &maps.sg, (int)c0, bar);
         bulk_load(st + S::kVec, vec + c0, kCols * 4, bar);
         if (W2) {
           bulk_load(st + S::kBw, theta + ob2 + c0, kCols * 4, bar);
           bulk_load(st + S::kBst, step + ob2 + c0, kCols * 4, bar);
-          bulk_load(st + S::kBsg, sign + ob2 + c0, kCols, bar);
         }
       };
       auto issue_stores = [&](long long k) {
@@ -218,11 +214,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_wpass_bulk(const __gri
         const long long c0 = (blockIdx.x + k * gridDim.x) * kCols;
         tma_store_box(&maps.w, (int)c0, st + S::kW);
         tma_store_box(&maps.st, (int)c0, st + S::kSt);
-        tma_store_box(&maps.sg, (int)c0, st + S::kSg);
         if (W2) {
           bulk_store(theta + ob2 + c0, st + S::kBw, kCols * 4);
           bulk_store(step + ob2 + c0, st + S::kBst, kCols * 4);
-          bulk_store(sign + ob2 + c0, st + S::kBsg, kCols);
         }
         bulk_commit();
       };
@@ -264,18 +258,14 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_wpass_bulk(const __gri
       uint8_t* st = smem + q * S::kBytes;
       float* w = reinterpret_cast<float*>(st + S::kW);
       float* sp = reinterpret_cast<float*>(st + S::kSt);
-      int8_t* sg = reinterpret_cast<int8_t*>(st + S::kSg);
       const float v = reinterpret_cast<const float*>(st + S::kVec)[col];  // dt_i or f_i
       if (rg == 0) {
         if (W2) {
           float* bw = reinterpret_cast<float*>(st + S::kBw);
           float* bst = reinterpret_cast<float*>(st + S::kBst);
-          int8_t* bsg = reinterpret_cast<int8_t*>(st + S::kBsg);
           float bs = bst[col];
-          int8_t bg = bsg[col];
-          bw[col] = rprop1(bw[col], v, bs, bg, rc);
+          bw[col] = rprop1(bw[col], v, bs, rc);
           bst[col] = bs;
-          bsg[col] = bg;
         } else {
           accf += v;
         }
@@ -287,17 +277,15 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_wpass_bulk(const __gri
         const int e = j * kCols + col;
         float wj = w[e];
         float sj = sp[e];
-        int8_t gj = sg[e];
         if (W2) {
           acc[l] += wj * v;  // dh_j with the old weights
-          wj = rprop1(wj, hr[l] * v, sj, gj, rc);
+          wj = rprop1(wj, hr[l] * v, sj, rc);
         } else {
-          wj = rprop1(wj, hr[l] * v, sj, gj, rc);
+          wj = rprop1(wj, hr[l] * v, sj, rc);
           acc[l] += wj * v;  // next pre-activation with the new weights
         }
         w[e] = wj;
         sp[e] = sj;
-        sg[e] = gj;
       }
       fence_async_smem();  // the producer's tensor stores read what this thread wrote
       bar_arrive(s_u32(&empty[q]));
@@ -337,10 +325,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_wpass_bulk(const __gri
         const float dp = (float)sum * (p > 0.f ? 1.f : slope);
         dpre_io[j] = dp;
         float stp = step[ob1 + j];
-        int8_t sgn = sign[ob1 + j];
-        theta[ob1 + j] = rprop1(theta[ob1 + j], dp, stp, sgn, rc);
+        theta[ob1 + j] = rprop1(theta[ob1 + j], dp, stp, rc);
         step[ob1 + j] = stp;
-        sign[ob1 + j] = sgn;
       });
     } else {
       final_sum(partials, H + 1, [&](int j, double sum) {
@@ -409,21 +395,20 @@ typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void
                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// H x n rows starting at base (row stride n elements), box kCols x H, no swizzle.
-bool make_rows_map(CUtensorMap* m, void* base, long long n, int H, bool bytes) {
+// H x n FP32 rows starting at base (row stride n elements), box kCols x H, no swizzle.
+bool make_rows_map(CUtensorMap* m, void* base, long long n, int H) {
   EncodeFn enc = reinterpret_cast<EncodeFn>(tma_encoder());
   if (!enc) return false;
-  const cuuint64_t es = bytes ? 1 : 4;
   cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)H};
-  cuuint64_t strides[1] = {(cuuint64_t)n * es};
+  cuuint64_t strides[1] = {(cuuint64_t)n * 4};
   cuuint32_t box[2] = {(cuuint32_t)kCols, (cuuint32_t)H};
   cuuint32_t estr[2] = {1u, 1u};
-  return enc(m, bytes ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides,
-             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
 }
 
-template <int H, bool W2> cudaError_t launch_bulk(float* theta, float* step, int8_t* sign, const float* vec,
+template <int H, bool W2> cudaError_t launch_bulk(float* theta, float* step, const float* vec,
                                                    const float* hid, const float* pre, float* dpre, float* pre_out,
                                                    float* hid_out, double* scal, long long n, double* partials,
                                                    unsigned int* counter, unsigned int* flags,
@@ -438,11 +423,10 @@ template <int H, bool W2> cudaError_t launch_bulk(float* theta, float* step, int
   }
   const long long rowoff = W2 ? (long long)H * n : 0;  // W2^T or W1 rows
   WMaps maps;
-  if (!make_rows_map(&maps.w, theta + rowoff, n, H, false) || !make_rows_map(&maps.st, step + rowoff, n, H, false) ||
-      !make_rows_map(&maps.sg, sign + rowoff, n, H, true))
+  if (!make_rows_map(&maps.w, theta + rowoff, n, H) || !make_rows_map(&maps.st, step + rowoff, n, H))
     return cudaErrorInvalidValue;
   const long long grid = bulk_grid(n);
-  k_wpass_bulk<H, W2><<<(unsigned)grid, kThreads, smem, s>>>(maps, theta, step, sign, vec, hid, pre, dpre, pre_out,
+  k_wpass_bulk<H, W2><<<(unsigned)grid, kThreads, smem, s>>>(maps, theta, step, vec, hid, pre, dpre, pre_out,
                                                              hid_out, scal, n, partials, counter, flags, rc, slope);
   return cudaGetLastError();
 }
@@ -467,11 +451,11 @@ bool wpass_bulk_ok(int H, long long n) {
     default: return cudaErrorInvalidValue;                      \
   }
 
-cudaError_t w2_pass_bulk(const Dims& D, float* theta, float* step, int8_t* sign, const float* dt, const float* hid,
+cudaError_t w2_pass_bulk(const Dims& D, float* theta, float* step, const float* dt, const float* hid,
                          const float* pre, float* dpre, double* partials, unsigned int* counter, unsigned int* flags,
                          const NetCfg& c, cudaStream_t s) {
   RpropCfg<float> rc{(float)c.eta_minus, (float)c.eta_plus, (float)c.step_min, (float)c.step_max};
-  QST_BULK_SWITCH(D.H, return (launch_bulk<HH, true>(theta, step, sign, dt, hid, pre, dpre, nullptr, nullptr, nullptr,
+  QST_BULK_SWITCH(D.H, return (launch_bulk<HH, true>(theta, step, dt, hid, pre, dpre, nullptr, nullptr, nullptr,
                                                      D.n, partials, counter, flags, rc, (float)c.slope, s)));
   return cudaSuccess;
 }
@@ -484,11 +468,11 @@ cudaError_t l1_forward_bulk(const Dims& D, const float* theta, const float* f, f
   return cudaGetLastError();
 }
 
-cudaError_t w1_pass_bulk(const Dims& D, float* theta, float* step, int8_t* sign, const float* f, float* dpre,
+cudaError_t w1_pass_bulk(const Dims& D, float* theta, float* step, const float* f, float* dpre,
                          float* pre, float* hid, double* scal, double* partials, unsigned int* counter,
                          unsigned int* flags, const NetCfg& c, cudaStream_t s) {
   RpropCfg<float> rc{(float)c.eta_minus, (float)c.eta_plus, (float)c.step_min, (float)c.step_max};
-  QST_BULK_SWITCH(D.H, return (launch_bulk<HH, false>(theta, step, sign, f, nullptr, nullptr, dpre, pre, hid, scal,
+  QST_BULK_SWITCH(D.H, return (launch_bulk<HH, false>(theta, step, f, nullptr, nullptr, dpre, pre, hid, scal,
                                                       D.n, partials, counter, flags, rc, (float)c.slope, s)));
   return cudaSuccess;
 }

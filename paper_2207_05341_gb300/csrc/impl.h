@@ -27,8 +27,7 @@ cudaError_t ensure_dynamic_smem(const void* fn, size_t bytes);
 template <class R> struct Work {
   using V = cx_t<R>;
   R* theta;            // parameters, qst_theta_size(N)
-  R* step;             // Rprop step sizes, same layout
-  int8_t* sign;        // Rprop previous-gradient signs, same layout
+  R* step;             // Rprop state, same layout: step with the previous gradient sign (rprop_encode)
   R* pre;              // hidden pre-activation [H]
   R* hid;              // hidden activation [H]
   R* dpre;             // dL/dpre [H]
@@ -98,24 +97,24 @@ template <class R> cudaError_t net_l1_forward(const Dims& D, const R* theta, con
 template <class R>
 cudaError_t net_build_T(const Dims& D, const R* theta, const R* hid, R* t, cx_t<R>* T, unsigned int* amax,
                         cudaStream_t s);
-template <class R> cudaError_t net_w2_pass(const Dims& D, R* theta, R* step, int8_t* sign, const R* dt,
+template <class R> cudaError_t net_w2_pass(const Dims& D, R* theta, R* step, const R* dt,
                                            const R* hid, const R* pre, R* dpre, R* dtheta,
                                            double* partials, unsigned int* counter, const NetCfg& c,
                                            bool update, cudaStream_t s);
-template <class R> cudaError_t net_w1_pass(const Dims& D, R* theta, R* step, int8_t* sign, const R* f,
+template <class R> cudaError_t net_w1_pass(const Dims& D, R* theta, R* step, const R* f,
                                            const R* dpre, R* pre, R* hid, R* dtheta, double* scal,
                                            double* partials, unsigned int* counter, const NetCfg& c,
                                            bool update, cudaStream_t s);
 // FP32 in-place weight passes with bulk-copy staging (fnn_bulk.cu); usable when wpass_bulk_ok(H, n)
 // and every streamed array is 16-byte aligned.  flags: a timed-out wait ORs 4 into *flags.
 bool wpass_bulk_ok(int H, long long n);
-cudaError_t w2_pass_bulk(const Dims& D, float* theta, float* step, int8_t* sign, const float* dt, const float* hid,
+cudaError_t w2_pass_bulk(const Dims& D, float* theta, float* step, const float* dt, const float* hid,
                          const float* pre, float* dpre, double* partials, unsigned int* counter, unsigned int* flags,
                          const NetCfg& c, cudaStream_t s);
 // layer-1 forward with the same summation partition as w1_pass_bulk
 cudaError_t l1_forward_bulk(const Dims& D, const float* theta, const float* f, float* pre, float* hid, double* scal,
                             double* partials, unsigned int* counter, const NetCfg& c, cudaStream_t s);
-cudaError_t w1_pass_bulk(const Dims& D, float* theta, float* step, int8_t* sign, const float* f, float* dpre,
+cudaError_t w1_pass_bulk(const Dims& D, float* theta, float* step, const float* f, float* dpre,
                          float* pre, float* hid, double* scal, double* partials, unsigned int* counter,
                          unsigned int* flags, const NetCfg& c, cudaStream_t s);
 // dL/dt from Y = G T:  dR_ij = 2(Re Y_ij + Re Y_ji), dR_ji = 2(Im Y_ij - Im Y_ji) (i > j), dR_ii = 2 Re Y_ii

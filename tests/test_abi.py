@@ -56,3 +56,14 @@ def test_binding_povm_matches_paper():
     import oracle as O
     flat = qst.tetrahedral_povm_flat().reshape(4, 2, 2, 2)
     np.testing.assert_allclose(flat[..., 0] + 1j * flat[..., 1], O.tetrahedral_povm(), atol=1e-16)
+
+
+def test_rprop_bounds_are_checked_on_the_host(lib):
+    """lr, step_min and step_max must lie in [2^-33, 2^30]: the Rprop state word then encodes the
+    previous gradient sign exactly.  The check runs before any device call (no GPU needed here)."""
+    for field, value in (("step_max", 2.0 ** 31), ("step_min", 2.0 ** -34), ("lr", 2.0 ** 31), ("lr", 1e-12)):
+        o = qst.qst_default_options()
+        setattr(o, field, value)
+        with pytest.raises(qst.QstError) as e:
+            qst.qst_init(3, opt=o)
+        assert e.value.status == qst.QST_E_INVAL, (field, value)
