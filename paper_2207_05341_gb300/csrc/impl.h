@@ -76,12 +76,12 @@ template <class R> cudaError_t povm_hi_nll(const Dims& D, const R* W, const R* f
 template <class R>
 cudaError_t povm_lo_adj(const Dims& D, const R* Wadj, cx_t<R>* G, const PovmB<R>& B, unsigned int* amax,
                         cudaStream_t s);
-// register-row implementations of the high pass (povm_reg.cu), used when povm_hi_reg_ok(D)
-bool povm_hi_reg_ok(const Dims& D);
-template <class R> cudaError_t povm_hi_fwd_reg(const Dims& D, const R* W, R* p, const PovmB<R>& B, cudaStream_t s);
-template <class R> cudaError_t povm_hi_nll_reg(const Dims& D, const R* W, const R* f, double* scal, R* Wadj,
-                                               double* partials, unsigned int* counter, unsigned int* flags,
-                                               const PovmB<R>& B, bool adjoint, cudaStream_t s);
+// Pauli-basis implementations of the high pass (povm_pauli.cu), used when povm_hi_pauli_ok(D)
+bool povm_hi_pauli_ok(const Dims& D);
+template <class R> cudaError_t povm_hi_fwd_pauli(const Dims& D, const R* W, R* p, const PovmB<R>& B, cudaStream_t s);
+template <class R> cudaError_t povm_hi_nll_pauli(const Dims& D, const R* W, const R* f, double* scal, R* Wadj,
+                                                 double* partials, unsigned int* counter, unsigned int* flags,
+                                                 const PovmB<R>& B, bool adjoint, cudaStream_t s);
 // scal[0] = Tr X = sum_i Re X_ii of the computed X (fixed-order FP64 sum)
 template <class R> cudaError_t trace_X(const Dims& D, const cx_t<R>* X, double* scal, cudaStream_t s);
 // full Hermitian matrix from its lower tiles, scaled by 1 / scal[0] (rho = X / Tr X)

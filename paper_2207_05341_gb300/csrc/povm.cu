@@ -363,7 +363,7 @@ cudaError_t povm_lo_adj(const Dims& D, const R* Wadj, cx_t<R>* G, const PovmB<R>
 
 template <class R>
 cudaError_t povm_hi_fwd(const Dims& D, const R* W, R* p, const PovmB<R>& B, cudaStream_t s) {
-  if (povm_hi_reg_ok(D)) return povm_hi_fwd_reg<R>(D, W, p, B, s);
+  if (povm_hi_pauli_ok(D)) return povm_hi_fwd_pauli<R>(D, W, p, B, s);
   const size_t sm = (size_t)D.nb * D.nb * D.C * sizeof(cx_t<R>);
   cudaError_t e = set_smem<R>((const void*)k_povm_hi_fwd<R>, sm);
   if (e != cudaSuccess) return e;
@@ -376,7 +376,7 @@ template <class R>
 cudaError_t povm_hi_nll(const Dims& D, const R* W, const R* f, double* scal, R* Wadj, double* partials,
                         unsigned int* counter, unsigned int* flags, const PovmB<R>& B, bool adjoint,
                         cudaStream_t s) {
-  if (povm_hi_reg_ok(D)) return povm_hi_nll_reg<R>(D, W, f, scal, Wadj, partials, counter, flags, B, adjoint, s);
+  if (povm_hi_pauli_ok(D)) return povm_hi_nll_pauli<R>(D, W, f, scal, Wadj, partials, counter, flags, B, adjoint, s);
   const size_t sm = (size_t)D.nb * D.nb * D.C * sizeof(cx_t<R>);
   cudaError_t e = set_smem<R>((const void*)k_povm_hi_nll<R>, sm);
   if (e != cudaSuccess) return e;
