@@ -16,6 +16,8 @@ The steps follow the paper in this order:
             decomposition rho = T^dag T / Tr(T^dag T)   (eq. unified_DP, "Chol_H")
             or the P-order absolute projection
             rho = Q |Lambda|^P Q^dag / Tr|Lambda|^P     (eq. abs_P, "A_P");
+  Sec. 2.2.1 alternatively a complex lower-triangular T and
+            rho = T^dag T / Tr(T^dag T)                 (eq. T_matrix, "Chol_Delta");
   Sec. 3.3  probabilities P_k = Tr[(M_k1 x ... x M_kN) rho]  (eq. PS);
   Sec. 3.1  loss L = -sum_k f_k log P_k;
   Sec. 4.1  LeakyReLU hidden layer, Rprop with learning rate 0.001.
@@ -23,6 +25,7 @@ The steps follow the paper in this order:
 Readings where the paper is silent (each also listed in the design notes):
   * the 4^N outputs t become R = t reshaped row-major to d x d, and
     T_ii = R_ii, T_ij = R_ij + i R_ji (i > j), T_ji = conj(T_ij);
+    for Chol_Delta the same lower triangle with T_ji = 0 (i > j);
   * the output layer is linear; the LeakyReLU negative slope is 0.01;
   * Rprop: initial step lr, factors (0.5, 1.2), step bounds [1e-6, 50],
     sign(g * g_prev) decides the factor, and the gradient is zeroed where the
@@ -181,6 +184,35 @@ def hermitian_from_output(t: np.ndarray) -> np.ndarray:
     return L + L.conj().T + np.diag(np.diag(R))
 
 
+def lower_from_output(t: np.ndarray) -> np.ndarray:
+    """Sec. 2.2.1 eq. T_matrix: the 4^N real outputs become a complex lower-triangular T.
+
+    The same R = t reshaped row-major as for the Hermitian T: the diagonal of T is
+    R's diagonal, the strict lower triangle is R_ij + i R_ji, the upper triangle is 0.
+    """
+    d = int(round(np.sqrt(t.size)))
+    R = t.reshape(d, d)
+    return np.tril(R, -1) + 1j * np.tril(R.T, -1) + np.diag(np.diag(R))
+
+
+def output_grad_from_lower(Gam: np.ndarray) -> np.ndarray:
+    """Pull a gradient back through lower_from_output.
+
+    Gam is any complex matrix with dL = Re Tr[Gam dT] for lower-triangular dT.
+    dT_ii = dR_ii, and for i > j dT_ij = dR_ij + i dR_ji, so
+    dL/dR_ii = Re Gam_ii, dL/dR_ij = Re Gam_ji and dL/dR_ji = -Im Gam_ji.
+    Returned flat, row-major, like t.
+    """
+    d = Gam.shape[0]
+    dR = np.zeros((d, d))
+    il = np.tril_indices(d, -1)
+    GT = Gam.T
+    dR[il] = GT[il].real
+    dR[(il[1], il[0])] = -GT[il].imag
+    dR[np.diag_indices(d)] = np.diag(Gam).real
+    return dR.ravel()
+
+
 def output_grad_from_hermitian(Gam: np.ndarray) -> np.ndarray:
     """Pull a gradient back through hermitian_from_output.
 
@@ -200,6 +232,12 @@ def output_grad_from_hermitian(Gam: np.ndarray) -> np.ndarray:
 # --------------------------------------------------------------------------
 # State mapping (Sec. 3.2)
 # --------------------------------------------------------------------------
+
+def chol_delta(T: np.ndarray) -> np.ndarray:
+    """Sec. 2.2.1 eq. T_matrix: rho = T^dag T / Tr(T^dag T) for lower-triangular T."""
+    X = T.conj().T @ T
+    return X / np.trace(X).real
+
 
 def chol_h(T: np.ndarray) -> np.ndarray:
     """Sec. 3.2 eq. unified_DP: rho = T^dag T / Tr(T^dag T) for Hermitian T."""
@@ -257,6 +295,8 @@ def nll(p: np.ndarray, f: np.ndarray) -> float:
 
 def state_from_theta(theta, f, N, mapping="chol_h", P=2.0):
     pre, h, t = network_forward(theta, f, N)
+    if mapping == "chol_delta":
+        return chol_delta(lower_from_output(t))
     T = hermitian_from_output(t)
     rho = chol_h(T) if mapping == "chol_h" else abs_p(T, P)
     return rho
@@ -271,15 +311,17 @@ def loss_and_grad(theta, f, povm, N, mapping="chol_h", P=2.0):
       dL/drho   = sum_k dL/dp_k M_k                      (POVM adjoint)
       Chol_H:   rho = X / Tr X, X = T^dag T:
                 dL/dX = (dL/drho - <dL/drho, rho> I) / Tr X,  Gam = T G_X + G_X T
+      Chol_Delta: the same X and dL/dX with T lower triangular; dX = dT^dag T + T^dag dT
+                gives dL = 2 Re Tr[G_X T^dag dT], Gam = 2 G_X T^dag
       A_P:      Daleckii-Krein (see _abs_p_backward)
-      t         <- Gam (output_grad_from_hermitian)
+      t         <- Gam (output_grad_from_hermitian, or output_grad_from_lower)
       W2^T, b2, h <- t;  pre <- h (LeakyReLU');  W1, b1 <- pre.
     """
     W1, W2T, b2, b1 = unpack_theta(theta, N)
     pre, h, t = network_forward(theta, f, N)
-    T = hermitian_from_output(t)
+    T = lower_from_output(t) if mapping == "chol_delta" else hermitian_from_output(t)
     d = T.shape[0]
-    if mapping == "chol_h":
+    if mapping in ("chol_h", "chol_delta"):
         X = T.conj().T @ T
         tX = np.trace(X).real
         rho = X / tX
@@ -292,13 +334,13 @@ def loss_and_grad(theta, f, povm, N, mapping="chol_h", P=2.0):
     m = f > 0
     gp[m] = -f[m] / p[m]
     G_rho = povm_adjoint(gp, povm)
-    if mapping == "chol_h":
+    if mapping in ("chol_h", "chol_delta"):
         inner = np.real(np.vdot(G_rho, rho))
         G_X = (G_rho - inner * np.eye(d)) / tX
-        Gam = T @ G_X + G_X @ T
+        Gam = T @ G_X + G_X @ T if mapping == "chol_h" else 2.0 * G_X @ T.conj().T
     else:
         Gam = _abs_p_backward(T, P, G_rho)
-    dt = output_grad_from_hermitian(Gam)
+    dt = output_grad_from_lower(Gam) if mapping == "chol_delta" else output_grad_from_hermitian(Gam)
 
     db2 = dt
     dW2T = np.outer(h, dt)

@@ -95,6 +95,48 @@ def test_gradient_central_fd_chol_h_n3_sampled():
     _fd_check(3, "chol_h", 2.0, idx=idx, seed=3)
 
 
+@pytest.mark.parametrize("N", [1, 2])
+def test_gradient_central_fd_chol_delta_all_coordinates(N):
+    _fd_check(N, "chol_delta", 2.0, seed=7)
+
+
+def test_gradient_central_fd_chol_delta_n3_sampled():
+    idx = np.random.default_rng(1).choice(synth.theta_size(3), 80, replace=False)
+    _fd_check(3, "chol_delta", 2.0, idx=idx, seed=4)
+
+
+def test_chol_delta_reaches_every_state_via_numpy_cholesky():
+    """Sec. 2.2.1 eq. T_matrix: every density matrix is T^dag T / Tr with T lower triangular.
+
+    With the exchange matrix E, E rho E = C C^dag (numpy's Cholesky, C lower) gives
+    rho = T^dag T for T = E C^dag E, which is lower triangular with a positive diagonal.
+    Reading its entries back into R (T_ii = R_ii, T_ij = R_ij + i R_ji) and mapping
+    forward must return rho; an orientation or index slip in the map fails here.
+    """
+    for N, r, seed in ((1, 1, 0), (2, 3, 1), (3, 8, 2), (3, 2, 3)):
+        d = 1 << N
+        rho = synth.ginibre_mixed(N, r, seed)
+        rho = rho + 1e-9 * np.eye(d)  # full rank for the Cholesky factorisation
+        rho /= np.trace(rho).real
+        E = np.eye(d)[::-1]
+        C = np.linalg.cholesky(E @ rho @ E)
+        T = E @ C.conj().T @ E
+        assert np.allclose(T, np.tril(T)) and np.all(np.diag(T).real > 0)
+        R = np.zeros((d, d))
+        for i in range(d):
+            R[i, i] = T[i, i].real
+            for j in range(i):
+                R[i, j], R[j, i] = T[i, j].real, T[i, j].imag
+        Tm = O.lower_from_output(R.ravel())
+        np.testing.assert_allclose(O.chol_delta(Tm), rho, atol=1e-12)
+        # upper triangle of the map is zero, and the state is physical for any t
+        t = np.random.default_rng(seed).standard_normal(d * d)
+        Tr_ = O.lower_from_output(t)
+        assert np.all(np.triu(Tr_, 1) == 0)
+        rho2 = O.chol_delta(Tr_)
+        assert abs(np.trace(rho2).real - 1) < 1e-13 and np.linalg.eigvalsh(rho2).min() > -1e-14
+
+
 @pytest.mark.parametrize("P", [0.5, 1.0, 1.5, 2.0, 3.0])
 def test_gradient_central_fd_abs_p(P):
     _fd_check(2, "abs_p", P, seed=int(P * 10))
