@@ -237,12 +237,14 @@ def time_steps(torch, qst, ctx, f_dev, K, stream):
     return e0.elapsed_time(e1), qst.qst_kernel_launches(ctx) - l0
 
 
-def run_precision(torch, qst, synth, dev, stream, prec, theta0, f, K, W, dist):
+def run_precision(torch, qst, synth, dev, stream, prec, theta0, f, K, W, dist, mapping=None):
     """K timed iterations replayed from the captured CUDA graph (the headline), the same
     K launched kernel by kernel, per-phase device times from timed graph replays, and the
     end-to-end rate through qst_step with a page-locked host f and the loss read back."""
     opt = qst.qst_default_options()
     opt.precision = prec
+    if mapping is not None:
+        opt.mapping = mapping
     ctx = qst.qst_init(NQ, opt=opt, stream=stream.cuda_stream)
     try:
         qst.qst_set_params(ctx, theta0)
@@ -508,6 +510,9 @@ def main_ours(args):
     with torch.cuda.stream(stream):
         for name, prec in precs:
             res[name] = run_precision(torch, qst, synth, dev, stream, prec, theta0, f, args.steps, args.warmup, dist)
+        # Chol_Delta (Sec. 2.2.1 eq. T_matrix), FP32: not this metric's map, reported beside it
+        res["chol_delta_fp32"] = run_precision(torch, qst, synth, dev, stream, qst.QST_FP32, theta0, f, args.steps,
+                                               args.warmup, dist, mapping=qst.QST_MAP_CHOL_DELTA)
 
     head = "mixed_fp16x3" if mixed_ok else "plain_fp32"
     # max over ranks of the timed region

@@ -66,9 +66,12 @@ typedef enum {
 } qst_status;
 
 /* State maps of Sec. 3.2.  QST_MAP_ABS_P (eq. abs_P, any P > 0) diagonalises T every
- * iteration with a cyclic Jacobi method on the GPU (FP32 / FP64 contexts; the mixed
- * modes support QST_MAP_CHOL_H only). */
-enum { QST_MAP_CHOL_H = 0, QST_MAP_ABS_P = 1 };
+ * iteration with a cyclic Jacobi method on the GPU.  QST_MAP_CHOL_DELTA is the Cholesky
+ * decomposition of Sec. 2.2.1 (eq. T_matrix): T is complex lower triangular (T_ii = R_ii,
+ * T_ij = R_ij + i R_ji for i > j, 0 above the diagonal, from the same R = reshape(t)) and
+ * rho = T^dag T / Tr(T^dag T).  The mixed modes support QST_MAP_CHOL_H only
+ * (QST_E_UNSUPPORTED otherwise). */
+enum { QST_MAP_CHOL_H = 0, QST_MAP_ABS_P = 1, QST_MAP_CHOL_DELTA = 2 };
 /* Precisions.  QST_MIXED runs the two complex d x d products on tensor cores
  * (tcgen05) with each FP32 operand split into FP16 hi + lo after a power-of-two
  * scaling (about 2^-21 relative error); QST_MIXED_BF16 uses a BF16 hi + lo split
@@ -77,7 +80,8 @@ enum { QST_MAP_CHOL_H = 0, QST_MAP_ABS_P = 1 };
 enum { QST_FP64 = 0, QST_FP32 = 1, QST_MIXED = 2, QST_MIXED_BF16 = 3 };
 
 typedef struct qst_options {
-    int mapping;        /* QST_MAP_CHOL_H (paper default, Sec. 4.3) or QST_MAP_ABS_P (eq. abs_P) */
+    int mapping;        /* QST_MAP_CHOL_H (paper default, Sec. 4.3), QST_MAP_ABS_P (eq. abs_P) or
+                           QST_MAP_CHOL_DELTA (eq. T_matrix) */
     int precision;      /* QST_FP64, QST_FP32, QST_MIXED or QST_MIXED_BF16 (see above) */
     double P;           /* order of the absolute projection A_P; used when mapping == QST_MAP_ABS_P */
     double lr;          /* Rprop initial step (Sec. 4.1: 0.001); lr, step_min and step_max must lie in

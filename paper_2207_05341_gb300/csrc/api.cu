@@ -241,7 +241,10 @@ template <class R> struct Engine {
     const Dims& D = c->D;
     const bool mixed = is_mixed(c);
     // t = W2 h + b2 in the dt buffer (free until the backward writes dL/dt), then T (or its 16-bit planes)
-    QST_CU(net_build_T<R>(D, theta, w->hid, w->dt, mixed ? nullptr : w->T, amax_slot(c, CNT_AMAXT), c->stream));
+    // Chol_Delta: T lower triangular and T^dag (in Y, free until the backward) for X = T^dag T
+    const bool delta = c->opt.mapping == QST_MAP_CHOL_DELTA;
+    QST_CU(net_build_T<R>(D, theta, w->hid, w->dt, mixed ? nullptr : w->T, amax_slot(c, CNT_AMAXT), c->stream,
+                          delta ? w->Y : nullptr));
     if (mixed) {
       QST_CU(tc_planes_T(D.d, reinterpret_cast<const float*>(w->dt), w->Tb, tc_fmt(c), w->scal,
                          amax_slot(c, CNT_AMAXT), c->stream));
@@ -260,7 +263,7 @@ template <class R> struct Engine {
       QST_CU(tc_herm_square(D.d, w->Tb, tc_fmt(c), w->scal, reinterpret_cast<float2*>(w->X), w->flags + 1,
                             amax_slot(c, CNT_AMAXT), c->stream));
     } else {
-      QST_CU(cgemm_simt<R>(D.d, w->T, w->T, w->X, true, c->stream));
+      QST_CU(cgemm_simt<R>(D.d, delta ? w->Y : w->T, w->T, w->X, true, c->stream));
     }
     QST_CU(trace_X<R>(D, w->X, w->scal, c->stream));
     c->launches += 2;
@@ -305,6 +308,13 @@ template <class R> struct Engine {
       c->launches += 4;
       tmark(c, QST_PH_GT);
       QST_CU(net_symmetrize<R>(D, w->Y, w->dt, c->stream));
+      tmark(c, QST_PH_SYM);
+      c->launches += 2;
+    } else if (c->opt.mapping == QST_MAP_CHOL_DELTA) {
+      // dL = 2 Re Tr[G T^dag dT] for lower-triangular dT: only the lower tiles of Z = T G are needed
+      QST_CU(cgemm_simt<R>(D.d, w->T, w->G, w->Y, true, c->stream));
+      tmark(c, QST_PH_GT);
+      QST_CU(net_tri_grad<R>(D, w->Y, w->dt, c->stream));
       tmark(c, QST_PH_SYM);
       c->launches += 2;
     } else {
@@ -653,7 +663,10 @@ qst_status qst_init(qst_ctx** out, int N, const double* povm, int K, const qst_o
       o.precision != QST_MIXED_BF16)
     return QST_E_INVAL;
   if (N < 1 || N > (o.precision == QST_FP64 ? 10 : 12)) return QST_E_INVAL;
-  if (o.mapping != QST_MAP_CHOL_H && o.mapping != QST_MAP_ABS_P) return QST_E_INVAL;
+  if (o.mapping != QST_MAP_CHOL_H && o.mapping != QST_MAP_ABS_P && o.mapping != QST_MAP_CHOL_DELTA)
+    return QST_E_INVAL;
+  if (o.mapping == QST_MAP_CHOL_DELTA && (o.precision == QST_MIXED || o.precision == QST_MIXED_BF16))
+    return QST_E_UNSUPPORTED;
   if (o.mapping == QST_MAP_ABS_P) {
     if (!(o.P > 0.0) || !isfinite(o.P) || o.eig_sweeps < 0) return QST_E_INVAL;
     if (o.precision == QST_MIXED || o.precision == QST_MIXED_BF16) return QST_E_UNSUPPORTED;

@@ -155,8 +155,12 @@ __global__ void __launch_bounds__(256) k_layer2(const R* __restrict__ theta, con
   if (amax) block_absmax_to(m, amax);
 }
 
+// With Tt != NULL (Chol_Delta, Sec. 2.2.1 eq. T_matrix) the same entries are split: the lower triangle
+// with the diagonal goes to T (upper triangle 0), the upper triangle with the diagonal, which is T^dag,
+// to Tt (lower triangle 0).
 template <class R>
-__global__ void __launch_bounds__(256) k_hermitian_T(const R* __restrict__ t, int N, cx_t<R>* __restrict__ T) {
+__global__ void __launch_bounds__(256) k_hermitian_T(const R* __restrict__ t, int N, cx_t<R>* __restrict__ T,
+                                                      cx_t<R>* __restrict__ Tt) {
   using V = cx_t<R>;
   __shared__ R Ra[32][33];
   __shared__ R Rb[32][33];
@@ -170,6 +174,7 @@ __global__ void __launch_bounds__(256) k_hermitian_T(const R* __restrict__ t, in
     if (I != J) Rb[r][c] = t[(long long)(J * TS + r) * d + I * TS + c];
   }
   __syncthreads();
+  const V zero = cmake<V>(R(0), R(0));
   for (int e = threadIdx.x; e < TS * TS; e += blockDim.x) {
     const int r = e / TS, c = e % TS;
     R re, im;
@@ -177,12 +182,25 @@ __global__ void __launch_bounds__(256) k_hermitian_T(const R* __restrict__ t, in
     else if (r > c) { re = Ra[r][c]; im = Ra[c][r]; }
     else if (r < c) { re = Ra[c][r]; im = -Ra[r][c]; }
     else { re = Ra[r][r]; im = R(0); }
-    T[(long long)(I * TS + r) * d + J * TS + c] = cmake<V>(re, im);
+    const long long o = (long long)(I * TS + r) * d + J * TS + c;
+    if (!Tt) {
+      T[o] = cmake<V>(re, im);
+    } else {  // tile (I, J) holds the lower triangle of T; Tt = T^dag keeps only the upper one
+      const bool lower = I != J || r >= c, upper = I == J && r <= c;
+      T[o] = lower ? cmake<V>(re, im) : zero;
+      Tt[o] = upper ? cmake<V>(re, im) : zero;
+    }
   }
   if (I != J) {
     for (int e = threadIdx.x; e < TS * TS; e += blockDim.x) {
       const int a = e / TS, b = e % TS;
-      T[(long long)(J * TS + a) * d + I * TS + b] = cmake<V>(Ra[b][a], -Rb[a][b]);
+      const long long o = (long long)(J * TS + a) * d + I * TS + b;
+      if (!Tt) {
+        T[o] = cmake<V>(Ra[b][a], -Rb[a][b]);
+      } else {
+        T[o] = zero;
+        Tt[o] = cmake<V>(Ra[b][a], -Rb[a][b]);
+      }
     }
   }
 }
@@ -378,6 +396,33 @@ __global__ void __launch_bounds__(256) k_symmetrize(const cx_t<R>* __restrict__ 
   }
 }
 
+// Chol_Delta backward (Sec. 2.2.1 eq. T_matrix): with X = T^dag T and Z = T G (lower tiles computed),
+// dL = 2 Re Tr[G T^dag dT] gives dR_ii = 2 Re Z_ii and, for i > j, dR_ij = 2 Re Z_ij, dR_ji = 2 Im Z_ij.
+template <class R>
+__global__ void __launch_bounds__(256) k_tri_grad(const cx_t<R>* __restrict__ Z, R* __restrict__ dt, int d) {
+  __shared__ R Zr[32][33], Zi[32][33];
+  const int TS = d < 32 ? d : 32;
+  int I, J;
+  tri_decode(blockIdx.x, I, J);
+  for (int e = threadIdx.x; e < TS * TS; e += blockDim.x) {
+    const int r = e / TS, c = e % TS;
+    const cx_t<R> z = Z[(long long)(I * TS + r) * d + J * TS + c];
+    Zr[r][c] = z.x;
+    Zi[r][c] = z.y;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < TS * TS; e += blockDim.x) {
+    const int r = e / TS, c = e % TS;
+    if (I != J) {
+      dt[(long long)(I * TS + r) * d + J * TS + c] = R(2) * Zr[r][c];
+      dt[(long long)(J * TS + r) * d + I * TS + c] = R(2) * Zi[c][r];  // (J TS + r, I TS + c): Im Z at (I TS + c, J TS + r)
+    } else {
+      const R v = r > c ? R(2) * Zr[r][c] : (r < c ? R(2) * Zi[c][r] : R(2) * Zr[r][r]);
+      dt[(long long)(I * TS + r) * d + J * TS + c] = v;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ launchers
 #define QST_SWITCH_H(H, ...)                      \
   switch (H) {                                    \
@@ -415,7 +460,7 @@ cudaError_t net_l1_forward(const Dims& D, const R* theta, const R* f, R* pre, R*
 
 template <class R>
 cudaError_t net_build_T(const Dims& D, const R* theta, const R* hid, R* t, cx_t<R>* T, unsigned int* amax,
-                        cudaStream_t s) {
+                        cudaStream_t s, cx_t<R>* Tt) {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -434,7 +479,7 @@ cudaError_t net_build_T(const Dims& D, const R* theta, const R* hid, R* t, cx_t<
   const int TS = D.d < 32 ? D.d : 32;
   const int nt = D.d / TS;
   const unsigned pairs = (unsigned)(nt * (nt + 1) / 2);
-  k_hermitian_T<R><<<pairs, 256, 0, s>>>(t, D.N, T);
+  k_hermitian_T<R><<<pairs, 256, 0, s>>>(t, D.N, T, Tt);
   return cudaGetLastError();
 }
 
@@ -480,10 +525,19 @@ template <class R> cudaError_t net_symmetrize(const Dims& D, const cx_t<R>* Y, R
   return cudaGetLastError();
 }
 
+template <class R> cudaError_t net_tri_grad(const Dims& D, const cx_t<R>* Z, R* dt, cudaStream_t s) {
+  const int TS = D.d < 32 ? D.d : 32;
+  const int nt = D.d / TS;
+  k_tri_grad<R><<<(unsigned)(nt * (nt + 1) / 2), 256, 0, s>>>(Z, dt, D.d);
+  return cudaGetLastError();
+}
+
 #define QST_INST(R)                                                                                              \
   template cudaError_t net_l1_forward<R>(const Dims&, const R*, const R*, R*, R*, double*, double*, unsigned int*, \
                                          const NetCfg&, cudaStream_t);                                           \
-  template cudaError_t net_build_T<R>(const Dims&, const R*, const R*, R*, cx_t<R>*, unsigned int*, cudaStream_t);                 \
+  template cudaError_t net_build_T<R>(const Dims&, const R*, const R*, R*, cx_t<R>*, unsigned int*, cudaStream_t,  \
+                                      cx_t<R>*);                                                                 \
+  template cudaError_t net_tri_grad<R>(const Dims&, const cx_t<R>*, R*, cudaStream_t);                         \
   template cudaError_t net_w2_pass<R>(const Dims&, R*, R*, const R*, const R*, const R*, R*, R*, double*, \
                                       unsigned int*, const NetCfg&, bool, cudaStream_t);                         \
   template cudaError_t net_w1_pass<R>(const Dims&, R*, R*, const R*, const R*, R*, R*, R*, double*,     \

@@ -94,9 +94,12 @@ template <class R> cudaError_t net_l1_forward(const Dims& D, const R* theta, con
                                               const NetCfg& c, cudaStream_t s);
 // t = W2 h + b2 into the scratch t (n reals); then, when T != NULL, the Hermitian T of t (a second
 // launch).  amax (may be NULL): max |t_i| (= the largest |re|, |im| of T) is folded into *amax (float bits).
+// With Tt != NULL (Chol_Delta) T is the lower-triangular matrix of eq. T_matrix and Tt = T^dag.
 template <class R>
 cudaError_t net_build_T(const Dims& D, const R* theta, const R* hid, R* t, cx_t<R>* T, unsigned int* amax,
-                        cudaStream_t s);
+                        cudaStream_t s, cx_t<R>* Tt = nullptr);
+// Chol_Delta: dL/dt from Z = T G (lower tiles): dR_ii = 2 Re Z_ii, dR_ij = 2 Re Z_ij, dR_ji = 2 Im Z_ij (i > j)
+template <class R> cudaError_t net_tri_grad(const Dims& D, const cx_t<R>* Z, R* dt, cudaStream_t s);
 template <class R> cudaError_t net_w2_pass(const Dims& D, R* theta, R* step, const R* dt,
                                            const R* hid, const R* pre, R* dpre, R* dtheta,
                                            double* partials, unsigned int* counter, const NetCfg& c,

@@ -27,6 +27,7 @@ QST_W_CLAMP = 1
 
 QST_MAP_CHOL_H = 0
 QST_MAP_ABS_P = 1
+QST_MAP_CHOL_DELTA = 2
 QST_FP64 = 0
 QST_FP32 = 1
 QST_MIXED = 2
