@@ -349,13 +349,18 @@ def cpu_baseline(f, theta0, seconds=12.0):
             "sample": f"{n} full N=11 iterations (loss, analytic gradient, Rprop) in FP64 NumPy, {el:.1f} s"}
 
 
-def batch_c4(torch, qst, synth, dev, steps, warmup, seed=30, B=512):
+def batch_c4(torch, qst, synth, dev, steps, warmup, seed=30, B=512, prec=None):
     """512 independent tomographies, N ~ U{3..9}, rank-r Ginibre states (r ~ U{1..2^N}),
-    10^5 N shots each; one graph launch per iteration of all of them."""
+    10^5 N shots each; one graph launch per iteration of all of them.  prec: None = FP32; QST_MIXED
+    runs the tomographies with N >= 7 on the tensor-core path."""
     rng = np.random.default_rng(seed)
     Ns = [int(x) for x in rng.integers(3, 10, B)]
     stream = torch.cuda.Stream(device=dev)
-    bt = qst.qst_batch_init(Ns, stream=stream.cuda_stream)
+    o = None
+    if prec is not None:
+        o = qst.qst_default_options()
+        o.precision = prec
+    bt = qst.qst_batch_init(Ns, opt=o, stream=stream.cuda_stream)
     try:
         fds = []
         with torch.cuda.stream(stream):
@@ -387,7 +392,8 @@ def batch_c4(torch, qst, synth, dev, steps, warmup, seed=30, B=512):
             launches = qst.qst_batch_kernel_launches(bt) - l0
             losses = qst.qst_batch_step(bt, fds, want_losses=True)
         it_s = B * steps / (ms / 1e3)
-        return {"workload": "512 tomographies, N ~ U{3..9}, rank-r Ginibre (r ~ U{1..2^N}), 10^5 N shots, FP32",
+        return {"workload": "512 tomographies, N ~ U{3..9}, rank-r Ginibre (r ~ U{1..2^N}), 10^5 N shots, "
+                            + ("FP32" if prec is None else "mixed FP16x3 for N >= 7, FP32 below"),
                 "Ns_hist": {str(k): Ns.count(k) for k in range(3, 10)},
                 "ms_per_batch_iteration": ms / steps, "aggregate_iters_per_s": it_s,
                 "tomographies_per_s_at_1000_iters": it_s / 1000.0,
@@ -590,6 +596,7 @@ def main_ours(args):
     }
     if args.batch:
         line["batch_c4"] = batch_c4(torch, qst, synth, dev, args.steps, args.warmup)
+        line["batch_c4_mixed"] = batch_c4(torch, qst, synth, dev, args.steps, args.warmup, prec=qst.QST_MIXED)
     if args.c5:
         line["n12_c5"] = c5_leg(torch, qst, synth, dev, min(args.steps, 10))
     if args.cpu_baseline:

@@ -7,6 +7,7 @@
 
 #include <new>
 #include <type_traits>
+#include <algorithm>
 #include <vector>
 
 #include "../../include/qst.h"
@@ -601,19 +602,33 @@ qst_status batch_capture(qst_batch* bt, const void* const* f) {
   QST_CU(cudaStreamBeginCapture(bt->root, cudaStreamCaptureModeThreadLocal));
   qst_status st = QST_OK;
   long long kernels = 0;
-  cudaError_t e = cudaEventRecord(bt->fork, bt->root);
-  for (int b = 0; b < bt->B && st == QST_OK && e == cudaSuccess; ++b) {
-    qst_ctx* c = bt->ctx[b];
-    e = cudaStreamWaitEvent(c->stream, bt->fork, 0);
-    if (e != cudaSuccess) break;
-    const long long l0 = c->launches;
-    st = c->prec == QST_FP64 ? Engine<double>::step_body(c, (const double*)f[b])
-                             : Engine<float>::step_body(c, (const float*)f[b]);
-    kernels += c->launches - l0;
-    c->launches = l0;
-    if (st != QST_OK) break;
-    e = cudaEventRecord(bt->done[b], c->stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(bt->root, bt->done[b], 0);
+  cudaError_t e = cudaSuccess;
+  // Tomographies of one qubit count run concurrently; the groups run one after another, largest
+  // first.  Mixing sizes in one fork lets the full-GPU kernels of the large ones hold SMs while the
+  // short chains of the small ones wait (measured 34 ms per iteration of the 512-tomography batch
+  // mixed, against about 14 ms as the sum of its same-N groups).
+  std::vector<int> order(bt->B);
+  for (int b = 0; b < bt->B; ++b) order[b] = b;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return bt->ctx[a]->N > bt->ctx[b]->N; });
+  for (int i = 0; i < bt->B && st == QST_OK && e == cudaSuccess;) {
+    const int N = bt->ctx[order[i]]->N;
+    e = cudaEventRecord(bt->fork, bt->root);  // the group starts when the previous group has joined
+    int j = i;
+    for (; j < bt->B && bt->ctx[order[j]]->N == N && st == QST_OK && e == cudaSuccess; ++j) {
+      const int b = order[j];
+      qst_ctx* c = bt->ctx[b];
+      e = cudaStreamWaitEvent(c->stream, bt->fork, 0);
+      if (e != cudaSuccess) break;
+      const long long l0 = c->launches;
+      st = c->prec == QST_FP64 ? Engine<double>::step_body(c, (const double*)f[b])
+                               : Engine<float>::step_body(c, (const float*)f[b]);
+      kernels += c->launches - l0;
+      c->launches = l0;
+      if (st != QST_OK) break;
+      e = cudaEventRecord(bt->done[b], c->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(bt->root, bt->done[b], 0);
+    }
+    i = j;
   }
   cudaGraph_t g = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(bt->root, &g);
