@@ -371,12 +371,27 @@ __global__ void __launch_bounds__(256) k_symmetrize(const cx_t<R>* __restrict__ 
   const int TS = d < 32 ? d : 32;
   int I, J;
   tri_decode(blockIdx.x, I, J);
-  for (int e = threadIdx.x; e < TS * TS; e += blockDim.x) {
-    const int r = e / TS, c = e % TS;
-    const long long ia = (long long)(I * TS + r) * d + J * TS + c;
-    const long long ib = (long long)(J * TS + r) * d + I * TS + c;
-    const cx_t<R> a = Y[ia], b = Y[ib];
-    Ar[r][c] = a.x; Ai[r][c] = a.y; Br[r][c] = b.x; Bi[r][c] = b.y;
+  if (TS == 32 && blockDim.x == 256) {  // all 8 loads of a thread in flight at once
+    cx_t<R> a[4], b[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int e = threadIdx.x + 256 * k, r = e >> 5, c = e & 31;
+      a[k] = Y[(long long)(I * 32 + r) * d + J * 32 + c];
+      b[k] = Y[(long long)(J * 32 + r) * d + I * 32 + c];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int e = threadIdx.x + 256 * k, r = e >> 5, c = e & 31;
+      Ar[r][c] = a[k].x; Ai[r][c] = a[k].y; Br[r][c] = b[k].x; Bi[r][c] = b[k].y;
+    }
+  } else {
+    for (int e = threadIdx.x; e < TS * TS; e += blockDim.x) {
+      const int r = e / TS, c = e % TS;
+      const long long ia = (long long)(I * TS + r) * d + J * TS + c;
+      const long long ib = (long long)(J * TS + r) * d + I * TS + c;
+      const cx_t<R> a = Y[ia], b = Y[ib];
+      Ar[r][c] = a.x; Ai[r][c] = a.y; Br[r][c] = b.x; Bi[r][c] = b.y;
+    }
   }
   __syncthreads();
   for (int e = threadIdx.x; e < TS * TS; e += blockDim.x) {

@@ -336,10 +336,20 @@ __global__ void __launch_bounds__(256) k_hermitian_planes(const float* __restric
   const long long nn = (long long)d * d;
   int I, J;
   tri_decode(blockIdx.x, I, J);
-  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
-    const int r = e >> 5, c = e & 31;
-    Ra[r][c] = t[(long long)(I * 32 + r) * d + J * 32 + c];
-    if (I != J) Rb[r][c] = t[(long long)(J * 32 + r) * d + I * 32 + c];
+  {  // all 8 loads of a thread in flight at once (blockDim.x == 256)
+    float a[4], b[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int e = threadIdx.x + 256 * k, r = e >> 5, c = e & 31;
+      a[k] = t[(long long)(I * 32 + r) * d + J * 32 + c];
+      b[k] = I != J ? t[(long long)(J * 32 + r) * d + I * 32 + c] : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int e = threadIdx.x + 256 * k, r = e >> 5, c = e & 31;
+      Ra[r][c] = a[k];
+      Rb[r][c] = b[k];
+    }
   }
   __syncthreads();
   auto put = [&](long long idx, float re0, float im0, float re1, float im1) {
@@ -358,7 +368,8 @@ __global__ void __launch_bounds__(256) k_hermitian_planes(const float* __restric
       *reinterpret_cast<typename Pair16<H>::T*>(P + p * nn + idx) = v;
     }
   };
-  for (int e = threadIdx.x; e < 32 * 16; e += blockDim.x) {
+#pragma unroll
+  for (int e = threadIdx.x; e < 32 * 16; e += 256) {
     const int r = e >> 4, c = (e & 15) * 2;
     float re[2], im[2];
 #pragma unroll

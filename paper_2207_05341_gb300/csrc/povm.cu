@@ -94,6 +94,69 @@ __device__ void apply_modes(cx_t<R>* Z, int side_log2, int pitch, int logC, int 
   }
 }
 
+// The mode maps of all g qubits of an S x S tile (S = 2^g), two qubits per sweep: a thread takes
+// the 4 x 4 elements that bits (b, b+1) of the row and column index span, applies qubit b and
+// then qubit b + 1 in registers and stores them back (each element sees the same operations in
+// the same order as with one qubit per sweep, so the result is bit-identical, with half the
+// shared-memory traffic and barriers).
+template <class R, bool ADJ>
+__device__ void apply_modes_tile(cx_t<R>* Z, int g, int pitch, const PovmB<R>& B) {
+  using V = cx_t<R>;
+  int b = 0;
+  for (; b + 1 < g; b += 2) {
+    const int gh = g - 2;
+    const int groups = 1 << (2 * gh);
+    const int low = (1 << b) - 1;
+    for (int t = threadIdx.x; t < groups; t += blockDim.x) {
+      const int rr = t >> gh, cc = t & ((1 << gh) - 1);
+      const int r0 = ((rr & ~low) << 2) | (rr & low);
+      const int c0 = ((cc & ~low) << 2) | (cc & low);
+      V x[4][4];  // [k][l]: row offset (k >> 1) << (b + 1) | (k & 1) << b, column offset likewise
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int l = 0; l < 4; ++l)
+          x[k][l] = Z[(r0 + (((k >> 1) << (b + 1)) | ((k & 1) << b))) * pitch + c0 + (((l >> 1) << (b + 1)) | ((l & 1) << b))];
+#pragma unroll
+      for (int hk = 0; hk < 2; ++hk)
+#pragma unroll
+        for (int hl = 0; hl < 2; ++hl) {  // qubit b: row bit k & 1, column bit l & 1
+          if (ADJ) mode_adj(B, x[2 * hk][2 * hl], x[2 * hk][2 * hl + 1], x[2 * hk + 1][2 * hl], x[2 * hk + 1][2 * hl + 1]);
+          else mode_fwd(B, x[2 * hk][2 * hl], x[2 * hk][2 * hl + 1], x[2 * hk + 1][2 * hl], x[2 * hk + 1][2 * hl + 1]);
+        }
+#pragma unroll
+      for (int lk = 0; lk < 2; ++lk)
+#pragma unroll
+        for (int ll = 0; ll < 2; ++ll) {  // qubit b + 1: row bit k >> 1, column bit l >> 1
+          if (ADJ) mode_adj(B, x[lk][ll], x[lk][2 + ll], x[2 + lk][ll], x[2 + lk][2 + ll]);
+          else mode_fwd(B, x[lk][ll], x[lk][2 + ll], x[2 + lk][ll], x[2 + lk][2 + ll]);
+        }
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int l = 0; l < 4; ++l)
+          Z[(r0 + (((k >> 1) << (b + 1)) | ((k & 1) << b))) * pitch + c0 + (((l >> 1) << (b + 1)) | ((l & 1) << b))] = x[k][l];
+    }
+    __syncthreads();
+  }
+  if (b < g) {  // odd g: the last qubit alone
+    const int half = g - 1;
+    const int groups = 1 << (2 * half);
+    const int bit = 1 << b, low = bit - 1;
+    for (int t = threadIdx.x; t < groups; t += blockDim.x) {
+      const int rr = t >> half, cc = t & ((1 << half) - 1);
+      const int r0 = ((rr & ~low) << 1) | (rr & low);
+      const int c0 = ((cc & ~low) << 1) | (cc & low);
+      V* p00 = Z + r0 * pitch + c0;
+      V x00 = p00[0], x01 = p00[bit], x10 = p00[bit * pitch], x11 = p00[bit * pitch + bit];
+      if (ADJ) mode_adj(B, x00, x01, x10, x11);
+      else mode_fwd(B, x00, x01, x10, x11);
+      p00[0] = x00; p00[bit] = x01; p00[bit * pitch] = x10; p00[bit * pitch + bit] = x11;
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------- pass 1
 template <class R>
 __global__ void __launch_bounds__(256) k_povm_lo_fwd(const cx_t<R>* __restrict__ X, R* __restrict__ W,
@@ -106,9 +169,23 @@ __global__ void __launch_bounds__(256) k_povm_lo_fwd(const cx_t<R>* __restrict__
   int I, J;
   tri_decode(blockIdx.x, I, J);
   const V* src = X + (long long)I * S * d + (long long)J * S;
-  for (int e = threadIdx.x; e < S * S; e += blockDim.x) {
-    const int il = e >> g, jl = e & (S - 1);
-    Z[il * pitch + jl] = src[il * d + jl];
+  if (S * S == 16 * 256 && blockDim.x == 256) {  // 64 x 64 tiles: all 16 loads of a thread in flight at once
+    V v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int e = threadIdx.x + k * 256;
+      v[k] = src[(long long)(e >> 6) * d + (e & 63)];
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int e = threadIdx.x + k * 256;
+      Z[(e >> 6) * pitch + (e & 63)] = v[k];
+    }
+  } else {
+    for (int e = threadIdx.x; e < S * S; e += blockDim.x) {
+      const int il = e >> g, jl = e & (S - 1);
+      Z[il * pitch + jl] = src[il * d + jl];
+    }
   }
   __syncthreads();
   if (I == J) {  // diagonal tile: rebuild the upper triangle from the lower one
@@ -118,7 +195,7 @@ __global__ void __launch_bounds__(256) k_povm_lo_fwd(const cx_t<R>* __restrict__
     }
     __syncthreads();
   }
-  apply_modes<R, false>(Z, g, pitch, 0, g, B);
+  apply_modes_tile<R, false>(Z, g, pitch, B);
   const long long SS = (long long)S * S;
   R* wlo = W + ((long long)I * nb + J) * SS;
   R* whi = W + ((long long)J * nb + I) * SS;
@@ -142,13 +219,28 @@ __global__ void __launch_bounds__(256) k_povm_lo_adj(const R* __restrict__ W, cx
   const long long SS = (long long)S * S;
   const R* wlo = W + ((long long)I * nb + J) * SS;
   const R* whi = W + ((long long)J * nb + I) * SS;
-  for (int al = threadIdx.x; al < S * S; al += blockDim.x) {
-    const R re = wlo[al];
-    const R im = (I != J) ? whi[al] : R(0);
-    Z[row_of(al) * pitch + col_of(al)] = cmake<V>(re, im);
+  if (S * S == 16 * 256 && blockDim.x == 256) {  // 64 x 64 tiles: all loads of a thread in flight at once
+    R re[16], im[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int al = threadIdx.x + k * 256;
+      re[k] = wlo[al];
+      im[k] = (I != J) ? whi[al] : R(0);
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int al = threadIdx.x + k * 256;
+      Z[row_of(al) * pitch + col_of(al)] = cmake<V>(re[k], im[k]);
+    }
+  } else {
+    for (int al = threadIdx.x; al < S * S; al += blockDim.x) {
+      const R re = wlo[al];
+      const R im = (I != J) ? whi[al] : R(0);
+      Z[row_of(al) * pitch + col_of(al)] = cmake<V>(re, im);
+    }
   }
   __syncthreads();
-  apply_modes<R, true>(Z, g, pitch, 0, g, B);
+  apply_modes_tile<R, true>(Z, g, pitch, B);
   V* dst = G + (long long)I * S * d + (long long)J * S;
   float m = 0.f;
   for (int e = threadIdx.x; e < S * S; e += blockDim.x) {
