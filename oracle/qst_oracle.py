@@ -430,3 +430,32 @@ def fidelity_pure(rho_hat: np.ndarray, psi: np.ndarray) -> float:
 def classical_fidelity(P_hat: np.ndarray, P: np.ndarray) -> float:
     """Sec. 2.3 eq. F_CF: (sum_k sqrt(P_hat_k P_k))^2, an upper bound on F_q."""
     return float(np.sum(np.sqrt(np.clip(P_hat, 0, None) * np.clip(P, 0, None))) ** 2)
+
+
+_SM_GAMMA = 0x9E3779B97F4A7C15
+_SM_M1 = 0xBF58476D1CE4E5B9
+_SM_M2 = 0x94D049BB133111EB
+
+
+def splitmix64(seed: int, s: np.ndarray) -> np.ndarray:
+    """Output s (0-based) of the SplitMix64 generator started at `seed` (Steele, Lea and Flood,
+    OOPSLA 2014): x = seed + (s + 1) * gamma, then the published two-round mix of x."""
+    s = np.asarray(s, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + (s + np.uint64(1)) * np.uint64(_SM_GAMMA)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(_SM_M1)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(_SM_M2)
+    return z ^ (z >> np.uint64(31))
+
+
+def sampled_classical_fidelity(P_hat: np.ndarray, P: np.ndarray, samples: int, seed: int) -> float:
+    """Sec. 2.3 eq. fc_sample: F_c ~ (E_{k ~ P_hat}[sqrt(P_k / P_hat_k)])^2 from `samples` draws.
+
+    Draw s takes u_s = (splitmix64(seed, s) >> 11) 2^-53 in [0, 1) and k_s, the smallest k with
+    c_k > u_s c_{n-1}, where c is the running sum of max(P_hat, 0) (inverse CDF).
+    """
+    ph = np.clip(P_hat, 0, None)
+    c = np.cumsum(ph)
+    u = (splitmix64(seed, np.arange(samples)) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    k = np.searchsorted(c, u * c[-1], side="right")
+    return float(np.mean(np.sqrt(np.clip(P[k], 0, None) / ph[k])) ** 2)

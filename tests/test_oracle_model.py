@@ -214,3 +214,38 @@ def test_reconstruction_from_exact_probabilities_reaches_target():
     _, rho, losses = O.reconstruct(theta0, f, M, N, 1000)
     assert O.fidelity_pure(rho, psi) > 0.99
     assert losses[-1] < losses[0]
+
+
+def test_splitmix64_matches_published_outputs(golden_dir):
+    lines = [l.split() for l in open(os.path.join(golden_dir, "splitmix64.txt")) if l.strip() and not l.startswith("#")]
+    seed = int(lines[0][1])
+    want = np.array([int(l[0]) for l in lines[1:]], dtype=np.uint64)
+    np.testing.assert_array_equal(O.splitmix64(seed, np.arange(want.size)), want)
+
+
+def test_sampled_classical_fidelity_pins():
+    """Sec. 2.3 eq. fc_sample: equal distributions give exactly 1; the estimate converges to eq. F_CF;
+    the draws follow P_hat (chi-square against the expected counts)."""
+    rng = np.random.default_rng(5)
+    n = 256
+    P = rng.dirichlet(np.ones(n))
+    assert O.sampled_classical_fidelity(P, P, 1000, 7) == pytest.approx(1.0, abs=1e-15)
+    Ph = rng.dirichlet(np.ones(n) * 3)
+    exact = O.classical_fidelity(Ph, P)
+    S = 400_000
+    est = O.sampled_classical_fidelity(Ph, P, S, 11)
+    r = np.sqrt(P / Ph)
+    se = 2 * np.sqrt(exact) * np.sqrt(np.sum(Ph * r ** 2) - exact) / np.sqrt(S)  # delta method
+    assert abs(est - exact) < 5 * se, (est, exact, se)
+    # the inverse-CDF draws have the distribution P_hat
+    c = np.cumsum(Ph)
+    u = (O.splitmix64(3, np.arange(S)) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    k = np.searchsorted(c, u * c[-1], side="right")
+    counts = np.bincount(k, minlength=n)
+    chi2 = np.sum((counts - S * Ph) ** 2 / (S * Ph))
+    assert chi2 < n + 5 * np.sqrt(2 * n)
+    # zero-probability outcomes are never drawn
+    Pz = Ph.copy(); Pz[::3] = 0; Pz /= Pz.sum()
+    c = np.cumsum(Pz)
+    k = np.searchsorted(c, u * c[-1], side="right")
+    assert np.all(Pz[k] > 0)
