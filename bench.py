@@ -329,6 +329,47 @@ def fidelity_run(torch, qst, dev, stream, prec, theta0, f, psi, lam, max_iters, 
         qst.qst_destroy(ctx)
 
 
+def fidelity_eval(torch, qst, dev, stream, theta0, lam, seed, steps=200, samples=10**6):
+    """On-device classical fidelity (Sec. 2.3 eq. F_CF and the sampled eq. fc_sample, qst_classical_fidelity)
+    beside the state fidelity F_q of the harness (torch, complex128), after `steps` mixed iterations at
+    N = 11 from exact probabilities (the target distribution is then the input itself)."""
+    from paper_2207_05341_gb300 import synth
+    psi, P = make_inputs(torch, qst, synth, dev, lam, seed, exact=True)
+    opt = qst.qst_default_options()
+    opt.precision = qst.QST_MIXED
+    ctx = qst.qst_init(NQ, opt=opt, stream=stream.cuda_stream)
+    try:
+        qst.qst_set_params(ctx, theta0)
+        qst.qst_graph_enable(ctx, True)
+        P_dev = torch.from_numpy(P).to(dev)
+        time_steps(torch, qst, ctx, P_dev, steps, stream)
+        out = {"workload": f"N=11, depolarizing lambda={lam}, exact probabilities, {steps} mixed iterations"}
+        for name, S in (("exact", 0), ("sampled", samples)):
+            best, val = None, None
+            for _ in range(3):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                val = qst.qst_classical_fidelity(ctx, P_dev, P_dev, samples=S, seed=1)
+                dt = time.perf_counter() - t0
+                best = dt if best is None else min(best, dt)
+            out[f"Fc_{name}"] = val
+            out[f"Fc_{name}_ms"] = best * 1e3
+        out["samples"] = samples
+        d = 2 ** NQ
+        rho = torch.empty((d, d), dtype=torch.complex64, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        qst.qst_get_rho(ctx, P_dev, rho)
+        Fq = fidelity_depolarized(torch, rho, torch.from_numpy(psi.astype(np.complex64)).to(dev), lam)
+        torch.cuda.synchronize()
+        out["Fq_harness"] = Fq
+        out["Fq_harness_ms"] = (time.perf_counter() - t0) * 1e3
+        out["note"] = "F_c >= F_q (eq. F_CF is an upper bound); F_q here is the harness's complex128 evaluation"
+        return out
+    finally:
+        qst.qst_destroy(ctx)
+
+
 def cpu_baseline(f, theta0, seconds=12.0):
     """The FP64 oracle, as it stands, on the host cores: full N = 11 iterations."""
     import oracle as O
@@ -594,6 +635,9 @@ def main_ours(args):
                               **ttf} if ttf else None),
         "paper_context": "11-qubit tomography within 2 minutes on a laptop (GTX 1070); not this metric's baseline",
     }
+    if args.ttf:
+        with torch.cuda.stream(stream):
+            line["fidelity_on_device"] = fidelity_eval(torch, qst, dev, stream, theta0, LAMBDAS[1], STATE_SEEDS[1])
     if args.batch:
         line["batch_c4"] = batch_c4(torch, qst, synth, dev, args.steps, args.warmup)
         line["batch_c4_mixed"] = batch_c4(torch, qst, synth, dev, args.steps, args.warmup, prec=qst.QST_MIXED)

@@ -175,6 +175,19 @@ qst_status qst_reconstruct(qst_ctx* ctx, const void* f, int iters, void* rho_out
  * (device or host, d x d complex), and its loss if loss != NULL. */
 qst_status qst_get_rho(qst_ctx* ctx, const void* f, void* rho_out, double* loss);
 
+/* Classical fidelity of Sec. 2.3 between rho^ of the current parameters (network input f, device or
+ * host, n reals) and a target distribution P (device or host, n reals, P_k = Tr[M_k rho] of the
+ * target state), computed on the GPU:
+ *   samples == 0: eq. F_CF, F_c = (sum_k sqrt(P^_k P_k))^2 (an upper bound on the state fidelity);
+ *   samples  > 0: eq. fc_sample, (mean_s sqrt(P_{k_s} / P^_{k_s}))^2 over `samples` draws k_s ~ P^:
+ *                 u_s = (splitmix64(seed, s) >> 11) 2^-53 (SplitMix64, Steele, Lea and Flood 2014:
+ *                 x = seed + (s + 1) 0x9E3779B97F4A7C15, then its published mix) and k_s is the
+ *                 smallest k whose running sum of max(P^, 0) exceeds u_s times the total.
+ * P^_k are the Born probabilities of X / Tr X (Sec. 3.3).  Fc: host, written.  The first sampled
+ * call allocates (n + n / 2048) doubles of scratch for the running sum. */
+qst_status qst_classical_fidelity(qst_ctx* ctx, const void* f, const void* P, long long samples,
+                                  unsigned long long seed, double* Fc);
+
 /* Checkpoint of parameters, Rprop state and iteration count (and, for
  * QST_MAP_ABS_P, the eigenvectors that warm-start the next eigendecomposition),
  * as an opaque host byte buffer of qst_state_bytes(ctx) bytes.  Restoring it

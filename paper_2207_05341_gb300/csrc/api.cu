@@ -59,6 +59,7 @@ struct qst_ctx {
   std::vector<unsigned int> tmask;
   int tmax = 0, tcount = 0, tslot = -1;
   void* apw = nullptr;  // AbsPWork<R> (QST_MAP_ABS_P)
+  double* cdf = nullptr;  // scratch of the sampled classical fidelity, allocated on first use
   int sweeps = 10;       // cold-start Jacobi sweeps
   int warm_sweeps = 2;   // warm-start sweeps (0: never warm-start)
   bool warm_valid = false;
@@ -500,6 +501,44 @@ template <class R> struct Engine {
     return QST_OK;
   }
 
+  // Sec. 2.3 eq. F_CF (samples == 0) or eq. fc_sample between rho^ of the current parameters (input f)
+  // and the target distribution P.
+  static qst_status classical_fidelity(qst_ctx* c, const void* f_user, const void* P_user, long long samples,
+                                       unsigned long long seed, double* Fc) {
+    Work<R>* w = W<R>(c);
+    const Dims& D = c->D;
+    qst_status st;
+    const R* f = (const R*)stage_input(c, f_user, (size_t)D.n * sizeof(R), w->fstage, &st);
+    if (st != QST_OK) return st;
+    if (!c->hidden_valid || f_user != c->f_last) {
+      if ((st = validate_f<R>(c, f)) != QST_OK) return st;
+      if ((st = hidden(c, w->theta, f)) != QST_OK) return st;
+      c->hidden_valid = true;
+      c->f_last = f_user;
+    }
+    if ((st = forward_state(c, w->theta)) != QST_OK) return st;
+    const PovmB<R>& B = povmB<R>(c);
+    QST_CU(povm_lo_fwd<R>(D, w->X, w->Wlo, B, c->stream));
+    QST_CU(povm_hi_fwd<R>(D, w->Wlo, w->Whi, B, c->stream));  // q, unnormalised, in Whi
+    const R* P = (const R*)stage_input(c, P_user, (size_t)D.n * sizeof(R), w->fstage, &st);  // f is consumed
+    if (st != QST_OK) return st;
+    double* out = w->scal + 5;
+    if (samples == 0) {
+      QST_CU(classical_fidelity_exact<R>(D.n, w->Whi, P, w->scal, w->partials, w->counters + CNT_FID, out,
+                                         c->stream));
+      c->launches += 3;
+    } else {
+      if (!c->cdf) QST_CU(dalloc(c, &c->cdf, (size_t)fidelity_cdf_len(D.n)));
+      QST_CU(classical_fidelity_sampled<R>(D.n, w->Whi, P, samples, seed, w->scal, c->cdf, w->partials,
+                                           w->counters + CNT_FID, out, c->stream));
+      c->launches += 6;
+    }
+    QST_CU(cudaMemcpyAsync(c->h_scal, w->scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    QST_CU(cudaStreamSynchronize(c->stream));
+    *Fc = c->h_scal[5];
+    return QST_OK;
+  }
+
   static qst_status get_rho(qst_ctx* c, const void* f_user, void* rho_out, double* loss) {
     Work<R>* w = W<R>(c);
     const Dims& D = c->D;
@@ -775,6 +814,13 @@ qst_status qst_get_rho(qst_ctx* c, const void* f, void* rho_out, double* loss) {
   if (!c || !f) return QST_E_INVAL;
   if (!c->params_set) return QST_E_STATE;
   return QST_DISPATCH(c, get_rho(c, f, rho_out, loss));
+}
+
+qst_status qst_classical_fidelity(qst_ctx* c, const void* f, const void* P, long long samples,
+                                  unsigned long long seed, double* Fc) {
+  if (!c || !f || !P || !Fc || samples < 0) return QST_E_INVAL;
+  if (!c->params_set) return QST_E_STATE;
+  return QST_DISPATCH(c, classical_fidelity(c, f, P, samples, seed, Fc));
 }
 
 qst_status qst_reconstruct(qst_ctx* c, const void* f, int iters, void* rho_out, double* final_loss) {

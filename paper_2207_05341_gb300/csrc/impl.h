@@ -53,6 +53,7 @@ enum Counter {
   CNT_AMAXT = 8,  // max |re|, |im| of T as float bits: folded in by the producer of t, read by the plane
                   // writer, cleared by the product that reads the planes
   CNT_AMAXG = 9,  // the same for G
+  CNT_FID = 10,   // classical fidelity reductions
   CNT_COUNT = 16
 };
 constexpr int kScaleT = 3;  // scal slot of the power-of-two scale of T (mixed path)
@@ -162,6 +163,18 @@ cudaError_t tc_herm_square(int d, const void* Tb, int fmt, const double* scal, f
 cudaError_t tc_gt_product(int d, const void* Gb, const void* Tb, int fmt, const double* scal, float2* Y,
                           unsigned int* err, unsigned int* clear, cudaStream_t s);
 bool tc_available();
+
+// ---- classical fidelity (fidelity.cu) ----
+// eq. F_CF from q (unnormalised Born probabilities of X, Tr X in scal[0]) and a target P: (sum sqrt(q P / Tr X))^2
+// -> *out (device).  Sampled (eq. fc_sample): needs cdf with fidelity_cdf_len(n) doubles of scratch.
+long long fidelity_cdf_len(long long n);
+template <class R>
+cudaError_t classical_fidelity_exact(long long n, const R* q, const R* P, const double* scal, double* partials,
+                                     unsigned int* counter, double* out, cudaStream_t s);
+template <class R>
+cudaError_t classical_fidelity_sampled(long long n, const R* q, const R* P, long long samples,
+                                       unsigned long long seed, const double* scal, double* cdf, double* partials,
+                                       unsigned int* counter, double* out, cudaStream_t s);
 // cuTensorMapEncodeTiled from the driver (NULL when unavailable).
 void* tma_encoder();
 

@@ -41,6 +41,7 @@ EXPORTED = [
     "qst_timing_enable", "qst_timing_read", "qst_probs_static", "qst_graph_enable",
     "qst_batch_init", "qst_batch_context", "qst_batch_set_params", "qst_batch_step",
     "qst_batch_reconstruct", "qst_batch_kernel_launches", "qst_batch_sync", "qst_batch_destroy",
+    "qst_classical_fidelity",
 ]
 
 PHASES = ["hidden", "build_T", "x_fwd", "povm_lo", "povm_hi", "povm_adj", "gt", "sym", "w2", "w1"]
@@ -92,6 +93,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "qst_step": (i, [vp, vp, pd]),
         "qst_reconstruct": (i, [vp, vp, i, vp, pd]),
         "qst_get_rho": (i, [vp, vp, vp, pd]),
+        "qst_classical_fidelity": (i, [vp, vp, vp, ctypes.c_longlong, ctypes.c_ulonglong, pd]),
         "qst_state_bytes": (sz, [vp]),
         "qst_get_state": (i, [vp, vp, sz]),
         "qst_set_state": (i, [vp, vp, sz]),
@@ -215,6 +217,14 @@ def qst_reconstruct(ctx: int, f, iters: int, rho_out=None, want_loss: bool = Tru
     st = _check(load().qst_reconstruct(ctx, ptr(f), int(iters), ptr(rho_out),
                                        ctypes.byref(loss) if want_loss else None), "qst_reconstruct")
     return (loss.value if want_loss else None), st
+
+
+def qst_classical_fidelity(ctx: int, f, P, samples: int = 0, seed: int = 0) -> float:
+    """Classical fidelity (Sec. 2.3): exact eq. F_CF for samples == 0, else eq. fc_sample."""
+    out = ctypes.c_double()
+    _check(load().qst_classical_fidelity(ctx, ptr(f), ptr(P), int(samples), int(seed), ctypes.byref(out)),
+           "qst_classical_fidelity")
+    return out.value
 
 
 def qst_get_rho(ctx: int, f, rho_out, want_loss: bool = False) -> tuple[float | None, int]:
