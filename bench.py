@@ -370,6 +370,37 @@ def fidelity_eval(torch, qst, dev, stream, theta0, lam, seed, steps=200, samples
         qst.qst_destroy(ctx)
 
 
+def sampler_eval(torch, qst, synth, dev, stream, lam, seed):
+    """Synthetic data on the GPU (qst_test_state, qst_probs, qst_sample_counts) against the host
+    generator (numpy multinomial) for the headline workload's 10^7 shots at N = 11."""
+    opt = qst.qst_default_options()
+    ctx = qst.qst_init(NQ, opt=opt, stream=stream.cuda_stream)
+    try:
+        d, n = 2 ** NQ, 4 ** NQ
+        rho = torch.empty((d, d), dtype=torch.complex64, device=dev)
+        P32 = torch.empty(n, dtype=torch.float32, device=dev)
+        counts = torch.empty(n, dtype=torch.int64, device=dev)
+        f = torch.empty(n, dtype=torch.float32, device=dev)
+        qst.qst_test_state(ctx, qst.QST_STATE_GHZI, 1.0 - lam, rho)
+        qst.qst_probs(ctx, rho, P32)
+        P = P32.double()
+        qst.qst_sample_counts(ctx, P, SHOTS, seed, counts, f)  # warm-up (allocates the scratch)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        qst.qst_sample_counts(ctx, P, SHOTS, seed, counts, f)
+        torch.cuda.synchronize()
+        gpu_ms = (time.perf_counter() - t0) * 1e3
+        Ph = P.cpu().numpy()
+        t0 = time.perf_counter()
+        synth.multinomial_counts(Ph, SHOTS, seed)
+        host_ms = (time.perf_counter() - t0) * 1e3
+        return {"workload": f"N=11 GHZi state, depolarizing lambda={lam}, {SHOTS} shots",
+                "gpu_counts_ms": gpu_ms, "host_numpy_multinomial_ms": host_ms,
+                "counts_sum": int(counts.sum().item())}
+    finally:
+        qst.qst_destroy(ctx)
+
+
 def cpu_baseline(f, theta0, seconds=12.0):
     """The FP64 oracle, as it stands, on the host cores: full N = 11 iterations."""
     import oracle as O
@@ -638,6 +669,7 @@ def main_ours(args):
     if args.ttf:
         with torch.cuda.stream(stream):
             line["fidelity_on_device"] = fidelity_eval(torch, qst, dev, stream, theta0, LAMBDAS[1], STATE_SEEDS[1])
+            line["synthetic_data_on_device"] = sampler_eval(torch, qst, synth, dev, stream, LAMBDAS[1], 5)
     if args.batch:
         line["batch_c4"] = batch_c4(torch, qst, synth, dev, args.steps, args.warmup)
         line["batch_c4_mixed"] = batch_c4(torch, qst, synth, dev, args.steps, args.warmup, prec=qst.QST_MIXED)

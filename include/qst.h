@@ -188,6 +188,26 @@ qst_status qst_get_rho(qst_ctx* ctx, const void* f, void* rho_out, double* loss)
 qst_status qst_classical_fidelity(qst_ctx* ctx, const void* f, const void* P, long long samples,
                                   unsigned long long seed, double* Fc);
 
+/* ---- synthetic data on the GPU (Sec. 4: the test states of the sweeps, multinomial sampling) ---- */
+enum { QST_STATE_PRODUCT = 0,  /* ((|0> + |1>) / sqrt 2)^N */
+       QST_STATE_GHZI = 1,     /* (|0...0> + i |1...1>) / sqrt 2 */
+       QST_STATE_W = 2 };      /* equal superposition of the N one-excitation basis states */
+
+/* rho = w |psi><psi| + (1 - w) I / d for the state `kind`, with w in [0, 1]: white noise of strength p
+ * is w = p, the depolarising channel with lambda is w = 1 - lambda.  rho: device, d x d complex of the
+ * context's precision (complex64, or complex128 for QST_FP64), row-major, written. */
+qst_status qst_test_state(qst_ctx* ctx, int kind, double w, void* rho);
+
+/* Seeded multinomial counts of `shots` draws from P (device, n = 4^N doubles, each in [0, 1]; need not
+ * sum to 1 exactly).  Each P_k becomes the integer weight floor(P_k 2^52); shot s draws
+ * t_s = floor((splitmix64(seed, s) >> 11) W / 2^53) (W = total weight; SplitMix64 as in
+ * qst_classical_fidelity) and counts outcome k_s = the smallest k whose running weight exceeds t_s.
+ * All integer arithmetic: the counts are exact and reproducible.  counts: device, n int64, written;
+ * f: device or NULL, n reals of the context precision, written with counts / shots.  QST_E_INPUT for a
+ * P that is not finite, above 1, or all zero.  The first call allocates (n + n / 2048) words of scratch. */
+qst_status qst_sample_counts(qst_ctx* ctx, const double* P, long long shots, unsigned long long seed,
+                             long long* counts, void* f);
+
 /* Checkpoint of parameters, Rprop state and iteration count (and, for
  * QST_MAP_ABS_P, the eigenvectors that warm-start the next eigendecomposition),
  * as an opaque host byte buffer of qst_state_bytes(ctx) bytes.  Restoring it

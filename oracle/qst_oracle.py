@@ -448,6 +448,21 @@ def splitmix64(seed: int, s: np.ndarray) -> np.ndarray:
     return z ^ (z >> np.uint64(31))
 
 
+def multinomial_counts_integer(P: np.ndarray, shots: int, seed: int) -> np.ndarray:
+    """Seeded multinomial counts by integer inverse CDF (the sampler of the synthetic sweeps, Sec. 4).
+
+    Weights w_k = floor(max(P_k, 0) 2^52), exact running sums C, W = C[-1]; draw s takes
+    t_s = floor((splitmix64(seed, s) >> 11) W / 2^53) and counts k_s = the smallest k with C_k > t_s.
+    """
+    w = np.floor(np.clip(np.asarray(P, dtype=np.float64), 0, None) * 2.0 ** 52).astype(np.uint64)
+    C = np.cumsum(w, dtype=np.uint64)
+    W = int(C[-1])
+    a = (splitmix64(seed, np.arange(shots)) >> np.uint64(11)).astype(object)
+    t = np.array([(int(x) * W) >> 53 for x in a], dtype=np.uint64)
+    k = np.searchsorted(C, t, side="right")
+    return np.bincount(k, minlength=w.size).astype(np.int64)
+
+
 def sampled_classical_fidelity(P_hat: np.ndarray, P: np.ndarray, samples: int, seed: int) -> float:
     """Sec. 2.3 eq. fc_sample: F_c ~ (E_{k ~ P_hat}[sqrt(P_k / P_hat_k)])^2 from `samples` draws.
 

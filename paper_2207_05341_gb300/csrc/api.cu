@@ -60,6 +60,7 @@ struct qst_ctx {
   int tmax = 0, tcount = 0, tslot = -1;
   void* apw = nullptr;  // AbsPWork<R> (QST_MAP_ABS_P)
   double* cdf = nullptr;  // scratch of the sampled classical fidelity, allocated on first use
+  unsigned long long* samp = nullptr;  // scratch of qst_sample_counts, allocated on first use
   int sweeps = 10;       // cold-start Jacobi sweeps
   int warm_sweeps = 2;   // warm-start sweeps (0: never warm-start)
   bool warm_valid = false;
@@ -821,6 +822,44 @@ qst_status qst_classical_fidelity(qst_ctx* c, const void* f, const void* P, long
   if (!c || !f || !P || !Fc || samples < 0) return QST_E_INVAL;
   if (!c->params_set) return QST_E_STATE;
   return QST_DISPATCH(c, classical_fidelity(c, f, P, samples, seed, Fc));
+}
+
+qst_status qst_test_state(qst_ctx* c, int kind, double w, void* rho) {
+  if (!c || !rho || !(w >= 0.0 && w <= 1.0)) return QST_E_INVAL;
+  if (kind != QST_STATE_PRODUCT && kind != QST_STATE_GHZI && kind != QST_STATE_W) return QST_E_INVAL;
+  if (!is_device_ptr(rho)) return QST_E_INVAL;
+  cudaError_t e = c->prec == QST_FP64 ? make_test_state<double>(c->N, kind, w, (cx_t<double>*)rho, c->stream)
+                                      : make_test_state<float>(c->N, kind, w, (cx_t<float>*)rho, c->stream);
+  QST_CU(e);
+  c->launches += 1;
+  return QST_OK;
+}
+
+qst_status qst_sample_counts(qst_ctx* c, const double* P, long long shots, unsigned long long seed,
+                             long long* counts, void* f) {
+  if (!c || !P || !counts || shots < 0) return QST_E_INVAL;
+  if (!is_device_ptr(P) || !is_device_ptr(counts) || (f && !is_device_ptr(f))) return QST_E_INVAL;
+  const long long n = c->D.n;
+  if (!c->samp) QST_CU(dalloc(c, &c->samp, (size_t)sampler_scratch_words(n)));
+  unsigned int* flags = c->prec == QST_FP64 ? W<double>(c)->flags : W<float>(c)->flags;
+  QST_CU(cudaMemsetAsync(flags + 2, 0, sizeof(unsigned int), c->stream));
+  QST_CU(multinomial_prepare(n, P, c->samp, counts, flags + 2, c->stream));
+  // the total weight and the input check decide whether draws can be made
+  unsigned long long W = 0;
+  QST_CU(cudaMemcpyAsync(c->h_flags + 2, flags + 2, sizeof(unsigned int), cudaMemcpyDeviceToHost, c->stream));
+  QST_CU(cudaMemcpyAsync(&W, c->samp + n - 1, sizeof(W), cudaMemcpyDeviceToHost, c->stream));
+  QST_CU(cudaStreamSynchronize(c->stream));
+  c->launches += 3;
+  if (c->h_flags[2] != 0u || W == 0ull) return QST_E_INPUT;
+  QST_CU(multinomial_draw(n, shots, seed, c->samp, counts, c->stream));
+  c->launches += shots > 0 ? 1 : 0;
+  if (f && shots > 0) {
+    cudaError_t e = c->prec == QST_FP64 ? counts_to_frequencies<double>(n, counts, shots, (double*)f, c->stream)
+                                        : counts_to_frequencies<float>(n, counts, shots, (float*)f, c->stream);
+    QST_CU(e);
+    c->launches += 1;
+  }
+  return QST_OK;
 }
 
 qst_status qst_reconstruct(qst_ctx* c, const void* f, int iters, void* rho_out, double* final_loss) {

@@ -164,6 +164,20 @@ cudaError_t tc_gt_product(int d, const void* Gb, const void* Tb, int fmt, const 
                           unsigned int* err, unsigned int* clear, cudaStream_t s);
 bool tc_available();
 
+// ---- synthetic data on the GPU (sampler.cu) ----
+// rho = w |psi><psi| + (1 - w) I / d for the test state `kind` (QST_STATE_*), d x d complex.
+template <class R> cudaError_t make_test_state(int N, int kind, double w, cx_t<R>* rho, cudaStream_t s);
+// Multinomial counts: prepare (integer weights of P and their exact running sum into scratch of
+// sampler_scratch_words(n) words, counts zeroed, *bad |= 1 for a probability that is not in [0, 1]);
+// the total weight is scratch[n - 1]; then draw `shots` outcomes into counts.
+long long sampler_scratch_words(long long n);
+cudaError_t multinomial_prepare(long long n, const double* P, unsigned long long* scratch, long long* counts,
+                                unsigned int* bad, cudaStream_t s);
+cudaError_t multinomial_draw(long long n, long long shots, unsigned long long seed, const unsigned long long* scratch,
+                             long long* counts, cudaStream_t s);
+template <class R> cudaError_t counts_to_frequencies(long long n, const long long* counts, long long shots, R* f,
+                                                     cudaStream_t s);
+
 // ---- classical fidelity (fidelity.cu) ----
 // eq. F_CF from q (unnormalised Born probabilities of X, Tr X in scal[0]) and a target P: (sum sqrt(q P / Tr X))^2
 // -> *out (device).  Sampled (eq. fc_sample): needs cdf with fidelity_cdf_len(n) doubles of scratch.

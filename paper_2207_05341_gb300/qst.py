@@ -28,6 +28,9 @@ QST_W_CLAMP = 1
 QST_MAP_CHOL_H = 0
 QST_MAP_ABS_P = 1
 QST_MAP_CHOL_DELTA = 2
+QST_STATE_PRODUCT = 0
+QST_STATE_GHZI = 1
+QST_STATE_W = 2
 QST_FP64 = 0
 QST_FP32 = 1
 QST_MIXED = 2
@@ -41,7 +44,7 @@ EXPORTED = [
     "qst_timing_enable", "qst_timing_read", "qst_probs_static", "qst_graph_enable",
     "qst_batch_init", "qst_batch_context", "qst_batch_set_params", "qst_batch_step",
     "qst_batch_reconstruct", "qst_batch_kernel_launches", "qst_batch_sync", "qst_batch_destroy",
-    "qst_classical_fidelity",
+    "qst_classical_fidelity", "qst_test_state", "qst_sample_counts",
 ]
 
 PHASES = ["hidden", "build_T", "x_fwd", "povm_lo", "povm_hi", "povm_adj", "gt", "sym", "w2", "w1"]
@@ -94,6 +97,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "qst_reconstruct": (i, [vp, vp, i, vp, pd]),
         "qst_get_rho": (i, [vp, vp, vp, pd]),
         "qst_classical_fidelity": (i, [vp, vp, vp, ctypes.c_longlong, ctypes.c_ulonglong, pd]),
+        "qst_test_state": (i, [vp, i, d, vp]),
+        "qst_sample_counts": (i, [vp, vp, ctypes.c_longlong, ctypes.c_ulonglong, vp, vp]),
         "qst_state_bytes": (sz, [vp]),
         "qst_get_state": (i, [vp, vp, sz]),
         "qst_set_state": (i, [vp, vp, sz]),
@@ -225,6 +230,17 @@ def qst_classical_fidelity(ctx: int, f, P, samples: int = 0, seed: int = 0) -> f
     _check(load().qst_classical_fidelity(ctx, ptr(f), ptr(P), int(samples), int(seed), ctypes.byref(out)),
            "qst_classical_fidelity")
     return out.value
+
+
+def qst_test_state(ctx: int, kind: int, w: float, rho) -> int:
+    """rho = w |psi><psi| + (1 - w) I / d for QST_STATE_PRODUCT / GHZI / W (device d x d complex)."""
+    return _check(load().qst_test_state(ctx, int(kind), float(w), ptr(rho)), "qst_test_state")
+
+
+def qst_sample_counts(ctx: int, P, shots: int, seed: int, counts, f=None) -> int:
+    """Seeded multinomial counts of `shots` draws from P (device FP64) into counts (device int64)."""
+    return _check(load().qst_sample_counts(ctx, ptr(P), int(shots), int(seed), ptr(counts), ptr(f) if f is not None
+                                           else None), "qst_sample_counts")
 
 
 def qst_get_rho(ctx: int, f, rho_out, want_loss: bool = False) -> tuple[float | None, int]:

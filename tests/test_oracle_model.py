@@ -249,3 +249,25 @@ def test_sampled_classical_fidelity_pins():
     c = np.cumsum(Pz)
     k = np.searchsorted(c, u * c[-1], side="right")
     assert np.all(Pz[k] > 0)
+
+
+def test_integer_multinomial_sampler_pins():
+    """Sec. 4 sampling: counts sum to the shots, never land on zero-probability outcomes, follow P
+    (chi-square), and a one-outcome distribution takes every shot."""
+    rng = np.random.default_rng(8)
+    n = 64
+    P = rng.dirichlet(np.ones(n))
+    P[::5] = 0.0
+    P /= P.sum()
+    S = 200_000
+    c = O.multinomial_counts_integer(P, S, 21)
+    assert c.sum() == S and np.all(c[P == 0] == 0)
+    m = P > 0
+    chi2 = np.sum((c[m] - S * P[m]) ** 2 / (S * P[m]))
+    dof = m.sum() - 1
+    assert chi2 < dof + 5 * np.sqrt(2 * dof)
+    one = np.zeros(n); one[17] = 1.0
+    assert np.array_equal(O.multinomial_counts_integer(one, 1000, 3), 1000 * (np.arange(n) == 17))
+    # same seed, same counts; another seed, other counts
+    assert np.array_equal(O.multinomial_counts_integer(P, 5000, 4), O.multinomial_counts_integer(P, 5000, 4))
+    assert not np.array_equal(O.multinomial_counts_integer(P, 5000, 4), O.multinomial_counts_integer(P, 5000, 5))
