@@ -172,6 +172,114 @@ def network_forward(theta: np.ndarray, f: np.ndarray, N: int):
     return pre, h, t
 
 
+# --------------------------------------------------------------------------
+# The CNN mapping network of App. A
+# --------------------------------------------------------------------------
+
+CNN_MAPS = 10  # feature maps of the 3 x 3 convolution
+CNN_GRID = 8   # pooled grid per map (the pooling window is 2^(N-3) square): 10 x 8 x 8 = 640 features
+
+
+def cnn_sizes(N: int):
+    """(n, H, F): outputs 4^N, hidden width 4N, pooled features 640."""
+    return 4 ** N, 4 * N, CNN_MAPS * CNN_GRID ** 2
+
+
+def unpack_theta_cnn(theta: np.ndarray, N: int):
+    """[W2^T (H x n) | b2 (n) | W1 (H x F) | b1 (H) | conv W (10 x 3 x 3) | conv b (10)]."""
+    n, H, F = cnn_sizes(N)
+    o = 0
+    W2T = theta[o:o + H * n].reshape(H, n); o += H * n
+    b2 = theta[o:o + n]; o += n
+    W1 = theta[o:o + H * F].reshape(H, F); o += H * F
+    b1 = theta[o:o + H]; o += H
+    cW = theta[o:o + CNN_MAPS * 9].reshape(CNN_MAPS, 3, 3); o += CNN_MAPS * 9
+    cB = theta[o:o + CNN_MAPS]; o += CNN_MAPS
+    assert o == theta.size
+    return W2T, b2, W1, b1, cW, cB
+
+
+def pack_theta_cnn(W2T, b2, W1, b1, cW, cB) -> np.ndarray:
+    return np.concatenate([np.ravel(W2T), np.ravel(b2), np.ravel(W1), np.ravel(b1), np.ravel(cW), np.ravel(cB)])
+
+
+def conv3x3(img: np.ndarray, cW: np.ndarray, cB: np.ndarray, dtype=np.float64) -> np.ndarray:
+    """App. A: 3 x 3 convolution, stride 1, zero padding 1, 10 maps with bias.
+
+    out[c, y, x] = b_c + sum_{ky, kx} W[c, ky, kx] img[y + ky - 1, x + kx - 1], accumulated in `dtype`
+    in the order bias, then (ky, kx) row-major, each product and sum rounded to `dtype` (so a float32
+    evaluation decides the pooling argmax exactly as a float32 kernel that accumulates in this order).
+    """
+    d = img.shape[0]
+    pad = np.zeros((d + 2, d + 2), dtype=dtype)
+    pad[1:-1, 1:-1] = img.astype(dtype)
+    out = np.empty((cW.shape[0], d, d), dtype=dtype)
+    for c in range(cW.shape[0]):
+        acc = np.full((d, d), dtype(cB[c]), dtype=dtype)
+        for ky in range(3):
+            for kx in range(3):
+                acc = acc + dtype(cW[c, ky, kx]) * pad[ky:ky + d, kx:kx + d]
+        out[c] = acc
+    return out
+
+
+def cnn_features(f: np.ndarray, cW, cB, N: int, decision=np.float64):
+    """App. A: f as a d x d matrix (row-major) -> conv -> ReLU -> max-pool (window 2^(N-3), stride the
+    same) -> 640 features.  The argmax of each window is taken on the `decision`-precision convolution
+    (first row-major index on ties); the feature is ReLU of the FP64 convolution there.
+    Returns (features (640,), argmax positions (640, 2), FP64 convolution at them)."""
+    d = 1 << N
+    p = d // CNN_GRID
+    img = np.asarray(f, dtype=np.float64).reshape(d, d)
+    conv_dec = conv3x3(img, cW, cB, decision)
+    conv64 = conv3x3(img, cW, cB, np.float64)
+    feats, pos, vals = [], [], []
+    for c in range(CNN_MAPS):
+        for I in range(CNN_GRID):
+            for J in range(CNN_GRID):
+                win = conv_dec[c, I * p:(I + 1) * p, J * p:(J + 1) * p]
+                a = int(np.argmax(win))
+                y, x = I * p + a // p, J * p + a % p
+                v = conv64[c, y, x]
+                feats.append(max(v, 0.0)); pos.append((y, x)); vals.append(v)
+    return np.array(feats), np.array(pos), np.array(vals)
+
+
+def network_forward_cnn(theta: np.ndarray, f: np.ndarray, N: int, decision=np.float64):
+    """App. A network: features (640) -> 4N hidden (LeakyReLU) -> 4^N linear outputs."""
+    W2T, b2, W1, b1, cW, cB = unpack_theta_cnn(theta, N)
+    feats, pos, vals = cnn_features(f, cW, cB, N, decision)
+    pre = W1 @ feats + b1
+    h = leaky_relu(pre)
+    t = W2T.T @ h + b2
+    return pre, h, t, feats, pos, vals
+
+
+def network_backward_cnn(theta, f, N, dt, pre, h, feats, pos, vals):
+    """Chain rule of the App. A network back from dL/dt to dL/dtheta (CNN layout)."""
+    W2T, b2, W1, b1, cW, cB = unpack_theta_cnn(theta, N)
+    d = 1 << N
+    dW2T = np.outer(h, dt)
+    db2 = dt
+    dh = W2T @ dt
+    dpre = dh * np.where(pre > 0, 1.0, LEAKY_SLOPE)
+    dW1 = np.outer(dpre, feats)
+    db1 = dpre
+    dfeat = W1.T @ dpre
+    pad = np.zeros((d + 2, d + 2))
+    pad[1:-1, 1:-1] = np.asarray(f, dtype=np.float64).reshape(d, d)
+    dcW = np.zeros((CNN_MAPS, 3, 3))
+    dcB = np.zeros(CNN_MAPS)
+    for i in range(CNN_MAPS * CNN_GRID ** 2):
+        if vals[i] <= 0:
+            continue  # ReLU'(conv) = 0 at the pooled position
+        c = i // CNN_GRID ** 2
+        y, x = pos[i]
+        dcW[c] += dfeat[i] * pad[y:y + 3, x:x + 3]
+        dcB[c] += dfeat[i]
+    return pack_theta_cnn(dW2T, db2, dW1, db1, dcW, dcB)
+
+
 def hermitian_from_output(t: np.ndarray) -> np.ndarray:
     """Sec. 3.1/3.2: the 4^N real outputs become a Hermitian d x d matrix T.
 
@@ -293,8 +401,11 @@ def nll(p: np.ndarray, f: np.ndarray) -> float:
     return float(-np.sum(f[m] * np.log(p[m])))
 
 
-def state_from_theta(theta, f, N, mapping="chol_h", P=2.0):
-    pre, h, t = network_forward(theta, f, N)
+def state_from_theta(theta, f, N, mapping="chol_h", P=2.0, network="fnn", decision=np.float64):
+    if network == "cnn":
+        t = network_forward_cnn(theta, f, N, decision)[2]
+    else:
+        pre, h, t = network_forward(theta, f, N)
     if mapping == "chol_delta":
         return chol_delta(lower_from_output(t))
     T = hermitian_from_output(t)
@@ -302,7 +413,7 @@ def state_from_theta(theta, f, N, mapping="chol_h", P=2.0):
     return rho
 
 
-def loss_and_grad(theta, f, povm, N, mapping="chol_h", P=2.0):
+def loss_and_grad(theta, f, povm, N, mapping="chol_h", P=2.0, network="fnn", decision=np.float64):
     """One forward and backward pass of the Sec. 3 network through the likelihood.
 
     Returns (L, dL/dtheta, aux) with aux holding rho, p and the intermediates.
@@ -317,8 +428,11 @@ def loss_and_grad(theta, f, povm, N, mapping="chol_h", P=2.0):
       t         <- Gam (output_grad_from_hermitian, or output_grad_from_lower)
       W2^T, b2, h <- t;  pre <- h (LeakyReLU');  W1, b1 <- pre.
     """
-    W1, W2T, b2, b1 = unpack_theta(theta, N)
-    pre, h, t = network_forward(theta, f, N)
+    if network == "cnn":
+        pre, h, t, feats, pos, vals = network_forward_cnn(theta, f, N, decision)
+    else:
+        W1, W2T, b2, b1 = unpack_theta(theta, N)
+        pre, h, t = network_forward(theta, f, N)
     T = lower_from_output(t) if mapping == "chol_delta" else hermitian_from_output(t)
     d = T.shape[0]
     if mapping in ("chol_h", "chol_delta"):
@@ -341,6 +455,10 @@ def loss_and_grad(theta, f, povm, N, mapping="chol_h", P=2.0):
     else:
         Gam = _abs_p_backward(T, P, G_rho)
     dt = output_grad_from_lower(Gam) if mapping == "chol_delta" else output_grad_from_hermitian(Gam)
+    if network == "cnn":
+        grad = network_backward_cnn(theta, f, N, dt, pre, h, feats, pos, vals)
+        aux = dict(rho=rho, p=p, T=T, t=t, h=h, pre=pre, Gam=Gam, dt=dt)
+        return L, grad, aux
 
     db2 = dt
     dW2T = np.outer(h, dt)
@@ -384,7 +502,8 @@ def rprop_update(theta, grad, state: RpropState,
     return theta - sg * state.step
 
 
-def reconstruct(theta0, f, povm, N, iters, mapping="chol_h", P=2.0, callback=None):
+def reconstruct(theta0, f, povm, N, iters, mapping="chol_h", P=2.0, callback=None, network="fnn",
+                decision=np.float64):
     """The NN-QST loop of Fig. 1: forward, likelihood, backward, Rprop, repeated.
 
     Returns (theta, rho, losses).  ``callback(it, rho)`` runs after each step
@@ -394,12 +513,12 @@ def reconstruct(theta0, f, povm, N, iters, mapping="chol_h", P=2.0, callback=Non
     st = RpropState(theta.size)
     losses = []
     for it in range(iters):
-        L, g, aux = loss_and_grad(theta, f, povm, N, mapping, P)
+        L, g, aux = loss_and_grad(theta, f, povm, N, mapping, P, network, decision)
         losses.append(L)
         theta = rprop_update(theta, g, st)
         if callback is not None:
             callback(it, aux["rho"])
-    rho = state_from_theta(theta, f, N, mapping, P)
+    rho = state_from_theta(theta, f, N, mapping, P, network, decision)
     return theta, rho, np.array(losses)
 
 

@@ -111,6 +111,28 @@ def theta_size(N: int) -> int:
     return 2 * H * n + n + H
 
 
+def theta_size_cnn(N: int) -> int:
+    """Parameters of the CNN mapping network: W2^T (4N x n), b2, W1 (4N x 640), b1, conv (10 x 9), conv bias."""
+    n, H = 4 ** N, 4 * N
+    return H * n + n + H * 640 + H + 90 + 10
+
+
+def init_theta_cnn(N: int, seed: int) -> np.ndarray:
+    """Seeded initial CNN parameters (FP64, flat, the library's CNN layout
+    [W2^T | b2 | W1 | b1 | conv W | conv b]); each layer uniform in +-1/sqrt(fan_in):
+    the convolution has fan_in 9, the first dense layer 640, the output layer 4N."""
+    n, H = 4 ** N, 4 * N
+    r = _rng(seed)
+    ac, a1, a2 = 1.0 / 3.0, 1.0 / np.sqrt(640.0), 1.0 / np.sqrt(H)
+    cW = r.uniform(-ac, ac, size=90)
+    cB = r.uniform(-ac, ac, size=10)
+    W1 = r.uniform(-a1, a1, size=H * 640)
+    b1 = r.uniform(-a1, a1, size=H)
+    W2T = r.uniform(-a2, a2, size=H * n)
+    b2 = r.uniform(-a2, a2, size=n)
+    return np.concatenate([W2T, b2, W1, b1, cW, cB])
+
+
 def init_theta(N: int, seed: int) -> np.ndarray:
     """Seeded initial network parameters in FP64, flat, in the library's theta layout.
 

@@ -271,3 +271,45 @@ def test_integer_multinomial_sampler_pins():
     # same seed, same counts; another seed, other counts
     assert np.array_equal(O.multinomial_counts_integer(P, 5000, 4), O.multinomial_counts_integer(P, 5000, 4))
     assert not np.array_equal(O.multinomial_counts_integer(P, 5000, 4), O.multinomial_counts_integer(P, 5000, 5))
+
+
+def test_cnn_conv_and_pool_match_library_routines():
+    """App. A: the 3 x 3 convolution with zero padding is scipy's 2-D correlation plus the bias; the
+    pooled features are the maxima of ReLU(conv) over 2^(N-3)-square windows (block-reshape max)."""
+    scipy_signal = pytest.importorskip("scipy.signal")
+    rng = np.random.default_rng(12)
+    for N in (3, 4, 5):
+        d = 1 << N
+        f = rng.dirichlet(np.ones(d * d))
+        th = synth.init_theta_cnn(N, 13 + N)
+        W2T, b2, W1, b1, cW, cB = O.unpack_theta_cnn(th, N)
+        conv = O.conv3x3(f.reshape(d, d), cW, cB)
+        for c in range(O.CNN_MAPS):
+            want = scipy_signal.correlate2d(f.reshape(d, d), cW[c], mode="same", boundary="fill") + cB[c]
+            np.testing.assert_allclose(conv[c], want, atol=1e-15)
+        feats, pos, vals = O.cnn_features(f, cW, cB, N)
+        p = d // O.CNN_GRID
+        blocks = np.maximum(conv, 0).reshape(O.CNN_MAPS, O.CNN_GRID, p, O.CNN_GRID, p).max(axis=(2, 4))
+        np.testing.assert_allclose(feats, blocks.ravel(), atol=1e-15)
+        assert feats.size == 640 and th.size == synth.theta_size_cnn(N)
+
+
+def test_gradient_central_fd_cnn_sampled():
+    """The CNN network's backward (dense layers, max-pool routing, convolution) against central differences:
+    every convolution parameter and a sample of the dense ones."""
+    M = O.tetrahedral_povm()
+    N = 3
+    rho = synth.ginibre_mixed(N, 4, 70)
+    f = O.born_probabilities(rho, M).real  # distinct entries: no pooling ties
+    theta = synth.init_theta_cnn(N, 71)
+    L, g, _ = O.loss_and_grad(theta, f, M, N, network="cnn")
+    rng = np.random.default_rng(3)
+    n_conv = 100
+    idx = np.r_[np.arange(theta.size - n_conv, theta.size), rng.choice(theta.size - n_conv, 60, replace=False)]
+    h = 1e-6
+    for i in idx:
+        tp = theta.copy(); tp[i] += h
+        tm = theta.copy(); tm[i] -= h
+        fd = (O.loss_and_grad(tp, f, M, N, network="cnn")[0] - O.loss_and_grad(tm, f, M, N, network="cnn")[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 2e-6 * max(1.0, np.abs(g).max()), (i, fd, g[i])
+    assert np.abs(g[-n_conv:]).max() > 0  # the convolution does receive gradient
