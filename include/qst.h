@@ -96,13 +96,27 @@ typedef struct qst_options {
                            to even) */
     int eig_warm_sweeps;/* QST_MAP_ABS_P: sweeps when qst_step starts from the previous iteration's
                            eigenvectors (0 = default 2; -1 = always cold; rounded up to even) */
+    int network;        /* QST_NET_FNN (Sec. 3.1, default) or QST_NET_CNN (App. A, N >= 3) */
 } qst_options;
+
+/* Mapping networks.  QST_NET_FNN: the 3-layer network of Sec. 3.1, theta as described above.
+ * QST_NET_CNN: the convolutional network of App. A: f as a 2^N x 2^N matrix (row-major), a 3 x 3
+ * convolution (stride 1, zero padding 1, 10 maps with bias), ReLU, max-pooling over 2^(N-3)-square
+ * windows (640 features), a dense layer to 4N units (LeakyReLU), a dense linear layer to 4^N outputs.
+ * Its theta (qst_theta_size_net(N, QST_NET_CNN) reals) is
+ *   [W2^T (4N x 4^N) | b2 (4^N) | W1 (4N x 640) | b1 (4N) | conv W (10 x 3 x 3) | conv b (10)],
+ * features ordered (map, window row, window column); on pooling ties the first row-major position of
+ * the window is taken. */
+enum { QST_NET_FNN = 0, QST_NET_CNN = 1 };
 
 /* Fill *opt with the paper's settings (Sec. 4.1) and the defaults stated above. */
 void qst_default_options(qst_options* opt);
 
 /* Number of reals in theta for N qubits: 2*H*n + n + H. */
 size_t qst_theta_size(int N);
+
+/* Number of reals in theta for N qubits and mapping network `network` (0 when unsupported). */
+size_t qst_theta_size_net(int N, int network);
 
 /* Create a context for N qubits.
  *   povm   host, K*2*2 complex doubles (interleaved re, im), element a at

@@ -60,6 +60,8 @@ struct qst_ctx {
   int tmax = 0, tcount = 0, tslot = -1;
   void* apw = nullptr;  // AbsPWork<R> (QST_MAP_ABS_P)
   double* cdf = nullptr;  // scratch of the sampled classical fidelity, allocated on first use
+  size_t P = 0;           // parameters: qst_theta_size_net(N, network)
+  bool cnn = false;       // the App. A CNN head instead of the 3-layer FNN
   unsigned long long* samp = nullptr;  // scratch of qst_sample_counts, allocated on first use
   int sweeps = 10;       // cold-start Jacobi sweeps
   int warm_sweeps = 2;   // warm-start sweeps (0: never warm-start)
@@ -138,13 +140,18 @@ template <class R> qst_status alloc_work(qst_ctx* c) {
   memset(w, 0, sizeof(*w));
   c->work = w;
   const Dims& D = c->D;
-  const size_t P = theta_size(c->N);
+  const size_t P = c->P;
   const size_t nn = (size_t)D.d * D.d;
   QST_CU(dalloc(c, &w->theta, P));
   QST_CU(dalloc(c, &w->step, P));
-  QST_CU(dalloc(c, &w->pre, 32));
-  QST_CU(dalloc(c, &w->hid, 32));
-  QST_CU(dalloc(c, &w->dpre, 32));
+  QST_CU(dalloc(c, &w->pre, 64));
+  QST_CU(dalloc(c, &w->hid, 64));
+  QST_CU(dalloc(c, &w->dpre, 64));
+  if (c->cnn) {
+    QST_CU(dalloc(c, &w->feats, 640));
+    QST_CU(dalloc(c, &w->vals, 640));
+    QST_CU(dalloc(c, &w->pos, 640));
+  }
   QST_CU(dalloc(c, &w->T, nn));
   QST_CU(dalloc(c, &w->X, nn));
   QST_CU(dalloc(c, &w->G, nn));
@@ -246,8 +253,13 @@ template <class R> struct Engine {
     // t = W2 h + b2 in the dt buffer (free until the backward writes dL/dt), then T (or its 16-bit planes)
     // Chol_Delta: T lower triangular and T^dag (in Y, free until the backward) for X = T^dag T
     const bool delta = c->opt.mapping == QST_MAP_CHOL_DELTA;
-    QST_CU(net_build_T<R>(D, theta, w->hid, w->dt, mixed ? nullptr : w->T, amax_slot(c, CNT_AMAXT), c->stream,
-                          delta ? w->Y : nullptr));
+    if (c->cnn) {
+      QST_CU(cnn_output<R>(D, theta, w->hid, w->dt, amax_slot(c, CNT_AMAXT), c->stream));
+      if (!mixed) QST_CU(net_hermitian_T<R>(D, w->dt, w->T, delta ? w->Y : nullptr, c->stream));
+    } else {
+      QST_CU(net_build_T<R>(D, theta, w->hid, w->dt, mixed ? nullptr : w->T, amax_slot(c, CNT_AMAXT), c->stream,
+                            delta ? w->Y : nullptr));
+    }
     if (mixed) {
       QST_CU(tc_planes_T(D.d, reinterpret_cast<const float*>(w->dt), w->Tb, tc_fmt(c), w->scal,
                          amax_slot(c, CNT_AMAXT), c->stream));
@@ -333,12 +345,19 @@ template <class R> struct Engine {
   // The bulk weight passes apply to FP32 contexts with H >= 8 and a 16-byte aligned f.
   static bool use_bulk(qst_ctx* c, const R* f) {
     if constexpr (std::is_same<R, float>::value)
-      return c->bulk_passes && wpass_bulk_ok(c->D.H, c->D.n) && ((uintptr_t)f & 15u) == 0;
+      return !c->cnn && c->bulk_passes && wpass_bulk_ok(c->D.H, c->D.n) && ((uintptr_t)f & 15u) == 0;
     return false;
   }
 
   static qst_status hidden(qst_ctx* c, const R* theta, const R* f) {
     Work<R>* w = W<R>(c);
+    if (c->cnn) {  // convolution, pooling and the first dense layer of the CNN head (App. A)
+      QST_CU(cnn_hidden<R>(c->D, theta, f, w->feats, w->pos, w->vals, w->pre, w->hid, c->net.slope, w->partials,
+                           w->counters + CNT_L1, w->scal, c->stream));
+      c->launches += 2;
+      tmark(c, QST_PH_HIDDEN);
+      return QST_OK;
+    }
     bool done = false;
     if constexpr (std::is_same<R, float>::value) {
       if (use_bulk(c, f)) {
@@ -379,10 +398,16 @@ template <class R> struct Engine {
     Work<R>* w = W<R>(c);
     const Dims& D = c->D;
     qst_status st;
+    if (c->cnn && (st = hidden(c, w->theta, f)) != QST_OK) return st;  // the head changes every step
     if ((st = forward_state(c, w->theta)) != QST_OK) return st;
     if ((st = povm_likelihood(c, f, true)) != QST_OK) return st;
     if ((st = backward_state(c)) != QST_OK) return st;
-    if (use_bulk(c, f)) {
+    if (c->cnn) {
+      QST_CU(cnn_backward<R>(D, w->theta, w->step, nullptr, f, w->dt, w->feats, w->pos, w->vals, w->pre, w->hid,
+                             w->dpre, w->partials, w->counters + CNT_W2, c->net, c->stream));
+      tmark(c, QST_PH_W2);
+      tmark(c, QST_PH_W1);
+    } else if (use_bulk(c, f)) {
       if constexpr (std::is_same<R, float>::value) {
         QST_CU(w2_pass_bulk(D, w->theta, w->step, w->dt, w->hid, w->pre, w->dpre, w->partials,
                             w->counters + CNT_W2, w->flags + 1, c->net, c->stream));
@@ -458,7 +483,7 @@ template <class R> struct Engine {
       if (kind != 2 && st != QST_OK) return st;
       if (new_f && (st = validate_f<R>(c, f)) != QST_OK) return st;
       tmark_begin(c);
-      if (new_f) {
+      if (new_f && !c->cnn) {
         if ((st = hidden(c, w->theta, f)) != QST_OK) return st;
       }
       if ((st = step_body(c, f)) != QST_OK) return st;
@@ -485,10 +510,15 @@ template <class R> struct Engine {
     if ((st = forward_state(c, theta, false)) != QST_OK) return st;
     if ((st = povm_likelihood(c, f, true)) != QST_OK) return st;
     if ((st = backward_state(c)) != QST_OK) return st;
-    QST_CU(net_w2_pass<R>(D, theta, nullptr, w->dt, w->hid, w->pre, w->dpre, dtheta, w->partials,
-                          w->counters + CNT_W2, c->net, false, c->stream));
-    QST_CU(net_w1_pass<R>(D, theta, nullptr, f, w->dpre, w->pre, w->hid, dtheta, w->scal, w->partials,
-                          w->counters + CNT_W1, c->net, false, c->stream));
+    if (c->cnn) {
+      QST_CU(cnn_backward<R>(D, theta, nullptr, dtheta, f, w->dt, w->feats, w->pos, w->vals, w->pre, w->hid,
+                             w->dpre, w->partials, w->counters + CNT_W2, c->net, c->stream));
+    } else {
+      QST_CU(net_w2_pass<R>(D, theta, nullptr, w->dt, w->hid, w->pre, w->dpre, dtheta, w->partials,
+                            w->counters + CNT_W2, c->net, false, c->stream));
+      QST_CU(net_w1_pass<R>(D, theta, nullptr, f, w->dpre, w->pre, w->hid, dtheta, w->scal, w->partials,
+                            w->counters + CNT_W1, c->net, false, c->stream));
+    }
     c->launches += 2;
     return read_loss(c, loss);
   }
@@ -511,7 +541,7 @@ template <class R> struct Engine {
     qst_status st;
     const R* f = (const R*)stage_input(c, f_user, (size_t)D.n * sizeof(R), w->fstage, &st);
     if (st != QST_OK) return st;
-    if (!c->hidden_valid || f_user != c->f_last) {
+    if (c->cnn || !c->hidden_valid || f_user != c->f_last) {
       if ((st = validate_f<R>(c, f)) != QST_OK) return st;
       if ((st = hidden(c, w->theta, f)) != QST_OK) return st;
       c->hidden_valid = true;
@@ -546,7 +576,7 @@ template <class R> struct Engine {
     qst_status st;
     const R* f = (const R*)stage_input(c, f_user, (size_t)D.n * sizeof(R), w->fstage, &st);
     if (st != QST_OK) return st;
-    if (!c->hidden_valid || f_user != c->f_last) {
+    if (c->cnn || !c->hidden_valid || f_user != c->f_last) {
       if ((st = validate_f<R>(c, f)) != QST_OK) return st;
       if ((st = hidden(c, w->theta, f)) != QST_OK) return st;
       c->hidden_valid = true;
@@ -599,7 +629,7 @@ qst_status check_povm(const double* povm, int K, PovmB<double>* Bd) {
 
 template <class R> qst_status reset_rprop(qst_ctx* c) {
   Work<R>* w = W<R>(c);
-  const size_t P = theta_size(c->N);
+  const size_t P = c->P;
   std::vector<R> h(P, rprop_encode((R)c->opt.lr, 0));  // step lr, previous sign 0
   QST_CU(cudaMemcpyAsync(w->step, h.data(), P * sizeof(R), cudaMemcpyHostToDevice, c->stream));
   QST_CU(cudaStreamSynchronize(c->stream));
@@ -701,11 +731,17 @@ void qst_default_options(qst_options* o) {
   o->leaky_slope = 0.01;
   o->eig_sweeps = 0;
   o->eig_warm_sweeps = 0;
+  o->network = QST_NET_FNN;
 }
 
 size_t qst_theta_size(int N) {
   if (N < 1 || N > 12) return 0;
   return theta_size(N);
+}
+
+size_t qst_theta_size_net(int N, int network) {
+  if (network == QST_NET_CNN) return N < 3 || N > 12 ? 0 : cnn_theta_size(N);
+  return network == QST_NET_FNN ? qst_theta_size(N) : 0;
 }
 
 qst_status qst_init(qst_ctx** out, int N, const double* povm, int K, const qst_options* opt, void* stream) {
@@ -722,6 +758,8 @@ qst_status qst_init(qst_ctx** out, int N, const double* povm, int K, const qst_o
     return QST_E_INVAL;
   if (o.mapping == QST_MAP_CHOL_DELTA && (o.precision == QST_MIXED || o.precision == QST_MIXED_BF16))
     return QST_E_UNSUPPORTED;
+  if (o.network != QST_NET_FNN && o.network != QST_NET_CNN) return QST_E_INVAL;
+  if (o.network == QST_NET_CNN && N < 3) return QST_E_INVAL;  // 2^(N-3)-square pooling windows
   if (o.mapping == QST_MAP_ABS_P) {
     if (!(o.P > 0.0) || !isfinite(o.P) || o.eig_sweeps < 0) return QST_E_INVAL;
     if (o.precision == QST_MIXED || o.precision == QST_MIXED_BF16) return QST_E_UNSUPPORTED;
@@ -744,6 +782,12 @@ qst_status qst_init(qst_ctx** out, int N, const double* povm, int K, const qst_o
   c->opt = o;
   c->prec = o.precision;
   c->D = make_dims(N, o.precision == QST_FP64);
+  c->cnn = o.network == QST_NET_CNN;
+  if (c->cnn) {
+    c->D.cnn = 1;
+    c->D.H = 4 * N;
+  }
+  c->P = c->cnn ? cnn_theta_size(N) : theta_size(N);
   c->stream = (cudaStream_t)stream;
   c->Bd = Bd;
   for (int a = 0; a < 4; ++a)
@@ -771,7 +815,7 @@ qst_status qst_init(qst_ctx** out, int N, const double* povm, int K, const qst_o
 
 qst_status qst_set_params(qst_ctx* c, const void* theta) {
   if (!c || !theta) return QST_E_INVAL;
-  const size_t bytes = theta_size(c->N) * rsize(c);
+  const size_t bytes = c->P * rsize(c);
   void* dst = c->prec == QST_FP64 ? (void*)W<double>(c)->theta : (void*)W<float>(c)->theta;
   QST_CU(cudaMemcpyAsync(dst, theta, bytes, cudaMemcpyDefault, c->stream));
   qst_status st = c->prec == QST_FP64 ? reset_rprop<double>(c) : reset_rprop<float>(c);
@@ -786,7 +830,7 @@ qst_status qst_set_params(qst_ctx* c, const void* theta) {
 qst_status qst_get_params(qst_ctx* c, void* theta) {
   if (!c || !theta) return QST_E_INVAL;
   if (!c->params_set) return QST_E_STATE;
-  const size_t bytes = theta_size(c->N) * rsize(c);
+  const size_t bytes = c->P * rsize(c);
   const void* src = c->prec == QST_FP64 ? (void*)W<double>(c)->theta : (void*)W<float>(c)->theta;
   QST_CU(cudaMemcpyAsync(theta, src, bytes, cudaMemcpyDefault, c->stream));
   if (!is_device_ptr(theta)) QST_CU(cudaStreamSynchronize(c->stream));
@@ -886,7 +930,7 @@ void* warm_q(qst_ctx* c) {
 
 size_t qst_state_bytes(const qst_ctx* c) {
   if (!c) return 0;
-  const size_t P = theta_size(c->N);
+  const size_t P = c->P;
   return 4 * sizeof(unsigned long long) + 2 * P * rsize(c) + warm_bytes(c);
 }
 
@@ -894,7 +938,7 @@ qst_status qst_get_state(qst_ctx* c, void* host_buf, size_t bytes) {
   if (!c || !host_buf) return QST_E_INVAL;
   if (!c->params_set) return QST_E_STATE;
   if (bytes < qst_state_bytes(c)) return QST_E_INVAL;
-  const size_t P = theta_size(c->N), rs = rsize(c);
+  const size_t P = c->P, rs = rsize(c);
   unsigned long long* hdr = (unsigned long long*)host_buf;
   hdr[0] = kStateMagic;
   hdr[1] = (unsigned long long)c->N | ((unsigned long long)c->prec << 8);
@@ -920,7 +964,7 @@ qst_status qst_get_state(qst_ctx* c, void* host_buf, size_t bytes) {
 qst_status qst_set_state(qst_ctx* c, const void* host_buf, size_t bytes) {
   if (!c || !host_buf) return QST_E_INVAL;
   if (bytes < qst_state_bytes(c)) return QST_E_INVAL;
-  const size_t P = theta_size(c->N), rs = rsize(c);
+  const size_t P = c->P, rs = rsize(c);
   const unsigned long long* hdr = (const unsigned long long*)host_buf;
   if (hdr[0] != kStateMagic || hdr[1] != ((unsigned long long)c->N | ((unsigned long long)c->prec << 8)) ||
       hdr[3] != (unsigned long long)P)

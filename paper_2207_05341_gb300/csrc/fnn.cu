@@ -491,6 +491,10 @@ cudaError_t net_build_T(const Dims& D, const R* theta, const R* hid, R* t, cx_t<
     k_layer2<R, HH><<<(unsigned)grid, 256, 0, s>>>(theta, hid, D.n, t, amax);
   });
   if (!T) return cudaGetLastError();
+  return net_hermitian_T<R>(D, t, T, Tt, s);
+}
+
+template <class R> cudaError_t net_hermitian_T(const Dims& D, const R* t, cx_t<R>* T, cx_t<R>* Tt, cudaStream_t s) {
   const int TS = D.d < 32 ? D.d : 32;
   const int nt = D.d / TS;
   const unsigned pairs = (unsigned)(nt * (nt + 1) / 2);
@@ -553,6 +557,7 @@ template <class R> cudaError_t net_tri_grad(const Dims& D, const cx_t<R>* Z, R* 
   template cudaError_t net_build_T<R>(const Dims&, const R*, const R*, R*, cx_t<R>*, unsigned int*, cudaStream_t,  \
                                       cx_t<R>*);                                                                 \
   template cudaError_t net_tri_grad<R>(const Dims&, const cx_t<R>*, R*, cudaStream_t);                         \
+  template cudaError_t net_hermitian_T<R>(const Dims&, const R*, cx_t<R>*, cx_t<R>*, cudaStream_t);            \
   template cudaError_t net_w2_pass<R>(const Dims&, R*, R*, const R*, const R*, const R*, R*, R*, double*, \
                                       unsigned int*, const NetCfg&, bool, cudaStream_t);                         \
   template cudaError_t net_w1_pass<R>(const Dims&, R*, R*, const R*, const R*, R*, R*, R*, double*,     \

@@ -16,6 +16,7 @@ namespace qst {
 struct Dims {
   int N, d, H, g, h, S, nb, C;
   long long n;
+  int cnn = 0;  // the App. A CNN head (H = 4N) instead of the 3-layer FNN (H = 2N)
 };
 
 Dims make_dims(int N, bool fp64);
@@ -38,6 +39,9 @@ template <class R> struct Work {
   R* Wlo;              // packed low-pass intermediate, n reals
   R* Whi;              // packed adjoint intermediate, n reals
   R* dt;               // dL/dt, n reals
+  R* feats;            // CNN: the 640 pooled features, their convolution values and positions
+  R* vals;
+  int* pos;
   R* fstage;           // staging copy of a host f, n reals
   double* scal;        // [0] Tr X, [1] sum f, [2] loss, [3] scale of T, [4] scale of G
   double* partials;    // per-block partial sums
@@ -99,6 +103,24 @@ template <class R> cudaError_t net_l1_forward(const Dims& D, const R* theta, con
 template <class R>
 cudaError_t net_build_T(const Dims& D, const R* theta, const R* hid, R* t, cx_t<R>* T, unsigned int* amax,
                         cudaStream_t s, cx_t<R>* Tt = nullptr);
+// The Hermitian (or, with Tt, lower-triangular) T of an already computed t (second half of net_build_T).
+template <class R> cudaError_t net_hermitian_T(const Dims& D, const R* t, cx_t<R>* T, cx_t<R>* Tt, cudaStream_t s);
+
+// ---- the CNN head of App. A (cnn.cu); theta [W2^T (H x n) | b2 | W1 (H x 640) | b1 | conv W (90) | conv b (10)]
+size_t cnn_theta_size(int N);
+// features (conv, ReLU, max-pool) and the first dense layer: pre, hid (H = 4N); sum f -> scal[1]
+template <class R>
+cudaError_t cnn_hidden(const Dims& D, const R* theta, const R* f, R* feats, int* pos, R* vals, R* pre, R* hid,
+                       double slope, double* partials, unsigned int* counter, double* scal, cudaStream_t s);
+// t = W2 h + b2 (amax as for net_build_T)
+template <class R>
+cudaError_t cnn_output(const Dims& D, const R* theta, const R* hid, R* t, unsigned int* amax, cudaStream_t s);
+// backward from dt: with dtheta == NULL Rprop in place on theta / state, else the gradient into dtheta
+template <class R>
+cudaError_t cnn_backward(const Dims& D, R* theta, R* state, R* dtheta, const R* f, const R* dt, const R* feats,
+                         const int* pos, const R* vals, const R* pre, const R* hid, R* dpre, double* partials,
+                         unsigned int* counter, const NetCfg& c, cudaStream_t s);
+
 // Chol_Delta: dL/dt from Z = T G (lower tiles): dR_ii = 2 Re Z_ii, dR_ij = 2 Re Z_ij, dR_ji = 2 Im Z_ij (i > j)
 template <class R> cudaError_t net_tri_grad(const Dims& D, const cx_t<R>* Z, R* dt, cudaStream_t s);
 template <class R> cudaError_t net_w2_pass(const Dims& D, R* theta, R* step, const R* dt,

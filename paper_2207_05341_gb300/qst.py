@@ -28,6 +28,8 @@ QST_W_CLAMP = 1
 QST_MAP_CHOL_H = 0
 QST_MAP_ABS_P = 1
 QST_MAP_CHOL_DELTA = 2
+QST_NET_FNN = 0
+QST_NET_CNN = 1
 QST_STATE_PRODUCT = 0
 QST_STATE_GHZI = 1
 QST_STATE_W = 2
@@ -44,7 +46,7 @@ EXPORTED = [
     "qst_timing_enable", "qst_timing_read", "qst_probs_static", "qst_graph_enable",
     "qst_batch_init", "qst_batch_context", "qst_batch_set_params", "qst_batch_step",
     "qst_batch_reconstruct", "qst_batch_kernel_launches", "qst_batch_sync", "qst_batch_destroy",
-    "qst_classical_fidelity", "qst_test_state", "qst_sample_counts",
+    "qst_classical_fidelity", "qst_test_state", "qst_sample_counts", "qst_theta_size_net",
 ]
 
 PHASES = ["hidden", "build_T", "x_fwd", "povm_lo", "povm_hi", "povm_adj", "gt", "sym", "w2", "w1"]
@@ -63,6 +65,7 @@ class qst_options(ctypes.Structure):
         ("leaky_slope", ctypes.c_double),
         ("eig_sweeps", ctypes.c_int),
         ("eig_warm_sweeps", ctypes.c_int),
+        ("network", ctypes.c_int),
     ]
 
 
@@ -88,6 +91,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     sig = {
         "qst_default_options": (None, [ctypes.POINTER(qst_options)]),
         "qst_theta_size": (sz, [i]),
+        "qst_theta_size_net": (sz, [i, i]),
         "qst_init": (i, [ctypes.POINTER(vp), i, vp, i, ctypes.POINTER(qst_options), vp]),
         "qst_set_params": (i, [vp, vp]),
         "qst_get_params": (i, [vp, vp]),
@@ -191,6 +195,10 @@ def qst_init(N: int, povm=None, K: int = 4, opt: qst_options | None = None, stre
                          ctypes.byref(opt) if opt is not None else None, stream or None)
     _check(st, "qst_init")
     return h.value
+
+
+def qst_theta_size_net(N: int, network: int) -> int:
+    return load().qst_theta_size_net(int(N), int(network))
 
 
 def qst_set_params(ctx: int, theta) -> int:
