@@ -237,7 +237,7 @@ def time_steps(torch, qst, ctx, f_dev, K, stream):
     return e0.elapsed_time(e1), qst.qst_kernel_launches(ctx) - l0
 
 
-def run_precision(torch, qst, synth, dev, stream, prec, theta0, f, K, W, dist, mapping=None):
+def run_precision(torch, qst, synth, dev, stream, prec, theta0, f, K, W, dist, mapping=None, network=None):
     """K timed iterations replayed from the captured CUDA graph (the headline), the same
     K launched kernel by kernel, per-phase device times from timed graph replays, and the
     end-to-end rate through qst_step with a page-locked host f and the loss read back."""
@@ -245,6 +245,8 @@ def run_precision(torch, qst, synth, dev, stream, prec, theta0, f, K, W, dist, m
     opt.precision = prec
     if mapping is not None:
         opt.mapping = mapping
+    if network is not None:
+        opt.network = network
     ctx = qst.qst_init(NQ, opt=opt, stream=stream.cuda_stream)
     try:
         qst.qst_set_params(ctx, theta0)
@@ -538,11 +540,14 @@ def profile_only(args):
     qst.load()
     dev = torch.device("cuda", 0)
     psi, f = make_inputs(torch, qst, synth, dev, LAMBDAS[1], STATE_SEEDS[1])
-    theta0 = synth.init_theta(NQ, THETA_SEED).astype(np.float32)
+    cnn = args.profile_net == "cnn"
+    theta0 = (synth.init_theta_cnn if cnn else synth.init_theta)(NQ, THETA_SEED).astype(np.float32)
     f_dev = torch.from_numpy(f).to(dev)
-    for prec in (qst.QST_FP32, qst.QST_MIXED, qst.QST_MIXED_BF16):
+    for prec in (qst.QST_MIXED,) if cnn else (qst.QST_FP32, qst.QST_MIXED, qst.QST_MIXED_BF16):
         o = qst.qst_default_options()
         o.precision = prec
+        if cnn:
+            o.network = qst.QST_NET_CNN
         try:
             ctx = qst.qst_init(NQ, opt=o)
         except qst.QstError:
@@ -591,6 +596,10 @@ def main_ours(args):
         # Chol_Delta (Sec. 2.2.1 eq. T_matrix), FP32: not this metric's map, reported beside it
         res["chol_delta_fp32"] = run_precision(torch, qst, synth, dev, stream, qst.QST_FP32, theta0, f, args.steps,
                                                args.warmup, dist, mapping=qst.QST_MAP_CHOL_DELTA)
+        # the CNN mapping network of App. A (4N hidden units, about the FNN's parameter count), mixed
+        theta_cnn = synth.init_theta_cnn(NQ, THETA_SEED).astype(np.float32)
+        res["cnn_mixed_fp16x3"] = run_precision(torch, qst, synth, dev, stream, qst.QST_MIXED, theta_cnn, f, args.steps,
+                                                args.warmup, dist, network=qst.QST_NET_CNN)
 
     head = "mixed_fp16x3" if mixed_ok else "plain_fp32"
     # max over ranks of the timed region
@@ -731,6 +740,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="profiling aid: only run this many plain and mixed steps at N=11 and exit (no JSON line)")
+    ap.add_argument("--profile-net", choices=["fnn", "cnn"], default="fnn",
+                    help="with --profile-steps: the FNN in FP32, mixed FP16x3 and BF16x3, or the CNN (mixed)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -151,6 +151,7 @@ template <class R> qst_status alloc_work(qst_ctx* c) {
     QST_CU(dalloc(c, &w->feats, 640));
     QST_CU(dalloc(c, &w->vals, 640));
     QST_CU(dalloc(c, &w->pos, 640));
+    QST_CU(dalloc(c, &w->cnn_part, cnn_part_doubles(D.N, sizeof(R))));
   }
   QST_CU(dalloc(c, &w->T, nn));
   QST_CU(dalloc(c, &w->X, nn));
@@ -352,8 +353,8 @@ template <class R> struct Engine {
   static qst_status hidden(qst_ctx* c, const R* theta, const R* f) {
     Work<R>* w = W<R>(c);
     if (c->cnn) {  // convolution, pooling and the first dense layer of the CNN head (App. A)
-      QST_CU(cnn_hidden<R>(c->D, theta, f, w->feats, w->pos, w->vals, w->pre, w->hid, c->net.slope, w->partials,
-                           w->counters + CNT_L1, w->scal, c->stream));
+      QST_CU(cnn_hidden<R>(c->D, theta, f, w->feats, w->pos, w->vals, w->pre, w->hid, c->net.slope, w->cnn_part,
+                           w->partials, w->counters + CNT_L1, w->scal, c->stream));
       c->launches += 2;
       tmark(c, QST_PH_HIDDEN);
       return QST_OK;
@@ -403,10 +404,14 @@ template <class R> struct Engine {
     if ((st = povm_likelihood(c, f, true)) != QST_OK) return st;
     if ((st = backward_state(c)) != QST_OK) return st;
     if (c->cnn) {
-      QST_CU(cnn_backward<R>(D, w->theta, w->step, nullptr, f, w->dt, w->feats, w->pos, w->vals, w->pre, w->hid,
-                             w->dpre, w->partials, w->counters + CNT_W2, c->net, c->stream));
+      const bool bulk = std::is_same<R, float>::value && c->bulk_passes && cnn_bulk_ok(D);
+      QST_CU(cnn_output_backward<R>(D, w->theta, w->step, nullptr, w->dt, w->hid, w->pre, w->dpre, w->partials,
+                                    w->counters + CNT_W2, w->flags + 1, c->net, bulk, c->stream));
       tmark(c, QST_PH_W2);
+      QST_CU(cnn_head_backward<R>(D, w->theta, w->step, nullptr, f, w->feats, w->pos, w->vals, w->dpre, c->net,
+                                  c->stream));
       tmark(c, QST_PH_W1);
+      c->launches += bulk ? 2 : 1;  // the output layer in two halves; the head in two kernels
     } else if (use_bulk(c, f)) {
       if constexpr (std::is_same<R, float>::value) {
         QST_CU(w2_pass_bulk(D, w->theta, w->step, w->dt, w->hid, w->pre, w->dpre, w->partials,
@@ -511,8 +516,11 @@ template <class R> struct Engine {
     if ((st = povm_likelihood(c, f, true)) != QST_OK) return st;
     if ((st = backward_state(c)) != QST_OK) return st;
     if (c->cnn) {
-      QST_CU(cnn_backward<R>(D, theta, nullptr, dtheta, f, w->dt, w->feats, w->pos, w->vals, w->pre, w->hid,
-                             w->dpre, w->partials, w->counters + CNT_W2, c->net, c->stream));
+      QST_CU(cnn_output_backward<R>(D, theta, nullptr, dtheta, w->dt, w->hid, w->pre, w->dpre, w->partials,
+                                    w->counters + CNT_W2, w->flags + 1, c->net, false, c->stream));
+      QST_CU(cnn_head_backward<R>(D, theta, nullptr, dtheta, f, w->feats, w->pos, w->vals, w->dpre, c->net,
+                                  c->stream));
+      c->launches += 1;  // the head in two kernels
     } else {
       QST_CU(net_w2_pass<R>(D, theta, nullptr, w->dt, w->hid, w->pre, w->dpre, dtheta, w->partials,
                             w->counters + CNT_W2, c->net, false, c->stream));

@@ -7,13 +7,22 @@
 //
 // theta (CNN layout): [W2^T (H x n) | b2 (n) | W1 (H x 640) | b1 (H) | conv W (10 x 3 x 3) | conv b (10)],
 // H = 4N; the Rprop state has the same layout.  The output layer streams like the FNN's (one pass for t,
-// one backward pass with Rprop fused); the convolution, pooling and first dense layer are small.
+// one backward pass with Rprop fused: in FP32 the bulk-copy W2 pass of the FNN, run on the two halves
+// of the 4N rows); the convolution, pooling and first dense layer are small.
+//
+// Pooling windows of at least 64 x 64 pixels (N >= 9) are cut into 32 x 64 tiles: a CTA stages its
+// tile with a one-pixel halo in shared memory, evaluates all 10 maps there and leaves per map the
+// tile's best (value, position); a second kernel reduces the tiles of each window.  The best of a set
+// is the largest value, on equal values the smallest row-major position, a total order, so the result
+// does not depend on how the set is split.  Smaller windows take one CTA per feature.
 //
 // The pooling argmax is a decision taken in floating point: each convolution value is accumulated in
 // the context's precision in a fixed order (bias, then the 9 taps row-major), every product and sum
 // rounded separately (no fused multiply-add), and ties go to the first row-major position of the
 // window, so that a reference evaluating the same expression in the same precision takes the same
 // decisions.  All reductions have a fixed order.
+#include <type_traits>
+
 #include "impl.h"
 
 namespace qst {
@@ -25,6 +34,11 @@ constexpr int kGrid = 8;
 constexpr int kFeat = kMaps * kGrid * kGrid;  // 640
 constexpr int kStride = 64;                   // doubles per block in partials (>= H = 4N <= 48)
 constexpr int kMaxBlocks = kPartialBlocks * kPartialStride / kStride;  // within the context's partials
+constexpr int kColsPer = 2;                   // tile columns per thread
+constexpr int kRowsPer = 8;                   // tile rows per thread
+constexpr int kTW = 32 * kColsPer;            // tile columns: a warp across
+constexpr int kTH = kRowsPer * 8;             // tile rows: the 8 warps of 256 threads down
+constexpr int kTileMinP = 64;                 // tiled path for windows of at least 64 x 64
 
 template <class R> __device__ __forceinline__ R mul_rn(R a, R b);
 template <class R> __device__ __forceinline__ R add_rn(R a, R b);
@@ -111,19 +125,192 @@ __global__ void __launch_bounds__(256) k_cnn_features(const R* __restrict__ f, i
   }
 }
 
-// Dense 640 -> H with LeakyReLU: one thread per hidden unit, terms in index order.
+// The dense layer 640 -> H with LeakyReLU, features in shared memory sf: warp w of the block takes
+// units w, w + nw, ...; lane l the terms m = l, l + 32, ... (in order, the 20 loads issued together),
+// then a fixed shuffle tree and b1.
 template <class R>
-__global__ void __launch_bounds__(64) k_cnn_dense1(const R* __restrict__ feats, const R* __restrict__ W1,
-                                                    const R* __restrict__ b1, int H, R* pre, R* hid, R slope) {
+__device__ __forceinline__ void dense1_block(int H, const R* sf, const R* __restrict__ W1, const R* __restrict__ b1,
+                                             R* pre, R* hid, R slope) {
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = threadIdx.x >> 5; j < H; j += nw) {
+    R w[kFeat / 32];
+#pragma unroll
+    for (int r = 0; r < kFeat / 32; ++r) w[r] = W1[(long long)j * kFeat + r * 32 + lane];
+    R acc = R(0);
+#pragma unroll
+    for (int r = 0; r < kFeat / 32; ++r) acc += w[r] * sf[r * 32 + lane];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      acc += b1[j];
+      pre[j] = acc;
+      hid[j] = leaky_c(acc, slope);
+    }
+  }
+}
+
+// Dense 640 -> H with LeakyReLU (one block of 1024 threads: a warp per unit).
+template <class R>
+__global__ void __launch_bounds__(1024) k_cnn_dense1(const R* __restrict__ feats, const R* __restrict__ W1,
+                                                     const R* __restrict__ b1, int H, R* pre, R* hid, R slope) {
   __shared__ R sf[kFeat];
   for (int m = threadIdx.x; m < kFeat; m += blockDim.x) sf[m] = feats[m];
   __syncthreads();
-  const int j = threadIdx.x;
-  if (j < H) {
-    R acc = b1[j];
-    for (int m = 0; m < kFeat; ++m) acc += W1[(long long)j * kFeat + m] * sf[m];
-    pre[j] = acc;
-    hid[j] = leaky_c(acc, slope);
+  dense1_block(H, sf, W1, b1, pre, hid, slope);
+}
+
+// (v2, i2) beats (v, i): larger value, or equal value at a smaller position.
+template <class R> __device__ __forceinline__ bool beats(R v2, int i2, R v, int i) {
+  return v2 > v || (v2 == v && i2 < i);
+}
+
+// Tiled convolution (windows of p >= 64): CTA b takes tile b % per_win of window b / per_win (tiles
+// row-major within the window), lane l of warp w the 16 pixels of columns 2l, 2l + 1 in rows
+// 8w .. 8w + 7 of the 64 x 64 tile (scanned row-major, so a thread keeps its first position on ties).
+// Per map: the tile's best (value, image position) to tv / ti; sum of f over the tile (FP64, fixed
+// order) to tf.
+template <class R>
+__global__ void __launch_bounds__(256) k_cnn_conv_tiles(const R* __restrict__ f, int N, const R* __restrict__ cW,
+                                                         const R* __restrict__ cB, R* __restrict__ tv,
+                                                         int* __restrict__ ti, double* __restrict__ tf) {
+  __shared__ R tile[kTH + 2][kTW + 2];
+  __shared__ R sw[kMaps][10];  // 9 taps row-major, then the bias
+  __shared__ R rv[8][kMaps];
+  __shared__ int ri[8][kMaps];
+  __shared__ double rf[8];
+  const int d = 1 << N, p = d / kGrid;
+  const int tx = p / kTW, per_win = tx * (p / kTH);
+  const int win = blockIdx.x / per_win, r = blockIdx.x % per_win;
+  const int y0 = (win / kGrid) * p + (r / tx) * kTH, x0 = (win % kGrid) * p + (r % tx) * kTW;
+  for (int e = threadIdx.x; e < (kTH + 2) * (kTW + 2); e += blockDim.x) {
+    const int ry = e / (kTW + 2), rx = e % (kTW + 2);
+    const int y = y0 + ry - 1, x = x0 + rx - 1;
+    tile[ry][rx] = (y >= 0 && y < d && x >= 0 && x < d) ? f[(long long)y * d + x] : R(0);
+  }
+  if (threadIdx.x < kMaps * 10) {
+    const int c = threadIdx.x / 10, k = threadIdx.x % 10;
+    sw[c][k] = k < 9 ? cW[c * 9 + k] : cB[c];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int cx = lane * kColsPer, rg = warp;
+  R v[kRowsPer + 2][kColsPer + 2];
+#pragma unroll
+  for (int a = 0; a < kRowsPer + 2; ++a)
+#pragma unroll
+    for (int b = 0; b < kColsPer + 2; ++b) v[a][b] = tile[rg * kRowsPer + a][cx + b];
+  double fs = 0.0;
+#pragma unroll
+  for (int rr = 0; rr < kRowsPer; ++rr)
+#pragma unroll
+    for (int cc = 0; cc < kColsPer; ++cc) fs += (double)v[rr + 1][cc + 1];
+#pragma unroll 1
+  for (int c = 0; c < kMaps; ++c) {
+    R w[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) w[k] = sw[c][k];
+    const R b = sw[c][9];
+    R best = R(0);
+    int bi = 0;  // rr * kColsPer + cc of the best
+#pragma unroll
+    for (int rr = 0; rr < kRowsPer; ++rr)
+#pragma unroll
+      for (int cc = 0; cc < kColsPer; ++cc) {
+        R acc = b;
+#pragma unroll
+        for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+          for (int kx = 0; kx < 3; ++kx) acc = add_rn(acc, mul_rn(w[ky * 3 + kx], v[rr + ky][cc + kx]));
+        if ((rr == 0 && cc == 0) || acc > best) {  // row-major scan: the first position is kept on ties
+          best = acc;
+          bi = rr * kColsPer + cc;
+        }
+      }
+    int idx = (y0 + rg * kRowsPer + bi / kColsPer) * d + x0 + cx + bi % kColsPer;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const R v2 = __shfl_xor_sync(0xffffffffu, best, o);
+      const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+      if (beats(v2, i2, best, idx)) {
+        best = v2;
+        idx = i2;
+      }
+    }
+    if (lane == 0) {
+      rv[warp][c] = best;
+      ri[warp][c] = idx;
+    }
+  }
+  fs = warp_sum(fs);
+  if (lane == 0) rf[warp] = fs;
+  __syncthreads();
+  if (threadIdx.x < kMaps) {
+    const int c = threadIdx.x;
+    R best = rv[0][c];
+    int idx = ri[0][c];
+    for (int q = 1; q < 8; ++q)
+      if (beats(rv[q][c], ri[q][c], best, idx)) {
+        best = rv[q][c];
+        idx = ri[q][c];
+      }
+    tv[(size_t)blockIdx.x * kMaps + c] = best;
+    ti[(size_t)blockIdx.x * kMaps + c] = idx;
+  }
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += rf[q];
+    tf[blockIdx.x] = t;
+  }
+}
+
+// Pooling over the tiles of each window: warp i < 640 reduces feature i (map i / 64, window i % 64)
+// over its window's per_win tiles; warp 640 sums tf (fixed order) into scal[1].  The last block to
+// finish evaluates the dense layer 640 -> H (blocks of 1024 threads: a warp per hidden unit).
+template <class R>
+__global__ void __launch_bounds__(1024) k_cnn_pool(const R* __restrict__ tv, const int* __restrict__ ti,
+                                                   const double* __restrict__ tf, int per_win, R* feats, int* pos,
+                                                   R* vals, const R* __restrict__ W1, const R* __restrict__ b1, int H,
+                                                   R* pre, R* hid, R slope, double* scal, unsigned int* counter) {
+  __shared__ R sf[kFeat];
+  const int lane = threadIdx.x & 31, gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (gw < kFeat) {
+    const int c = gw / (kGrid * kGrid), win = gw % (kGrid * kGrid);
+    R best = R(0);
+    int idx = -1;
+    for (int t = lane; t < per_win; t += 32) {
+      const size_t o = (size_t)(win * per_win + t) * kMaps + c;
+      const R v2 = tv[o];
+      const int i2 = ti[o];
+      if (idx < 0 || beats(v2, i2, best, idx)) {
+        best = v2;
+        idx = i2;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const R v2 = __shfl_xor_sync(0xffffffffu, best, o);
+      const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+      if (i2 >= 0 && (idx < 0 || beats(v2, i2, best, idx))) {
+        best = v2;
+        idx = i2;
+      }
+    }
+    if (lane == 0) {
+      pos[gw] = idx;
+      vals[gw] = best;
+      feats[gw] = best > R(0) ? best : R(0);
+    }
+  } else if (gw == kFeat) {
+    double t = 0.0;
+    for (int b = lane; b < kGrid * kGrid * per_win; b += 32) t += tf[b];
+    t = warp_sum(t);
+    if (lane == 0) scal[1] = t;
+  }
+  if (last_block_arrived(counter)) {
+    for (int m = threadIdx.x; m < kFeat; m += blockDim.x) sf[m] = __ldcg(feats + m);
+    __syncthreads();
+    dense1_block(H, sf, W1, b1, pre, hid, slope);
+    if (threadIdx.x == 0) *counter = 0u;
   }
 }
 
@@ -255,71 +442,98 @@ __global__ void __launch_bounds__(256) k_cnn_output_back(R* __restrict__ W2T, R*
 // Backward of the dense layer 640 -> H and of the convolution through the pooling argmax, with Rprop:
 //   dfeat_m = sum_j W1[j][m] dpre_j (old W1), dW1[j][m] = dpre_j feat_m, db1 = dpre,
 //   for each feature i of map c with positive convolution value at its position (y, x):
-//   dW_c[ky][kx] += dfeat_i f[y + ky - 1][x + kx - 1], db_c += dfeat_i (features in index order).
-// One CTA of 1024 threads.  UPD: Rprop in place; else the gradients go to the d* pointers.
-template <class R, bool UPD>
-__global__ void __launch_bounds__(1024) k_cnn_head_back(const R* __restrict__ f, int N, const R* __restrict__ feats,
-                                                         const int* __restrict__ pos, const R* __restrict__ vals,
-                                                         const R* __restrict__ dpre, int H, R* W1, R* S1, R* b1, R* Sb1,
-                                                         R* cW, R* ScW, R* cB, R* ScB, R* dW1, R* db1, R* dcW,
-                                                         R* dcB, RpropCfg<R> rc) {
+//   dW_c[ky][kx] += dfeat_i f[y + ky - 1][x + kx - 1], db_c += dfeat_i.
+// k_cnn_head_grad (one CTA of 1024 threads) takes dfeat, b1 and the convolution; k_cnn_w1_update,
+// launched after it (every read of the old W1 is done), W1.  The 100 convolution gradients are 10
+// strided partial sums each (features q = r, r + 10, ... of the map), added in order.
+// UPD: Rprop in place; else the gradients go to the d* pointers.
+template <class R, int H, bool UPD>
+__global__ void __launch_bounds__(1024) k_cnn_head_grad(const R* __restrict__ f, int N, const int* __restrict__ pos,
+                                                         const R* __restrict__ vals, const R* __restrict__ dpre,
+                                                         const R* __restrict__ W1, R* b1, R* Sb1, R* cW, R* ScW,
+                                                         R* cB, R* ScB, R* db1, R* dcW, R* dcB, RpropCfg<R> rc) {
   __shared__ R dfeat[kFeat];
-  __shared__ R dp[64];
-  const int d = 1 << N;
-  if (threadIdx.x < H) dp[threadIdx.x] = dpre[threadIdx.x];
+  __shared__ R dp[H];
+  __shared__ R part[kMaps * 10][10];
+  const int d = 1 << N, t = threadIdx.x;
+  if (t < H) dp[t] = dpre[t];
   __syncthreads();
-  for (int m = threadIdx.x; m < kFeat; m += blockDim.x) {
+  if (t < kFeat) {
+    R w[H];
+#pragma unroll
+    for (int j = 0; j < H; ++j) w[j] = W1[(long long)j * kFeat + t];
     R acc = R(0);
-    for (int j = 0; j < H; ++j) acc += W1[(long long)j * kFeat + m] * dp[j];
-    dfeat[m] = vals[m] > R(0) ? acc : R(0);  // ReLU'(conv) at the pooled position
+#pragma unroll
+    for (int j = 0; j < H; ++j) acc += w[j] * dp[j];
+    dfeat[t] = vals[t] > R(0) ? acc : R(0);  // ReLU'(conv) at the pooled position
   }
-  __syncthreads();
-  for (int e = threadIdx.x; e < H * kFeat; e += blockDim.x) {
-    const int j = e / kFeat, m = e % kFeat;
-    const R g = dp[j] * feats[m];
+  if (t < H) {
     if (UPD) {
-      R s = S1[e];
-      W1[e] = rprop1(W1[e], g, s, rc);
-      S1[e] = s;
+      R sj = Sb1[t];
+      b1[t] = rprop1(b1[t], dp[t], sj, rc);
+      Sb1[t] = sj;
     } else {
-      dW1[e] = g;
+      db1[t] = dp[t];
     }
   }
-  for (int j = threadIdx.x; j < H; j += blockDim.x) {
-    if (UPD) {
-      R s = Sb1[j];
-      b1[j] = rprop1(b1[j], dp[j], s, rc);
-      Sb1[j] = s;
-    } else {
-      db1[j] = dp[j];
-    }
-  }
-  // convolution: one thread per weight (10 x 9) and per bias (10)
-  const int t = threadIdx.x;
-  if (t < kMaps * 10) {
-    const int c = t / 10, k = t % 10;  // k < 9: tap (k / 3, k % 3); k == 9: bias
-    R acc = R(0);
-    for (int q = 0; q < kGrid * kGrid; ++q) {
-      const int i = c * kGrid * kGrid + q;
-      const R g = dfeat[i];
-      if (k == 9) {
-        acc += g;
-      } else {
+  __syncthreads();
+  // convolution: output o = (map c, k) with k < 9 the tap (k / 3, k % 3) and k == 9 the bias;
+  // thread (o, r) sums the features q = r, r + 10, ... of map c
+  constexpr int kPer = (kGrid * kGrid + 9) / 10;
+  if (t < kMaps * 10 * 10) {
+    const int o = t / 10, r = t % 10, c = o / 10, k = o % 10;
+    R v[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int q = r + 10 * u;
+      v[u] = R(1);
+      if (q < kGrid * kGrid && k < 9) {
+        const int i = c * kGrid * kGrid + q;
         const int y = pos[i] / d + k / 3 - 1, x = pos[i] % d + k % 3 - 1;
-        const R v = (y >= 0 && y < d && x >= 0 && x < d) ? f[(long long)y * d + x] : R(0);
-        acc += g * v;
+        v[u] = (y >= 0 && y < d && x >= 0 && x < d) ? f[(long long)y * d + x] : R(0);
       }
     }
+    R acc = R(0);
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int q = r + 10 * u;
+      if (q < kGrid * kGrid) acc += dfeat[c * kGrid * kGrid + q] * v[u];  // v = 1 for the bias
+    }
+    part[o][r] = acc;
+  }
+  __syncthreads();
+  if (t < kMaps * 10) {
+    const int c = t / 10, k = t % 10;
+    R acc = R(0);
+#pragma unroll
+    for (int r = 0; r < 10; ++r) acc += part[t][r];
     R* P = k == 9 ? cB + c : cW + c * 9 + k;
     R* S = k == 9 ? ScB + c : ScW + c * 9 + k;
     if (UPD) {
-      R s = *S;
-      *P = rprop1(*P, acc, s, rc);
-      *S = s;
+      R sv = *S;
+      *P = rprop1(*P, acc, sv, rc);
+      *S = sv;
     } else {
       if (k == 9) dcB[c] = acc;
       else dcW[c * 9 + k] = acc;
     }
+  }
+}
+
+// dW1[j][m] = dpre_j feat_m for the H x 640 weights, one per thread; Rprop in place (UPD) or to dW1.
+template <class R, bool UPD>
+__global__ void __launch_bounds__(256) k_cnn_w1_update(const R* __restrict__ feats, const R* __restrict__ dpre, int H,
+                                                        R* __restrict__ W1, R* __restrict__ S1, R* __restrict__ dW1,
+                                                        RpropCfg<R> rc) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= H * kFeat) return;
+  const R g = dpre[e / kFeat] * feats[e % kFeat];
+  if (UPD) {
+    R st = S1[e];
+    W1[e] = rprop1(W1[e], g, st, rc);
+    S1[e] = st;
+  } else {
+    dW1[e] = g;
   }
 }
 
@@ -372,12 +586,36 @@ size_t cnn_theta_size(int N) {
   return H * n + n + H * kFeat + H + kMaps * 9 + kMaps;
 }
 
+static long long conv_tiles(int N) {
+  const long long p = (1LL << N) / kGrid;
+  return p >= kTileMinP ? (long long)kGrid * kGrid * (p / kTW) * (p / kTH) : 0;
+}
+
+size_t cnn_part_doubles(int N, size_t real_bytes) {
+  const size_t t = (size_t)conv_tiles(N);
+  const size_t bytes = t * 8 + t * kMaps * real_bytes + t * kMaps * 4;
+  return bytes / 8 + 2;
+}
+
 template <class R>
 cudaError_t cnn_hidden(const Dims& D, const R* theta, const R* f, R* feats, int* pos, R* vals, R* pre, R* hid,
-                       double slope, double* partials, unsigned int* counter, double* scal, cudaStream_t s) {
+                       double slope, double* part, double* partials, unsigned int* counter, double* scal,
+                       cudaStream_t s) {
   CnnParams<R> p = cnn_params(const_cast<R*>(theta), D.H, D.n);
-  k_cnn_features<R><<<kFeat, 256, 0, s>>>(f, D.N, p.cW, p.cB, feats, pos, vals, partials, counter, scal);
-  k_cnn_dense1<R><<<1, 64, 0, s>>>(feats, p.W1, p.b1, D.H, pre, hid, (R)slope);
+  const long long tiles = conv_tiles(D.N);
+  if (tiles > 0) {
+    // part: tf [tiles] doubles | tv [tiles x 10] reals | ti [tiles x 10] ints
+    double* tf = part;
+    R* tv = reinterpret_cast<R*>(tf + tiles);
+    int* ti = reinterpret_cast<int*>(tv + tiles * kMaps);
+    k_cnn_conv_tiles<R><<<(unsigned)tiles, 256, 0, s>>>(f, D.N, p.cW, p.cB, tv, ti, tf);
+    const int per_win = (int)(tiles / (kGrid * kGrid));
+    k_cnn_pool<R><<<(kFeat + 1 + 31) / 32, 1024, 0, s>>>(tv, ti, tf, per_win, feats, pos, vals, p.W1, p.b1, D.H, pre,
+                                                      hid, (R)slope, scal, counter);
+  } else {
+    k_cnn_features<R><<<kFeat, 256, 0, s>>>(f, D.N, p.cW, p.cB, feats, pos, vals, partials, counter, scal);
+    k_cnn_dense1<R><<<1, 1024, 0, s>>>(feats, p.W1, p.b1, D.H, pre, hid, (R)slope);
+  }
   return cudaGetLastError();
 }
 
@@ -391,11 +629,24 @@ cudaError_t cnn_output(const Dims& D, const R* theta, const R* hid, R* t, unsign
   return cudaGetLastError();
 }
 
+bool cnn_bulk_ok(const Dims& D) { return D.H % 2 == 0 && wpass_bulk_ok(D.H / 2, D.n); }
+
 template <class R>
-cudaError_t cnn_backward(const Dims& D, R* theta, R* state, R* dtheta, const R* f, const R* dt, const R* feats,
-                         const int* pos, const R* vals, const R* pre, const R* hid, R* dpre, double* partials,
-                         unsigned int* counter, const NetCfg& c, cudaStream_t s) {
+cudaError_t cnn_output_backward(const Dims& D, R* theta, R* state, R* dtheta, const R* dt, const R* hid,
+                                const R* pre, R* dpre, double* partials, unsigned int* counter, unsigned int* flags,
+                                const NetCfg& c, bool bulk, cudaStream_t s) {
   const bool upd = dtheta == nullptr;
+  if constexpr (std::is_same<R, float>::value) {
+    if (upd && bulk) {  // the FNN's bulk W2 pass on rows [0, H/2) (with b2), then on rows [H/2, H)
+      const int h2 = D.H / 2;
+      const long long n = D.n, ob2 = (long long)D.H * n;
+      cudaError_t e = w2_rows_pass_bulk(n, h2, theta, state, 0, ob2, dt, hid, pre, dpre, partials, counter, flags,
+                                        c, s);
+      if (e != cudaSuccess) return e;
+      return w2_rows_pass_bulk(n, h2, theta, state, (long long)h2 * n, -1, dt, hid + h2, pre + h2, dpre + h2,
+                               partials, counter, flags, c, s);
+    }
+  }
   CnnParams<R> p = cnn_params(theta, D.H, D.n);
   CnnParams<R> q = upd ? cnn_params(state, D.H, D.n) : CnnParams<R>{};
   CnnParams<R> g = upd ? CnnParams<R>{} : cnn_params(dtheta, D.H, D.n);
@@ -411,22 +662,41 @@ cudaError_t cnn_backward(const Dims& D, R* theta, R* state, R* dtheta, const R* 
                                                            g.b2, D.n, partials, counter, rc, (R)c.slope);
     }
   });
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t cnn_head_backward(const Dims& D, R* theta, R* state, R* dtheta, const R* f, const R* feats,
+                              const int* pos, const R* vals, const R* dpre, const NetCfg& c, cudaStream_t s) {
+  const bool upd = dtheta == nullptr;
+  CnnParams<R> p = cnn_params(theta, D.H, D.n);
+  CnnParams<R> q = upd ? cnn_params(state, D.H, D.n) : CnnParams<R>{};
+  CnnParams<R> g = upd ? CnnParams<R>{} : cnn_params(dtheta, D.H, D.n);
+  RpropCfg<R> rc{(R)c.eta_minus, (R)c.eta_plus, (R)c.step_min, (R)c.step_max};
+  QST_SWITCH_H4(D.H, {
+    if (upd)
+      k_cnn_head_grad<R, HH, true><<<1, 1024, 0, s>>>(f, D.N, pos, vals, dpre, p.W1, p.b1, q.b1, p.cW, q.cW, p.cB,
+                                                      q.cB, nullptr, nullptr, nullptr, rc);
+    else
+      k_cnn_head_grad<R, HH, false><<<1, 1024, 0, s>>>(f, D.N, pos, vals, dpre, p.W1, p.b1, nullptr, p.cW, nullptr,
+                                                       p.cB, nullptr, g.b1, g.cW, g.cB, rc);
+  });
+  const int blocks = (D.H * kFeat + 255) / 256;
   if (upd)
-    k_cnn_head_back<R, true><<<1, 1024, 0, s>>>(f, D.N, feats, pos, vals, dpre, D.H, p.W1, q.W1, p.b1, q.b1, p.cW,
-                                                q.cW, p.cB, q.cB, nullptr, nullptr, nullptr, nullptr, rc);
+    k_cnn_w1_update<R, true><<<blocks, 256, 0, s>>>(feats, dpre, D.H, p.W1, q.W1, nullptr, rc);
   else
-    k_cnn_head_back<R, false><<<1, 1024, 0, s>>>(f, D.N, feats, pos, vals, dpre, D.H, p.W1, nullptr, p.b1, nullptr,
-                                                 p.cW, nullptr, p.cB, nullptr, g.W1, g.b1, g.cW, g.cB, rc);
+    k_cnn_w1_update<R, false><<<blocks, 256, 0, s>>>(feats, dpre, D.H, p.W1, nullptr, g.W1, rc);
   return cudaGetLastError();
 }
 
 #define QST_CNN_INST(R)                                                                                          \
   template cudaError_t cnn_hidden<R>(const Dims&, const R*, const R*, R*, int*, R*, R*, R*, double, double*,       \
-                                     unsigned int*, double*, cudaStream_t);                                     \
+                                     double*, unsigned int*, double*, cudaStream_t);                            \
   template cudaError_t cnn_output<R>(const Dims&, const R*, const R*, R*, unsigned int*, cudaStream_t);          \
-  template cudaError_t cnn_backward<R>(const Dims&, R*, R*, R*, const R*, const R*, const R*, const int*,         \
-                                       const R*, const R*, const R*, R*, double*, unsigned int*, const NetCfg&,  \
-                                       cudaStream_t);
+  template cudaError_t cnn_output_backward<R>(const Dims&, R*, R*, R*, const R*, const R*, const R*, R*, double*, \
+                                              unsigned int*, unsigned int*, const NetCfg&, bool, cudaStream_t);  \
+  template cudaError_t cnn_head_backward<R>(const Dims&, R*, R*, R*, const R*, const R*, const int*, const R*,   \
+                                            const R*, const NetCfg&, cudaStream_t);
 QST_CNN_INST(float)
 QST_CNN_INST(double)
 #undef QST_CNN_INST

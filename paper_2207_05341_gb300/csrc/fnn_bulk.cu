@@ -159,7 +159,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_wpass_bulk(const __gri
                                                           const float* __restrict__ vec,
                                                           const float* __restrict__ hidv, const float* __restrict__ pre,
                                                           float* dpre_io, float* pre_out, float* hid_out, double* scal,
-                                                          long long n, double* partials, unsigned int* counter,
+                                                          long long n, long long ob2, long long ob1,
+                                                          double* partials, unsigned int* counter,
                                                           unsigned int* flags, RpropCfg<float> rc, float slope) {
   using S = Stage<H, W2>;
   extern __shared__ __align__(128) uint8_t smem_raw[];
@@ -168,7 +169,10 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_wpass_bulk(const __gri
   __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
   __shared__ float hs[H];
   __shared__ int s_fail;
-  const long long ob2 = 2LL * H * n, ob1 = 2LL * H * n + n;
+  // ob2: offset of b2 in theta and step, < 0 when this launch leaves b2 alone (W2 pass);
+  // ob1: offset of b1, < 0 when the W2 pass only writes dpre (the caller updates b1)
+  const bool with_b2 = W2 && ob2 >= 0;
+  const uint32_t tx = with_b2 ? S::kTx : (uint32_t)S::kBw;  // bytes one chunk's copies bring in
   const long long nchunks = n / kCols;
   const long long nk = blockIdx.x < nchunks ? (nchunks - 1 - blockIdx.x) / gridDim.x + 1 : 0;  // chunks of this CTA
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -199,11 +203,11 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_wpass_bulk(const __gri
         uint8_t* st = smem + q * S::kBytes;
         const long long c0 = (blockIdx.x + k * gridDim.x) * kCols;
         const uint32_t bar = s_u32(&full[q]);
-        bar_expect(bar, S::kTx);
+        bar_expect(bar, tx);
         tma_load_box(st + S::kW, &maps.w, (int)c0, bar);
         tma_load_box(st + S::kSt, &maps.st, (int)c0, bar);
         bulk_load(st + S::kVec, vec + c0, kCols * 4, bar);
-        if (W2) {
+        if (with_b2) {
           bulk_load(st + S::kBw, theta + ob2 + c0, kCols * 4, bar);
           bulk_load(st + S::kBst, step + ob2 + c0, kCols * 4, bar);
         }
@@ -214,7 +218,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_wpass_bulk(const __gri
         const long long c0 = (blockIdx.x + k * gridDim.x) * kCols;
         tma_store_box(&maps.w, (int)c0, st + S::kW);
         tma_store_box(&maps.st, (int)c0, st + S::kSt);
-        if (W2) {
+        if (with_b2) {
           bulk_store(theta + ob2 + c0, st + S::kBw, kCols * 4);
           bulk_store(step + ob2 + c0, st + S::kBst, kCols * 4);
         }
@@ -260,13 +264,13 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_wpass_bulk(const __gri
       float* sp = reinterpret_cast<float*>(st + S::kSt);
       const float v = reinterpret_cast<const float*>(st + S::kVec)[col];  // dt_i or f_i
       if (rg == 0) {
-        if (W2) {
+        if (with_b2) {
           float* bw = reinterpret_cast<float*>(st + S::kBw);
           float* bst = reinterpret_cast<float*>(st + S::kBst);
           float bs = bst[col];
           bw[col] = rprop1(bw[col], v, bs, rc);
           bst[col] = bs;
-        } else {
+        } else if (!W2) {
           accf += v;
         }
       }
@@ -324,9 +328,11 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_wpass_bulk(const __gri
         const float p = pre[j];
         const float dp = (float)sum * (p > 0.f ? 1.f : slope);
         dpre_io[j] = dp;
-        float stp = step[ob1 + j];
-        theta[ob1 + j] = rprop1(theta[ob1 + j], dp, stp, rc);
-        step[ob1 + j] = stp;
+        if (ob1 >= 0) {
+          float stp = step[ob1 + j];
+          theta[ob1 + j] = rprop1(theta[ob1 + j], dp, stp, rc);
+          step[ob1 + j] = stp;
+        }
       });
     } else {
       final_sum(partials, H + 1, [&](int j, double sum) {
@@ -408,9 +414,12 @@ bool make_rows_map(CUtensorMap* m, void* base, long long n, int H) {
          CUDA_SUCCESS;
 }
 
+// rowoff: first element of the H x n rows this launch streams (in theta and step); ob2, ob1 as in
+// k_wpass_bulk.
 template <int H, bool W2> cudaError_t launch_bulk(float* theta, float* step, const float* vec,
                                                    const float* hid, const float* pre, float* dpre, float* pre_out,
-                                                   float* hid_out, double* scal, long long n, double* partials,
+                                                   float* hid_out, double* scal, long long n, long long rowoff,
+                                                   long long ob2, long long ob1, double* partials,
                                                    unsigned int* counter, unsigned int* flags,
                                                    const RpropCfg<float>& rc, float slope, cudaStream_t s) {
   using S = Stage<H, W2>;
@@ -421,13 +430,13 @@ template <int H, bool W2> cudaError_t launch_bulk(float* theta, float* step, con
     if (e != cudaSuccess) return e;
     set = true;
   }
-  const long long rowoff = W2 ? (long long)H * n : 0;  // W2^T or W1 rows
   WMaps maps;
   if (!make_rows_map(&maps.w, theta + rowoff, n, H) || !make_rows_map(&maps.st, step + rowoff, n, H))
     return cudaErrorInvalidValue;
   const long long grid = bulk_grid(n);
   k_wpass_bulk<H, W2><<<(unsigned)grid, kThreads, smem, s>>>(maps, theta, step, vec, hid, pre, dpre, pre_out,
-                                                             hid_out, scal, n, partials, counter, flags, rc, slope);
+                                                             hid_out, scal, n, ob2, ob1, partials, counter, flags, rc,
+                                                             slope);
   return cudaGetLastError();
 }
 
@@ -455,8 +464,20 @@ cudaError_t w2_pass_bulk(const Dims& D, float* theta, float* step, const float* 
                          const float* pre, float* dpre, double* partials, unsigned int* counter, unsigned int* flags,
                          const NetCfg& c, cudaStream_t s) {
   RpropCfg<float> rc{(float)c.eta_minus, (float)c.eta_plus, (float)c.step_min, (float)c.step_max};
+  const long long n = D.n, H = D.H;  // theta = [W1 | W2^T | b2 | b1]
   QST_BULK_SWITCH(D.H, return (launch_bulk<HH, true>(theta, step, dt, hid, pre, dpre, nullptr, nullptr, nullptr,
-                                                     D.n, partials, counter, flags, rc, (float)c.slope, s)));
+                                                     n, H * n, 2 * H * n, 2 * H * n + n, partials, counter, flags, rc,
+                                                     (float)c.slope, s)));
+  return cudaSuccess;
+}
+
+cudaError_t w2_rows_pass_bulk(long long n, int rows, float* theta, float* step, long long rowoff, long long ob2,
+                              const float* dt, const float* hid, const float* pre, float* dpre, double* partials,
+                              unsigned int* counter, unsigned int* flags, const NetCfg& c, cudaStream_t s) {
+  RpropCfg<float> rc{(float)c.eta_minus, (float)c.eta_plus, (float)c.step_min, (float)c.step_max};
+  QST_BULK_SWITCH(rows, return (launch_bulk<HH, true>(theta, step, dt, hid, pre, dpre, nullptr, nullptr, nullptr, n,
+                                                      rowoff, ob2, -1, partials, counter, flags, rc, (float)c.slope,
+                                                      s)));
   return cudaSuccess;
 }
 
@@ -472,8 +493,10 @@ cudaError_t w1_pass_bulk(const Dims& D, float* theta, float* step, const float* 
                          float* pre, float* hid, double* scal, double* partials, unsigned int* counter,
                          unsigned int* flags, const NetCfg& c, cudaStream_t s) {
   RpropCfg<float> rc{(float)c.eta_minus, (float)c.eta_plus, (float)c.step_min, (float)c.step_max};
-  QST_BULK_SWITCH(D.H, return (launch_bulk<HH, false>(theta, step, f, nullptr, nullptr, dpre, pre, hid, scal,
-                                                      D.n, partials, counter, flags, rc, (float)c.slope, s)));
+  const long long n = D.n, H = D.H;
+  QST_BULK_SWITCH(D.H, return (launch_bulk<HH, false>(theta, step, f, nullptr, nullptr, dpre, pre, hid, scal, n, 0,
+                                                      -1, 2 * H * n + n, partials, counter, flags, rc,
+                                                      (float)c.slope, s)));
   return cudaSuccess;
 }
 

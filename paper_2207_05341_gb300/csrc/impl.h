@@ -42,6 +42,7 @@ template <class R> struct Work {
   R* feats;            // CNN: the 640 pooled features, their convolution values and positions
   R* vals;
   int* pos;
+  double* cnn_part;    // CNN: per-tile pooling scratch (cnn_part_doubles)
   R* fstage;           // staging copy of a host f, n reals
   double* scal;        // [0] Tr X, [1] sum f, [2] loss, [3] scale of T, [4] scale of G
   double* partials;    // per-block partial sums
@@ -108,18 +109,28 @@ template <class R> cudaError_t net_hermitian_T(const Dims& D, const R* t, cx_t<R
 
 // ---- the CNN head of App. A (cnn.cu); theta [W2^T (H x n) | b2 | W1 (H x 640) | b1 | conv W (90) | conv b (10)]
 size_t cnn_theta_size(int N);
-// features (conv, ReLU, max-pool) and the first dense layer: pre, hid (H = 4N); sum f -> scal[1]
+// doubles of the per-tile pooling scratch `part` of cnn_hidden (reals of real_bytes bytes)
+size_t cnn_part_doubles(int N, size_t real_bytes);
+// features (conv, ReLU, max-pool) and the first dense layer: pre, hid (H = 4N); sum f -> scal[1]; two launches
 template <class R>
 cudaError_t cnn_hidden(const Dims& D, const R* theta, const R* f, R* feats, int* pos, R* vals, R* pre, R* hid,
-                       double slope, double* partials, unsigned int* counter, double* scal, cudaStream_t s);
+                       double slope, double* part, double* partials, unsigned int* counter, double* scal,
+                       cudaStream_t s);
 // t = W2 h + b2 (amax as for net_build_T)
 template <class R>
 cudaError_t cnn_output(const Dims& D, const R* theta, const R* hid, R* t, unsigned int* amax, cudaStream_t s);
-// backward from dt: with dtheta == NULL Rprop in place on theta / state, else the gradient into dtheta
+// backward from dt, with dtheta == NULL Rprop in place on theta / state, else the gradient into dtheta:
+// the output layer (dpre out; bulk: FP32 update through two bulk-copy W2 passes, usable when cnn_bulk_ok,
+// two launches, else one; a timed-out wait ORs 4 into *flags), then the dense head and the convolution
+// (two launches).
+bool cnn_bulk_ok(const Dims& D);
 template <class R>
-cudaError_t cnn_backward(const Dims& D, R* theta, R* state, R* dtheta, const R* f, const R* dt, const R* feats,
-                         const int* pos, const R* vals, const R* pre, const R* hid, R* dpre, double* partials,
-                         unsigned int* counter, const NetCfg& c, cudaStream_t s);
+cudaError_t cnn_output_backward(const Dims& D, R* theta, R* state, R* dtheta, const R* dt, const R* hid,
+                                const R* pre, R* dpre, double* partials, unsigned int* counter, unsigned int* flags,
+                                const NetCfg& c, bool bulk, cudaStream_t s);
+template <class R>
+cudaError_t cnn_head_backward(const Dims& D, R* theta, R* state, R* dtheta, const R* f, const R* feats,
+                              const int* pos, const R* vals, const R* dpre, const NetCfg& c, cudaStream_t s);
 
 // Chol_Delta: dL/dt from Z = T G (lower tiles): dR_ii = 2 Re Z_ii, dR_ij = 2 Re Z_ij, dR_ji = 2 Im Z_ij (i > j)
 template <class R> cudaError_t net_tri_grad(const Dims& D, const cx_t<R>* Z, R* dt, cudaStream_t s);
@@ -134,6 +145,11 @@ template <class R> cudaError_t net_w1_pass(const Dims& D, R* theta, R* step, con
 // FP32 in-place weight passes with bulk-copy staging (fnn_bulk.cu); usable when wpass_bulk_ok(H, n)
 // and every streamed array is 16-byte aligned.  flags: a timed-out wait ORs 4 into *flags.
 bool wpass_bulk_ok(int H, long long n);
+// the W2 pass over `rows` rows of W2^T starting at element rowoff of theta / step, with b2 at ob2 (< 0: b2
+// left alone); hid, pre, dpre point at the rows' first hidden unit; only dpre is written (no b1 update)
+cudaError_t w2_rows_pass_bulk(long long n, int rows, float* theta, float* step, long long rowoff, long long ob2,
+                              const float* dt, const float* hid, const float* pre, float* dpre, double* partials,
+                              unsigned int* counter, unsigned int* flags, const NetCfg& c, cudaStream_t s);
 cudaError_t w2_pass_bulk(const Dims& D, float* theta, float* step, const float* dt, const float* hid,
                          const float* pre, float* dpre, double* partials, unsigned int* counter, unsigned int* flags,
                          const NetCfg& c, cudaStream_t s);
