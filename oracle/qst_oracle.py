@@ -546,6 +546,44 @@ def fidelity_pure(rho_hat: np.ndarray, psi: np.ndarray) -> float:
     return float(np.real(np.vdot(psi, rho_hat @ psi)))
 
 
+def fidelity_decomposed(Q: np.ndarray, sigma: np.ndarray, rho: np.ndarray) -> float:
+    """Sec. 2.3 eq. fq_decom: with rho~ = Q diag(sigma) Q^dag known, F_q(rho~, rho) = (sum_i sqrt(s'_i))^2,
+    s' the eigenvalues of Q sqrt(Sigma) Q^dag rho Q sqrt(Sigma) Q^dag (clamped at 0): one decomposition."""
+    S = (Q * np.sqrt(np.clip(sigma, 0.0, None))) @ Q.conj().T
+    M = S @ rho @ S
+    ev = np.linalg.eigvalsh(0.5 * (M + M.conj().T))
+    return float(np.sum(np.sqrt(np.clip(ev, 0.0, None))) ** 2)
+
+
+def noisy_target(psi: np.ndarray, w: float) -> np.ndarray:
+    """The targets of the Sec. 4 sweeps: w |psi><psi| / <psi|psi> + (1 - w) I / d (white noise with
+    p = w, the depolarising channel with lambda = 1 - w, the pure state with w = 1)."""
+    u = np.asarray(psi, dtype=np.complex128)
+    u = u / np.linalg.norm(u)
+    d = u.size
+    return w * np.outer(u, u.conj()) + (1.0 - w) * np.eye(d) / d
+
+
+def state_fidelity_decomposed(theta, f, N, psi, w, mapping="chol_h", P=2.0, network="fnn",
+                              decision=np.float64) -> float:
+    """F_q of the network's state against noisy_target(psi, w) through eq. fq_decom, with the
+    decomposition of rho^ taken from that of T (Sec. 3.2): T = Q Lambda Q^dag gives
+    rho^ = Q diag(g) Q^dag / sum g, g = lambda^2 for Chol_H (T^dag T = T^2 for Hermitian T) and
+    g = |lambda|^P for A_P (with its floor for P <= 1)."""
+    if mapping not in ("chol_h", "abs_p"):
+        raise ValueError("eq. fq_decom needs the decomposition of a Hermitian T")
+    t = network_forward_cnn(theta, f, N, decision)[2] if network == "cnn" else network_forward(theta, f, N)[2]
+    lam, Q = np.linalg.eigh(hermitian_from_output(t))
+    if mapping == "chol_h":
+        g = lam ** 2
+    else:
+        a = np.abs(lam)
+        if P <= 1.0:
+            a = np.maximum(a, ABS_P_EPS * a.max())
+        g = a ** P
+    return fidelity_decomposed(Q, g / g.sum(), noisy_target(psi, w))
+
+
 def classical_fidelity(P_hat: np.ndarray, P: np.ndarray) -> float:
     """Sec. 2.3 eq. F_CF: (sum_k sqrt(P_hat_k P_k))^2, an upper bound on F_q."""
     return float(np.sum(np.sqrt(np.clip(P_hat, 0, None) * np.clip(P, 0, None))) ** 2)

@@ -203,6 +203,49 @@ def test_fidelity_properties_and_printed_formulas(golden_dir):
         assert abs(np.sum(np.abs(r) ** 2) - ((1 - 1 / d) * p * p + 1 / d)) < 1e-12
 
 
+def test_decomposed_fidelity_pins():
+    """Sec. 2.3 eq. fq_decom (one decomposition) against eq. F_QF by the singular-value route, the
+    pure-target form <psi|rho^|psi>, a closed form, and the network's own decomposition of T."""
+    rng = np.random.default_rng(5)
+    for N, r1, r2 in ((2, 1, 4), (3, 3, 2), (4, 16, 5)):
+        rt = synth.ginibre_mixed(N, r1, 10 + N)
+        rho = synth.ginibre_mixed(N, r2, 20 + N)
+        ev, Q = np.linalg.eigh(rt)
+        got = O.fidelity_decomposed(Q, ev, rho)
+        assert abs(got - O.fidelity(rt, rho)) < 1e-7 * max(got, 1e-3), (N, got)
+        # the roles swap (eq. F_QF is symmetric): decompose the other state
+        ev2, Q2 = np.linalg.eigh(rho)
+        assert abs(O.fidelity_decomposed(Q2, ev2, rt) - got) < 1e-7
+    # closed form: a pure rho~ = |phi><phi| against w |psi><psi| + (1 - w) I / d
+    N, d = 3, 8
+    phi = synth.haar_pure(N, 3)
+    psi = synth.haar_pure(N, 4)
+    Q = np.linalg.qr(np.column_stack([phi] + [rng.standard_normal(d) + 1j * rng.standard_normal(d)
+                                              for _ in range(d - 1)]))[0]
+    sigma = np.zeros(d)
+    sigma[0] = 1.0
+    for w in (0.0, 0.35, 1.0):
+        want = w * abs(np.vdot(phi, psi)) ** 2 + (1 - w) / d
+        # the d - 1 zero eigenvalues come out at ~1e-17, their square roots at ~3e-9
+        assert abs(O.fidelity_decomposed(Q, sigma, O.noisy_target(psi, w)) - want) < 1e-7
+    # the network's state: Chol_H and A_P, mixed and pure targets
+    M = O.tetrahedral_povm()
+    N = 3
+    psi = synth.haar_pure(N, 7)
+    f = O.born_probabilities(synth.depolarized(psi, 0.2), M).real
+    theta = synth.init_theta(N, 8)
+    for mapping, P in (("chol_h", 2.0), ("abs_p", 1.5), ("abs_p", 1.0)):
+        rh = O.state_from_theta(theta, f, N, mapping=mapping, P=P)
+        for w in (1.0, 0.8, 0.1):
+            got = O.state_fidelity_decomposed(theta, f, N, psi, w, mapping=mapping, P=P)
+            assert abs(got - O.fidelity(rh, O.noisy_target(psi, w))) < 1e-7
+        # w = 1: M is rank one, its other 7 eigenvalues come out at ~1e-17 (square roots ~3e-9)
+        assert abs(O.state_fidelity_decomposed(theta, f, N, psi, 1.0, mapping=mapping, P=P)
+                   - O.fidelity_pure(rh, psi)) < 1e-7
+    with pytest.raises(ValueError):
+        O.state_fidelity_decomposed(theta, f, N, psi, 0.5, mapping="chol_delta")
+
+
 def test_reconstruction_from_exact_probabilities_reaches_target():
     """Sec. 4.2: Chol_H reaches fidelity ~1 from exact (noise-free) probabilities."""
     M = O.tetrahedral_povm()
