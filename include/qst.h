@@ -202,6 +202,21 @@ qst_status qst_get_rho(qst_ctx* ctx, const void* f, void* rho_out, double* loss)
 qst_status qst_classical_fidelity(qst_ctx* ctx, const void* f, const void* P, long long samples,
                                   unsigned long long seed, double* Fc);
 
+/* Quantum (state) fidelity of Sec. 2.3 eq. F_QF between rho^ of the current parameters (network input
+ * f, device or host, n reals) and the target rho = w |psi><psi| / <psi|psi> + (1 - w) I / d of the Sec. 4
+ * sweeps (pure: w = 1; white noise of strength p: w = p; depolarising channel lambda: w = 1 - lambda),
+ * computed on the GPU by the decomposition route of eq. fq_decom.  The decomposition of rho^ comes from
+ * that of T (Sec. 3.2: T = Q Lambda Q^dag, rho^ = Q g(Lambda) Q^dag / Tr g(Lambda), g = lambda^2 for
+ * Chol_H, |lambda|^P for A_P): for Chol_H a cold Jacobi run of `sweeps` sweeps (0: 10; rounded up to
+ * even), for A_P the decomposition of the forward pass.  The eigenvalues of sqrt(rho^) rho sqrt(rho^)
+ * (diagonal plus rank one in the basis Q) are the roots of its secular equation, found by bisection in
+ * FP64; F_q = (sum sqrt(eigenvalue))^2.
+ *   psi  device or host, d complex of the context precision (interleaved re, im), not all zero;
+ *   w    in [0, 1];  Fq  host, written.
+ * QST_E_UNSUPPORTED for Chol_Delta contexts.  The first call of a Chol_H context allocates the
+ * eigensolver's workspace (6 d x d complex); every call allocates nothing more after its first. */
+qst_status qst_state_fidelity(qst_ctx* ctx, const void* f, const void* psi, double w, int sweeps, double* Fq);
+
 /* ---- synthetic data on the GPU (Sec. 4: the test states of the sweeps, multinomial sampling) ---- */
 enum { QST_STATE_PRODUCT = 0,  /* ((|0> + |1>) / sqrt 2)^N */
        QST_STATE_GHZI = 1,     /* (|0...0> + i |1...1>) / sqrt 2 */

@@ -51,7 +51,7 @@ struct qst_ctx {
   const void* f_last = nullptr;
   long long iters = 0;
   long long launches = 0;
-  double* h_scal = nullptr;     // pinned host mirror of scal[0..4]
+  double* h_scal = nullptr;     // pinned host mirror of scal (16 doubles)
   unsigned int* h_flags = nullptr;
   size_t partial_doubles = 0;
   // per-phase timing (qst_timing_enable)
@@ -60,6 +60,7 @@ struct qst_ctx {
   int tmax = 0, tcount = 0, tslot = -1;
   void* apw = nullptr;  // AbsPWork<R> (QST_MAP_ABS_P)
   double* cdf = nullptr;  // scratch of the sampled classical fidelity, allocated on first use
+  double* fq = nullptr;   // scratch of the state fidelity, allocated on first use
   size_t P = 0;           // parameters: qst_theta_size_net(N, network)
   bool cnn = false;       // the App. A CNN head instead of the 3-layer FNN
   unsigned long long* samp = nullptr;  // scratch of qst_sample_counts, allocated on first use
@@ -578,6 +579,68 @@ template <class R> struct Engine {
     return QST_OK;
   }
 
+  // Sec. 2.3 eq. F_QF through eq. fq_decom between rho^ of the current parameters (input f) and
+  // w |psi><psi| / <psi|psi> + (1 - w) I / d, from the eigendecomposition of T (Chol_H: a cold Jacobi
+  // run of `sweeps` sweeps on a workspace made on first use; A_P: the decomposition of the forward).
+  static qst_status state_fidelity(qst_ctx* c, const void* f_user, const void* psi_user, double wgt, int sweeps,
+                                   double* Fq) {
+    Work<R>* w = W<R>(c);
+    const Dims& D = c->D;
+    qst_status st;
+    const R* f = (const R*)stage_input(c, f_user, (size_t)D.n * sizeof(R), w->fstage, &st);
+    if (st != QST_OK) return st;
+    if (c->cnn || !c->hidden_valid || f_user != c->f_last) {
+      if ((st = validate_f<R>(c, f)) != QST_OK) return st;
+      if ((st = hidden(c, w->theta, f)) != QST_OK) return st;
+      c->hidden_valid = true;
+      c->f_last = f_user;
+    }
+    if (c->opt.mapping == QST_MAP_ABS_P) {
+      if ((st = forward_state(c, w->theta)) != QST_OK) return st;
+    } else {
+      // T itself (complex, also in the mixed-precision path), then its decomposition
+      if (c->cnn) {
+        QST_CU(cnn_output<R>(D, w->theta, w->hid, w->dt, nullptr, c->stream));
+        QST_CU(net_hermitian_T<R>(D, w->dt, w->T, nullptr, c->stream));
+      } else {
+        QST_CU(net_build_T<R>(D, w->theta, w->hid, w->dt, w->T, nullptr, c->stream));
+      }
+      c->launches += 2;
+      if (!c->apw) {
+        AbsPWork<R>* ap = new (std::nothrow) AbsPWork<R>();
+        if (!ap) return QST_E_NOMEM;
+        memset(ap, 0, sizeof(*ap));
+        c->apw = ap;
+        const size_t nn = (size_t)D.d * D.d;
+        QST_CU(dalloc(c, &ap->A0, nn));
+        QST_CU(dalloc(c, &ap->A1, nn));
+        QST_CU(dalloc(c, &ap->V0, nn));
+        QST_CU(dalloc(c, &ap->V1, nn));
+        QST_CU(dalloc(c, &ap->W, nn));
+        QST_CU(dalloc(c, &ap->Qh, nn));
+        QST_CU(dalloc(c, &ap->lam, (size_t)D.d));
+        QST_CU(dalloc(c, &ap->s, (size_t)D.d));
+        QST_CU(dalloc(c, &ap->sp, (size_t)D.d));
+      }
+      const int sw = (sweeps > 0 ? sweeps : c->sweeps) + ((sweeps > 0 ? sweeps : c->sweeps) & 1);
+      QST_CU(abs_p_forward<R>(D.d, w->T, *reinterpret_cast<AbsPWork<R>*>(c->apw), sw, false, 2.0, w->X,
+                              c->stream));
+      c->launches += 4 + (long long)sw * (D.d - 1);
+    }
+    const V* psi = (const V*)stage_input(c, psi_user, (size_t)D.d * sizeof(V), w->Wlo, &st);
+    if (st != QST_OK) return st;
+    if (!c->fq) QST_CU(dalloc(c, &c->fq, state_fidelity_scratch_doubles(D.d)));
+    const AbsPWork<R>& ap = *reinterpret_cast<AbsPWork<R>*>(c->apw);
+    double* out = w->scal + 8;
+    QST_CU(state_fidelity_from_decomposition<R>(D.d, ap.Qh, ap.s, psi, wgt, c->fq, out, w->counters + CNT_FID,
+                                                c->stream));
+    c->launches += 3;
+    QST_CU(cudaMemcpyAsync(c->h_scal, w->scal, 11 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    QST_CU(cudaStreamSynchronize(c->stream));
+    *Fq = c->h_scal[10];
+    return QST_OK;
+  }
+
   static qst_status get_rho(qst_ctx* c, const void* f_user, void* rho_out, double* loss) {
     Work<R>* w = W<R>(c);
     const Dims& D = c->D;
@@ -874,6 +937,13 @@ qst_status qst_classical_fidelity(qst_ctx* c, const void* f, const void* P, long
   if (!c || !f || !P || !Fc || samples < 0) return QST_E_INVAL;
   if (!c->params_set) return QST_E_STATE;
   return QST_DISPATCH(c, classical_fidelity(c, f, P, samples, seed, Fc));
+}
+
+qst_status qst_state_fidelity(qst_ctx* c, const void* f, const void* psi, double w, int sweeps, double* Fq) {
+  if (!c || !f || !psi || !Fq || !(w >= 0.0 && w <= 1.0) || sweeps < 0) return QST_E_INVAL;
+  if (c->opt.mapping == QST_MAP_CHOL_DELTA) return QST_E_UNSUPPORTED;
+  if (!c->params_set) return QST_E_STATE;
+  return QST_DISPATCH(c, state_fidelity(c, f, psi, w, sweeps, Fq));
 }
 
 qst_status qst_test_state(qst_ctx* c, int kind, double w, void* rho) {

@@ -44,7 +44,8 @@ template <class R> struct Work {
   int* pos;
   double* cnn_part;    // CNN: per-tile pooling scratch (cnn_part_doubles)
   R* fstage;           // staging copy of a host f, n reals
-  double* scal;        // [0] Tr X, [1] sum f, [2] loss, [3] scale of T, [4] scale of G
+  double* scal;        // [0] Tr X, [1] sum f, [2] loss, [3] scale of T, [4] scale of G, [5] F_c,
+                       // [8..10] state fidelity (sum g, bracket bound, F_q)
   double* partials;    // per-block partial sums
   unsigned int* counters;  // last-block counters, one per reduction site
   unsigned int* flags;     // [0] clamp count, [1] device-side wait timeouts
@@ -177,6 +178,16 @@ template <class R> cudaError_t abs_p_forward(int d, const cx_t<R>* T, AbsPWork<R
 template <class R> cudaError_t abs_p_restore_q(int d, AbsPWork<R>& w, cudaStream_t s);
 // Y with Y + Y^dag = dL/dT = Q (D o (Q^dag G Q)) Q^dag, from G = dL/dX
 template <class R> cudaError_t abs_p_backward(int d, const cx_t<R>* G, AbsPWork<R>& w, cx_t<R>* Y, cudaStream_t s);
+
+// ---- quantum state fidelity (fidelity_q.cu) ----
+// F_q (Sec. 2.3 eq. F_QF via eq. fq_decom) between rho^ = Q diag(g) Q^dag / sum g (Qh = Q^dag, d x d;
+// g >= 0, d) and w |psi><psi| / <psi|psi> + (1 - w) I / d; scratch: state_fidelity_scratch_doubles(d);
+// out[0] = sum g, out[1] = bracket bound, out[2] = F_q.  d a power of two up to 4096.
+size_t state_fidelity_scratch_doubles(int d);
+template <class R>
+cudaError_t state_fidelity_from_decomposition(int d, const cx_t<R>* Qh, const R* g, const cx_t<R>* psi, double w,
+                                              double* scratch, double* out, unsigned int* counter,
+                                              cudaStream_t s);
 
 // ---- complex products (gemm_simt.cu) ----
 // C = A B for d x d complex row-major matrices; lower == true computes only tiles I >= J.

@@ -47,6 +47,7 @@ EXPORTED = [
     "qst_batch_init", "qst_batch_context", "qst_batch_set_params", "qst_batch_step",
     "qst_batch_reconstruct", "qst_batch_kernel_launches", "qst_batch_sync", "qst_batch_destroy",
     "qst_classical_fidelity", "qst_test_state", "qst_sample_counts", "qst_theta_size_net",
+    "qst_state_fidelity",
 ]
 
 PHASES = ["hidden", "build_T", "x_fwd", "povm_lo", "povm_hi", "povm_adj", "gt", "sym", "w2", "w1"]
@@ -101,6 +102,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "qst_reconstruct": (i, [vp, vp, i, vp, pd]),
         "qst_get_rho": (i, [vp, vp, vp, pd]),
         "qst_classical_fidelity": (i, [vp, vp, vp, ctypes.c_longlong, ctypes.c_ulonglong, pd]),
+        "qst_state_fidelity": (i, [vp, vp, vp, ctypes.c_double, i, pd]),
         "qst_test_state": (i, [vp, i, d, vp]),
         "qst_sample_counts": (i, [vp, vp, ctypes.c_longlong, ctypes.c_ulonglong, vp, vp]),
         "qst_state_bytes": (sz, [vp]),
@@ -237,6 +239,14 @@ def qst_classical_fidelity(ctx: int, f, P, samples: int = 0, seed: int = 0) -> f
     out = ctypes.c_double()
     _check(load().qst_classical_fidelity(ctx, ptr(f), ptr(P), int(samples), int(seed), ctypes.byref(out)),
            "qst_classical_fidelity")
+    return out.value
+
+
+def qst_state_fidelity(ctx: int, f, psi, w: float = 1.0, sweeps: int = 0) -> float:
+    """Quantum fidelity (Sec. 2.3 eq. F_QF via eq. fq_decom) against w |psi><psi| + (1 - w) I / d."""
+    out = ctypes.c_double()
+    _check(load().qst_state_fidelity(ctx, ptr(f), ptr(psi), float(w), int(sweeps), ctypes.byref(out)),
+           "qst_state_fidelity")
     return out.value
 
 
