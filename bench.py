@@ -54,6 +54,22 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(dist, ws, ms_local):
+    """The timed region's length as the job sees it: the max over the ranks (one float64 all-reduced on
+    the host; the replicas exchange nothing else)."""
+    if ws <= 1:
+        return ms_local
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ws, steps, ms_max):
+    """Whole-job iterations per second: every rank ran `steps` iterations within ms_max."""
+    return ws * steps / (ms_max / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi clocks sampled every 200 ms while the timed region runs."""
 
@@ -258,6 +274,8 @@ def run_precision(torch, qst, synth, dev, stream, prec, theta0, f, K, W, dist, m
         dist.barrier()
         with ClockSampler(torch.cuda.current_device()) as clk:
             ms, launches = time_steps(torch, qst, ctx, f_dev, K, stream)
+        torch.cuda.synchronize()
+        dist.barrier()
         # launch by launch, for comparison (same kernels, host launch gaps included)
         qst.qst_graph_enable(ctx, False)
         for _ in range(2):
@@ -615,13 +633,8 @@ def main_ours(args):
 
     head = "mixed_fp16x3" if mixed_ok else "plain_fp32"
     # max over ranks of the timed region
-    ms_local = res[head]["ms"]
-    ms_max = ms_local
-    if ws > 1:
-        t = torch.tensor([ms_local], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = ws * args.steps / (ms_max / 1e3)
+    ms_max = max_over_ranks(dist, ws, res[head]["ms"])
+    value = job_rate(ws, args.steps, ms_max)
 
     ttf = {}
     if args.ttf and rank == 0:
