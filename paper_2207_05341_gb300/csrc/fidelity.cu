@@ -7,6 +7,7 @@
 // the published counter-based generator (Steele, Lea and Flood, OOPSLA 2014): x = seed + (s + 1) gamma,
 // then its two-round mix.  Every sum has a fixed order (block partials, last block), so results repeat.
 #include "impl.h"
+#include "rng.cuh"
 
 namespace qst {
 
@@ -14,13 +15,6 @@ namespace {
 
 constexpr int kScanPer = 8;                   // elements per thread in the block scan
 constexpr int kScanBlock = 256 * kScanPer;    // elements per block
-
-__device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed, unsigned long long s) {
-  unsigned long long z = seed + (s + 1ull) * 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
 
 // Sum of one double per thread over the block (warp shuffles, then warps in order); valid in thread 0.
 __device__ __forceinline__ double block_sum(double v) {

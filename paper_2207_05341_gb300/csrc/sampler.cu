@@ -14,6 +14,7 @@
 // on the order).  Every decision is integer arithmetic, so the counts are bit-exact and reproducible.
 #include "../../include/qst.h"
 #include "impl.h"
+#include "rng.cuh"
 
 namespace qst {
 
@@ -21,13 +22,6 @@ namespace {
 
 constexpr int kPer = 8;
 constexpr int kBlockElems = 256 * kPer;
-
-__device__ __forceinline__ unsigned long long splitmix64_s(unsigned long long seed, unsigned long long s) {
-  unsigned long long z = seed + (s + 1ull) * 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
 
 template <class R>
 __global__ void __launch_bounds__(256) k_test_state(cx_t<R>* __restrict__ rho, int N, int kind, double w) {
@@ -135,7 +129,7 @@ __global__ void __launch_bounds__(256) k_draw(const unsigned long long* __restri
                                                unsigned long long seed, long long* __restrict__ counts) {
   const unsigned long long W = C[n - 1];
   for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < shots; s += (long long)gridDim.x * blockDim.x) {
-    const unsigned long long a = splitmix64_s(seed, (unsigned long long)s) >> 11;  // < 2^53
+    const unsigned long long a = splitmix64(seed, (unsigned long long)s) >> 11;  // < 2^53
     const unsigned long long hi = __umul64hi(a, W), lo = a * W;
     const unsigned long long t = (hi << 11) | (lo >> 53);                         // floor(a W / 2^53) < W
     long long l = 0, h = n - 1;
