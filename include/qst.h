@@ -282,8 +282,9 @@ qst_status qst_timing_read(qst_ctx* ctx, double* phase_ms, long long* phase_coun
  * captured on the first qst_step whose input f was also given to the previous
  * step (the hidden layer is then known) and is re-captured when f's pointer
  * changes.  f may be device memory or page-locked host memory (then a copy node
- * of the graph stages it on every replay); pageable host inputs use the
- * launch-by-launch path.  A replay has no host work between kernels.
+ * of the graph stages it on every replay, on a side stream beside the kernels that
+ * come before the first read of f; the context owns that stream); pageable host
+ * inputs use the launch-by-launch path.  A replay has no host work between kernels.
  * Instrumentation of the library, not part of the method. */
 qst_status qst_graph_enable(qst_ctx* ctx, int enable);
 

@@ -75,6 +75,10 @@ struct qst_ctx {
   const void* gf = nullptr;
   long long gnodes = 0;  // kernel launches in one replay of gexec
   bool capturing = false;
+  // a captured step with a page-locked host f copies f on a side stream, beside its first kernels
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_f = nullptr;
+  bool f_wait = false;  // the stream must join ev_f before its first read of f
 };
 
 namespace {
@@ -90,6 +94,14 @@ qst_status cuda_status(cudaError_t e) {
     cudaError_t _e = (expr);                       \
     if (_e != cudaSuccess) return cuda_status(_e); \
   } while (0)
+
+// Before the first read of f: join the copy of a host f issued on the side stream (a captured step's
+// copy runs beside the kernels that come before this point).
+cudaError_t join_f(qst_ctx* c) {
+  if (!c->f_wait) return cudaSuccess;
+  c->f_wait = false;
+  return cudaStreamWaitEvent(c->stream, c->ev_f, 0);
+}
 
 // Under stream capture an event record becomes a graph node only with cudaEventRecordExternal.
 void record_mark(qst_ctx* c, cudaEvent_t e) {
@@ -290,6 +302,7 @@ template <class R> struct Engine {
 
   // loss -> scal[2]; with backward, G = sum_k g_k M_k -> w->G
   static qst_status povm_likelihood(qst_ctx* c, const R* f, bool backward) {
+    QST_CU(join_f(c));  // the first read of f in a step (the CNN's comes earlier, in its hidden layer)
     Work<R>* w = W<R>(c);
     const Dims& D = c->D;
     const PovmB<R>& B = povmB<R>(c);
@@ -400,7 +413,10 @@ template <class R> struct Engine {
     Work<R>* w = W<R>(c);
     const Dims& D = c->D;
     qst_status st;
-    if (c->cnn && (st = hidden(c, w->theta, f)) != QST_OK) return st;  // the head changes every step
+    if (c->cnn) {  // the head changes every step, and its convolution reads f first
+      QST_CU(join_f(c));
+      if ((st = hidden(c, w->theta, f)) != QST_OK) return st;
+    }
     if ((st = forward_state(c, w->theta)) != QST_OK) return st;
     if ((st = povm_likelihood(c, f, true)) != QST_OK) return st;
     if ((st = backward_state(c)) != QST_OK) return st;
@@ -441,19 +457,32 @@ template <class R> struct Engine {
     Work<R>* w = W<R>(c);
     const long long l0 = c->launches;
     const bool timed = c->tmax > 0;
+    if (host_f && !c->copy_stream) {
+      QST_CU(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+      QST_CU(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+      QST_CU(cudaEventCreateWithFlags(&c->ev_f, cudaEventDisableTiming));
+    }
     QST_CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     c->capturing = true;
     const R* f = (const R*)f_user;
     cudaError_t ec = cudaSuccess;
-    if (host_f) {
-      ec = cudaMemcpyAsync(w->fstage, f_user, (size_t)c->D.n * sizeof(R), cudaMemcpyHostToDevice, c->stream);
+    if (host_f) {  // fork: the copy node runs beside the kernels up to the first read of f
+      ec = cudaEventRecord(c->ev_fork, c->stream);
+      if (ec == cudaSuccess) ec = cudaStreamWaitEvent(c->copy_stream, c->ev_fork, 0);
+      if (ec == cudaSuccess)
+        ec = cudaMemcpyAsync(w->fstage, f_user, (size_t)c->D.n * sizeof(R), cudaMemcpyHostToDevice,
+                             c->copy_stream);
+      if (ec == cudaSuccess) ec = cudaEventRecord(c->ev_f, c->copy_stream);
+      c->f_wait = ec == cudaSuccess;
       f = (const R*)w->fstage;
     }
     if (timed) {  // the phase events become nodes of the graph; every replay re-records them (slot 0)
       c->tcount = 0;
       tmark_begin(c);
     }
-    const qst_status st = ec == cudaSuccess ? step_body(c, f) : cuda_status(ec);
+    qst_status st = ec == cudaSuccess ? step_body(c, f) : cuda_status(ec);
+    const cudaError_t ej = join_f(c);  // the side stream must have joined before the capture ends
+    if (st == QST_OK && ej != cudaSuccess) st = cuda_status(ej);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     c->capturing = false;
@@ -1167,6 +1196,9 @@ void qst_destroy(qst_ctx* c) {
   }
   if (c->h_scal) cudaFreeHost(c->h_scal);
   if (c->h_flags) cudaFreeHost(c->h_flags);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_f) cudaEventDestroy(c->ev_f);
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   delete c;
 }
 

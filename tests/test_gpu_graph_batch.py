@@ -28,10 +28,11 @@ def _inputs(N, seed):
     return f.astype(np.float32), synth.init_theta(N, 60 + seed).astype(np.float32)
 
 
-def _run(N, f, theta, steps, prec, graph, timing=False, extra=None):
+def _run(N, f, theta, steps, prec, graph, timing=False, extra=None, host=False, network=qst.QST_NET_FNN):
     stream = torch.cuda.Stream()
     o = qst.qst_default_options()
     o.precision = prec
+    o.network = network
     ctx = qst.qst_init(N, opt=o, stream=stream.cuda_stream)
     try:
         if graph:
@@ -39,7 +40,7 @@ def _run(N, f, theta, steps, prec, graph, timing=False, extra=None):
         if timing:
             qst.qst_timing_enable(ctx, steps)
         qst.qst_set_params(ctx, theta)
-        fd = torch.from_numpy(f).cuda()
+        fd = torch.from_numpy(f).pin_memory() if host else torch.from_numpy(f).cuda()
         torch.cuda.synchronize()
         losses = [qst.qst_step(ctx, fd)[0] for _ in range(steps)]
         out = torch.empty(theta.size, device="cuda")
@@ -81,6 +82,23 @@ def test_timed_graph_replay(prec):
     assert all(tm[p][1] == 1 and tm[p][0] > 0 for p in timed)
     # the launch-by-launch path recorded all five steps
     assert xa["timing"]["w2"][1] == 5 and xa["timing"]["hidden"][1] == 1
+
+
+@pytest.mark.parametrize("N,prec,network", [(6, qst.QST_FP32, qst.QST_NET_FNN), (8, qst.QST_MIXED, qst.QST_NET_FNN),
+                                            (6, qst.QST_FP32, qst.QST_NET_CNN)])
+def test_graph_replay_with_page_locked_host_f(N, prec, network):
+    """A captured step copies a page-locked host f on a side stream beside its first kernels (the FNN
+    reads f first in the likelihood, the CNN at once): same losses and parameters as device f."""
+    f, theta = _inputs(N, 20 + N)
+    if network == qst.QST_NET_CNN:
+        theta = synth.init_theta_cnn(N, 70 + N).astype(np.float32)
+    la, ta, _ = _run(N, f, theta, 6, prec, graph=False, network=network)
+    lb, tb, ib = _run(N, f, theta, 6, prec, graph=True, host=True, network=network)
+    xc = {}
+    lc, tc, _ = _run(N, f, theta, 6, prec, graph=True, host=True, timing=True, extra=xc, network=network)
+    assert la == lb == lc and ib == 6
+    assert np.array_equal(ta, tb) and np.array_equal(ta, tc)
+    assert xc["timing"]["w2"][1] == 1
 
 
 def test_graph_needs_a_stream():
