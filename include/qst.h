@@ -213,8 +213,9 @@ qst_status qst_classical_fidelity(qst_ctx* ctx, const void* f, const void* P, lo
  * FP64; F_q = (sum sqrt(eigenvalue))^2.
  *   psi  device or host, d complex of the context precision (interleaved re, im), not all zero;
  *   w    in [0, 1];  Fq  host, written.
+ * For Chol_H the sweeps rotate psi along (phi = Q^dag psi) instead of forming Q.
  * QST_E_UNSUPPORTED for Chol_Delta contexts.  The first call of a Chol_H context allocates the
- * eigensolver's workspace (6 d x d complex); every call allocates nothing more after its first. */
+ * eigensolver's workspace (2 d x d complex); no call allocates anything after the first. */
 qst_status qst_state_fidelity(qst_ctx* ctx, const void* f, const void* psi, double w, int sweeps, double* Fq);
 
 /* ---- synthetic data on the GPU (Sec. 4: the test states of the sweeps, multinomial sampling) ---- */

@@ -610,7 +610,8 @@ template <class R> struct Engine {
 
   // Sec. 2.3 eq. F_QF through eq. fq_decom between rho^ of the current parameters (input f) and
   // w |psi><psi| / <psi|psi> + (1 - w) I / d, from the eigendecomposition of T (Chol_H: a cold Jacobi
-  // run of `sweeps` sweeps on a workspace made on first use; A_P: the decomposition of the forward).
+  // run of `sweeps` sweeps that rotates psi instead of forming Q, on a workspace made on first use;
+  // A_P: the decomposition of the forward, with Q).
   static qst_status state_fidelity(qst_ctx* c, const void* f_user, const void* psi_user, double wgt, int sweeps,
                                    double* Fq) {
     Work<R>* w = W<R>(c);
@@ -635,7 +636,7 @@ template <class R> struct Engine {
         QST_CU(net_build_T<R>(D, w->theta, w->hid, w->dt, w->T, nullptr, c->stream));
       }
       c->launches += 2;
-      if (!c->apw) {
+      if (!c->apw) {  // the eigenvalue workspace only: two d x d buffers and three d-vectors
         AbsPWork<R>* ap = new (std::nothrow) AbsPWork<R>();
         if (!ap) return QST_E_NOMEM;
         memset(ap, 0, sizeof(*ap));
@@ -643,26 +644,26 @@ template <class R> struct Engine {
         const size_t nn = (size_t)D.d * D.d;
         QST_CU(dalloc(c, &ap->A0, nn));
         QST_CU(dalloc(c, &ap->A1, nn));
-        QST_CU(dalloc(c, &ap->V0, nn));
-        QST_CU(dalloc(c, &ap->V1, nn));
-        QST_CU(dalloc(c, &ap->W, nn));
-        QST_CU(dalloc(c, &ap->Qh, nn));
         QST_CU(dalloc(c, &ap->lam, (size_t)D.d));
         QST_CU(dalloc(c, &ap->s, (size_t)D.d));
         QST_CU(dalloc(c, &ap->sp, (size_t)D.d));
       }
-      const int sw = (sweeps > 0 ? sweeps : c->sweeps) + ((sweeps > 0 ? sweeps : c->sweeps) & 1);
-      QST_CU(abs_p_forward<R>(D.d, w->T, *reinterpret_cast<AbsPWork<R>*>(c->apw), sw, false, 2.0, w->X,
-                              c->stream));
-      c->launches += 4 + (long long)sw * (D.d - 1);
     }
     const V* psi = (const V*)stage_input(c, psi_user, (size_t)D.d * sizeof(V), w->Wlo, &st);
     if (st != QST_OK) return st;
-    if (!c->fq) QST_CU(dalloc(c, &c->fq, state_fidelity_scratch_doubles(D.d)));
-    const AbsPWork<R>& ap = *reinterpret_cast<AbsPWork<R>*>(c->apw);
+    // scratch: the fidelity's 4 d doubles, then phi = Q^dag psi (d complex)
+    if (!c->fq) QST_CU(dalloc(c, &c->fq, state_fidelity_scratch_doubles(D.d) + 2 * (size_t)D.d));
+    V* phi = reinterpret_cast<V*>(c->fq + state_fidelity_scratch_doubles(D.d));
+    AbsPWork<R>& ap = *reinterpret_cast<AbsPWork<R>*>(c->apw);
+    const bool absp = c->opt.mapping == QST_MAP_ABS_P;
+    if (!absp) {
+      const int sw = (sweeps > 0 ? sweeps : c->sweeps) + ((sweeps > 0 ? sweeps : c->sweeps) & 1);
+      QST_CU(jacobi_values_project<R>(D.d, w->T, ap, sw, 2.0, psi, phi, c->stream));
+      c->launches += 1 + (long long)sw * (D.d - 1);
+    }
     double* out = w->scal + 8;
-    QST_CU(state_fidelity_from_decomposition<R>(D.d, ap.Qh, ap.s, psi, wgt, c->fq, out, w->counters + CNT_FID,
-                                                c->stream));
+    QST_CU(state_fidelity_from_decomposition<R>(D.d, absp ? ap.Qh : nullptr, phi, ap.s, psi, wgt, c->fq, out,
+                                                w->counters + CNT_FID, c->stream));
     c->launches += 3;
     QST_CU(cudaMemcpyAsync(c->h_scal, w->scal, 11 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     QST_CU(cudaStreamSynchronize(c->stream));

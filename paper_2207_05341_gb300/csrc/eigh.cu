@@ -96,10 +96,12 @@ __device__ __forceinline__ PairRot<R> pair_rotation(const cx_t<R>* A, int d, int
 
 // One round: every thread owns the 2 x 2 block (rows of pair k) x (columns of pair l) of A and of V,
 // so each entry is read and written once: A' = R^dag A R on the block, V' = V R on rows {p_k, q_k}.
+// Vi == NULL: no eigenvectors are accumulated; phi != NULL: the vector phi <- R^dag phi in place (the
+// first block column, one thread per pair), so that after the sweeps phi = Q^dag phi_0.
 template <class R>
 __global__ void __launch_bounds__(256) k_jacobi_round(const cx_t<R>* __restrict__ A, cx_t<R>* __restrict__ Ao,
                                                        const cx_t<R>* __restrict__ Vi, cx_t<R>* __restrict__ Vo,
-                                                       int d, int r) {
+                                                       cx_t<R>* __restrict__ phi, int d, int r) {
   using V = cx_t<R>;
   constexpr int TP = 16;
   __shared__ PairRot<R> rk[TP], rl[TP];
@@ -109,6 +111,12 @@ __global__ void __launch_bounds__(256) k_jacobi_round(const cx_t<R>* __restrict_
   if (t < TP && k0 + t < half) rk[t] = pair_rotation<R>(A, d, k0 + t, r);
   else if (t >= 32 && t < 32 + TP && l0 + t - 32 < half) rl[t - 32] = pair_rotation<R>(A, d, l0 + t - 32, r);
   __syncthreads();
+  if (phi != nullptr && blockIdx.x == 0 && t < TP && k0 + t < half) {
+    const PairRot<R> a = rk[t];
+    const V xp = phi[a.p], xq = phi[a.q];
+    phi[a.p] = cadd(cmulc(a.r_pp, xp), cmulc(a.r_qp, xq));
+    phi[a.q] = cadd(cmulc(a.r_pq, xp), cmulc(a.r_qq, xq));
+  }
   const int k = k0 + t / TP, l = l0 + t % TP;
   if (k >= half || l >= half) return;
   const PairRot<R> a = rk[t / TP], b = rl[t % TP];
@@ -124,6 +132,7 @@ __global__ void __launch_bounds__(256) k_jacobi_round(const cx_t<R>* __restrict_
   Ao[rp + b.q] = cadd(cmulc(a.r_pp, u_pq), cmulc(a.r_qp, u_qq));
   Ao[rq + b.p] = cadd(cmulc(a.r_pq, u_pp), cmulc(a.r_qq, u_qp));
   Ao[rq + b.q] = cadd(cmulc(a.r_pq, u_pq), cmulc(a.r_qq, u_qq));
+  if (Vi == nullptr) return;
   // V' = V R on rows p_k, q_k, columns p_l, q_l
   const V v_pp = Vi[rp + b.p], v_pq = Vi[rp + b.q], v_qp = Vi[rq + b.p], v_qq = Vi[rq + b.q];
   Vo[rp + b.p] = cadd(cmul(v_pp, b.r_pp), cmul(v_pq, b.r_qp));
@@ -238,7 +247,7 @@ cudaError_t abs_p_forward(int d, const cx_t<R>* T, AbsPWork<R>& w, int sweeps, b
   const dim3 grid((d / 2 + 15) / 16, (d / 2 + 15) / 16);
   for (int sw = 0; sw < sweeps; ++sw) {
     for (int r = 0; r < d - 1; ++r) {
-      k_jacobi_round<R><<<grid, 256, 0, s>>>(Ain, Aout, Vin, Vout, d, r);
+      k_jacobi_round<R><<<grid, 256, 0, s>>>(Ain, Aout, Vin, Vout, nullptr, d, r);
       V* t = Ain; Ain = Aout; Aout = t;
       t = Vin; Vin = Vout; Vout = t;
     }
@@ -253,6 +262,27 @@ cudaError_t abs_p_forward(int d, const cx_t<R>* T, AbsPWork<R>& w, int sweeps, b
   if (e != cudaSuccess) return e;
   // X = (Q diag(s)) Q^dag, lower tiles
   return cgemm_simt<R>(d, w.W, w.Qh, X, true, s);
+}
+
+template <class R>
+cudaError_t jacobi_values_project(int d, const cx_t<R>* T, AbsPWork<R>& w, int sweeps, double P, const cx_t<R>* psi,
+                                  cx_t<R>* phi, cudaStream_t s) {
+  using V = cx_t<R>;
+  const long long nn = (long long)d * d;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(w.A0, T, nn * sizeof(V), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(phi, psi, (size_t)d * sizeof(V), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+  V *Ain = w.A0, *Aout = w.A1;
+  const dim3 grid((d / 2 + 15) / 16, (d / 2 + 15) / 16);
+  for (int sw = 0; sw < sweeps; ++sw) {
+    for (int r = 0; r < d - 1; ++r) {
+      k_jacobi_round<R><<<grid, 256, 0, s>>>(Ain, Aout, nullptr, nullptr, phi, d, r);
+      V* t = Ain; Ain = Aout; Aout = t;
+    }
+  }
+  w.A = Ain;
+  k_absp_spectrum<R><<<1, 1024, 0, s>>>(w.A, w.lam, w.s, w.sp, d, P, sizeof(R) == 4 ? 1e-7 : 1e-15);
+  return cudaGetLastError();
 }
 
 template <class R> cudaError_t abs_p_restore_q(int d, AbsPWork<R>& w, cudaStream_t s) {
@@ -281,6 +311,10 @@ template cudaError_t abs_p_forward<float>(int, const float2*, AbsPWork<float>&, 
                                           cudaStream_t);
 template cudaError_t abs_p_forward<double>(int, const double2*, AbsPWork<double>&, int, bool, double, double2*,
                                            cudaStream_t);
+template cudaError_t jacobi_values_project<float>(int, const float2*, AbsPWork<float>&, int, double, const float2*,
+                                                  float2*, cudaStream_t);
+template cudaError_t jacobi_values_project<double>(int, const double2*, AbsPWork<double>&, int, double,
+                                                   const double2*, double2*, cudaStream_t);
 template cudaError_t abs_p_restore_q<float>(int, AbsPWork<float>&, cudaStream_t);
 template cudaError_t abs_p_restore_q<double>(int, AbsPWork<double>&, cudaStream_t);
 template cudaError_t abs_p_backward<float>(int, const float2*, AbsPWork<float>&, float2*, cudaStream_t);

@@ -39,6 +39,13 @@ __global__ void __launch_bounds__(256) k_fq_phi(const cx_t<R>* __restrict__ Qh, 
   if (lane == 0) phi2[i] = re * re + im * im;
 }
 
+// phi2_i = |phi_i|^2 of a projection already formed.
+template <class R>
+__global__ void __launch_bounds__(256) k_fq_abs2(const cx_t<R>* __restrict__ phi, int d, double* __restrict__ phi2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < d) phi2[i] = (double)phi[i].x * (double)phi[i].x + (double)phi[i].y * (double)phi[i].y;
+}
+
 // One CTA: S = sum g, <psi|psi>, the poles c g_i and weights e g_i phi2_i sorted by pole (bitonic sort
 // in shared memory, d a power of two), the upper end of the last bracket; out[0] = S, out[1] = bound.
 template <class R>
@@ -154,14 +161,15 @@ __global__ void __launch_bounds__(256) k_fq_roots(const double* __restrict__ pol
 size_t state_fidelity_scratch_doubles(int d) { return 4 * (size_t)d; }
 
 template <class R>
-cudaError_t state_fidelity_from_decomposition(int d, const cx_t<R>* Qh, const R* g, const cx_t<R>* psi, double w,
-                                              double* scratch, double* out, unsigned int* counter,
-                                              cudaStream_t s) {
+cudaError_t state_fidelity_from_decomposition(int d, const cx_t<R>* Qh, const cx_t<R>* phi, const R* g,
+                                              const cx_t<R>* psi, double w, double* scratch, double* out,
+                                              unsigned int* counter, cudaStream_t s) {
   double* phi2 = scratch;
   double* pole = scratch + d;
   double* wt = scratch + 2 * (size_t)d;
   double* rs = scratch + 3 * (size_t)d;
-  k_fq_phi<R><<<(d + 7) / 8, 256, 0, s>>>(Qh, psi, d, phi2);
+  if (Qh) k_fq_phi<R><<<(d + 7) / 8, 256, 0, s>>>(Qh, psi, d, phi2);
+  else k_fq_abs2<R><<<(d + 255) / 256, 256, 0, s>>>(phi, d, phi2);
   const size_t smem = 2 * (size_t)d * sizeof(double);
   cudaError_t e = ensure_dynamic_smem((const void*)k_fq_sort<R>, smem);
   if (e != cudaSuccess) return e;
@@ -170,9 +178,11 @@ cudaError_t state_fidelity_from_decomposition(int d, const cx_t<R>* Qh, const R*
   return cudaGetLastError();
 }
 
-template cudaError_t state_fidelity_from_decomposition<float>(int, const float2*, const float*, const float2*, double,
-                                                              double*, double*, unsigned int*, cudaStream_t);
-template cudaError_t state_fidelity_from_decomposition<double>(int, const double2*, const double*, const double2*,
-                                                               double, double*, double*, unsigned int*, cudaStream_t);
+template cudaError_t state_fidelity_from_decomposition<float>(int, const float2*, const float2*, const float*,
+                                                              const float2*, double, double*, double*, unsigned int*,
+                                                              cudaStream_t);
+template cudaError_t state_fidelity_from_decomposition<double>(int, const double2*, const double2*, const double*,
+                                                               const double2*, double, double*, double*,
+                                                               unsigned int*, cudaStream_t);
 
 }  // namespace qst

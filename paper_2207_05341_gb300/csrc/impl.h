@@ -174,6 +174,10 @@ template <class R> struct AbsPWork {
 // from the previous eigenvectors (V0, with Q^dag in Qh).  Leaves Q in V0 and Q^dag in Qh.
 template <class R> cudaError_t abs_p_forward(int d, const cx_t<R>* T, AbsPWork<R>& w, int sweeps, bool warm,
                                              double P, cx_t<R>* X, cudaStream_t s);
+// Eigenvalues of Hermitian T (lam, s = |lam|^P, into w) and phi = Q^dag psi (d complex) from `sweeps` cold
+// Jacobi sweeps that rotate the vector instead of accumulating Q: only w.A0, w.A1, w.lam, w.s, w.sp are used.
+template <class R> cudaError_t jacobi_values_project(int d, const cx_t<R>* T, AbsPWork<R>& w, int sweeps, double P,
+                                                     const cx_t<R>* psi, cx_t<R>* phi, cudaStream_t s);
 // After restoring Q into V0 (checkpoint), recompute Q^dag.
 template <class R> cudaError_t abs_p_restore_q(int d, AbsPWork<R>& w, cudaStream_t s);
 // Y with Y + Y^dag = dL/dT = Q (D o (Q^dag G Q)) Q^dag, from G = dL/dX
@@ -183,11 +187,12 @@ template <class R> cudaError_t abs_p_backward(int d, const cx_t<R>* G, AbsPWork<
 // F_q (Sec. 2.3 eq. F_QF via eq. fq_decom) between rho^ = Q diag(g) Q^dag / sum g (Qh = Q^dag, d x d;
 // g >= 0, d) and w |psi><psi| / <psi|psi> + (1 - w) I / d; scratch: state_fidelity_scratch_doubles(d);
 // out[0] = sum g, out[1] = bracket bound, out[2] = F_q.  d a power of two up to 4096.
+// The same from phi = Q^dag psi already formed (Qh == NULL, phi given) instead of Qh.
 size_t state_fidelity_scratch_doubles(int d);
 template <class R>
-cudaError_t state_fidelity_from_decomposition(int d, const cx_t<R>* Qh, const R* g, const cx_t<R>* psi, double w,
-                                              double* scratch, double* out, unsigned int* counter,
-                                              cudaStream_t s);
+cudaError_t state_fidelity_from_decomposition(int d, const cx_t<R>* Qh, const cx_t<R>* phi, const R* g,
+                                              const cx_t<R>* psi, double w, double* scratch, double* out,
+                                              unsigned int* counter, cudaStream_t s);
 
 // ---- complex products (gemm_simt.cu) ----
 // C = A B for d x d complex row-major matrices; lower == true computes only tiles I >= J.
