@@ -2,9 +2,12 @@
 //   X = T T   (Sec. 3.2 eq. unified_DP, Hermitian: only tiles I >= J are computed)
 //   Y = G T   (backward of X = T T)
 // Row-major complex operands.  Classic register-blocked tiling: a CTA computes a
-// BM x BN tile, each thread a TM x TN block split into two halves per axis so
-// that its shared-memory reads are contiguous 16-byte vectors; the next K slice
-// is prefetched into registers while the current one is multiplied.
+// BM x BN tile, each thread a TM x TN block; the next K slice is prefetched into
+// registers while the current one is multiplied.  Shared-memory layout: A is
+// stored transposed with rows of BM + 4 entries, so that the stores of a warp
+// (8 k by 4 m) fall in distinct bank groups; a thread's TN columns of B are
+// 16-byte chunks (CW complex each) spaced by the chunks of the other threads of
+// its row, so that the 16 threads of a row read consecutive chunks.
 #include "impl.h"
 
 namespace qst {
@@ -16,7 +19,9 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_cgemm(int d, const cx
   using V = cx_t<R>;
   constexpr int NTX = BN / TN, NTY = BM / TM, NT = NTX * NTY;
   constexpr int LA = BM * BK / NT, LB = BK * BN / NT;
-  constexpr int PAD = 2;
+  constexpr int PAD = 4;
+  constexpr int CW = 16 / (int)sizeof(V);  // complex entries per 16-byte chunk
+  static_assert(TN % CW == 0, "a thread's columns are whole 16-byte chunks");
   static_assert(LA >= 1 && LB >= 1, "tile too small for the thread count");
   __shared__ __align__(16) V As[2][BK][BM + PAD];
   __shared__ __align__(16) V Bs[2][BK][BN + PAD];
@@ -78,10 +83,9 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_cgemm(int d, const cx
         a[TM / 2 + i] = As[buf][k][BM / 2 + ty * (TM / 2) + i];
       }
 #pragma unroll
-      for (int j = 0; j < TN / 2; ++j) {
-        b[j] = Bs[buf][k][tx * (TN / 2) + j];
-        b[TN / 2 + j] = Bs[buf][k][BN / 2 + tx * (TN / 2) + j];
-      }
+      for (int g = 0; g < TN / CW; ++g)
+#pragma unroll
+        for (int j = 0; j < CW; ++j) b[g * CW + j] = Bs[buf][k][g * (NTX * CW) + tx * CW + j];
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -102,7 +106,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_cgemm(int d, const cx
     const int m = m0 + (i < TM / 2 ? ty * (TM / 2) + i : BM / 2 + ty * (TM / 2) + (i - TM / 2));
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
-      const int nn = n0 + (j < TN / 2 ? tx * (TN / 2) + j : BN / 2 + tx * (TN / 2) + (j - TN / 2));
+      const int nn = n0 + (j / CW) * (NTX * CW) + tx * CW + j % CW;
       C[(long long)m * d + nn] = cmake<V>(accr[i][j], acci[i][j]);
     }
   }
