@@ -67,3 +67,32 @@ def test_rprop_bounds_are_checked_on_the_host(lib):
         with pytest.raises(qst.QstError) as e:
             qst.qst_init(3, opt=o)
         assert e.value.status == qst.QST_E_INVAL, (field, value)
+
+
+def test_option_validation_before_any_device_call(lib):
+    """Invalid combinations are refused by qst_init on the host, before it touches a device."""
+    def status(N, **kw):
+        o = qst.qst_default_options()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        with pytest.raises(qst.QstError) as e:
+            qst.qst_init(N, opt=o)
+        return e.value.status
+    assert status(2, network=qst.QST_NET_CNN) == qst.QST_E_INVAL  # 2^(N-3)-square pooling windows
+    assert status(5, network=7) == qst.QST_E_INVAL
+    assert status(8, mapping=qst.QST_MAP_CHOL_DELTA, precision=qst.QST_MIXED) == qst.QST_E_UNSUPPORTED
+    assert status(8, mapping=qst.QST_MAP_ABS_P, precision=qst.QST_MIXED) == qst.QST_E_UNSUPPORTED
+    assert status(4, mapping=qst.QST_MAP_ABS_P, P=0.0) == qst.QST_E_INVAL
+    assert status(6, precision=qst.QST_MIXED) == qst.QST_E_UNSUPPORTED  # the tensor-core path starts at N = 7
+    assert status(11, precision=qst.QST_FP64) == qst.QST_E_INVAL  # FP64 contexts stop at N = 10
+    assert status(13) == qst.QST_E_INVAL
+    assert status(4, mapping=9) == qst.QST_E_INVAL
+    assert status(4, eta_plus=1.0) == qst.QST_E_INVAL
+
+
+def test_parameter_counts_of_both_networks(lib):
+    for N in (3, 7, 11, 12):
+        n, H = 4 ** N, 4 * N
+        assert qst.qst_theta_size_net(N, qst.QST_NET_CNN) == H * n + n + H * 640 + H + 90 + 10
+        assert qst.qst_theta_size_net(N, qst.QST_NET_FNN) == qst.qst_theta_size(N)
+    assert qst.qst_theta_size_net(2, qst.QST_NET_CNN) == 0 and qst.qst_theta_size_net(13, qst.QST_NET_CNN) == 0
