@@ -96,3 +96,16 @@ def test_parameter_counts_of_both_networks(lib):
         assert qst.qst_theta_size_net(N, qst.QST_NET_CNN) == H * n + n + H * 640 + H + 90 + 10
         assert qst.qst_theta_size_net(N, qst.QST_NET_FNN) == qst.qst_theta_size(N)
     assert qst.qst_theta_size_net(2, qst.QST_NET_CNN) == 0 and qst.qst_theta_size_net(13, qst.QST_NET_CNN) == 0
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No fallback: without libqst.so the binding raises instead of computing anything elsewhere."""
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2207_05341_gb300 import qst\n"
+            "try:\n    qst.load(%r)\nexcept RuntimeError as e:\n    print('raised', 'not found' in str(e))\n"
+            % (ROOT, str(tmp_path / "libqst.so")))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == "raised True"
