@@ -371,6 +371,49 @@ __global__ void __launch_bounds__(256) k_symmetrize(const cx_t<R>* __restrict__ 
   const int TS = d < 32 ? d : 32;
   int I, J;
   tri_decode(blockIdx.x, I, J);
+  if constexpr (sizeof(R) == 4) {
+    if (TS == 32 && blockDim.x == 256) {
+      // FP32: 16-byte accesses (two complex per load, four outputs per store), so that a tile pair
+      // takes a quarter of the global stores and half the loads of the element-wise form below
+      const int t = threadIdx.x;
+      float4 a[2], b[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int q = t + 256 * k, row = q >> 4, col = (q & 15) * 2;
+        a[k] = *reinterpret_cast<const float4*>(Y + (long long)(I * 32 + row) * d + J * 32 + col);
+        b[k] = I != J ? *reinterpret_cast<const float4*>(Y + (long long)(J * 32 + row) * d + I * 32 + col)
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int q = t + 256 * k, row = q >> 4, col = (q & 15) * 2;
+        Ar[row][col] = a[k].x; Ai[row][col] = a[k].y; Ar[row][col + 1] = a[k].z; Ai[row][col + 1] = a[k].w;
+        Br[row][col] = b[k].x; Bi[row][col] = b[k].y; Br[row][col + 1] = b[k].z; Bi[row][col + 1] = b[k].w;
+      }
+      __syncthreads();
+      const int r = t >> 3, c = (t & 7) * 4;
+      float v[4];
+      if (I != J) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = R(2) * (Ar[r][c + u] + Br[c + u][r]);
+        *reinterpret_cast<float4*>(dt + (long long)(I * 32 + r) * d + J * 32 + c) = make_float4(v[0], v[1], v[2], v[3]);
+        // upper tile (J, I): element (J 32 + r, I 32 + c + u) = 2 Im Gamma_{(I 32 + c + u), (J 32 + r)}
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = R(2) * (Ai[c + u][r] - Bi[r][c + u]);
+        *reinterpret_cast<float4*>(dt + (long long)(J * 32 + r) * d + I * 32 + c) = make_float4(v[0], v[1], v[2], v[3]);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int cc = c + u;
+          if (r > cc) v[u] = R(2) * (Ar[r][cc] + Ar[cc][r]);
+          else if (r < cc) v[u] = R(2) * (Ai[cc][r] - Ai[r][cc]);
+          else v[u] = R(2) * Ar[r][r];
+        }
+        *reinterpret_cast<float4*>(dt + (long long)(I * 32 + r) * d + J * 32 + c) = make_float4(v[0], v[1], v[2], v[3]);
+      }
+      return;
+    }
+  }
   if (TS == 32 && blockDim.x == 256) {  // all 8 loads of a thread in flight at once
     cx_t<R> a[4], b[4];
 #pragma unroll

@@ -324,7 +324,9 @@ __global__ void __launch_bounds__(256) k_split(const float2* __restrict__ A, H* 
 // The Hermitian T of t (R = t as d x d row-major; T_ii = R_ii, T_ij = R_ij + i R_ji for i > j,
 // T_ji = conj T_ij), written straight into the 6 planes of s * T: re, im, -im (hi), then (lo);
 // s = split_scale(amax) (max |t| folded in by the kernel that wrote t), written to *s_slot.  One CTA
-// per 32 x 32 tile pair (I, J), I >= J; a thread writes 2 adjacent columns of every plane.
+// per 32 x 32 tile pair (I, J), I >= J (d >= 32): each thread loads one float4 of each tile, and
+// writes 8 adjacent columns of one row of every plane with one 16-byte store (threads 0-127 the
+// tile (I, J), 128-255 the tile (J, I)).
 template <class H>
 __global__ void __launch_bounds__(256) k_hermitian_planes(const float* __restrict__ t, int d, H* __restrict__ P,
                                                            const unsigned int* amax, double* s_slot) {
@@ -336,54 +338,43 @@ __global__ void __launch_bounds__(256) k_hermitian_planes(const float* __restric
   const long long nn = (long long)d * d;
   int I, J;
   tri_decode(blockIdx.x, I, J);
-  {  // all 8 loads of a thread in flight at once (blockDim.x == 256)
-    float a[4], b[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int e = threadIdx.x + 256 * k, r = e >> 5, c = e & 31;
-      a[k] = t[(long long)(I * 32 + r) * d + J * 32 + c];
-      b[k] = I != J ? t[(long long)(J * 32 + r) * d + I * 32 + c] : 0.f;
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int e = threadIdx.x + 256 * k, r = e >> 5, c = e & 31;
-      Ra[r][c] = a[k];
-      Rb[r][c] = b[k];
-    }
+  const int tid = threadIdx.x;
+  {
+    const int row = tid >> 3, col = (tid & 7) * 4;
+    const float4 a = *reinterpret_cast<const float4*>(t + (long long)(I * 32 + row) * d + J * 32 + col);
+    const float4 b = I != J ? *reinterpret_cast<const float4*>(t + (long long)(J * 32 + row) * d + I * 32 + col)
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+    Ra[row][col] = a.x; Ra[row][col + 1] = a.y; Ra[row][col + 2] = a.z; Ra[row][col + 3] = a.w;
+    Rb[row][col] = b.x; Rb[row][col + 1] = b.y; Rb[row][col + 2] = b.z; Rb[row][col + 3] = b.w;
   }
   __syncthreads();
-  auto put = [&](long long idx, float re0, float im0, float re1, float im1) {
-    H h[6][2];
-    hi_lo(sc * re0, h[0][0], h[3][0]);
-    hi_lo(sc * im0, h[1][0], h[4][0]);
-    hi_lo(-(sc * im0), h[2][0], h[5][0]);
-    hi_lo(sc * re1, h[0][1], h[3][1]);
-    hi_lo(sc * im1, h[1][1], h[4][1]);
-    hi_lo(-(sc * im1), h[2][1], h[5][1]);
+  const bool upper = tid >= 128;
+  if (upper && I == J) return;
+  const int r = (tid & 127) >> 2, c = (tid & 3) * 8;
+  float re[8], im[8];
 #pragma unroll
-    for (int p = 0; p < 6; ++p) {
-      typename Pair16<H>::T v;
-      v.x = h[p][0];
-      v.y = h[p][1];
-      *reinterpret_cast<typename Pair16<H>::T*>(P + p * nn + idx) = v;
-    }
-  };
-#pragma unroll
-  for (int e = threadIdx.x; e < 32 * 16; e += 256) {
-    const int r = e >> 4, c = (e & 15) * 2;
-    float re[2], im[2];
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int cc = c + u;
-      if (I != J) { re[u] = Ra[r][cc]; im[u] = Rb[cc][r]; }
-      else if (r > cc) { re[u] = Ra[r][cc]; im[u] = Ra[cc][r]; }
-      else if (r < cc) { re[u] = Ra[cc][r]; im[u] = -Ra[r][cc]; }
-      else { re[u] = Ra[r][r]; im[u] = 0.f; }
-    }
-    put((long long)(I * 32 + r) * d + J * 32 + c, re[0], im[0], re[1], im[1]);
-    if (I != J)  // tile (J, I): T[J*32 + r][I*32 + c] = conj T[I*32 + c][J*32 + r]
-      put((long long)(J * 32 + r) * d + I * 32 + c, Ra[c][r], -Rb[r][c], Ra[c + 1][r], -Rb[r][c + 1]);
+  for (int u = 0; u < 8; ++u) {
+    const int cc = c + u;
+    if (upper) { re[u] = Ra[cc][r]; im[u] = -Rb[r][cc]; }  // T[J 32 + r][I 32 + cc] = conj T[I 32 + cc][J 32 + r]
+    else if (I != J) { re[u] = Ra[r][cc]; im[u] = Rb[cc][r]; }
+    else if (r > cc) { re[u] = Ra[r][cc]; im[u] = Ra[cc][r]; }
+    else if (r < cc) { re[u] = Ra[cc][r]; im[u] = -Ra[r][cc]; }
+    else { re[u] = Ra[r][r]; im[u] = 0.f; }
   }
+  union Pack {
+    uint4 v;
+    H h[8];
+  };
+  Pack pk[6];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    hi_lo(sc * re[u], pk[0].h[u], pk[3].h[u]);
+    hi_lo(sc * im[u], pk[1].h[u], pk[4].h[u]);
+    hi_lo(-(sc * im[u]), pk[2].h[u], pk[5].h[u]);
+  }
+  const long long idx = upper ? (long long)(J * 32 + r) * d + I * 32 + c : (long long)(I * 32 + r) * d + J * 32 + c;
+#pragma unroll
+  for (int p = 0; p < 6; ++p) *reinterpret_cast<uint4*>(P + p * nn + idx) = pk[p].v;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
