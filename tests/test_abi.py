@@ -109,3 +109,29 @@ def test_missing_library_fails_loudly(tmp_path):
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == "raised True"
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    """include/qst.h is a C ABI: it compiles as strict C99 and a C program links against libqst.so
+    (only host-only entry points are called)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_qst.c"
+    src.write_text('#include "qst.h"\n#include <stdio.h>\n'
+                   "int main(void) {\n"
+                   "  qst_options o;\n  qst_default_options(&o);\n"
+                   '  printf("%zu %zu %d\\n", qst_theta_size(3), qst_theta_size_net(3, QST_NET_CNN), o.precision);\n'
+                   "  return 0;\n}\n")
+    exe = tmp_path / "use_qst"
+    libdir = os.path.dirname(qst.LIB_PATH)
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", f"-I{os.path.join(ROOT, 'include')}",
+                        str(src), f"-L{libdir}", "-lqst", f"-Wl,-rpath,{libdir}", "-o", str(exe)],
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stderr
+    n3, H = 4 ** 3, 6
+    assert out.stdout.split() == [str(2 * H * n3 + n3 + H), str(12 * n3 + n3 + 12 * 640 + 12 + 100), str(qst.QST_FP32)]
