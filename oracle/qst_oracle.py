@@ -35,7 +35,12 @@ Readings where the paper is silent (each also listed in the design notes):
   * eq. PS writes b_i Tr[M_j B] for the second term; the Born rule of Sec. 2.1
     gives the coefficient (M_i)_{21} = c_i there, which is what is used;
   * terms with f_k = 0 contribute nothing to L; for A_P with P <= 1 the
-    eigenvalue magnitudes are floored at eps * max|lambda| (eps = 1e-15).
+    eigenvalue magnitudes are floored at eps * max|lambda| (eps = 1e-15);
+  * a term with f_k > 0 whose unnormalised Born value q_k = Tr[M_k X] lies
+    below q_min (the smallest normal number of the precision compared with;
+    for the PSD X of the state maps only rounding can bring q_k to 0 or
+    below) is clamped: it adds the constant -f_k log q_min to L, nothing to
+    dL/dq_k, and is counted.
 
 Parity unpinned: long multi-step Rprop trajectories (a sign-driven optimiser
 amplifies rounding); single steps, gradients and final fidelities are pinned.
@@ -353,35 +358,39 @@ def chol_h(T: np.ndarray) -> np.ndarray:
     return X / np.trace(X).real
 
 
-def abs_p(T: np.ndarray, P: float) -> np.ndarray:
-    """Sec. 3.2 eq. abs_P: T = Q Lambda Q^dag, rho = Q |Lambda|^P Q^dag / Tr |Lambda|^P."""
-    lam, Q = np.linalg.eigh(T)
-    a = np.abs(lam)
-    if P <= 1.0:
-        a = np.maximum(a, ABS_P_EPS * a.max())
-    s = a ** P
-    return (Q * (s / s.sum())) @ Q.conj().T
-
-
-def _abs_p_backward(T: np.ndarray, P: float, G_rho: np.ndarray) -> np.ndarray:
-    """Gradient of L through eq. abs_P: returns Gam with dL = Re Tr[Gam dT].
-
-    S = Q diag(g(lambda)) Q^dag with g = |lambda|^P, rho = S / s, s = Tr S.
-    dL/dS = (G_rho - <G_rho, rho> I) / s; through the spectral function the
-    Daleckii-Krein formula gives Gam = Q (D o (Q^dag (dL/dS) Q)) Q^dag with
-    D_ij = (g_i - g_j) / (lambda_i - lambda_j), or g'(lambda_i) when equal.
-    """
+def _abs_p_spectrum(T: np.ndarray, P: float):
+    """Sec. 3.2 eq. abs_P on T = Q Lambda Q^dag: returns (lam, Q, g, g') with g = |lambda|^P
+    (magnitudes floored at ABS_P_EPS * max|lambda| for P <= 1) and g' = dg/dlambda (0 below the floor)."""
     lam, Q = np.linalg.eigh(T)
     a = np.abs(lam)
     floor = ABS_P_EPS * a.max() if P <= 1.0 else 0.0
     a_used = np.maximum(a, floor)
     g = a_used ** P
     gp = np.where(a > floor, P * a_used ** (P - 1.0) * np.sign(lam), 0.0)
-    s = g.sum()
-    rho = (Q * (g / s)) @ Q.conj().T
-    inner = np.real(np.vdot(G_rho, rho))
-    dS = (G_rho - inner * np.eye(T.shape[0])) / s
-    C = Q.conj().T @ dS @ Q
+    return lam, Q, g, gp
+
+
+def abs_p_unnormalised(T: np.ndarray, P: float) -> np.ndarray:
+    """S = Q |Lambda|^P Q^dag, so that eq. abs_P reads rho = S / Tr S."""
+    lam, Q, g, _ = _abs_p_spectrum(T, P)
+    return (Q * g) @ Q.conj().T
+
+
+def abs_p(T: np.ndarray, P: float) -> np.ndarray:
+    """Sec. 3.2 eq. abs_P: T = Q Lambda Q^dag, rho = Q |Lambda|^P Q^dag / Tr |Lambda|^P."""
+    lam, Q, g, _ = _abs_p_spectrum(T, P)
+    return (Q * (g / g.sum())) @ Q.conj().T
+
+
+def _abs_p_backward(T: np.ndarray, P: float, G_S: np.ndarray) -> np.ndarray:
+    """Gradient of L through S = Q g(Lambda) Q^dag, g = |lambda|^P: returns Gam with dL = Re Tr[Gam dT].
+
+    G_S = dL/dS.  Through the spectral function the Daleckii-Krein formula gives
+    Gam = Q (D o (Q^dag G_S Q)) Q^dag with D_ij = (g_i - g_j) / (lambda_i - lambda_j),
+    or g'(lambda_i) when equal (the mean of the two derivatives).
+    """
+    lam, Q, g, gp = _abs_p_spectrum(T, P)
+    C = Q.conj().T @ G_S @ Q
     li, lj = np.meshgrid(lam, lam, indexing="ij")
     gi, gj = np.meshgrid(g, g, indexing="ij")
     dl = li - lj
@@ -401,6 +410,31 @@ def nll(p: np.ndarray, f: np.ndarray) -> float:
     return float(-np.sum(f[m] * np.log(p[m])))
 
 
+Q_MIN_FP64 = float(np.finfo(np.float64).tiny)
+Q_MIN_FP32 = float(np.finfo(np.float32).tiny)
+
+
+def likelihood_terms(q: np.ndarray, f: np.ndarray, t: float, q_min: float = Q_MIN_FP64):
+    """Sec. 3.1 / Sec. 2.1 eq. MLE on the unnormalised Born values q_k = Tr[M_k X] of X = t rho.
+
+    With p_k = q_k / t:  L = -sum_k f_k log p_k = -sum_k f_k log q_k + (sum_k f_k) log t, and
+    g_k = dL/dq_k = -f_k / q_k + (sum_k f_k) / t.  Terms with f_k = 0 are omitted from the sum (they
+    keep g_k = sum f / t).  A term with f_k > 0 and q_k < q_min is clamped: it contributes the
+    constant -f_k log q_min to L and its g_k keeps only sum f / t.
+    Returns (L, g, number of clamped terms).
+    """
+    q = np.asarray(q, dtype=np.float64)
+    f = np.asarray(f, dtype=np.float64)
+    sumf = float(np.sum(f))
+    pos = f > 0
+    clamp = pos & ~(q >= q_min)
+    live = pos & ~clamp
+    L = -np.sum(f[live] * np.log(q[live])) - np.sum(f[clamp]) * np.log(q_min) + sumf * np.log(t)
+    g = np.full(q.shape, sumf / t)
+    g[live] -= f[live] / q[live]
+    return float(L), g, int(np.count_nonzero(clamp))
+
+
 def state_from_theta(theta, f, N, mapping="chol_h", P=2.0, network="fnn", decision=np.float64):
     if network == "cnn":
         t = network_forward_cnn(theta, f, N, decision)[2]
@@ -413,17 +447,20 @@ def state_from_theta(theta, f, N, mapping="chol_h", P=2.0, network="fnn", decisi
     return rho
 
 
-def loss_and_grad(theta, f, povm, N, mapping="chol_h", P=2.0, network="fnn", decision=np.float64):
+def loss_and_grad(theta, f, povm, N, mapping="chol_h", P=2.0, network="fnn", decision=np.float64,
+                  q_min=Q_MIN_FP64):
     """One forward and backward pass of the Sec. 3 network through the likelihood.
 
-    Returns (L, dL/dtheta, aux) with aux holding rho, p and the intermediates.
-    The backward pass is the chain rule written out step by step:
-      dL/dp_k   = -f_k / p_k
-      dL/drho   = sum_k dL/dp_k M_k                      (POVM adjoint)
-      Chol_H:   rho = X / Tr X, X = T^dag T:
-                dL/dX = (dL/drho - <dL/drho, rho> I) / Tr X,  Gam = T G_X + G_X T
-      Chol_Delta: the same X and dL/dX with T lower triangular; dX = dT^dag T + T^dag dT
-                gives dL = 2 Re Tr[G_X T^dag dT], Gam = 2 G_X T^dag
+    Returns (L, dL/dtheta, aux) with aux holding rho, p and the intermediates
+    (and "clamped", the number of terms clamped at q_min; see likelihood_terms).
+    The state map gives an unnormalised S with rho = S / t, t = Tr S
+    (Chol_H / Chol_Delta: S = X = T^dag T; A_P: S = Q |Lambda|^P Q^dag); then
+      q_k       = Tr[M_k S]                               (eq. PS on S; p = q / t)
+      L, g_k    = likelihood_terms(q, f, t):  L = -sum f log q + (sum f) log t,
+                  g_k = dL/dq_k = -f_k / q_k + (sum f) / t
+      G_S       = sum_k g_k M_k                           (POVM adjoint; dL/dS)
+      Chol_H:   Gam = T G_S + G_S T            (dS = dT T + T dT for Hermitian T)
+      Chol_Delta: dS = dT^dag T + T^dag dT gives dL = 2 Re Tr[G_S T^dag dT], Gam = 2 G_S T^dag
       A_P:      Daleckii-Krein (see _abs_p_backward)
       t         <- Gam (output_grad_from_hermitian, or output_grad_from_lower)
       W2^T, b2, h <- t;  pre <- h (LeakyReLU');  W1, b1 <- pre.
@@ -434,30 +471,25 @@ def loss_and_grad(theta, f, povm, N, mapping="chol_h", P=2.0, network="fnn", dec
         W1, W2T, b2, b1 = unpack_theta(theta, N)
         pre, h, t = network_forward(theta, f, N)
     T = lower_from_output(t) if mapping == "chol_delta" else hermitian_from_output(t)
-    d = T.shape[0]
     if mapping in ("chol_h", "chol_delta"):
-        X = T.conj().T @ T
-        tX = np.trace(X).real
-        rho = X / tX
+        S = T.conj().T @ T
     else:
-        rho = abs_p(T, P)
-    p = born_probabilities(rho, povm).real
-    L = nll(p, f)
-
-    gp = np.zeros_like(p)
-    m = f > 0
-    gp[m] = -f[m] / p[m]
-    G_rho = povm_adjoint(gp, povm)
-    if mapping in ("chol_h", "chol_delta"):
-        inner = np.real(np.vdot(G_rho, rho))
-        G_X = (G_rho - inner * np.eye(d)) / tX
-        Gam = T @ G_X + G_X @ T if mapping == "chol_h" else 2.0 * G_X @ T.conj().T
+        S = abs_p_unnormalised(T, P)
+    tS = np.trace(S).real
+    rho = S / tS
+    q = born_probabilities(S, povm).real
+    L, gq, nclamp = likelihood_terms(q, f, tS, q_min)
+    G_S = povm_adjoint(gq, povm)
+    if mapping == "chol_h":
+        Gam = T @ G_S + G_S @ T
+    elif mapping == "chol_delta":
+        Gam = 2.0 * G_S @ T.conj().T
     else:
-        Gam = _abs_p_backward(T, P, G_rho)
+        Gam = _abs_p_backward(T, P, G_S)
     dt = output_grad_from_lower(Gam) if mapping == "chol_delta" else output_grad_from_hermitian(Gam)
+    aux = dict(rho=rho, p=q / tS, T=T, t=t, h=h, pre=pre, Gam=Gam, dt=dt, clamped=nclamp)
     if network == "cnn":
         grad = network_backward_cnn(theta, f, N, dt, pre, h, feats, pos, vals)
-        aux = dict(rho=rho, p=p, T=T, t=t, h=h, pre=pre, Gam=Gam, dt=dt)
         return L, grad, aux
 
     db2 = dt
@@ -467,7 +499,6 @@ def loss_and_grad(theta, f, povm, N, mapping="chol_h", P=2.0, network="fnn", dec
     db1 = dpre
     dW1 = np.outer(dpre, f)
     grad = pack_theta(dW1, dW2T, db2, db1)
-    aux = dict(rho=rho, p=p, T=T, t=t, h=h, pre=pre, Gam=Gam, dt=dt)
     return L, grad, aux
 
 

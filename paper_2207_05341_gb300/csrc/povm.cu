@@ -332,9 +332,13 @@ __global__ void __launch_bounds__(256) k_povm_hi_nll(const R* __restrict__ W, co
     const R fk = f[(long long)ah * SS + al0 + c];
     R gk = gconst;
     if (fk > R(0)) {
-      if (!(q >= qmin)) { q = qmin; ++nclamp; }
-      acc += (double)fk * (double)log(q);
-      gk -= fk / q;
+      if (!(q >= qmin)) {  // clamped: the constant -f_k log q_min, nothing added to dL/dq_k
+        ++nclamp;
+        acc += (double)fk * (double)log(qmin);
+      } else {
+        acc += (double)fk * (double)log(q);
+        gk -= fk / q;
+      }
     }
     Z[zi] = cmake<V>(gk, R(0));
   }

@@ -192,9 +192,13 @@ __global__ void __launch_bounds__(256) k_povm_hi_pauli(const R* __restrict__ W, 
     const R fk = fs[interleave_ij(x, z) * CB + c];
     R gk = gconst;
     if (fk > R(0)) {
-      if (!(q >= qmin)) { q = qmin; ++nclamp; }
-      accr += fk * log(q);
-      gk -= fk / q;
+      if (!(q >= qmin)) {  // clamped: the constant -f_k log q_min, nothing added to dL/dq_k
+        ++nclamp;
+        accr += fk * log(qmin);
+      } else {
+        accr += fk * log(q);
+        gk -= fk / q;
+      }
     }
     w[z] = gk;
   }

@@ -356,3 +356,84 @@ def test_gradient_central_fd_cnn_sampled():
         fd = (O.loss_and_grad(tp, f, M, N, network="cnn")[0] - O.loss_and_grad(tm, f, M, N, network="cnn")[0]) / (2 * h)
         assert abs(fd - g[i]) <= 2e-6 * max(1.0, np.abs(g).max()), (i, fd, g[i])
     assert np.abs(g[-n_conv:]).max() > 0  # the convolution does receive gradient
+
+
+def test_network_forward_hand_values():
+    """Sec. 3.1 at N = 1 (4 inputs, 2 hidden units, 4 outputs), values worked out by hand.
+
+    One hidden pre-activation is negative, so the LeakyReLU slope (0.01, Sec. 4.1 reading) is
+    hit: with ReLU, slope 0.1 or an untransposed output layer the outputs differ.
+      pre = W1 f + b1 = (3 + 0.5, -0.1 - 0.4) = (3.5, -0.5),  h = (3.5, -0.005)
+      t_i = sum_j W2^T[j][i] h_j + b2_i = (3.5 - 0.5 + 0.25, -1 + 0.5, -3.5 + 1, 7 + 0.5 - 2)
+    """
+    f = np.array([0.1, 0.2, 0.3, 0.4])
+    W1 = np.array([[1.0, 2.0, 3.0, 4.0], [-1.0, 0.0, 0.0, 0.0]])
+    b1 = np.array([0.5, -0.4])
+    W2T = np.array([[1.0, 0.0, -1.0, 2.0], [100.0, 200.0, 0.0, -100.0]])
+    b2 = np.array([0.25, 0.5, 1.0, -2.0])
+    theta = np.concatenate([W1.ravel(), W2T.ravel(), b2, b1])
+    pre, h, t = O.network_forward(theta, f, 1)
+    np.testing.assert_allclose(pre, [3.5, -0.5], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(h, [3.5, -0.005], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(t, [3.25, -0.5, -2.5, 5.5], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(O.leaky_relu(np.array([-2.0, 0.0, 3.0])), [-0.02, 0.0, 3.0], rtol=0, atol=1e-15)
+
+
+def test_theta_layout_markers():
+    """theta = [W1 (H x n) | W2^T (H x n) | b2 (n) | b1 (H)], both matrices row-major."""
+    N, n, H = 1, 4, 2
+    theta = np.concatenate([1000 + np.arange(H * n), 2000 + np.arange(H * n), 3000 + np.arange(n),
+                            4000 + np.arange(H)]).astype(float)
+    W1, W2T, b2, b1 = O.unpack_theta(theta, N)
+    assert W1.shape == (H, n) and W2T.shape == (H, n)
+    assert W1[1, 2] == 1000 + 1 * n + 2 and W2T[0, 3] == 2003 and W2T[1, 0] == 2000 + n
+    assert b2[2] == 3002 and b1[1] == 4001
+    np.testing.assert_array_equal(O.pack_theta(W1, W2T, b2, b1), theta)
+    assert theta.size == synth.theta_size(N) == 2 * H * n + n + H
+
+
+def _zero_one_plus_minus_povm():
+    """{|0><0|, |1><1|, |+><+|, |-><-|} / 2: a valid POVM (sums to I) whose |1><1| outcome has
+    probability exactly 0 on |0><0|."""
+    kets = [np.array([1, 0]), np.array([0, 1]), np.array([1, 1]) / np.sqrt(2), np.array([1, -1]) / np.sqrt(2)]
+    return np.stack([np.outer(k, k.conj()).astype(complex) / 2 for k in kets])
+
+
+def test_likelihood_clamp_terms_by_hand():
+    """Clamp reading of the likelihood (q_k < q_min with f_k > 0 becomes the constant -f_k log q_min):
+    q = (2, 0, 1, 1), t = 4, f = 1/4 each:
+      L = -(1/4)(log 2 + log q_min + 0 + 0) + log 4 = (7 log 2 - log q_min) / 4
+      g = -f/q + 1/t on the live terms, 1/t on the clamped one: (1/8, 1/4, 0, 0)."""
+    for qmin in (O.Q_MIN_FP64, O.Q_MIN_FP32):
+        L, g, nc = O.likelihood_terms(np.array([2.0, 0.0, 1.0, 1.0]), np.full(4, 0.25), 4.0, qmin)
+        assert nc == 1
+        assert abs(L - (7 * np.log(2) - np.log(qmin)) / 4) < 1e-13 * abs(L)
+        np.testing.assert_allclose(g, [0.125, 0.25, 0.0, 0.0], rtol=0, atol=1e-15)
+    # negative values are clamped too; f_k = 0 terms are never counted
+    L, g, nc = O.likelihood_terms(np.array([-1e-30, 0.0, 1.0]), np.array([0.5, 0.0, 0.5]), 1.0, 1e-20)
+    assert nc == 1 and abs(L - (-0.5 * np.log(1e-20))) < 1e-12
+    np.testing.assert_allclose(g, [1.0, 1.0, 0.5], rtol=0, atol=1e-15)
+    # without clamps it is the paper's L = -sum f log p with p = q / t
+    rng = np.random.default_rng(5)
+    q = rng.uniform(0.1, 1, 16); f = rng.dirichlet(np.ones(16)); t = q.sum() * 1.7
+    assert abs(O.likelihood_terms(q, f, t)[0] - O.nll(q / t, f)) < 1e-13
+
+
+def test_loss_and_grad_clamp_case_by_hand():
+    """N = 1 with the |0>, |1>, |+>, |-> POVM and theta giving t = (2, 0, 0, 0): T = diag(2, 0),
+    X = diag(4, 0), t_X = 4, q = (2, 0, 1, 1); the |1><1| outcome is clamped.
+      L = (7 log 2 - log q_min) / 4
+      G_X = (1/8) |0><0|/2 + (1/4) |1><1|/2 = diag(1/16, 1/8);  Gam = T G_X + G_X T = diag(1/4, 0)
+      dL/dt = (1/4, 0, 0, 0) = dL/db2; h = LeakyReLU(0) = 0, so every other gradient is 0."""
+    M = _zero_one_plus_minus_povm()
+    n, H = 4, 2
+    theta = np.zeros(2 * H * n + n + H)
+    theta[2 * H * n] = 2.0  # b2[0]
+    f = np.full(4, 0.25)
+    for qmin in (O.Q_MIN_FP64, O.Q_MIN_FP32):
+        L, g, aux = O.loss_and_grad(theta, f, M, 1, q_min=qmin)
+        assert aux["clamped"] == 1
+        assert abs(L - (7 * np.log(2) - np.log(qmin)) / 4) < 1e-13 * abs(L)
+        want = np.zeros_like(theta)
+        want[2 * H * n] = 0.25
+        np.testing.assert_allclose(g, want, rtol=0, atol=1e-15)
