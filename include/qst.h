@@ -39,8 +39,11 @@
  *   Every call returns a qst_status; nothing is thrown across the ABI.  A
  *   negative status means the call did nothing observable (or, for QST_E_CUDA,
  *   that a CUDA call failed and the context should be destroyed).
- *   QST_W_CLAMP (positive) is a warning: some q_k <= 0 with f_k > 0 was
- *   clamped to the smallest normal number of the precision before its log.
+ *   QST_W_CLAMP (positive) is a warning: some q_k below q_min (the smallest
+ *   normal number of the precision; for the positive semidefinite X of the
+ *   state maps only rounding brings q_k to 0 or below) had f_k > 0.  Such a
+ *   term is clamped: it adds the constant -f_k log q_min to the loss and
+ *   nothing to its gradient; the results are otherwise complete.
  */
 #ifndef QST_H
 #define QST_H
@@ -152,7 +155,8 @@ qst_status qst_probs(qst_ctx* ctx, const void* rho, void* p);
  *           which every GPU that loads the library holds until the process exits.
  *   povm    as for qst_init (host, K = 4, Hermitian, summing to I).
  *   rho, p  device, FP32: d x d complex rho (lower triangle read, as qst_probs)
- *           and n reals written.
+ *           and n reals written.  Host memory is refused (QST_E_INVAL) before
+ *           anything is launched.
  *   stream  cudaStream_t (as void*), may be NULL.
  * The first call on a device looks up the array's device address (set-up, once
  * per device, with that device current); make that first call before any

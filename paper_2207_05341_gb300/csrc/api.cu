@@ -15,11 +15,8 @@
 
 using namespace qst;
 
-namespace {
+namespace qst {
 
-constexpr unsigned long long kStateMagic = 0x5153545354415432ULL;  // "QSTSTAT2": theta, Rprop state words
-
-// 0: pageable or unknown host memory, 1: page-locked host memory, 2: device or managed memory.
 int ptr_kind(const void* p) {
   if (p == nullptr) return 0;
   cudaPointerAttributes a;
@@ -31,6 +28,36 @@ int ptr_kind(const void* p) {
   return a.type == cudaMemoryTypeHost ? 1 : 0;
 }
 bool is_device_ptr(const void* p) { return ptr_kind(p) == 2; }
+
+int check_povm(const double* povm, int K, PovmB<double>* Bd) {
+  if (povm == nullptr || K != 4) return QST_E_INVAL;
+  double sum[8] = {0};
+  for (int a = 0; a < 4; ++a) {
+    const double* m = povm + 8 * a;  // m00 (re, im), m01, m10, m11
+    for (int q = 0; q < 8; ++q) {
+      if (!isfinite(m[q])) return QST_E_INVAL;
+      sum[q] += m[q];
+    }
+    // Hermitian: real diagonal, m01 = conj(m10)
+    if (fabs(m[1]) > 1e-12 || fabs(m[7]) > 1e-12) return QST_E_INVAL;
+    if (fabs(m[2] - m[4]) > 1e-12 || fabs(m[3] + m[5]) > 1e-12) return QST_E_INVAL;
+    // Pauli coefficients: M = b0 I + b1 X + b2 Y + b3 Z, m10 = b1 + i b2
+    Bd->b[a][0] = 0.5 * (m[0] + m[6]);
+    Bd->b[a][1] = m[4];
+    Bd->b[a][2] = m[5];
+    Bd->b[a][3] = 0.5 * (m[0] - m[6]);
+  }
+  const double eye[8] = {1, 0, 0, 0, 0, 0, 1, 0};
+  for (int q = 0; q < 8; ++q)
+    if (fabs(sum[q] - eye[q]) > 1e-12) return QST_E_INVAL;
+  return QST_OK;
+}
+
+}  // namespace qst
+
+namespace {
+
+constexpr unsigned long long kStateMagic = 0x5153545354415432ULL;  // "QSTSTAT2": theta, Rprop state words
 
 }  // namespace
 
@@ -704,30 +731,6 @@ template <class R> struct Engine {
 
 #define QST_DISPATCH(c, call) ((c)->prec == QST_FP64 ? Engine<double>::call : Engine<float>::call)
 
-qst_status check_povm(const double* povm, int K, PovmB<double>* Bd) {
-  if (povm == nullptr || K != 4) return QST_E_INVAL;
-  double sum[8] = {0};
-  for (int a = 0; a < 4; ++a) {
-    const double* m = povm + 8 * a;  // m00 (re, im), m01, m10, m11
-    for (int q = 0; q < 8; ++q) {
-      if (!isfinite(m[q])) return QST_E_INVAL;
-      sum[q] += m[q];
-    }
-    // Hermitian: real diagonal, m01 = conj(m10)
-    if (fabs(m[1]) > 1e-12 || fabs(m[7]) > 1e-12) return QST_E_INVAL;
-    if (fabs(m[2] - m[4]) > 1e-12 || fabs(m[3] + m[5]) > 1e-12) return QST_E_INVAL;
-    // Pauli coefficients: M = b0 I + b1 X + b2 Y + b3 Z, m10 = b1 + i b2
-    Bd->b[a][0] = 0.5 * (m[0] + m[6]);
-    Bd->b[a][1] = m[4];
-    Bd->b[a][2] = m[5];
-    Bd->b[a][3] = 0.5 * (m[0] - m[6]);
-  }
-  const double eye[8] = {1, 0, 0, 0, 0, 0, 1, 0};
-  for (int q = 0; q < 8; ++q)
-    if (fabs(sum[q] - eye[q]) > 1e-12) return QST_E_INVAL;
-  return QST_OK;
-}
-
 template <class R> qst_status reset_rprop(qst_ctx* c) {
   Work<R>* w = W<R>(c);
   const size_t P = c->P;
@@ -871,7 +874,7 @@ qst_status qst_init(qst_ctx** out, int N, const double* povm, int K, const qst_o
       !(o.step_min >= lo) || !(o.step_max >= o.step_min && o.step_max <= hi) || !(o.leaky_slope >= 0))
     return QST_E_INVAL;
   PovmB<double> Bd;
-  qst_status st = check_povm(povm, K, &Bd);
+  qst_status st = (qst_status)check_povm(povm, K, &Bd);
   if (st != QST_OK) return st;
   if (o.precision == QST_MIXED || o.precision == QST_MIXED_BF16) {
     if (N < 7) return QST_E_UNSUPPORTED;

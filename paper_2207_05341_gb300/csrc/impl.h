@@ -54,6 +54,15 @@ template <class R> struct Work {
   void* Gb;            // 4 planes of d x d bf16: re_hi, im_hi, re_lo, im_lo
 };
 
+// Host helpers of the C ABI entry points (api.cu).
+// 0: pageable or unknown host memory, 1: page-locked host memory, 2: device or managed memory.
+int ptr_kind(const void* p);
+bool is_device_ptr(const void* p);
+// Validate a K = 4 POVM of Hermitian 2 x 2 matrices (interleaved complex doubles, element a at
+// povm[8a .. 8a+7]) summing to I within 1e-12, and write its Pauli coefficients; returns a
+// qst_status (QST_OK or QST_E_INVAL).
+int check_povm(const double* povm, int K, PovmB<double>* Bd);
+
 enum Counter {
   CNT_L1 = 0, CNT_T = 1, CNT_NLL = 2, CNT_W2 = 3, CNT_W1 = 4,
   CNT_AMAXT = 8,  // max |re|, |im| of T as float bits: folded in by the producer of t, read by the plane

@@ -8,8 +8,6 @@
 // For them this entry point runs the same two kernels as qst_probs, with the
 // packed intermediate in a fixed, file-scope device array instead of context
 // memory.  It allocates nothing and calls no allocating library routine.
-#include <math.h>
-
 #include <mutex>
 
 #include "../../include/qst.h"
@@ -47,37 +45,19 @@ cudaError_t scratch_address(float** out) {
   return cudaSuccess;
 }
 
-// Pauli coefficients of the four Hermitian 2 x 2 POVM elements (same checks as qst_init).
-qst_status povm_coefficients(const double* povm, int K, qst::PovmB<float>* B) {
-  if (povm == nullptr || K != 4) return QST_E_INVAL;
-  double sum[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int a = 0; a < 4; ++a) {
-    const double* m = povm + 8 * a;
-    for (int q = 0; q < 8; ++q) {
-      if (!(m[q] == m[q]) || m[q] > 1e300 || m[q] < -1e300) return QST_E_INVAL;
-      sum[q] += m[q];
-    }
-    if (fabs(m[1]) > 1e-12 || fabs(m[7]) > 1e-12) return QST_E_INVAL;
-    if (fabs(m[2] - m[4]) > 1e-12 || fabs(m[3] + m[5]) > 1e-12) return QST_E_INVAL;
-    B->b[a][0] = (float)(0.5 * (m[0] + m[6]));
-    B->b[a][1] = (float)m[4];
-    B->b[a][2] = (float)m[5];
-    B->b[a][3] = (float)(0.5 * (m[0] - m[6]));
-  }
-  const double eye[8] = {1, 0, 0, 0, 0, 0, 1, 0};
-  for (int q = 0; q < 8; ++q)
-    if (fabs(sum[q] - eye[q]) > 1e-12) return QST_E_INVAL;
-  return QST_OK;
-}
-
 }  // namespace
 
 extern "C" qst_status qst_probs_static(int N, const double* povm, int K, const void* rho, void* p, void* stream) {
   if (N < 1 || N > kStaticMaxQubits) return QST_E_INVAL;
   if (rho == nullptr || p == nullptr) return QST_E_INVAL;
-  qst::PovmB<float> B;
-  qst_status st = povm_coefficients(povm, K, &B);
+  // the kernels read rho and write p directly: host memory is refused before anything is launched
+  if (!qst::is_device_ptr(rho) || !qst::is_device_ptr(p)) return QST_E_INVAL;
+  qst::PovmB<double> Bd;
+  const qst_status st = (qst_status)qst::check_povm(povm, K, &Bd);
   if (st != QST_OK) return st;
+  qst::PovmB<float> B;  // the FP32 coefficients, rounded as qst_init rounds them
+  for (int a = 0; a < 4; ++a)
+    for (int m = 0; m < 4; ++m) B.b[a][m] = (float)Bd.b[a][m];
   float* scratch = nullptr;
   if (scratch_address(&scratch) != cudaSuccess) return QST_E_CUDA;
   const qst::Dims D = qst::make_dims(N, false);

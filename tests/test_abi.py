@@ -135,3 +135,14 @@ def test_header_is_plain_c_and_links(lib, tmp_path):
     assert out.returncode == 0, out.stderr
     n3, H = 4 ** 3, 6
     assert out.stdout.split() == [str(2 * H * n3 + n3 + H), str(12 * n3 + n3 + 12 * 640 + 12 + 100), str(qst.QST_FP32)]
+
+
+def test_static_probs_refuses_host_buffers_before_any_launch(lib):
+    """qst_probs_static checks that rho and p are device memory before it launches anything: host
+    buffers (or a machine without a GPU) give QST_E_INVAL, never a kernel fault."""
+    import numpy as np
+    rho = np.zeros((8, 8), dtype=np.complex64)
+    p = np.zeros(64, dtype=np.float32)
+    with pytest.raises(qst.QstError) as e:
+        qst.qst_probs_static(3, rho, p)
+    assert e.value.status == qst.QST_E_INVAL

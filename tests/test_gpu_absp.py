@@ -3,7 +3,9 @@
 The eigendecomposition is a Jacobi method run for a fixed number of sweeps; after
 10 sweeps it has converged to rounding level for these sizes, so the FP64 path
 is held to 1e-8 and the FP32 path to 1e-4 on the loss and 2e-3 (normwise) on
-the gradient, whose Daleckii-Krein factors divide by eigenvalue gaps.
+the gradient, whose Daleckii-Krein factors divide by eigenvalue gaps.  N = 8 and
+N = 10 (d = 256, 1024) exercise the pair-blocked rounds at the sizes where their
+blocks change shape.
 """
 import numpy as np
 import pytest
@@ -55,7 +57,8 @@ def _gpu(N, theta, f, opt):
 
 
 CASES = [(qst.QST_FP64, N, P) for N in (1, 2, 4, 6) for P in (0.5, 1.5, 2.0, 4.0)] + \
-        [(qst.QST_FP32, N, P) for N in (3, 6) for P in (1.0, 2.0, 3.0)]
+        [(qst.QST_FP32, N, P) for N in (3, 6) for P in (1.0, 2.0, 3.0)] + \
+        [(prec, N, 1.5) for prec in (qst.QST_FP64, qst.QST_FP32) for N in (8, 10)]
 
 
 @pytest.mark.parametrize("prec,N,P", CASES)
