@@ -72,6 +72,9 @@ struct qst_ctx {
   void* work = nullptr;  // Work<float> or Work<double>
   PovmB<float> Bf;
   PovmB<double> Bd;
+  PovmPlan plan;  // FP32 fast POVM kernels (povm_fast.cu): structure of the POVM
+  const void* fperm_of = nullptr;  // the f whose permuted copy is in Work::fperm (values fixed while the pointer is)
+  bool fperm_stale = false;        // set by calls whose f may hold new values under the same pointer
   NetCfg net;
   bool params_set = false;
   bool hidden_valid = false;
@@ -201,6 +204,8 @@ template <class R> qst_status alloc_work(qst_ctx* c) {
   QST_CU(dalloc(c, &w->Whi, (size_t)D.n));
   QST_CU(dalloc(c, &w->dt, (size_t)D.n));
   QST_CU(dalloc(c, &w->fstage, (size_t)D.n));
+  if (std::is_same<R, float>::value && povm_fast_ok(D) && povm_needs_fperm(c->plan))
+    QST_CU(dalloc(c, &w->fperm, (size_t)D.n));
   QST_CU(dalloc(c, &w->scal, 16));
   // per-block partial sums: the largest reducing grid is the tile-pair grid of build_T
   const int TS = D.d < 32 ? D.d : 32;
@@ -327,11 +332,40 @@ template <class R> struct Engine {
     return QST_OK;
   }
 
+  // FP32 contexts with N in [7, 11] run the register-blocked POVM kernels of povm_fast.cu
+  static bool fast_povm(const qst_ctx* c) { return std::is_same<R, float>::value && povm_fast_ok(c->D); }
+
   // loss -> scal[2]; with backward, G = sum_k g_k M_k -> w->G
   static qst_status povm_likelihood(qst_ctx* c, const R* f, bool backward) {
     QST_CU(join_f(c));  // the first read of f in a step (the CNN's comes earlier, in its hidden layer)
     Work<R>* w = W<R>(c);
     const Dims& D = c->D;
+    if constexpr (std::is_same<R, float>::value) {
+      if (fast_povm(c)) {
+        const float* fl = f;
+        if (povm_needs_fperm(c->plan)) {  // f in the likelihood pass's order, made again only for a new f
+          if (f != c->fperm_of || f == w->fstage || c->fperm_stale) {
+            QST_CU(povm_permute_f(D, f, w->fperm, c->plan, c->stream));
+            c->launches += 1;
+            c->fperm_of = f;
+            c->fperm_stale = false;
+          }
+          fl = w->fperm;
+        }
+        QST_CU(povm_lo_fwd_fast(D, w->X, w->Wlo, c->plan, c->stream));
+        tmark(c, QST_PH_POVM_LO);
+        QST_CU(povm_hi_nll_fast(D, w->Wlo, fl, w->scal, w->Whi, w->partials, w->counters + CNT_NLL, w->flags,
+                                c->plan, backward, c->stream));
+        tmark(c, QST_PH_POVM_HI);
+        c->launches += 2;
+        if (backward) {
+          QST_CU(povm_lo_adj_fast(D, w->Whi, w->G, c->plan, amax_slot(c, CNT_AMAXG), c->stream));
+          c->launches += 1;
+          tmark(c, QST_PH_POVM_ADJ);
+        }
+        return QST_OK;
+      }
+    }
     const PovmB<R>& B = povmB<R>(c);
     QST_CU(povm_lo_fwd<R>(D, w->X, w->Wlo, B, c->stream));
     tmark(c, QST_PH_POVM_LO);
@@ -568,6 +602,7 @@ template <class R> struct Engine {
     if (st != QST_OK) return st;
     if ((st = validate_f<R>(c, f)) != QST_OK) return st;
     c->hidden_valid = false;  // the hidden buffers now hold the external parameters' activation
+    c->fperm_stale = true;    // f is taken as new on every call
     if ((st = hidden(c, theta, f)) != QST_OK) return st;
     if ((st = forward_state(c, theta, false)) != QST_OK) return st;
     if ((st = povm_likelihood(c, f, true)) != QST_OK) return st;
@@ -590,6 +625,13 @@ template <class R> struct Engine {
 
   static qst_status probs(qst_ctx* c, const void* rho, void* p) {
     Work<R>* w = W<R>(c);
+    if constexpr (std::is_same<R, float>::value) {
+      if (fast_povm(c)) {
+        QST_CU(povm_fwd_fast(c->D, (const float2*)rho, w->Wlo, (float*)p, c->plan, c->stream));
+        c->launches += 2;
+        return QST_OK;
+      }
+    }
     const PovmB<R>& B = povmB<R>(c);
     QST_CU(povm_lo_fwd<R>(c->D, (const V*)rho, w->Wlo, B, c->stream));
     QST_CU(povm_hi_fwd<R>(c->D, w->Wlo, (R*)p, B, c->stream));
@@ -613,9 +655,18 @@ template <class R> struct Engine {
       c->f_last = f_user;
     }
     if ((st = forward_state(c, w->theta)) != QST_OK) return st;
-    const PovmB<R>& B = povmB<R>(c);
-    QST_CU(povm_lo_fwd<R>(D, w->X, w->Wlo, B, c->stream));
-    QST_CU(povm_hi_fwd<R>(D, w->Wlo, w->Whi, B, c->stream));  // q, unnormalised, in Whi
+    bool done = false;
+    if constexpr (std::is_same<R, float>::value) {
+      if (fast_povm(c)) {
+        QST_CU(povm_fwd_fast(D, w->X, w->Wlo, w->Whi, c->plan, c->stream));  // q, unnormalised, in Whi
+        done = true;
+      }
+    }
+    if (!done) {
+      const PovmB<R>& B = povmB<R>(c);
+      QST_CU(povm_lo_fwd<R>(D, w->X, w->Wlo, B, c->stream));
+      QST_CU(povm_hi_fwd<R>(D, w->Wlo, w->Whi, B, c->stream));  // q, unnormalised, in Whi
+    }
     const R* P = (const R*)stage_input(c, P_user, (size_t)D.n * sizeof(R), w->fstage, &st);  // f is consumed
     if (st != QST_OK) return st;
     double* out = w->scal + 5;
@@ -896,6 +947,7 @@ qst_status qst_init(qst_ctx** out, int N, const double* povm, int K, const qst_o
   c->Bd = Bd;
   for (int a = 0; a < 4; ++a)
     for (int m = 0; m < 4; ++m) c->Bf.b[a][m] = (float)Bd.b[a][m];
+  c->plan = make_povm_plan(Bd);
   c->net.slope = o.leaky_slope;
   c->net.eta_minus = o.eta_minus;
   c->net.eta_plus = o.eta_plus;

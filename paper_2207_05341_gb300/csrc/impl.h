@@ -44,6 +44,7 @@ template <class R> struct Work {
   int* pos;
   double* cnn_part;    // CNN: per-tile pooling scratch (cnn_part_doubles)
   R* fstage;           // staging copy of a host f, n reals
+  R* fperm;            // f in the order of the structured likelihood pass (FP32 fast path), n reals
   double* scal;        // [0] Tr X, [1] sum f, [2] loss, [3] scale of T, [4] scale of G, [5] F_c,
                        // [8..10] state fidelity (sum g, bracket bound, F_q)
   double* partials;    // per-block partial sums
@@ -103,6 +104,37 @@ template <class R> cudaError_t trace_X(const Dims& D, const cx_t<R>* X, double* 
 // full Hermitian matrix from its lower tiles, scaled by 1 / scal[0] (rho = X / Tr X)
 template <class R> cudaError_t hermitian_complete(const Dims& D, const cx_t<R>* Xlow, cx_t<R>* rho,
                                                   const double* scal, cudaStream_t s);
+
+// ---- POVM map for FP32 contexts with g = 6 low qubits and N >= 7 (povm_fast.cu) ----
+// A POVM is "structured" when its Pauli coefficients factor as
+//   b[a][mu] = beta_mu (-1)^(alpha(a) x_mu + zeta(a) z_mu)   (mu = I, X, Y, Z with (x, z) = (0,0), (1,0),
+//                                                              (1,1), (0,1); (alpha, zeta) a bijection)
+// i.e. every single-qubit map is a scaling of the Pauli components followed by a Walsh-Hadamard
+// transform over (x, z): the tetrahedral POVM of Sec. 4.1 is of this form.
+struct PovmPlan {
+  PovmB<float> B;      // the generic coefficients b[a][mu]
+  int structured;      // 1: beta and out below describe the POVM
+  float beta[4];       // beta_mu
+  int out[4];          // the outcome a of the canonical slot s = 2 alpha + zeta (identity when generic)
+};
+PovmPlan make_povm_plan(const PovmB<double>& Bd);
+// fast kernels apply: FP32, N in [7, 11] (g = 6, h = N - 6 high qubits)
+bool povm_fast_ok(const Dims& D);
+// Pass 1 (low qubits) forward: X lower tiles -> packed W (slot layout: XOR diagonals when structured,
+// row-major tile pairs otherwise).  Pass 2 (high qubits): the structured path's own kernels, else the
+// Pauli-basis kernels of povm_pauli.cu on the row-major layout.
+cudaError_t povm_fwd_fast(const Dims& D, const float2* X, float* W, float* p, const PovmPlan& P, cudaStream_t s);
+cudaError_t povm_lo_fwd_fast(const Dims& D, const float2* X, float* W, const PovmPlan& P, cudaStream_t s);
+// The structured likelihood pass reads f permuted into its own consumption order (povm_permute_f,
+// n reals): f is constant while its pointer is, so the copy is made once per new f.
+bool povm_needs_fperm(const PovmPlan& P);
+cudaError_t povm_permute_f(const Dims& D, const float* f, float* fperm, const PovmPlan& P, cudaStream_t s);
+// f: the permuted copy when povm_needs_fperm(P), else f itself
+cudaError_t povm_hi_nll_fast(const Dims& D, const float* W, const float* f, double* scal, float* Wadj,
+                             double* partials, unsigned int* counter, unsigned int* flags, const PovmPlan& P,
+                             bool adjoint, cudaStream_t s);
+cudaError_t povm_lo_adj_fast(const Dims& D, const float* Wadj, float2* G, const PovmPlan& P, unsigned int* amax,
+                             cudaStream_t s);
 
 // ---- network (fnn.cu) ----
 template <class R> cudaError_t net_l1_forward(const Dims& D, const R* theta, const R* f, R* pre, R* hid,

@@ -55,16 +55,18 @@ extern "C" qst_status qst_probs_static(int N, const double* povm, int K, const v
   qst::PovmB<double> Bd;
   const qst_status st = (qst_status)qst::check_povm(povm, K, &Bd);
   if (st != QST_OK) return st;
-  qst::PovmB<float> B;  // the FP32 coefficients, rounded as qst_init rounds them
-  for (int a = 0; a < 4; ++a)
-    for (int m = 0; m < 4; ++m) B.b[a][m] = (float)Bd.b[a][m];
+  const qst::PovmPlan plan = qst::make_povm_plan(Bd);  // FP32 coefficients rounded as qst_init rounds them
   float* scratch = nullptr;
   if (scratch_address(&scratch) != cudaSuccess) return QST_E_CUDA;
   const qst::Dims D = qst::make_dims(N, false);
   if (D.n > kStaticScratchFloats) return QST_E_INVAL;
   cudaStream_t s = (cudaStream_t)stream;
   // Pass 1 writes every packed entry that pass 2 reads, so the array needs no clearing.
-  if (qst::povm_lo_fwd<float>(D, (const float2*)rho, scratch, B, s) != cudaSuccess) return QST_E_CUDA;
-  if (qst::povm_hi_fwd<float>(D, scratch, (float*)p, B, s) != cudaSuccess) return QST_E_CUDA;
+  if (qst::povm_fast_ok(D)) {
+    if (qst::povm_fwd_fast(D, (const float2*)rho, scratch, (float*)p, plan, s) != cudaSuccess) return QST_E_CUDA;
+    return QST_OK;
+  }
+  if (qst::povm_lo_fwd<float>(D, (const float2*)rho, scratch, plan.B, s) != cudaSuccess) return QST_E_CUDA;
+  if (qst::povm_hi_fwd<float>(D, scratch, (float*)p, plan.B, s) != cudaSuccess) return QST_E_CUDA;
   return QST_OK;
 }
