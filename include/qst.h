@@ -100,6 +100,10 @@ typedef struct qst_options {
     int eig_warm_sweeps;/* QST_MAP_ABS_P: sweeps when qst_step starts from the previous iteration's
                            eigenvectors (0 = default 2; -1 = always cold; rounded up to even) */
     int network;        /* QST_NET_FNN (Sec. 3.1, default) or QST_NET_CNN (App. A, N >= 3) */
+    size_t device_memory_limit; /* bytes of device memory the context may hold (parameters, Rprop state,
+                           scratch, and the scratch some calls allocate on first use); 0 = no limit.  An
+                           allocation that would exceed it fails with QST_E_NOMEM before cudaMalloc is
+                           called, and qst_init then frees what it had allocated. */
 } qst_options;
 
 /* Mapping networks.  QST_NET_FNN: the 3-layer network of Sec. 3.1, theta as described above.
@@ -303,7 +307,10 @@ qst_status qst_sync(qst_ctx* ctx);
  * cudaGraphLaunch on `stream` whose graph forks to one kernel chain per
  * tomography and joins them.  QST_MIXED / QST_MIXED_BF16 apply to the
  * tomographies with N >= 7; smaller ones run FP32.  The tomographies share
- * nothing, so this is the method applied B times (Sec. 4 runs many states). */
+ * nothing, so this is the method applied B times (Sec. 4 runs many states).
+ * qst_batch_step validates every new input (as qst_step does) before any
+ * tomography steps: a call that returns QST_E_INPUT or QST_E_INVAL has
+ * advanced none of them. */
 typedef struct qst_batch qst_batch;
 qst_status qst_batch_init(qst_batch** out, int B, const int* Ns, const double* povm, int K,
                           const qst_options* opt, void* stream);

@@ -69,6 +69,7 @@ struct qst_ctx {
   cudaStream_t stream = nullptr;
   int device = 0;
   std::vector<void*> allocs;
+  size_t dev_bytes = 0;  // device memory held in allocs
   void* work = nullptr;  // Work<float> or Work<double>
   PovmB<float> Bf;
   PovmB<double> Bd;
@@ -156,8 +157,13 @@ void tmark(qst_ctx* c, int phase) {
 
 template <class T> cudaError_t dalloc(qst_ctx* c, T** p, size_t count) {
   void* q = nullptr;
-  cudaError_t e = cudaMalloc(&q, count * sizeof(T) < 256 ? 256 : count * sizeof(T));
+  const size_t bytes = count * sizeof(T) < 256 ? 256 : count * sizeof(T);
+  // the context's device-memory budget (qst_options.device_memory_limit): refused before cudaMalloc
+  if (c->opt.device_memory_limit && c->dev_bytes + bytes > c->opt.device_memory_limit)
+    return cudaErrorMemoryAllocation;
+  cudaError_t e = cudaMalloc(&q, bytes);
   if (e != cudaSuccess) return e;
+  c->dev_bytes += bytes;
   c->allocs.push_back(q);
   *p = reinterpret_cast<T*>(q);
   return cudaSuccess;
@@ -887,6 +893,7 @@ void qst_default_options(qst_options* o) {
   o->eig_sweeps = 0;
   o->eig_warm_sweeps = 0;
   o->network = QST_NET_FNN;
+  o->device_memory_limit = 0;
 }
 
 size_t qst_theta_size(int N) {
@@ -1323,7 +1330,14 @@ qst_status qst_batch_step(qst_batch* bt, const void* const* f, double* losses) {
     if (!c->hidden_valid || c->f_last != f[b]) steady = false;
   }
   if (!steady) {
-    // first iteration for these inputs: validate them and build each hidden layer (not captured)
+    // first iteration for these inputs: validate all of them before any tomography steps (a refused call
+    // changes nothing), then build each hidden layer (not captured)
+    for (int b = 0; b < bt->B; ++b) {
+      qst_ctx* c = bt->ctx[b];
+      if (c->hidden_valid && c->f_last == f[b]) continue;
+      const qst_status st = c->prec == QST_FP64 ? validate_f<double>(c, f[b]) : validate_f<float>(c, f[b]);
+      if (st != QST_OK) return st;
+    }
     QST_CU(cudaEventRecord(bt->fork, bt->root));
     for (int b = 0; b < bt->B; ++b) {
       qst_ctx* c = bt->ctx[b];

@@ -67,6 +67,7 @@ class qst_options(ctypes.Structure):
         ("eig_sweeps", ctypes.c_int),
         ("eig_warm_sweeps", ctypes.c_int),
         ("network", ctypes.c_int),
+        ("device_memory_limit", ctypes.c_size_t),
     ]
 
 
