@@ -104,6 +104,10 @@ typedef struct qst_options {
                            scratch, and the scratch some calls allocate on first use); 0 = no limit.  An
                            allocation that would exceed it fails with QST_E_NOMEM before cudaMalloc is
                            called, and qst_init then frees what it had allocated. */
+    int fused_max_qubits; /* FP32 contexts of the 3-layer network with QST_MAP_CHOL_H and N at most this
+                           run each qst_step iteration (and their share of a batch iteration) as one
+                           kernel on one CTA (QST_PH_FUSED); 0 = the library's tuned default (7), -1 =
+                           never; at most 7.  The result is the same method, summed in another order. */
 } qst_options;
 
 /* Mapping networks.  QST_NET_FNN: the 3-layer network of Sec. 3.1, theta as described above.
@@ -280,7 +284,9 @@ enum {
     QST_PH_SYM = 7,      /* dL/dt from Y */
     QST_PH_W2 = 8,       /* layer-2 backward + Rprop */
     QST_PH_W1 = 9,       /* layer-1 backward + Rprop + next hidden layer */
-    QST_NPHASE = 10
+    QST_PH_FUSED = 10,   /* the whole iteration as one kernel (qst_options.fused_max_qubits): the
+                            phases 1-9 are then not recorded */
+    QST_NPHASE = 11
 };
 qst_status qst_timing_enable(qst_ctx* ctx, int max_steps);
 qst_status qst_timing_read(qst_ctx* ctx, double* phase_ms, long long* phase_count, int nphase);

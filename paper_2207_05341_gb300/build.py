@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqst.so")
-SOURCES = ["api.cu", "povm.cu", "fnn.cu", "gemm_simt.cu", "gemm_tc.cu", "probs_static.cu", "eigh.cu", "fnn_bulk.cu", "povm_pauli.cu", "povm_fast.cu", "fidelity.cu", "sampler.cu", "cnn.cu", "fidelity_q.cu"]
+SOURCES = ["api.cu", "povm.cu", "fnn.cu", "gemm_simt.cu", "gemm_tc.cu", "probs_static.cu", "eigh.cu", "fnn_bulk.cu", "povm_pauli.cu", "povm_fast.cu", "fidelity.cu", "sampler.cu", "cnn.cu", "fidelity_q.cu", "tomo_fused.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

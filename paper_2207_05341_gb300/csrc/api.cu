@@ -473,6 +473,32 @@ template <class R> struct Engine {
     return QST_OK;
   }
 
+  // Small FP32 tomographies of the 3-layer network with Chol_H run a whole iteration in one CTA
+  static bool fused(const qst_ctx* c) {
+    return std::is_same<R, float>::value && !c->cnn && c->opt.mapping == QST_MAP_CHOL_H && !is_mixed(c) &&
+           tomo_fused_ok(c->N, c->opt.fused_max_qubits);
+  }
+  static TomoDesc tomo_desc(qst_ctx* c, const R* f) {
+    TomoDesc td{};
+    if constexpr (std::is_same<R, float>::value) {
+      Work<R>* w = W<R>(c);
+      td.theta = w->theta;
+      td.step = w->step;
+      td.f = f;
+      td.pre = w->pre;
+      td.hid = w->hid;
+      td.t = w->dt;
+      td.T = w->T;
+      td.X = w->X;
+      td.G = w->G;
+      td.Y = w->Y;
+      td.scal = w->scal;
+      td.flags = w->flags;
+      td.N = c->N;
+    }
+    return td;
+  }
+
   // The steady-state iteration after the hidden layer is known: forward, likelihood,
   // backward, Rprop on W2 / b2 / b1, Rprop on W1 with the next hidden layer.  Stream
   // work only (no host synchronisation), so that it can be captured into a graph.
@@ -480,6 +506,15 @@ template <class R> struct Engine {
     Work<R>* w = W<R>(c);
     const Dims& D = c->D;
     qst_status st;
+    if (fused(c)) {
+      if constexpr (std::is_same<R, float>::value) {
+        QST_CU(join_f(c));
+        QST_CU(tomo_fused_one(tomo_desc(c, f), c->Bf, c->net, c->stream));
+        c->launches += 1;
+        tmark(c, QST_PH_FUSED);
+        return QST_OK;
+      }
+    }
     if (c->cnn) {  // the head changes every step, and its convolution reads f first
       QST_CU(join_f(c));
       if ((st = hidden(c, w->theta, f)) != QST_OK) return st;
@@ -822,6 +857,12 @@ struct qst_batch {
   double** d_scal = nullptr;
   double* d_losses = nullptr;
   double* h_losses = nullptr;
+  // the tomographies that run as one-CTA iterations: one persistent launch over this work list
+  TomoDesc* d_list = nullptr;
+  int list_cap = 0;
+  unsigned int* d_next = nullptr;
+  cudaStream_t fused_stream = nullptr;
+  cudaEvent_t fused_done = nullptr;
 };
 
 namespace {
@@ -830,22 +871,60 @@ namespace {
 // the root stream forks to one stream per tomography and joins them again.
 qst_status batch_capture(qst_batch* bt, const void* const* f) {
   if (bt->gexec) { cudaGraphExecDestroy(bt->gexec); bt->gexec = nullptr; }
+  std::vector<int> order(bt->B);
+  for (int b = 0; b < bt->B; ++b) order[b] = b;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return bt->ctx[a]->N > bt->ctx[b]->N; });
+  // The work list of the fused tomographies, largest first (the last CTAs to start get the shortest work).
+  std::vector<TomoDesc> list;
+  const qst_ctx* fc = nullptr;
+  for (int b : order) {
+    qst_ctx* c = bt->ctx[b];
+    if (c->prec == QST_FP64 || !Engine<float>::fused(c)) continue;
+    list.push_back(Engine<float>::tomo_desc(c, (const float*)f[b]));
+    fc = c;
+  }
+  if (!list.empty()) {
+    QST_CU(cudaStreamSynchronize(bt->root));  // an earlier graph may still read the old list
+    if ((int)list.size() > bt->list_cap) {
+      if (bt->d_list) cudaFree(bt->d_list);
+      bt->d_list = nullptr;
+      bt->list_cap = 0;
+      QST_CU(cudaMalloc(&bt->d_list, list.size() * sizeof(TomoDesc)));
+      bt->list_cap = (int)list.size();
+    }
+    if (!bt->d_next) QST_CU(cudaMalloc(&bt->d_next, sizeof(unsigned int)));
+    if (!bt->fused_stream) {
+      QST_CU(cudaStreamCreateWithFlags(&bt->fused_stream, cudaStreamNonBlocking));
+      QST_CU(cudaEventCreateWithFlags(&bt->fused_done, cudaEventDisableTiming));
+    }
+    QST_CU(cudaMemcpy(bt->d_list, list.data(), list.size() * sizeof(TomoDesc), cudaMemcpyHostToDevice));
+  }
   QST_CU(cudaStreamBeginCapture(bt->root, cudaStreamCaptureModeThreadLocal));
   qst_status st = QST_OK;
   long long kernels = 0;
   cudaError_t e = cudaSuccess;
+  if (!list.empty()) {  // forked at the start: beside the chains of the other tomographies
+    e = cudaEventRecord(bt->fork, bt->root);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(bt->fused_stream, bt->fork, 0);
+    if (e == cudaSuccess)
+      e = tomo_fused_list(bt->d_list, (int)list.size(), fc->Bf, fc->net, bt->d_next, bt->fused_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(bt->fused_done, bt->fused_stream);
+    kernels += 1;
+  }
   // Tomographies of one qubit count run concurrently; the groups run one after another, largest
   // first.  Mixing sizes in one fork lets the full-GPU kernels of the large ones hold SMs while the
   // short chains of the small ones wait (measured 34 ms per iteration of the 512-tomography batch
   // mixed, against about 14 ms as the sum of its same-N groups).
-  std::vector<int> order(bt->B);
-  for (int b = 0; b < bt->B; ++b) order[b] = b;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return bt->ctx[a]->N > bt->ctx[b]->N; });
-  for (int i = 0; i < bt->B && st == QST_OK && e == cudaSuccess;) {
+  // the tomographies that are not fused
+  order.erase(std::remove_if(order.begin(), order.end(),
+                             [&](int b) { return bt->ctx[b]->prec != QST_FP64 && Engine<float>::fused(bt->ctx[b]); }),
+              order.end());
+  const int nrest = (int)order.size();
+  for (int i = 0; i < nrest && st == QST_OK && e == cudaSuccess;) {
     const int N = bt->ctx[order[i]]->N;
     e = cudaEventRecord(bt->fork, bt->root);  // the group starts when the previous group has joined
     int j = i;
-    for (; j < bt->B && bt->ctx[order[j]]->N == N && st == QST_OK && e == cudaSuccess; ++j) {
+    for (; j < nrest && bt->ctx[order[j]]->N == N && st == QST_OK && e == cudaSuccess; ++j) {
       const int b = order[j];
       qst_ctx* c = bt->ctx[b];
       e = cudaStreamWaitEvent(c->stream, bt->fork, 0);
@@ -861,6 +940,7 @@ qst_status batch_capture(qst_batch* bt, const void* const* f) {
     }
     i = j;
   }
+  if (!list.empty() && e == cudaSuccess) e = cudaStreamWaitEvent(bt->root, bt->fused_done, 0);
   cudaGraph_t g = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(bt->root, &g);
   if (st != QST_OK) { if (g) cudaGraphDestroy(g); return st; }
@@ -894,6 +974,7 @@ void qst_default_options(qst_options* o) {
   o->eig_warm_sweeps = 0;
   o->network = QST_NET_FNN;
   o->device_memory_limit = 0;
+  o->fused_max_qubits = 0;
 }
 
 size_t qst_theta_size(int N) {
@@ -922,6 +1003,7 @@ qst_status qst_init(qst_ctx** out, int N, const double* povm, int K, const qst_o
     return QST_E_UNSUPPORTED;
   if (o.network != QST_NET_FNN && o.network != QST_NET_CNN) return QST_E_INVAL;
   if (o.network == QST_NET_CNN && N < 3) return QST_E_INVAL;  // 2^(N-3)-square pooling windows
+  if (o.fused_max_qubits < -1 || o.fused_max_qubits > kFusedMaxQubits) return QST_E_INVAL;
   if (o.mapping == QST_MAP_ABS_P) {
     if (!(o.P > 0.0) || !isfinite(o.P) || o.eig_sweeps < 0) return QST_E_INVAL;
     if (o.precision == QST_MIXED || o.precision == QST_MIXED_BF16) return QST_E_UNSUPPORTED;
@@ -1409,6 +1491,10 @@ void qst_batch_destroy(qst_batch* bt) {
   if (bt->d_scal) cudaFree(bt->d_scal);
   if (bt->d_losses) cudaFree(bt->d_losses);
   if (bt->h_losses) cudaFreeHost(bt->h_losses);
+  if (bt->d_list) cudaFree(bt->d_list);
+  if (bt->d_next) cudaFree(bt->d_next);
+  if (bt->fused_done) cudaEventDestroy(bt->fused_done);
+  if (bt->fused_stream) cudaStreamDestroy(bt->fused_stream);
   if (bt->own_root && bt->root) cudaStreamDestroy(bt->root);
   delete bt;
 }

@@ -136,6 +136,30 @@ cudaError_t povm_hi_nll_fast(const Dims& D, const float* W, const float* f, doub
 cudaError_t povm_lo_adj_fast(const Dims& D, const float* Wadj, float2* G, const PovmPlan& P, unsigned int* amax,
                              cudaStream_t s);
 
+// ---- one iteration of a small tomography in one CTA (tomo_fused.cu) ----
+// FP32, 3-layer network, Chol_H: t, T, X = T T, the POVM map, likelihood, G, Y = G T, dL/dt, and the
+// Rprop updates of both layers with the next hidden layer, for N <= kFusedMaxQubits (H <= 14).
+constexpr int kFusedMaxQubits = 7;
+struct TomoDesc {
+  float* theta;         // parameters and Rprop state (qst_theta_size(N) reals each)
+  float* step;
+  const float* f;       // frequencies, n reals
+  float* pre;           // hidden pre-activation and activation [H], read and replaced by the next ones
+  float* hid;
+  float* t;             // n reals: t, then dL/dt
+  float2 *T, *X, *G, *Y;  // d x d complex scratch
+  double* scal;         // [0] Tr X, [1] sum f (read, then rewritten), [2] loss
+  unsigned int* flags;  // [0] clamp count
+  int N;
+};
+// max_qubits: the context's option (0: the tuned default, < 0: never)
+bool tomo_fused_ok(int N, int max_qubits);
+cudaError_t tomo_fused_one(const TomoDesc& td, const PovmB<float>& B, const NetCfg& cfg, cudaStream_t s);
+// every tomography of the device array `list` (count entries, largest first is best) in one persistent
+// launch; next: a device counter (reset by this call on s)
+cudaError_t tomo_fused_list(const TomoDesc* list, int count, const PovmB<float>& B, const NetCfg& cfg,
+                            unsigned int* next, cudaStream_t s);
+
 // ---- network (fnn.cu) ----
 template <class R> cudaError_t net_l1_forward(const Dims& D, const R* theta, const R* f, R* pre, R* hid,
                                               double* scal, double* partials, unsigned int* counter,

@@ -50,7 +50,7 @@ EXPORTED = [
     "qst_state_fidelity",
 ]
 
-PHASES = ["hidden", "build_T", "x_fwd", "povm_lo", "povm_hi", "povm_adj", "gt", "sym", "w2", "w1"]
+PHASES = ["hidden", "build_T", "x_fwd", "povm_lo", "povm_hi", "povm_adj", "gt", "sym", "w2", "w1", "fused"]
 
 
 class qst_options(ctypes.Structure):
@@ -68,6 +68,7 @@ class qst_options(ctypes.Structure):
         ("eig_warm_sweeps", ctypes.c_int),
         ("network", ctypes.c_int),
         ("device_memory_limit", ctypes.c_size_t),
+        ("fused_max_qubits", ctypes.c_int),
     ]
 
 

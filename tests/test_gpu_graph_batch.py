@@ -28,11 +28,13 @@ def _inputs(N, seed):
     return f.astype(np.float32), synth.init_theta(N, 60 + seed).astype(np.float32)
 
 
-def _run(N, f, theta, steps, prec, graph, timing=False, extra=None, host=False, network=qst.QST_NET_FNN):
+def _run(N, f, theta, steps, prec, graph, timing=False, extra=None, host=False, network=qst.QST_NET_FNN,
+         fused_max=0):
     stream = torch.cuda.Stream()
     o = qst.qst_default_options()
     o.precision = prec
     o.network = network
+    o.fused_max_qubits = fused_max
     ctx = qst.qst_init(N, opt=o, stream=stream.cuda_stream)
     try:
         if graph:
@@ -64,24 +66,30 @@ def test_graph_replay_is_bit_identical(N, prec):
     assert np.array_equal(ta, tb)
 
 
-@pytest.mark.parametrize("prec", [qst.QST_FP32, qst.QST_MIXED])
-def test_timed_graph_replay(prec):
+@pytest.mark.parametrize("prec,fused_max", [(qst.QST_FP32, -1), (qst.QST_FP32, 0), (qst.QST_MIXED, 0)])
+def test_timed_graph_replay(prec, fused_max):
     """Phase events captured as graph nodes: same results and launch count as the
-    launch-by-launch path, and every phase of the latest replay is timed once."""
+    launch-by-launch path, and every phase of the latest replay is timed once (an FP32
+    N = 7 iteration is one fused kernel by default, timed as one phase)."""
     N = 7
     f, theta = _inputs(N, 3)
     xa, xb = {}, {}
-    la, ta, _ = _run(N, f, theta, 5, prec, graph=False, timing=True, extra=xa)
-    lb, tb, _ = _run(N, f, theta, 5, prec, graph=True, timing=True, extra=xb)
+    la, ta, _ = _run(N, f, theta, 5, prec, graph=False, timing=True, extra=xa, fused_max=fused_max)
+    lb, tb, _ = _run(N, f, theta, 5, prec, graph=True, timing=True, extra=xb, fused_max=fused_max)
     assert la == lb and np.array_equal(ta, tb)
     assert xa["launches"] == xb["launches"] > 0
     tm = xb["timing"]
     timed = [p for p in qst.PHASES if tm[p][1] > 0]
     assert "hidden" not in timed  # a replay does not recompute the f-dependent activation
-    assert {"build_T", "povm_lo", "povm_hi", "w2", "w1"} <= set(timed)
+    fused = prec == qst.QST_FP32 and fused_max == 0
+    last = "fused" if fused else "w2"
+    if fused:
+        assert timed == ["fused"]
+    else:
+        assert {"build_T", "povm_lo", "povm_hi", "w2", "w1"} <= set(timed)
     assert all(tm[p][1] == 1 and tm[p][0] > 0 for p in timed)
     # the launch-by-launch path recorded all five steps
-    assert xa["timing"]["w2"][1] == 5 and xa["timing"]["hidden"][1] == 1
+    assert xa["timing"][last][1] == 5 and xa["timing"]["hidden"][1] == 1
 
 
 @pytest.mark.parametrize("N,prec,network", [(6, qst.QST_FP32, qst.QST_NET_FNN), (8, qst.QST_MIXED, qst.QST_NET_FNN),
@@ -98,7 +106,8 @@ def test_graph_replay_with_page_locked_host_f(N, prec, network):
     lc, tc, _ = _run(N, f, theta, 6, prec, graph=True, host=True, timing=True, extra=xc, network=network)
     assert la == lb == lc and ib == 6
     assert np.array_equal(ta, tb) and np.array_equal(ta, tc)
-    assert xc["timing"]["w2"][1] == 1
+    fused = prec == qst.QST_FP32 and network == qst.QST_NET_FNN  # N = 6: one fused kernel per iteration
+    assert xc["timing"]["fused" if fused else "w2"][1] == 1
 
 
 def test_graph_needs_a_stream():
