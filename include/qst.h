@@ -106,7 +106,7 @@ typedef struct qst_options {
                            called, and qst_init then frees what it had allocated. */
     int fused_max_qubits; /* FP32 contexts of the 3-layer network with QST_MAP_CHOL_H and N at most this
                            run each qst_step iteration (and their share of a batch iteration) as one
-                           kernel on one CTA (QST_PH_FUSED); 0 = the library's tuned default (7), -1 =
+                           kernel on one CTA (QST_PH_FUSED); 0 = qst_tuning.fused_max_qubits, -1 =
                            never; at most 7.  The result is the same method, summed in another order. */
 } qst_options;
 
@@ -302,6 +302,26 @@ qst_status qst_timing_read(qst_ctx* ctx, double* phase_ms, long long* phase_coun
  * inputs use the launch-by-launch path.  A replay has no host work between kernels.
  * Instrumentation of the library, not part of the method. */
 qst_status qst_graph_enable(qst_ctx* ctx, int enable);
+
+/* Launch parameters of the library, process-wide (instrumentation of the library, not part of the
+ * method; the shipped defaults were chosen by the package's autotuner on the target GPU).
+ *   bulk_chunks_per_cta  least number of 256-column chunks that one CTA of an FP32 weight pass (and of
+ *                        the layer-1 forward that shares its partition) streams, >= 1; the grid is at
+ *                        most one CTA per SM.  It fixes how the passes' sums over 4^N terms are split,
+ *                        so results change in the last bits with it.
+ *   fused_ctas_per_sm    resident CTAs per SM of the persistent launch of a batch's fused tomographies
+ *                        (1 or 2); results do not depend on it.
+ *   fused_max_qubits     the limit qst_options.fused_max_qubits = 0 stands for (0..7; 0 = never).
+ * Set them between iterations, with no call of the library running on another thread; a batch captured
+ * earlier keeps the values it was captured with until its inputs change.  QST_E_INVAL for values out of
+ * range (nothing changed). */
+typedef struct qst_tuning {
+    int bulk_chunks_per_cta;
+    int fused_ctas_per_sm;
+    int fused_max_qubits;
+} qst_tuning;
+void qst_get_tuning(qst_tuning* t);
+qst_status qst_set_tuning(const qst_tuning* t);
 
 /* Wait for all work enqueued on the context's stream. */
 qst_status qst_sync(qst_ctx* ctx);

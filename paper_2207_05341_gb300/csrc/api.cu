@@ -8,10 +8,12 @@
 #include <new>
 #include <type_traits>
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "../../include/qst.h"
 #include "impl.h"
+#include "tuned.h"
 
 using namespace qst;
 
@@ -51,6 +53,50 @@ int check_povm(const double* povm, int K, PovmB<double>* Bd) {
   for (int q = 0; q < 8; ++q)
     if (fabs(sum[q] - eye[q]) > 1e-12) return QST_E_INVAL;
   return QST_OK;
+}
+
+static std::atomic<int> g_bulk_chunks{kTunedBulkChunksPerCta};
+static std::atomic<int> g_fused_ctas{kTunedFusedCtasPerSm};
+static std::atomic<int> g_fused_max{kTunedFusedMaxQubits};
+
+Tuning tuning() { return Tuning{g_bulk_chunks.load(), g_fused_ctas.load(), g_fused_max.load()}; }
+
+BatchRec*& batch_rec() {
+  static thread_local BatchRec* rec = nullptr;
+  return rec;
+}
+
+bool batch_take(BatchArgs& ba, std::initializer_list<const void*> ptrs, const void* blob, size_t blob_bytes) {
+  BatchRec* r = batch_rec();
+  ba = BatchArgs{};
+  if (r == nullptr) return false;
+  const int k = r->call++;
+  const int nptr = (int)ptrs.size() + (blob ? 1 : 0);
+  if (r->mode == BatchRec::LAUNCH) {
+    if (k >= (int)r->calls.size() || r->calls[k].nptr != nptr || r->calls[k].blob_bytes != blob_bytes) {
+      r->bad = true;  // not the sequence that was recorded: launch nothing
+      return true;
+    }
+    ba.tab = r->calls[k].dtab;
+    ba.nz = (unsigned)r->count;
+    return false;
+  }
+  if (r->member == 0 && k == (int)r->calls.size()) {
+    r->calls.emplace_back();
+    r->calls[k].nptr = nptr;
+    r->calls[k].blob_bytes = blob_bytes;
+  }
+  if (k >= (int)r->calls.size() || r->calls[k].nptr != nptr || r->calls[k].blob_bytes != blob_bytes) {
+    r->bad = true;
+    return true;
+  }
+  BatchRec::Call& c = r->calls[k];
+  c.ptrs.insert(c.ptrs.end(), ptrs.begin(), ptrs.end());
+  if (blob) {
+    const unsigned char* b = static_cast<const unsigned char*>(blob);
+    c.blobs.insert(c.blobs.end(), b, b + blob_bytes);
+  }
+  return true;
 }
 
 }  // namespace qst
@@ -499,6 +545,13 @@ template <class R> struct Engine {
     return td;
   }
 
+  // Iterations whose every launcher takes part in grouped launches (batch_take): the mixed or FP32 Chol_H
+  // path of the 3-layer network with the structured fast POVM kernels and the bulk weight passes.
+  static bool groupable(qst_ctx* c, const R* f) {
+    return std::is_same<R, float>::value && !c->cnn && c->opt.mapping == QST_MAP_CHOL_H && !fused(c) &&
+           fast_povm(c) && povm_needs_fperm(c->plan) && use_bulk(c, f) && c->tmax == 0;
+  }
+
   // The steady-state iteration after the hidden layer is known: forward, likelihood,
   // backward, Rprop on W2 / b2 / b1, Rprop on W1 with the next hidden layer.  Stream
   // work only (no host synchronisation), so that it can be captured into a graph.
@@ -863,9 +916,90 @@ struct qst_batch {
   unsigned int* d_next = nullptr;
   cudaStream_t fused_stream = nullptr;
   cudaEvent_t fused_done = nullptr;
+  // groups of tomographies of one size that run each kernel of their iteration as one launch
+  std::vector<BatchRec> groups;
+  unsigned char* d_tab = nullptr;  // their pointer tables and tensor-map copies
+  size_t tab_cap = 0;
 };
 
 namespace {
+
+// Record one iteration of every member of a group with the launches skipped (inside a capture that is
+// thrown away, so that a launcher that does not take part shows up as a node and nothing runs); false
+// when the group cannot run as grouped launches.
+bool record_group(qst_batch* bt, const std::vector<int>& mem, const void* const* f, BatchRec& rec) {
+  rec = BatchRec();
+  rec.mode = BatchRec::RECORD;
+  rec.count = (int)mem.size();
+  for (int i = 0; i < rec.count; ++i) {
+    qst_ctx* c = bt->ctx[mem[i]];
+    if (!Engine<float>::groupable(c, (const float*)f[mem[i]])) return false;
+    rec.member = i;
+    rec.call = 0;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+    const long long l0 = c->launches;
+    batch_rec() = &rec;
+    const qst_status st = Engine<float>::step_body(c, (const float*)f[mem[i]]);
+    batch_rec() = nullptr;
+    c->launches = l0;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    size_t nodes = 1;
+    if (g) {
+      if (cudaGraphGetNodes(g, nullptr, &nodes) != cudaSuccess) nodes = 1;
+      cudaGraphDestroy(g);
+    }
+    if (st != QST_OK || e != cudaSuccess || nodes != 0 || rec.bad || rec.call != (int)rec.calls.size()) {
+      cudaGetLastError();
+      return false;
+    }
+  }
+  return !rec.calls.empty();
+}
+
+// Copy the groups' pointer tables (row z: tomography z's pointers, a blob's device address first) and
+// blobs into one device buffer, and point every call at its table.
+cudaError_t upload_groups(qst_batch* bt) {
+  auto up = [](size_t x, size_t a) { return (x + a - 1) / a * a; };
+  size_t total = 0;
+  for (const BatchRec& r : bt->groups)
+    for (const BatchRec::Call& c : r.calls) {
+      if (c.blob_bytes) total = up(total, 128) + c.blob_bytes * r.count;
+      total = up(total, 16) + sizeof(void*) * c.nptr * r.count;
+    }
+  if (total == 0) return cudaSuccess;
+  if (total > bt->tab_cap) {
+    if (bt->d_tab) cudaFree(bt->d_tab);
+    bt->d_tab = nullptr;
+    bt->tab_cap = 0;
+    cudaError_t e = cudaMalloc(&bt->d_tab, total);
+    if (e != cudaSuccess) return e;
+    bt->tab_cap = total;
+  }
+  std::vector<unsigned char> img(total);
+  size_t off = 0;
+  for (BatchRec& r : bt->groups)
+    for (BatchRec::Call& c : r.calls) {
+      size_t boff = 0;
+      if (c.blob_bytes) {
+        off = up(off, 128);
+        boff = off;
+        memcpy(&img[off], c.blobs.data(), c.blob_bytes * r.count);
+        off += c.blob_bytes * r.count;
+      }
+      off = up(off, 16);
+      const void** row = reinterpret_cast<const void**>(&img[off]);
+      const int np = c.nptr - (c.blob_bytes ? 1 : 0);
+      for (int z = 0; z < r.count; ++z) {
+        int k = 0;
+        if (c.blob_bytes) row[(size_t)z * c.nptr + k++] = bt->d_tab + boff + (size_t)z * c.blob_bytes;
+        for (int q = 0; q < np; ++q) row[(size_t)z * c.nptr + k++] = c.ptrs[(size_t)z * np + q];
+      }
+      c.dtab = reinterpret_cast<const void* const*>(bt->d_tab + off);
+      off += sizeof(void*) * c.nptr * r.count;
+    }
+  return cudaMemcpy(bt->d_tab, img.data(), total, cudaMemcpyHostToDevice);
+}
 
 // One iteration of every tomography of the batch, captured once into a single graph:
 // the root stream forks to one stream per tomography and joins them again.
@@ -883,8 +1017,35 @@ qst_status batch_capture(qst_batch* bt, const void* const* f) {
     list.push_back(Engine<float>::tomo_desc(c, (const float*)f[b]));
     fc = c;
   }
+  // The others, in runs of one qubit count (largest first).  A run of two or more FP32-based tomographies
+  // runs each kernel of its iteration once for the whole run (grid z = the tomography) when every
+  // launcher of its iteration takes part; otherwise every tomography runs its own chain of kernels.
+  order.erase(std::remove_if(order.begin(), order.end(),
+                             [&](int b) { return bt->ctx[b]->prec != QST_FP64 && Engine<float>::fused(bt->ctx[b]); }),
+              order.end());
+  const int nrest = (int)order.size();
+  std::vector<std::pair<int, int>> runs;
+  for (int i = 0; i < nrest;) {
+    int j = i;
+    while (j < nrest && bt->ctx[order[j]]->N == bt->ctx[order[i]]->N) ++j;
+    runs.emplace_back(i, j);
+    i = j;
+  }
+  std::vector<int> run_group(runs.size(), -1);
+  bt->groups.clear();
+  for (size_t r = 0; r < runs.size(); ++r) {
+    const int i = runs[r].first, j = runs[r].second;
+    if (j - i < 2 || bt->ctx[order[i]]->prec == QST_FP64) continue;
+    const std::vector<int> mem(order.begin() + i, order.begin() + j);
+    BatchRec rec;
+    if (record_group(bt, mem, f, rec)) {
+      run_group[r] = (int)bt->groups.size();
+      bt->groups.push_back(std::move(rec));
+    }
+  }
+  if (!list.empty() || !bt->groups.empty())
+    QST_CU(cudaStreamSynchronize(bt->root));  // an earlier graph may still read the old list and tables
   if (!list.empty()) {
-    QST_CU(cudaStreamSynchronize(bt->root));  // an earlier graph may still read the old list
     if ((int)list.size() > bt->list_cap) {
       if (bt->d_list) cudaFree(bt->d_list);
       bt->d_list = nullptr;
@@ -899,11 +1060,12 @@ qst_status batch_capture(qst_batch* bt, const void* const* f) {
     }
     QST_CU(cudaMemcpy(bt->d_list, list.data(), list.size() * sizeof(TomoDesc), cudaMemcpyHostToDevice));
   }
+  QST_CU(upload_groups(bt));
   QST_CU(cudaStreamBeginCapture(bt->root, cudaStreamCaptureModeThreadLocal));
   qst_status st = QST_OK;
   long long kernels = 0;
   cudaError_t e = cudaSuccess;
-  if (!list.empty()) {  // forked at the start: beside the chains of the other tomographies
+  if (!list.empty()) {  // forked at the start: beside the launches of the other tomographies
     e = cudaEventRecord(bt->fork, bt->root);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(bt->fused_stream, bt->fork, 0);
     if (e == cudaSuccess)
@@ -911,21 +1073,37 @@ qst_status batch_capture(qst_batch* bt, const void* const* f) {
     if (e == cudaSuccess) e = cudaEventRecord(bt->fused_done, bt->fused_stream);
     kernels += 1;
   }
-  // Tomographies of one qubit count run concurrently; the groups run one after another, largest
-  // first.  Mixing sizes in one fork lets the full-GPU kernels of the large ones hold SMs while the
-  // short chains of the small ones wait (measured 34 ms per iteration of the 512-tomography batch
+  // The runs go one after another, largest first.  Within a run of chains the tomographies run
+  // concurrently: mixing sizes in one fork lets the full-GPU kernels of the large ones hold SMs while
+  // the short chains of the small ones wait (measured 34 ms per iteration of the 512-tomography batch
   // mixed, against about 14 ms as the sum of its same-N groups).
-  // the tomographies that are not fused
-  order.erase(std::remove_if(order.begin(), order.end(),
-                             [&](int b) { return bt->ctx[b]->prec != QST_FP64 && Engine<float>::fused(bt->ctx[b]); }),
-              order.end());
-  const int nrest = (int)order.size();
-  for (int i = 0; i < nrest && st == QST_OK && e == cudaSuccess;) {
-    const int N = bt->ctx[order[i]]->N;
-    e = cudaEventRecord(bt->fork, bt->root);  // the group starts when the previous group has joined
-    int j = i;
-    for (; j < nrest && bt->ctx[order[j]]->N == N && st == QST_OK && e == cudaSuccess; ++j) {
-      const int b = order[j];
+  for (size_t r = 0; r < runs.size() && st == QST_OK && e == cudaSuccess; ++r) {
+    const int i = runs[r].first, j = runs[r].second;
+    e = cudaEventRecord(bt->fork, bt->root);  // the run starts when the previous one has joined
+    if (e != cudaSuccess) break;
+    if (run_group[r] >= 0) {  // one launch per kernel, on the first member's stream
+      BatchRec& rec = bt->groups[run_group[r]];
+      const int b0 = order[i];
+      qst_ctx* c = bt->ctx[b0];
+      e = cudaStreamWaitEvent(c->stream, bt->fork, 0);
+      if (e != cudaSuccess) break;
+      rec.mode = BatchRec::LAUNCH;
+      rec.call = 0;
+      rec.bad = false;
+      const long long l0 = c->launches;
+      batch_rec() = &rec;
+      st = Engine<float>::step_body(c, (const float*)f[b0]);
+      batch_rec() = nullptr;
+      c->launches = l0;
+      if (st == QST_OK && (rec.bad || rec.call != (int)rec.calls.size())) st = QST_E_CUDA;
+      kernels += (long long)rec.calls.size();
+      if (st != QST_OK) break;
+      e = cudaEventRecord(bt->done[b0], c->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(bt->root, bt->done[b0], 0);
+      continue;
+    }
+    for (int k = i; k < j && st == QST_OK && e == cudaSuccess; ++k) {
+      const int b = order[k];
       qst_ctx* c = bt->ctx[b];
       e = cudaStreamWaitEvent(c->stream, bt->fork, 0);
       if (e != cudaSuccess) break;
@@ -938,7 +1116,6 @@ qst_status batch_capture(qst_batch* bt, const void* const* f) {
       e = cudaEventRecord(bt->done[b], c->stream);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(bt->root, bt->done[b], 0);
     }
-    i = j;
   }
   if (!list.empty() && e == cudaSuccess) e = cudaStreamWaitEvent(bt->root, bt->fused_done, 0);
   cudaGraph_t g = nullptr;
@@ -1295,6 +1472,24 @@ qst_status qst_timing_read(qst_ctx* c, double* phase_ms, long long* phase_count,
   return QST_OK;
 }
 
+void qst_get_tuning(qst_tuning* t) {
+  if (!t) return;
+  const Tuning u = tuning();
+  t->bulk_chunks_per_cta = u.bulk_chunks_per_cta;
+  t->fused_ctas_per_sm = u.fused_ctas_per_sm;
+  t->fused_max_qubits = u.fused_max_qubits;
+}
+
+qst_status qst_set_tuning(const qst_tuning* t) {
+  if (!t || t->bulk_chunks_per_cta < 1 || t->bulk_chunks_per_cta > (1 << 20) || t->fused_ctas_per_sm < 1 ||
+      t->fused_ctas_per_sm > kFusedCtasPerSmMax || t->fused_max_qubits < 0 || t->fused_max_qubits > kFusedMaxQubits)
+    return QST_E_INVAL;
+  g_bulk_chunks.store(t->bulk_chunks_per_cta);
+  g_fused_ctas.store(t->fused_ctas_per_sm);
+  g_fused_max.store(t->fused_max_qubits);
+  return QST_OK;
+}
+
 qst_status qst_graph_enable(qst_ctx* c, int enable) {
   if (!c) return QST_E_INVAL;
   if (enable && c->stream == nullptr) return QST_E_UNSUPPORTED;  // the legacy stream cannot be captured
@@ -1495,6 +1690,7 @@ void qst_batch_destroy(qst_batch* bt) {
   if (bt->d_next) cudaFree(bt->d_next);
   if (bt->fused_done) cudaEventDestroy(bt->fused_done);
   if (bt->fused_stream) cudaStreamDestroy(bt->fused_stream);
+  if (bt->d_tab) cudaFree(bt->d_tab);
   if (bt->own_root && bt->root) cudaStreamDestroy(bt->root);
   delete bt;
 }

@@ -165,4 +165,20 @@ __device__ __forceinline__ void block_absmax_to(float m, unsigned int* amax) {
   }
 }
 
+// A tensor map that host code copied into global memory: order the copy before this thread's next use
+// of the map by the tensor-map proxy (TMA).
+__device__ __forceinline__ void tensormap_acquire(const void* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(map) : "memory");
+}
+
+// Launches of one kernel for a group of tomographies of one size (grid z = the tomography): row z of
+// the device table `tab` holds that tomography's pointer arguments, in the order given here, and
+// replaces the kernel's own (which are those of a single tomography when tab is NULL).
+template <class... P> __device__ __forceinline__ void rebind(const void* const* tab, P&... ps) {
+  if (tab == nullptr) return;
+  const void* const* row = tab + (size_t)blockIdx.z * sizeof...(P);
+  int k = 0;
+  ((ps = (P)(const_cast<void*>(row[k++]))), ...);  // P: a (possibly restrict-qualified) pointer type
+}
+
 }  // namespace qst

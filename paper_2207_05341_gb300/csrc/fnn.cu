@@ -126,8 +126,9 @@ __global__ void __launch_bounds__(256) k_l1_forward(const R* __restrict__ theta,
 // mixed-precision path writes T's 16-bit planes from t instead, tc_planes_T in gemm_tc.cu).
 template <class R, int H>
 __global__ void __launch_bounds__(256) k_layer2(const R* __restrict__ theta, const R* __restrict__ hid, long long n,
-                                                 R* __restrict__ t, unsigned int* amax) {
+                                                 R* __restrict__ t, unsigned int* amax, const void* const* tab) {
   __shared__ R hs[H];
+  rebind(tab, theta, hid, t, amax);
   if (threadIdx.x < H) hs[threadIdx.x] = hid[threadIdx.x];
   __syncthreads();
   using VV = Vec<R>;
@@ -160,8 +161,9 @@ __global__ void __launch_bounds__(256) k_layer2(const R* __restrict__ theta, con
 // to Tt (lower triangle 0).
 template <class R>
 __global__ void __launch_bounds__(256) k_hermitian_T(const R* __restrict__ t, int N, cx_t<R>* __restrict__ T,
-                                                      cx_t<R>* __restrict__ Tt) {
+                                                      cx_t<R>* __restrict__ Tt, const void* const* tab) {
   using V = cx_t<R>;
+  rebind(tab, t, T, Tt);
   __shared__ R Ra[32][33];
   __shared__ R Rb[32][33];
   const int d = 1 << N;
@@ -366,8 +368,10 @@ __global__ void __launch_bounds__(256, 2) k_w1_pass(R* __restrict__ theta, R* __
 // ------------------------------------------------------------------ dL/dt from Y = G T
 // Gamma = Y + Y^dag;  dR_ij = 2 Re Gamma_ij, dR_ji = 2 Im Gamma_ij (i > j), dR_ii = Re Gamma_ii.
 template <class R>
-__global__ void __launch_bounds__(256) k_symmetrize(const cx_t<R>* __restrict__ Y, R* __restrict__ dt, int d) {
+__global__ void __launch_bounds__(256) k_symmetrize(const cx_t<R>* __restrict__ Y, R* __restrict__ dt, int d,
+                                                     const void* const* tab) {
   __shared__ R Ar[32][33], Ai[32][33], Br[32][33], Bi[32][33];
+  rebind(tab, Y, dt);
   const int TS = d < 32 ? d : 32;
   int I, J;
   tri_decode(blockIdx.x, I, J);
@@ -531,7 +535,9 @@ cudaError_t net_build_T(const Dims& D, const R* theta, const R* hid, R* t, cx_t<
       return b < 1 ? 1 : b;
     }();
     const long long grid = want < (long long)per_sm * sms ? want : (long long)per_sm * sms;
-    k_layer2<R, HH><<<(unsigned)grid, 256, 0, s>>>(theta, hid, D.n, t, amax);
+    BatchArgs ba;
+    if (!batch_take(ba, {theta, hid, t, amax}))
+      k_layer2<R, HH><<<dim3((unsigned)grid, 1, ba.nz), 256, 0, s>>>(theta, hid, D.n, t, amax, ba.tab);
   });
   if (!T) return cudaGetLastError();
   return net_hermitian_T<R>(D, t, T, Tt, s);
@@ -541,7 +547,9 @@ template <class R> cudaError_t net_hermitian_T(const Dims& D, const R* t, cx_t<R
   const int TS = D.d < 32 ? D.d : 32;
   const int nt = D.d / TS;
   const unsigned pairs = (unsigned)(nt * (nt + 1) / 2);
-  k_hermitian_T<R><<<pairs, 256, 0, s>>>(t, D.N, T, Tt);
+  BatchArgs ba;
+  if (batch_take(ba, {t, T, Tt})) return cudaSuccess;
+  k_hermitian_T<R><<<dim3(pairs, 1, ba.nz), 256, 0, s>>>(t, D.N, T, Tt, ba.tab);
   return cudaGetLastError();
 }
 
@@ -583,7 +591,9 @@ cudaError_t net_w1_pass(const Dims& D, R* theta, R* step, const R* f, const R* d
 template <class R> cudaError_t net_symmetrize(const Dims& D, const cx_t<R>* Y, R* dt, cudaStream_t s) {
   const int TS = D.d < 32 ? D.d : 32;
   const int nt = D.d / TS;
-  k_symmetrize<R><<<(unsigned)(nt * (nt + 1) / 2), 256, 0, s>>>(Y, dt, D.d);
+  BatchArgs ba;
+  if (batch_take(ba, {Y, dt})) return cudaSuccess;
+  k_symmetrize<R><<<dim3((unsigned)(nt * (nt + 1) / 2), 1, ba.nz), 256, 0, s>>>(Y, dt, D.d, ba.tab);
   return cudaGetLastError();
 }
 

@@ -161,8 +161,11 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_wpass_bulk(const __gri
                                                           float* dpre_io, float* pre_out, float* hid_out, double* scal,
                                                           long long n, long long ob2, long long ob1,
                                                           double* partials, unsigned int* counter,
-                                                          unsigned int* flags, RpropCfg<float> rc, float slope) {
+                                                          unsigned int* flags, RpropCfg<float> rc, float slope,
+                                                          const void* const* tab) {
   using S = Stage<H, W2>;
+  const WMaps* mp = &maps;
+  rebind(tab, mp, theta, step, vec, hidv, pre, dpre_io, pre_out, hid_out, scal, partials, counter, flags);
   extern __shared__ __align__(128) uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((128u - (s_u32(smem_raw) & 127u)) & 127u);  // 128-byte aligned ring
   constexpr int kStages = S::kStages;
@@ -198,14 +201,18 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_wpass_bulk(const __gri
   if (warp == kConsumers / 32) {
     // ---------------- producer
     if (lane == 0) {
+      if (tab) {  // the maps are this tomography's copies in global memory
+        tensormap_acquire(&mp->w);
+        tensormap_acquire(&mp->st);
+      }
       auto issue_loads = [&](long long k) {
         const int q = (int)(k % kStages);
         uint8_t* st = smem + q * S::kBytes;
         const long long c0 = (blockIdx.x + k * gridDim.x) * kCols;
         const uint32_t bar = s_u32(&full[q]);
         bar_expect(bar, tx);
-        tma_load_box(st + S::kW, &maps.w, (int)c0, bar);
-        tma_load_box(st + S::kSt, &maps.st, (int)c0, bar);
+        tma_load_box(st + S::kW, &mp->w, (int)c0, bar);
+        tma_load_box(st + S::kSt, &mp->st, (int)c0, bar);
         bulk_load(st + S::kVec, vec + c0, kCols * 4, bar);
         if (with_b2) {
           bulk_load(st + S::kBw, theta + ob2 + c0, kCols * 4, bar);
@@ -216,8 +223,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_wpass_bulk(const __gri
         const int q = (int)(k % kStages);
         uint8_t* st = smem + q * S::kBytes;
         const long long c0 = (blockIdx.x + k * gridDim.x) * kCols;
-        tma_store_box(&maps.w, (int)c0, st + S::kW);
-        tma_store_box(&maps.st, (int)c0, st + S::kSt);
+        tma_store_box(&mp->w, (int)c0, st + S::kW);
+        tma_store_box(&mp->st, (int)c0, st + S::kSt);
         if (with_b2) {
           bulk_store(theta + ob2 + c0, st + S::kBw, kCols * 4);
           bulk_store(step + ob2 + c0, st + S::kBst, kCols * 4);
@@ -392,7 +399,11 @@ long long bulk_grid(long long n) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   long long grid = (long long)kCtasPerSm * sms;
   const long long nchunks = n / kCols;
-  if (grid > nchunks) grid = nchunks;
+  // at least bulk_chunks_per_cta chunks per CTA: a CTA's ring fill and store drain are then a small
+  // share of its time, and a batch of small tomographies keeps few CTAs per tomography
+  const long long per = tuning().bulk_chunks_per_cta;
+  const long long want = nchunks / per < 1 ? 1 : nchunks / per;
+  if (grid > want) grid = want;
   if (grid > kPartialBlocks) grid = kPartialBlocks;
   return grid;
 }
@@ -434,9 +445,14 @@ template <int H, bool W2> cudaError_t launch_bulk(float* theta, float* step, con
   if (!make_rows_map(&maps.w, theta + rowoff, n, H) || !make_rows_map(&maps.st, step + rowoff, n, H))
     return cudaErrorInvalidValue;
   const long long grid = bulk_grid(n);
-  k_wpass_bulk<H, W2><<<(unsigned)grid, kThreads, smem, s>>>(maps, theta, step, vec, hid, pre, dpre, pre_out,
-                                                             hid_out, scal, n, ob2, ob1, partials, counter, flags, rc,
-                                                             slope);
+  BatchArgs ba;
+  if (batch_take(ba, {theta, step, vec, hid, pre, dpre, pre_out, hid_out, scal, partials, counter, flags}, &maps,
+                 sizeof(WMaps)))
+    return cudaSuccess;
+  k_wpass_bulk<H, W2><<<dim3((unsigned)grid, 1, ba.nz), kThreads, smem, s>>>(maps, theta, step, vec, hid, pre, dpre,
+                                                                             pre_out, hid_out, scal, n, ob2, ob1,
+                                                                             partials, counter, flags, rc, slope,
+                                                                             ba.tab);
   return cudaGetLastError();
 }
 

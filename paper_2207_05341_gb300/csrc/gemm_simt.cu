@@ -15,8 +15,10 @@ namespace qst {
 template <class R, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_cgemm(int d, const cx_t<R>* __restrict__ A,
                                                                  const cx_t<R>* __restrict__ B,
-                                                                 cx_t<R>* __restrict__ C, int lower) {
+                                                                 cx_t<R>* __restrict__ C, int lower,
+                                                                 const void* const* tab) {
   using V = cx_t<R>;
+  rebind(tab, A, B, C);
   constexpr int NTX = BN / TN, NTY = BM / TM, NT = NTX * NTY;
   constexpr int LA = BM * BK / NT, LB = BK * BN / NT;
   constexpr int PAD = 4;
@@ -132,10 +134,12 @@ template <class R, int BM, int BN, int BK, int TM, int TN>
 static cudaError_t run_tiled(int d, const cx_t<R>* A, const cx_t<R>* B, cx_t<R>* C, bool lower, cudaStream_t s) {
   constexpr int NT = (BM / TM) * (BN / TN);
   const int nt = d / BM;
+  BatchArgs ba;
+  if (batch_take(ba, {A, B, C})) return cudaSuccess;
   if (lower) {
-    k_cgemm<R, BM, BN, BK, TM, TN><<<(unsigned)(nt * (nt + 1) / 2), NT, 0, s>>>(d, A, B, C, 1);
+    k_cgemm<R, BM, BN, BK, TM, TN><<<dim3((unsigned)(nt * (nt + 1) / 2), 1, ba.nz), NT, 0, s>>>(d, A, B, C, 1, ba.tab);
   } else {
-    k_cgemm<R, BM, BN, BK, TM, TN><<<dim3(d / BN, d / BM), NT, 0, s>>>(d, A, B, C, 0);
+    k_cgemm<R, BM, BN, BK, TM, TN><<<dim3(d / BN, d / BM, ba.nz), NT, 0, s>>>(d, A, B, C, 0, ba.tab);
   }
   return cudaGetLastError();
 }

@@ -136,9 +136,13 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
       : "memory");
 }
 
+// tab: a batched launch (grid z = tomography); row z holds the tensor maps' device copy, C, sA, sB, err, clear
 __global__ void __launch_bounds__(128, 1) k_tc_cgemm(const __grid_constant__ TcMaps maps, float2* __restrict__ C,
                                                       int d, int lower, uint32_t idesc, const double* sA,
-                                                      const double* sB, unsigned int* err, unsigned int* clear) {
+                                                      const double* sB, unsigned int* err, unsigned int* clear,
+                                                      const void* const* tab) {
+  const TcMaps* mp = &maps;
+  rebind(tab, mp, C, sA, sB, err, clear);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
@@ -178,6 +182,10 @@ __global__ void __launch_bounds__(128, 1) k_tc_cgemm(const __grid_constant__ TcM
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
+    if (tab) {  // the maps are this tomography's copies in global memory
+      for (int p = 0; p < 4; ++p) tensormap_acquire(&mp->a[p]);
+      for (int p = 0; p < 6; ++p) tensormap_acquire(&mp->b[p]);
+    }
     int issued = 0;
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % kStages, it = kb / kStages;
@@ -190,12 +198,12 @@ __global__ void __launch_bounds__(128, 1) k_tc_cgemm(const __grid_constant__ TcM
       mbar_expect_tx(fb, kStageBytes);
       const int part = (kb * kBK) < d ? 0 : 1;
       const int col = kb * kBK - part * d;
-      const CUtensorMap* a_hi = &maps.a[part == 0 ? 0 : 1];
-      const CUtensorMap* a_lo = &maps.a[part == 0 ? 2 : 3];
-      const CUtensorMap* b1_hi = &maps.b[part == 0 ? 0 : 1];
-      const CUtensorMap* b1_lo = &maps.b[part == 0 ? 3 : 4];
-      const CUtensorMap* b2_hi = &maps.b[part == 0 ? 2 : 0];
-      const CUtensorMap* b2_lo = &maps.b[part == 0 ? 5 : 3];
+      const CUtensorMap* a_hi = &mp->a[part == 0 ? 0 : 1];
+      const CUtensorMap* a_lo = &mp->a[part == 0 ? 2 : 3];
+      const CUtensorMap* b1_hi = &mp->b[part == 0 ? 0 : 1];
+      const CUtensorMap* b1_lo = &mp->b[part == 0 ? 3 : 4];
+      const CUtensorMap* b2_hi = &mp->b[part == 0 ? 2 : 0];
+      const CUtensorMap* b2_lo = &mp->b[part == 0 ? 5 : 3];
       const uint32_t base = smem_u32(smem + s * kStageBytes);
       tma_load_2d(base + 0 * kTileBytes, a_hi, col, I * kBM, fb);
       tma_load_2d(base + 1 * kTileBytes, a_lo, col, I * kBM, fb);
@@ -308,7 +316,8 @@ template <class H> __device__ __forceinline__ void hi_lo(float v, H& hi, H& lo) 
 // written to *s_slot.
 template <class H>
 __global__ void __launch_bounds__(256) k_split(const float2* __restrict__ A, H* __restrict__ P, long long nn,
-                                                const unsigned int* amax, double* s_slot) {
+                                                const unsigned int* amax, double* s_slot, const void* const* tab) {
+  rebind(tab, A, P, amax, s_slot);
   const double sd = split_scale(amax);
   const float sc = (float)sd;
   if (blockIdx.x == 0 && threadIdx.x == 0) *s_slot = sd;
@@ -329,7 +338,9 @@ __global__ void __launch_bounds__(256) k_split(const float2* __restrict__ A, H* 
 // tile (I, J), 128-255 the tile (J, I)).
 template <class H>
 __global__ void __launch_bounds__(256) k_hermitian_planes(const float* __restrict__ t, int d, H* __restrict__ P,
-                                                           const unsigned int* amax, double* s_slot) {
+                                                           const unsigned int* amax, double* s_slot,
+                                                           const void* const* tab) {
+  rebind(tab, t, P, amax, s_slot);
   __shared__ float Ra[32][33];
   __shared__ float Rb[32][33];
   const double sd = split_scale(amax);
@@ -433,11 +444,13 @@ cudaError_t launch_tc(const TcMaps& M, float2* C, int d, bool lower, int fmt, co
     attr_set = true;
   }
   const int nt = d / kBM;
+  BatchArgs ba;
+  if (batch_take(ba, {C, sA, sB, err, clear}, &M, sizeof(TcMaps))) return cudaSuccess;
   if (lower) {
-    k_tc_cgemm<<<(unsigned)(nt * (nt + 1) / 2), 128, kSmemBytes, s>>>(M, C, d, 1, make_idesc(fmt), sA, sB, err,
-                                                                       clear);
+    k_tc_cgemm<<<dim3((unsigned)(nt * (nt + 1) / 2), 1, ba.nz), 128, kSmemBytes, s>>>(M, C, d, 1, make_idesc(fmt), sA,
+                                                                                      sB, err, clear, ba.tab);
   } else {
-    k_tc_cgemm<<<dim3(nt, nt), 128, kSmemBytes, s>>>(M, C, d, 0, make_idesc(fmt), sA, sB, err, clear);
+    k_tc_cgemm<<<dim3(nt, nt, ba.nz), 128, kSmemBytes, s>>>(M, C, d, 0, make_idesc(fmt), sA, sB, err, clear, ba.tab);
   }
   return cudaGetLastError();
 }
@@ -460,10 +473,14 @@ cudaError_t tc_planes_T(int d, const float* t, void* Tb, int fmt, double* scal, 
   if (d < 32 || d % 32) return cudaErrorInvalidValue;
   const int nt = d / 32;
   const unsigned pairs = (unsigned)(nt * (nt + 1) / 2);
+  const unsigned int* am = fmt == TC_BF16 ? nullptr : amax;
+  BatchArgs ba;
+  if (batch_take(ba, {t, Tb, am, scal + kScaleT})) return cudaSuccess;
   if (fmt == TC_BF16)
-    k_hermitian_planes<__nv_bfloat16><<<pairs, 256, 0, s>>>(t, d, (__nv_bfloat16*)Tb, nullptr, scal + kScaleT);
+    k_hermitian_planes<__nv_bfloat16><<<dim3(pairs, 1, ba.nz), 256, 0, s>>>(t, d, (__nv_bfloat16*)Tb, am,
+                                                                            scal + kScaleT, ba.tab);
   else
-    k_hermitian_planes<__half><<<pairs, 256, 0, s>>>(t, d, (__half*)Tb, amax, scal + kScaleT);
+    k_hermitian_planes<__half><<<dim3(pairs, 1, ba.nz), 256, 0, s>>>(t, d, (__half*)Tb, am, scal + kScaleT, ba.tab);
   return cudaGetLastError();
 }
 
@@ -472,10 +489,14 @@ cudaError_t tc_split_G(int d, const float2* G, void* Gb, int fmt, double* scal, 
   const long long nn = (long long)d * d;
   long long blocks = (nn + 255) / 256;
   if (blocks > 1024) blocks = 1024;
+  const unsigned int* am = fmt == TC_BF16 ? nullptr : amax;
+  BatchArgs ba;
+  if (batch_take(ba, {G, Gb, am, scal + kScaleG})) return cudaSuccess;
   if (fmt == TC_BF16)
-    k_split<__nv_bfloat16><<<(unsigned)blocks, 256, 0, s>>>(G, (__nv_bfloat16*)Gb, nn, nullptr, scal + kScaleG);
+    k_split<__nv_bfloat16><<<dim3((unsigned)blocks, 1, ba.nz), 256, 0, s>>>(G, (__nv_bfloat16*)Gb, nn, am,
+                                                                            scal + kScaleG, ba.tab);
   else
-    k_split<__half><<<(unsigned)blocks, 256, 0, s>>>(G, (__half*)Gb, nn, amax, scal + kScaleG);
+    k_split<__half><<<dim3((unsigned)blocks, 1, ba.nz), 256, 0, s>>>(G, (__half*)Gb, nn, am, scal + kScaleG, ba.tab);
   return cudaGetLastError();
 }
 

@@ -4,9 +4,52 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <initializer_list>
+#include <vector>
+
 #include "common.cuh"
 
 namespace qst {
+
+// ---- one launch per kernel for a group of tomographies of one size ----
+// The launchers of the iteration are called as for a single tomography.  While a recorder is active on
+// the calling thread, a batch-aware launcher, just before each kernel launch, either (RECORD) stores the
+// kernel's pointer arguments for the tomography being recorded and skips the launch, or (LAUNCH)
+// launches the kernel once with grid z = the group and the device table of that launch, whose row z
+// holds tomography z's pointers (rebind in common.cuh).  A per-tomography structure (tensor maps) is
+// stored as a blob; the table's entry is then the device address of the tomography's copy.
+struct BatchRec {
+  enum Mode { RECORD = 0, LAUNCH = 1 };
+  struct Call {
+    int nptr = 0;                       // entries per row (the blob's address first, when there is one)
+    size_t blob_bytes = 0;
+    std::vector<const void*> ptrs;      // RECORD: count rows of nptr - (blob ? 1 : 0) pointers
+    std::vector<unsigned char> blobs;   // RECORD: count blobs
+    const void* const* dtab = nullptr;  // LAUNCH: the device table
+  };
+  int mode = RECORD;
+  int count = 0;   // tomographies in the group
+  int member = 0;  // RECORD: the tomography being recorded
+  int call = 0;    // index of the next kernel launch of the iteration
+  bool bad = false;  // the members' launch sequences differ
+  std::vector<Call> calls;
+};
+BatchRec*& batch_rec();  // the calling thread's recorder (NULL: plain launches)
+struct BatchArgs {
+  const void* const* tab = nullptr;
+  unsigned nz = 1;
+};
+// Before each batch-aware kernel launch: true when the launch is to be skipped (RECORD).
+bool batch_take(BatchArgs& ba, std::initializer_list<const void*> ptrs, const void* blob = nullptr,
+                size_t blob_bytes = 0);
+
+// Process-wide launch parameters (qst_set_tuning; defaults in tuned.h).
+struct Tuning {
+  int bulk_chunks_per_cta;  // least 256-column chunks per CTA of a bulk weight pass (fixes its partition)
+  int fused_ctas_per_sm;    // resident CTAs per SM of the persistent fused batch launch (1 or 2)
+  int fused_max_qubits;     // largest N run as one fused iteration when the context asks for the default
+};
+Tuning tuning();
 
 // Sizes of one N-qubit problem and of the two-pass POVM split.
 //   d = 2^N, n = 4^N, H = 2N.

@@ -380,8 +380,10 @@ __global__ void __launch_bounds__(256) k_povm_hi_nll(const R* __restrict__ W, co
 // The likelihood and rho = X / Tr X use the trace of X as computed (not ||T||_F^2), so the
 // normalisation carries the same rounding as q and the loss stays invariant to the scale of T.
 template <class R>
-__global__ void __launch_bounds__(256) k_trace(const cx_t<R>* __restrict__ X, int d, double* scal) {
+__global__ void __launch_bounds__(256) k_trace(const cx_t<R>* __restrict__ X, int d, double* scal,
+                                                const void* const* tab) {
   __shared__ double red[8];
+  rebind(tab, X, scal);
   // every diagonal load of a thread is issued before the first add (one memory latency, not d / 256)
   constexpr int kPer = 16;  // d <= 4096 = 16 x 256
   R v[kPer];
@@ -485,7 +487,9 @@ cudaError_t povm_hi_nll(const Dims& D, const R* W, const R* f, double* scal, R* 
 
 template <class R> cudaError_t trace_X(const Dims& D, const cx_t<R>* X, double* scal, cudaStream_t s) {
   if (D.d > 4096) return cudaErrorInvalidValue;
-  k_trace<R><<<1, 256, 0, s>>>(X, D.d, scal);
+  BatchArgs ba;
+  if (batch_take(ba, {X, scal})) return cudaSuccess;
+  k_trace<R><<<dim3(1, 1, ba.nz), 256, 0, s>>>(X, D.d, scal, ba.tab);
   return cudaGetLastError();
 }
 

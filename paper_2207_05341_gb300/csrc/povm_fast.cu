@@ -184,8 +184,9 @@ __device__ __forceinline__ float4 ld4(const float2* p) {
 // ---------------------------------------------------------------- pass 1, forward
 template <class MAP, bool XOR>
 __global__ void __launch_bounds__(kLoThreads, 4) k_lo_fwd_fast(const float2* __restrict__ X, float* __restrict__ W,
-                                                                 int N, MAP m, Out4 outmap) {
+                                                                 int N, MAP m, Out4 outmap, const void* const* tab) {
   __shared__ float2 Z[kTile * kTile];
+  rebind(tab, X, W);
   pdl_trigger();
   const long long d = 1LL << N;
   const int nb = (int)(d >> 6);
@@ -276,8 +277,10 @@ __global__ void __launch_bounds__(kLoThreads, 4) k_lo_fwd_fast(const float2* __r
 // ---------------------------------------------------------------- pass 1, adjoint
 template <class MAP, bool XOR>
 __global__ void __launch_bounds__(kLoThreads, 4) k_lo_adj_fast(const float* Wadj, float2* __restrict__ G,
-                                                                 int N, MAP m, Out4 outmap, unsigned int* amax) {
+                                                                 int N, MAP m, Out4 outmap, unsigned int* amax,
+                                                                 const void* const* tab) {
   __shared__ float2 Z[kTile * kTile];
+  rebind(tab, Wadj, G, amax);
   const long long d = 1LL << N;
   const int nb = (int)(d >> 6);
   int I, J;
@@ -396,12 +399,15 @@ __device__ __forceinline__ float nll_term(float q, float fk, float gconst, float
 // least 16 when NB = 2 so that a CTA is a whole warp.
 template <int NB, int MODE> constexpr int cta_pairs() { return (MODE == 0 || NB < 4) ? 16 : 8; }
 
-template <int NB, int MODE, int kCP = cta_pairs<NB, MODE>()>
+// BATCH: the grouped variant (a separate instantiation, so that the single-tomography kernel keeps its
+// register allocation)
+template <int NB, int MODE, int kCP = cta_pairs<NB, MODE>(), bool BATCH = false>
 __global__ void __launch_bounds__(kCP * NB, (NB == 32 && kCP == 8) ? 2 : 1) k_hi_fast(const float* W, float* __restrict__ p,
                                                       const float* __restrict__ f, double* scal, float* __restrict__ Wadj,
                                                       double* partials, unsigned int* counter, unsigned int* flags,
-                                                      HiParams P, int adjoint) {
+                                                      HiParams P, int adjoint, const void* const* tab) {
   constexpr int H = msb_c(NB);
+  if constexpr (BATCH) rebind(tab, W, p, f, scal, Wadj, partials, counter, flags);
   extern __shared__ __align__(16) float2 smp[];
   float2* fac = smp;            // [x][z]: the sign of (-i)^|x & z| times prod_k beta_(x_k, z_k), twice
   float2* buf = smp + NB * NB;  // [x][zeta][cp]: the transpose between the two halves
@@ -608,17 +614,20 @@ cudaError_t launch_hi(const Dims& D, const float* W, float* p, const float* f, d
                       cudaStream_t s) {
   constexpr int kCP = cta_pairs<NB, MODE>();
   const size_t sm = (size_t)(NB * NB + NB * (NB * kCP + (kCP < 16 ? kCP : 0))) * sizeof(float2);
-  cudaError_t e = ensure_dynamic_smem((const void*)k_hi_fast<NB, MODE>, sm);
+  BatchArgs ba;
+  if (batch_take(ba, {W, p, f, scal, Wadj, partials, counter, flags})) return cudaSuccess;
+  const void* fn = ba.tab ? (const void*)k_hi_fast<NB, MODE, kCP, true> : (const void*)k_hi_fast<NB, MODE, kCP, false>;
+  cudaError_t e = ensure_dynamic_smem(fn, sm);
   if (e != cudaSuccess) return e;
   HiParams hp;
   for (int i = 0; i < 4; ++i) hp.beta[i] = P.beta[i];
   hp.out = out_of(P).bits;
   int adj = adjoint ? 1 : 0;
-  void* args[] = {(void*)&W, (void*)&p, (void*)&f, (void*)&scal, (void*)&Wadj, (void*)&partials, (void*)&counter,
-                  (void*)&flags, (void*)&hp, (void*)&adj};
   const unsigned blocks = (unsigned)((1LL << kLogSS) / (2 * kCP));
   if (MODE == 1 && blocks > (unsigned)kPartialBlocks * kPartialStride) return cudaErrorInvalidConfiguration;
-  return launch_pdl((const void*)k_hi_fast<NB, MODE>, dim3(blocks), dim3(kCP * NB), sm, s, args);
+  void* args[] = {(void*)&W, (void*)&p, (void*)&f, (void*)&scal, (void*)&Wadj, (void*)&partials, (void*)&counter,
+                  (void*)&flags, (void*)&hp, (void*)&adj, (void*)&ba.tab};
+  return launch_pdl(fn, dim3(blocks, 1, ba.nz), dim3(kCP * NB), sm, s, args);
 }
 
 template <int MODE>
@@ -695,12 +704,14 @@ bool povm_fast_ok(const Dims& D) { return D.g == 6 && D.N >= 7 && D.N <= 11 && D
 cudaError_t povm_lo_fwd_fast(const Dims& D, const float2* X, float* W, const PovmPlan& P, cudaStream_t s) {
   const unsigned tiles = (unsigned)(D.nb * (D.nb + 1) / 2);
   const Out4 o = out_of(P);
+  BatchArgs ba;
+  if (batch_take(ba, {X, W})) return cudaSuccess;
   if (P.structured) {
     const MapStruct m = map_struct(P);
-    k_lo_fwd_fast<MapStruct, true><<<tiles, kLoThreads, 0, s>>>(X, W, D.N, m, o);
+    k_lo_fwd_fast<MapStruct, true><<<dim3(tiles, 1, ba.nz), kLoThreads, 0, s>>>(X, W, D.N, m, o, ba.tab);
   } else {
     const MapGeneric m = map_generic(P);
-    k_lo_fwd_fast<MapGeneric, false><<<tiles, kLoThreads, 0, s>>>(X, W, D.N, m, o);
+    k_lo_fwd_fast<MapGeneric, false><<<dim3(tiles, 1, ba.nz), kLoThreads, 0, s>>>(X, W, D.N, m, o, ba.tab);
   }
   return cudaGetLastError();
 }
@@ -725,13 +736,16 @@ cudaError_t povm_lo_adj_fast(const Dims& D, const float* Wadj, float2* G, const 
                              cudaStream_t s) {
   const unsigned tiles = (unsigned)(D.nb * (D.nb + 1) / 2);
   const Out4 o = out_of(P);
+  BatchArgs ba;
+  if (batch_take(ba, {Wadj, G, amax})) return cudaSuccess;
   if (P.structured) {
     const MapStruct m = map_struct(P);
-    void* args[] = {(void*)&Wadj, (void*)&G, (void*)&D.N, (void*)&m, (void*)&o, (void*)&amax};
-    return launch_pdl((const void*)k_lo_adj_fast<MapStruct, true>, dim3(tiles), dim3(kLoThreads), 0, s, args);
+    void* args[] = {(void*)&Wadj, (void*)&G, (void*)&D.N, (void*)&m, (void*)&o, (void*)&amax, (void*)&ba.tab};
+    return launch_pdl((const void*)k_lo_adj_fast<MapStruct, true>, dim3(tiles, 1, ba.nz), dim3(kLoThreads), 0, s,
+                      args);
   }
   const MapGeneric m = map_generic(P);
-  k_lo_adj_fast<MapGeneric, false><<<tiles, kLoThreads, 0, s>>>(Wadj, G, D.N, m, o, amax);
+  k_lo_adj_fast<MapGeneric, false><<<dim3(tiles, 1, ba.nz), kLoThreads, 0, s>>>(Wadj, G, D.N, m, o, amax, ba.tab);
   return cudaGetLastError();
 }
 

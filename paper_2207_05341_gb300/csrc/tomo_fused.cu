@@ -281,7 +281,7 @@ __device__ void tomo_iteration(const TomoDesc& td, const PovmB<float>& Bm, const
 
 // Persistent CTAs over a work list (list != NULL: count entries, taken in turn through *next), or the
 // single tomography `one`.  Both run the same code on a shared-memory copy of the descriptor.
-__global__ void __launch_bounds__(kFusedThreads, kFusedCtasPerSm) k_tomo(const TomoDesc* __restrict__ list, int count, TomoDesc one,
+__global__ void __launch_bounds__(kFusedThreads, kFusedCtasPerSmMax) k_tomo(const TomoDesc* __restrict__ list, int count, TomoDesc one,
                                                          PovmB<float> Bm, NetCfg cfg, unsigned int* next) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(kFusedThreads, kFusedCtasPerSm) k_tomo(const T
 }  // namespace
 
 bool tomo_fused_ok(int N, int max_qubits) {
-  const int m = max_qubits == 0 ? kFusedMaxQubitsDefault : max_qubits;
+  const int m = max_qubits == 0 ? tuning().fused_max_qubits : max_qubits;
   return N >= 1 && N <= m && N <= kFusedMaxQubits;
 }
 
@@ -327,7 +327,8 @@ cudaError_t tomo_fused_list(const TomoDesc* list, int count, const PovmB<float>&
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tomo, kFusedThreads, smem)) != cudaSuccess)
     return e;
   if (per_sm < 1) per_sm = 1;
-  if (per_sm > kFusedCtasPerSm) per_sm = kFusedCtasPerSm;
+  const int cap = tuning().fused_ctas_per_sm;
+  if (per_sm > cap) per_sm = cap;
   const int ctas = count < sms * per_sm ? count : sms * per_sm;
   if ((e = cudaMemsetAsync(next, 0, sizeof(unsigned int), s)) != cudaSuccess) return e;
   k_tomo<<<ctas, kFusedThreads, smem, s>>>(list, count, TomoDesc{}, B, cfg, next);

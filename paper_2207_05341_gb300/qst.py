@@ -72,6 +72,14 @@ class qst_options(ctypes.Structure):
     ]
 
 
+class qst_tuning(ctypes.Structure):
+    _fields_ = [
+        ("bulk_chunks_per_cta", ctypes.c_int),
+        ("fused_ctas_per_sm", ctypes.c_int),
+        ("fused_max_qubits", ctypes.c_int),
+    ]
+
+
 class QstError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
@@ -119,6 +127,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "qst_timing_read": (i, [vp, pd, ctypes.POINTER(ctypes.c_longlong), i]),
         "qst_probs_static": (i, [i, vp, i, vp, vp, vp]),
         "qst_graph_enable": (i, [vp, i]),
+        "qst_get_tuning": (None, [ctypes.POINTER(qst_tuning)]),
+        "qst_set_tuning": (i, [ctypes.POINTER(qst_tuning)]),
         "qst_batch_init": (i, [ctypes.POINTER(vp), i, ctypes.POINTER(ctypes.c_int), vp, i,
                                ctypes.POINTER(qst_options), vp]),
         "qst_batch_context": (vp, [vp, i]),
@@ -327,6 +337,23 @@ def qst_probs_static(N: int, rho, p, povm=None, K: int = 4, stream: int = 0) -> 
 
 def qst_graph_enable(ctx: int, enable: bool = True) -> int:
     return _check(load().qst_graph_enable(ctx, 1 if enable else 0), "qst_graph_enable")
+
+
+def qst_get_tuning() -> dict:
+    t = qst_tuning()
+    load().qst_get_tuning(ctypes.byref(t))
+    return {k: getattr(t, k) for k, _ in qst_tuning._fields_}
+
+
+def qst_set_tuning(**kw) -> None:
+    """Change some of the process-wide launch parameters (the others keep their values)."""
+    t = qst_tuning()
+    load().qst_get_tuning(ctypes.byref(t))
+    for k, v in kw.items():
+        if k not in dict(qst_tuning._fields_):
+            raise KeyError(k)
+        setattr(t, k, int(v))
+    _check(load().qst_set_tuning(ctypes.byref(t)), "qst_set_tuning")
 
 
 def _ptr_array(xs):

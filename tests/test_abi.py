@@ -146,3 +146,43 @@ def test_static_probs_refuses_host_buffers_before_any_launch(lib):
     with pytest.raises(qst.QstError) as e:
         qst.qst_probs_static(3, rho, p)
     assert e.value.status == qst.QST_E_INVAL
+
+
+def _tuned_defaults():
+    src = open(os.path.join(os.path.dirname(__file__), "..", "paper_2207_05341_gb300", "csrc", "tuned.h")).read()
+    get = lambda name: int(re.search(r"constexpr int %s = (\d+);" % name, src).group(1))
+    return {"bulk_chunks_per_cta": get("kTunedBulkChunksPerCta"), "fused_ctas_per_sm": get("kTunedFusedCtasPerSm"),
+            "fused_max_qubits": get("kTunedFusedMaxQubits")}
+
+
+def test_tuning_defaults_and_validation(lib):
+    """qst_get_tuning starts from the autotuner's table; qst_set_tuning refuses values out of range and
+    leaves the others as they were (host only, no device call)."""
+    start = qst.qst_get_tuning()
+    assert start == _tuned_defaults()
+    try:
+        for bad in ({"bulk_chunks_per_cta": 0}, {"fused_ctas_per_sm": 3}, {"fused_ctas_per_sm": 0},
+                    {"fused_max_qubits": 8}, {"fused_max_qubits": -1}):
+            with pytest.raises(qst.QstError) as e:
+                qst.qst_set_tuning(**bad)
+            assert e.value.status == qst.QST_E_INVAL
+            assert qst.qst_get_tuning() == start
+        qst.qst_set_tuning(bulk_chunks_per_cta=4, fused_max_qubits=0)
+        assert qst.qst_get_tuning() == dict(start, bulk_chunks_per_cta=4, fused_max_qubits=0)
+    finally:
+        qst.qst_set_tuning(**start)
+
+
+def test_autotuner_writes_its_choice(tmp_path, monkeypatch):
+    from paper_2207_05341_gb300 import autotune
+    pkg = tmp_path / "pkg"
+    (pkg / "csrc").mkdir(parents=True)
+    src = open(os.path.join(autotune.HERE, "csrc", "tuned.h")).read()
+    (pkg / "csrc" / "tuned.h").write_text(src)
+    monkeypatch.setattr(autotune, "HERE", str(pkg))
+    log = tmp_path / "log.json"
+    log.write_text('{"best": {"bulk_chunks_per_cta": 23, "fused_max_qubits": 5, "fused_ctas_per_sm": 1}}')
+    autotune.main(["--apply", str(log)])
+    out = (pkg / "csrc" / "tuned.h").read_text()
+    assert "kTunedBulkChunksPerCta = 23;" in out and "kTunedFusedMaxQubits = 5;" in out
+    assert "kTunedFusedCtasPerSm = 1;" in out and "kFusedThreads = 512;" in out

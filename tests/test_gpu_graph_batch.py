@@ -143,3 +143,39 @@ def test_batch_matches_individual_contexts():
         assert qst.qst_batch_kernel_launches(bt) > 0
     finally:
         qst.qst_batch_destroy(bt)
+
+
+@pytest.mark.parametrize("prec,fused_max", [(qst.QST_FP32, 6), (qst.QST_MIXED, 0), (qst.QST_MIXED_BF16, 0)])
+def test_grouped_batch_matches_individual_contexts(prec, fused_max):
+    """Runs of tomographies of one size (N = 7, 8, 9) launch each kernel of their iteration once for the
+    whole run: losses and parameters bit-identical to each tomography run on its own context, and far
+    fewer launches per iteration than one chain per tomography."""
+    Ns = [9, 7, 8, 9, 8, 7, 7]
+    data = [_inputs(N, 30 + b) for b, N in enumerate(Ns)]
+    steps = 4
+    want = [_run(N, f, th, steps, prec, graph=False, fused_max=fused_max) for N, (f, th) in zip(Ns, data)]
+    stream = torch.cuda.Stream()
+    o = qst.qst_default_options()
+    o.precision = prec
+    o.fused_max_qubits = fused_max
+    bt = qst.qst_batch_init(Ns, opt=o, stream=stream.cuda_stream)
+    try:
+        fds = [torch.from_numpy(f).cuda() for f, _ in data]
+        for b, (_, th) in enumerate(data):
+            qst.qst_batch_set_params(bt, b, th)
+        torch.cuda.synchronize()
+        losses = [qst.qst_batch_step(bt, fds, want_losses=True)]
+        l0 = qst.qst_batch_kernel_launches(bt)
+        losses += [qst.qst_batch_step(bt, fds, want_losses=True) for _ in range(steps - 1)]
+        per_iter = (qst.qst_batch_kernel_launches(bt) - l0) / (steps - 1)
+        for b, N in enumerate(Ns):
+            out = torch.empty(data[b][1].size, device="cuda")
+            qst.qst_get_params(qst.qst_batch_context(bt, b), out)
+            qst.qst_batch_sync(bt)
+            torch.cuda.synchronize()
+            assert [l[b] for l in losses] == want[b][0], b
+            assert np.array_equal(out.cpu().numpy(), want[b][1]), b
+        # three runs of about a dozen launches each, against 7 chains of about a dozen
+        assert per_iter <= 3 * 16, per_iter
+    finally:
+        qst.qst_batch_destroy(bt)
