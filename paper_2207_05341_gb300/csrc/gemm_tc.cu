@@ -313,7 +313,8 @@ template <class H> __device__ __forceinline__ void hi_lo(float v, H& hi, H& lo) 
 }
 
 // Complex FP32 matrix -> 16-bit hi / lo planes of s * x (G: re, im (hi), re, im (lo)); s = split_scale(amax),
-// written to *s_slot.
+// written to *s_slot.  Each thread converts 8 consecutive entries (four 16-byte loads, one 16-byte store
+// per plane); nn is a multiple of 8.
 template <class H>
 __global__ void __launch_bounds__(256) k_split(const float2* __restrict__ A, H* __restrict__ P, long long nn,
                                                 const unsigned int* amax, double* s_slot, const void* const* tab) {
@@ -321,12 +322,26 @@ __global__ void __launch_bounds__(256) k_split(const float2* __restrict__ A, H* 
   const double sd = split_scale(amax);
   const float sc = (float)sd;
   if (blockIdx.x == 0 && threadIdx.x == 0) *s_slot = sd;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (long long)gridDim.x * blockDim.x) {
-    const float2 a = A[i];
-    H rh, rl, ih, il;
-    hi_lo(sc * a.x, rh, rl);
-    hi_lo(sc * a.y, ih, il);
-    P[i] = rh; P[nn + i] = ih; P[2 * nn + i] = rl; P[3 * nn + i] = il;
+  union Pack {
+    uint4 v;
+    H h[8];
+  };
+  const long long n8 = nn / 8;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n8; q += (long long)gridDim.x * blockDim.x) {
+    const float4* src = reinterpret_cast<const float4*>(A + 8 * q);
+    Pack rh, ih, rl, il;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float4 a = src[u];
+      hi_lo(sc * a.x, rh.h[2 * u], rl.h[2 * u]);
+      hi_lo(sc * a.y, ih.h[2 * u], il.h[2 * u]);
+      hi_lo(sc * a.z, rh.h[2 * u + 1], rl.h[2 * u + 1]);
+      hi_lo(sc * a.w, ih.h[2 * u + 1], il.h[2 * u + 1]);
+    }
+    *reinterpret_cast<uint4*>(P + 8 * q) = rh.v;
+    *reinterpret_cast<uint4*>(P + nn + 8 * q) = ih.v;
+    *reinterpret_cast<uint4*>(P + 2 * nn + 8 * q) = rl.v;
+    *reinterpret_cast<uint4*>(P + 3 * nn + 8 * q) = il.v;
   }
 }
 
@@ -487,7 +502,8 @@ cudaError_t tc_planes_T(int d, const float* t, void* Tb, int fmt, double* scal, 
 cudaError_t tc_split_G(int d, const float2* G, void* Gb, int fmt, double* scal, const unsigned int* amax,
                        cudaStream_t s) {
   const long long nn = (long long)d * d;
-  long long blocks = (nn + 255) / 256;
+  if (nn % 8) return cudaErrorInvalidValue;
+  long long blocks = (nn / 8 + 255) / 256;
   if (blocks > 1024) blocks = 1024;
   const unsigned int* am = fmt == TC_BF16 ? nullptr : amax;
   BatchArgs ba;

@@ -9,5 +9,5 @@ constexpr int kFusedThreads = 512;          // threads of the CTA that runs one 
 constexpr int kFusedCtasPerSmMax = 2;       // register budget of that kernel: resident CTAs per SM at most
 constexpr int kTunedFusedCtasPerSm = 2;     // resident CTAs per SM of the persistent batch launch
 constexpr int kTunedFusedMaxQubits = 7;     // largest N run as one fused iteration by default
-constexpr int kTunedBulkChunksPerCta = 16;  // least 256-column chunks per CTA of a bulk weight pass
+constexpr int kTunedBulkChunksPerCta = 32;  // least 256-column chunks per CTA of a bulk weight pass
 }  // namespace qst
