@@ -315,6 +315,18 @@ qst_status qst_graph_enable(qst_ctx* ctx, int enable);
  * Set them between iterations, with no call of the library running on another thread; a batch captured
  * earlier keeps the values it was captured with until its inputs change.  QST_E_INVAL for values out of
  * range (nothing changed). */
+/* Testing hook for the device-side wait limits; it involves no GPU fault.  With what =
+ * QST_INJECT_TC_LOADS the next `count` launches of the tensor-core products (QST_MIXED, QST_MIXED_BF16),
+ * with QST_INJECT_WPASS_LOADS the next `count` launches of the FP32 bulk weight passes, issue none of
+ * their operand copies: the waits for those copies run out after their limit (about 2 s), the kernels
+ * leave their results unwritten and return, and the call that reads the loss (qst_step, qst_loss_grad,
+ * qst_reconstruct) returns QST_E_TIMEOUT; the context stays usable (reload its parameters with
+ * qst_set_params: the failed step may have updated some of them).  count = 0 clears.  Process-wide;
+ * steps replayed from a captured graph are not affected.  QST_E_INVAL for an unknown `what` or
+ * count < 0. */
+enum { QST_INJECT_TC_LOADS = 1, QST_INJECT_WPASS_LOADS = 2 };
+qst_status qst_inject_wait_timeout(int what, int count);
+
 typedef struct qst_tuning {
     int bulk_chunks_per_cta;
     int fused_ctas_per_sm;

@@ -61,6 +61,15 @@ static std::atomic<int> g_fused_max{kTunedFusedMaxQubits};
 
 Tuning tuning() { return Tuning{g_bulk_chunks.load(), g_fused_ctas.load(), g_fused_max.load()}; }
 
+static std::atomic<int> g_inject[INJ_SITES];
+
+bool inject_take(int site) {
+  int v = g_inject[site].load();
+  while (v > 0)
+    if (g_inject[site].compare_exchange_weak(v, v - 1)) return true;
+  return false;
+}
+
 BatchRec*& batch_rec() {
   static thread_local BatchRec* rec = nullptr;
   return rec;
@@ -509,7 +518,10 @@ template <class R> struct Engine {
     QST_CU(cudaStreamSynchronize(c->stream));
     *loss = c->h_scal[2];
     if (c->h_flags[1] != 0u) {
-      QST_CU(cudaMemsetAsync(w->flags + 1, 0, sizeof(unsigned int), c->stream));
+      // a kernel that gave up returned before its last-block reduction: restart every counter
+      QST_CU(cudaMemsetAsync(w->flags, 0, 2 * sizeof(unsigned int), c->stream));
+      QST_CU(cudaMemsetAsync(w->counters, 0, CNT_COUNT * sizeof(unsigned int), c->stream));
+      QST_CU(cudaStreamSynchronize(c->stream));
       return QST_E_TIMEOUT;
     }
     if (c->h_flags[0] != 0u) {
@@ -1469,6 +1481,14 @@ qst_status qst_timing_read(qst_ctx* c, double* phase_ms, long long* phase_count,
     }
   }
   if (!c->graph_timed) c->tcount = 0;
+  return QST_OK;
+}
+
+qst_status qst_inject_wait_timeout(int what, int count) {
+  if (count < 0) return QST_E_INVAL;
+  if (what == QST_INJECT_TC_LOADS) g_inject[INJ_TC_LOADS].store(count);
+  else if (what == QST_INJECT_WPASS_LOADS) g_inject[INJ_WPASS_LOADS].store(count);
+  else return QST_E_INVAL;
   return QST_OK;
 }
 

@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_wpass_bulk(const __gri
                                                           long long n, long long ob2, long long ob1,
                                                           double* partials, unsigned int* counter,
                                                           unsigned int* flags, RpropCfg<float> rc, float slope,
-                                                          const void* const* tab) {
+                                                          int no_loads, const void* const* tab) {
   using S = Stage<H, W2>;
   const WMaps* mp = &maps;
   rebind(tab, mp, theta, step, vec, hidv, pre, dpre_io, pre_out, hid_out, scal, partials, counter, flags);
@@ -232,7 +232,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_wpass_bulk(const __gri
         bulk_commit();
       };
       long long loaded = 0;  // chunks [0, loaded) have been issued
-      for (; loaded < nk && loaded < kStages; ++loaded) issue_loads(loaded);
+      // no_loads (qst_inject_wait_timeout): issue nothing, so that every bounded wait of the pass runs out
+      const long long nload = no_loads ? 0 : nk;
+      for (; loaded < nload && loaded < kStages; ++loaded) issue_loads(loaded);
       for (long long k = 0; k < nk; ++k) {
         if (!bar_wait(s_u32(&empty[k % kStages]), (uint32_t)((k / kStages) & 1))) {
           atomicOr(flags, 4u);
@@ -241,7 +243,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_wpass_bulk(const __gri
         }
         issue_stores(k);
         // refill the stage of chunk k - 1, whose stores were committed one chunk ago
-        if (k >= 1 && loaded < nk) {
+        if (k >= 1 && loaded < nload) {
           bulk_wait_read_all_but_1();
           issue_loads(loaded++);
         }
@@ -449,10 +451,11 @@ template <int H, bool W2> cudaError_t launch_bulk(float* theta, float* step, con
   if (batch_take(ba, {theta, step, vec, hid, pre, dpre, pre_out, hid_out, scal, partials, counter, flags}, &maps,
                  sizeof(WMaps)))
     return cudaSuccess;
+  const int no_loads = inject_take(INJ_WPASS_LOADS) ? 1 : 0;
   k_wpass_bulk<H, W2><<<dim3((unsigned)grid, 1, ba.nz), kThreads, smem, s>>>(maps, theta, step, vec, hid, pre, dpre,
                                                                              pre_out, hid_out, scal, n, ob2, ob1,
                                                                              partials, counter, flags, rc, slope,
-                                                                             ba.tab);
+                                                                             no_loads, ba.tab);
   return cudaGetLastError();
 }
 

@@ -140,7 +140,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 __global__ void __launch_bounds__(128, 1) k_tc_cgemm(const __grid_constant__ TcMaps maps, float2* __restrict__ C,
                                                       int d, int lower, uint32_t idesc, const double* sA,
                                                       const double* sB, unsigned int* err, unsigned int* clear,
-                                                      const void* const* tab) {
+                                                      int no_loads, const void* const* tab) {
   const TcMaps* mp = &maps;
   rebind(tab, mp, C, sA, sB, err, clear);
   extern __shared__ uint8_t smem_raw[];
@@ -187,7 +187,8 @@ __global__ void __launch_bounds__(128, 1) k_tc_cgemm(const __grid_constant__ TcM
       for (int p = 0; p < 6; ++p) tensormap_acquire(&mp->b[p]);
     }
     int issued = 0;
-    for (int kb = 0; kb < nkb; ++kb) {
+    // no_loads (qst_inject_wait_timeout): issue nothing, so that the MMA warp's bounded wait runs out
+    for (int kb = 0; kb < (no_loads ? 0 : nkb); ++kb) {
       const int s = kb % kStages, it = kb / kStages;
       if (kb >= kStages && !mbar_wait(empty0 + 8 * s, (uint32_t)((it - 1) & 1))) {
         s_fail = 1;
@@ -461,11 +462,13 @@ cudaError_t launch_tc(const TcMaps& M, float2* C, int d, bool lower, int fmt, co
   const int nt = d / kBM;
   BatchArgs ba;
   if (batch_take(ba, {C, sA, sB, err, clear}, &M, sizeof(TcMaps))) return cudaSuccess;
+  const int no_loads = inject_take(INJ_TC_LOADS) ? 1 : 0;
   if (lower) {
     k_tc_cgemm<<<dim3((unsigned)(nt * (nt + 1) / 2), 1, ba.nz), 128, kSmemBytes, s>>>(M, C, d, 1, make_idesc(fmt), sA,
-                                                                                      sB, err, clear, ba.tab);
+                                                                                      sB, err, clear, no_loads, ba.tab);
   } else {
-    k_tc_cgemm<<<dim3(nt, nt, ba.nz), 128, kSmemBytes, s>>>(M, C, d, 0, make_idesc(fmt), sA, sB, err, clear, ba.tab);
+    k_tc_cgemm<<<dim3(nt, nt, ba.nz), 128, kSmemBytes, s>>>(M, C, d, 0, make_idesc(fmt), sA, sB, err, clear, no_loads,
+                                                            ba.tab);
   }
   return cudaGetLastError();
 }

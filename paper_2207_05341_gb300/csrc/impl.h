@@ -50,6 +50,9 @@ struct Tuning {
   int fused_max_qubits;     // largest N run as one fused iteration when the context asks for the default
 };
 Tuning tuning();
+// qst_inject_wait_timeout: true when this launch of `site` is to issue no operand copies (counts it off)
+enum InjectSite { INJ_TC_LOADS = 0, INJ_WPASS_LOADS = 1, INJ_SITES = 2 };
+bool inject_take(int site);
 
 // Sizes of one N-qubit problem and of the two-pass POVM split.
 //   d = 2^N, n = 4^N, H = 2N.

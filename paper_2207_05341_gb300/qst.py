@@ -128,6 +128,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "qst_probs_static": (i, [i, vp, i, vp, vp, vp]),
         "qst_graph_enable": (i, [vp, i]),
         "qst_get_tuning": (None, [ctypes.POINTER(qst_tuning)]),
+        "qst_inject_wait_timeout": (i, [i, i]),
         "qst_set_tuning": (i, [ctypes.POINTER(qst_tuning)]),
         "qst_batch_init": (i, [ctypes.POINTER(vp), i, ctypes.POINTER(ctypes.c_int), vp, i,
                                ctypes.POINTER(qst_options), vp]),
@@ -337,6 +338,15 @@ def qst_probs_static(N: int, rho, p, povm=None, K: int = 4, stream: int = 0) -> 
 
 def qst_graph_enable(ctx: int, enable: bool = True) -> int:
     return _check(load().qst_graph_enable(ctx, 1 if enable else 0), "qst_graph_enable")
+
+
+QST_INJECT_TC_LOADS = 1
+QST_INJECT_WPASS_LOADS = 2
+
+
+def qst_inject_wait_timeout(what: int, count: int = 1) -> None:
+    """Testing hook: the next `count` launches of a kernel kind issue no operand copies (see qst.h)."""
+    _check(load().qst_inject_wait_timeout(int(what), int(count)), "qst_inject_wait_timeout")
 
 
 def qst_get_tuning() -> dict:

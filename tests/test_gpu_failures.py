@@ -4,6 +4,9 @@
   refuses before cudaMalloc and frees what it had allocated.
 * QST_E_INPUT for frequencies that are not a distribution (sum != 1, NaN, negative) in qst_loss_grad,
   qst_step and the batch step; a refused batch step advances none of its tomographies.
+* QST_E_TIMEOUT from a bounded device-side wait that runs out: the tensor-core products or the bulk
+  weight passes are told to issue none of their operand copies (qst_inject_wait_timeout), so the waits
+  for those copies end at their limit (about 2 s) and the kernels return; the context is usable again.
 """
 import numpy as np
 import pytest
@@ -137,3 +140,37 @@ def test_batch_step_refuses_bad_frequencies_before_any_step():
             assert qst.qst_iterations(qst.qst_batch_context(bt, b)) == 1
     finally:
         qst.qst_batch_destroy(bt)
+
+
+@pytest.mark.parametrize("what,N,prec", [(qst.QST_INJECT_TC_LOADS, 7, qst.QST_MIXED),
+                                         (qst.QST_INJECT_WPASS_LOADS, 8, qst.QST_FP32)])
+def test_wait_that_runs_out_is_reported_and_the_context_recovers(what, N, prec):
+    f = torch.from_numpy(_f(N).astype(np.float32)).cuda()
+    theta = torch.from_numpy(synth.init_theta(N, 5).astype(np.float32)).cuda()
+    o = qst.qst_default_options()
+    o.precision = prec
+    ctx = qst.qst_init(N, opt=o)
+    try:
+        qst.qst_set_params(ctx, theta)
+        want = [qst.qst_step(ctx, f)[0] for _ in range(2)]
+        qst.qst_set_params(ctx, theta)
+        qst.qst_inject_wait_timeout(what, 1)
+        try:
+            with pytest.raises(qst.QstError) as e:
+                qst.qst_step(ctx, f)
+            assert e.value.status == qst.QST_E_TIMEOUT
+        finally:
+            qst.qst_inject_wait_timeout(what, 0)
+        # the context works again, bit for bit as before the timeout
+        qst.qst_set_params(ctx, theta)
+        got = [qst.qst_step(ctx, f)[0] for _ in range(2)]
+        assert got == want
+    finally:
+        qst.qst_destroy(ctx)
+
+
+def test_injection_hook_validates_its_arguments():
+    for what, count in ((0, 1), (3, 1), (qst.QST_INJECT_TC_LOADS, -1)):
+        with pytest.raises(qst.QstError) as e:
+            qst.qst_inject_wait_timeout(what, count)
+        assert e.value.status == qst.QST_E_INVAL
