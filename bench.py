@@ -551,8 +551,9 @@ def batch_c4(torch, qst, synth, dev, steps, warmup, seed=30, B=512, prec=None):
 
 def c5_leg(torch, qst, synth, dev, steps, seed=40):
     """N = 12 (rho 4096 x 4096, 4^12 outcomes), 10^8 shots, depolarised rank-r Ginibre state:
-    Chol_H (= A_2, Sec. 3.2) on the mixed tensor-core path, and A_P with P = 1.5 through the
-    Jacobi eigensolver (cold first step, then warm-started steps)."""
+    Chol_H (= A_2, Sec. 3.2) on the mixed tensor-core path, and A_P with P = 1.5: mixed (cold Jacobi
+    first step, then one tensor-core refinement of the previous eigenvectors per step) and FP32 (cold
+    first step, then warm-started Jacobi sweeps)."""
     N = 12
     rng = np.random.default_rng(seed)
     r = int(np.exp(rng.uniform(0, np.log(64))))
@@ -573,6 +574,7 @@ def c5_leg(torch, qst, synth, dev, steps, seed=40):
         f = torch.from_numpy(synth.frequencies(synth.multinomial_counts(P, 10**8, seed + 1), np.float32)).to(dev)
         theta = synth.init_theta(N, seed + 2).astype(np.float32)
         for name, prec, mapping, p_ord in (("chol_h_mixed_fp16x3", qst.QST_MIXED, qst.QST_MAP_CHOL_H, 2.0),
+                                           ("abs_p1.5_mixed_tc_refinement", qst.QST_MIXED, qst.QST_MAP_ABS_P, 1.5),
                                            ("abs_p1.5_fp32_jacobi", qst.QST_FP32, qst.QST_MAP_ABS_P, 1.5)):
             o = qst.qst_default_options()
             o.precision, o.mapping, o.P = prec, mapping, p_ord
@@ -580,7 +582,7 @@ def c5_leg(torch, qst, synth, dev, steps, seed=40):
             try:
                 qst.qst_set_params(ctx, theta)
                 L0, _ = qst.qst_step(ctx, f)  # first step: input validation, hidden layer, cold eigensolver
-                k = steps if mapping == qst.QST_MAP_CHOL_H else 2
+                k = 2 if prec == qst.QST_FP32 else steps  # the FP32 Jacobi path takes about a second per step
                 torch.cuda.synchronize()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
@@ -593,6 +595,9 @@ def c5_leg(torch, qst, synth, dev, steps, seed=40):
                 L1, _ = qst.qst_step(ctx, f)
                 out[name] = {"ms_per_iter": ms, "iters_per_s": 1e3 / ms, "steps_timed": k,
                              "loss_first": L0, "loss_after": L1}
+                if mapping == qst.QST_MAP_ABS_P and prec != qst.QST_FP32:
+                    ref, fb = qst.qst_eig_counts(ctx)
+                    out[name]["tc_refinements"], out[name]["steps_on_jacobi_sweeps"] = ref, fb
             finally:
                 qst.qst_destroy(ctx)
     out["note"] = "A_P with P = 2 is Chol_H (Sec. 3.2), so the P = 2 runs of this config use the T T path"

@@ -112,6 +112,13 @@ bool batch_take(BatchArgs& ba, std::initializer_list<const void*> ptrs, const vo
 
 namespace {
 
+// tensor-core eigenvector refinement of QST_MIXED A_P steps: accept / give up thresholds on max |E|
+constexpr float kOaAccept = 5e-3f;
+constexpr float kOaGiveUp = 0.25f;
+constexpr int kOaMaxIters = 4;
+constexpr float kOaLeft = 1e-5f;  // largest unresolved coupling, relative to max |lambda|
+constexpr int kOaBackoff = 15;    // after a step handed to the sweeps, the next attempt comes 16 steps later
+
 constexpr unsigned long long kStateMagic = 0x5153545354415432ULL;  // "QSTSTAT2": theta, Rprop state words
 
 }  // namespace
@@ -150,6 +157,10 @@ struct qst_ctx {
   size_t P = 0;           // parameters: qst_theta_size_net(N, network)
   bool cnn = false;       // the App. A CNN head instead of the 3-layer FNN
   unsigned long long* samp = nullptr;  // scratch of qst_sample_counts, allocated on first use
+  long long oa_refinements = 0;  // tensor-core refinements taken (QST_MIXED A_P), Jacobi fallbacks
+  long long oa_fallbacks = 0;
+  double oa_last[2] = {0.0, 0.0};  // max |E| and the unresolved coupling of the latest refinement
+  int oa_skip = 0;                 // warm steps left that go to the sweeps without a refinement attempt
   int sweeps = 10;       // cold-start Jacobi sweeps
   int warm_sweeps = 2;   // warm-start sweeps (0: never warm-start)
   bool warm_valid = false;
@@ -296,6 +307,19 @@ template <class R> qst_status alloc_work(qst_ctx* c) {
     QST_CU(dalloc(c, &ap->lam, (size_t)D.d));
     QST_CU(dalloc(c, &ap->s, (size_t)D.d));
     QST_CU(dalloc(c, &ap->sp, (size_t)D.d));
+    if (is_mixed(c)) {  // operand planes of the tensor-core refinement
+      const size_t pb = abs_p_tc_plane_bytes(D.d);
+      unsigned char* buf = nullptr;
+      QST_CU(dalloc(c, &buf, 3 * pb + 3 * (pb + pb / 2)));
+      ap->qa_n = buf;
+      ap->qa_h = buf + pb;
+      ap->wa = buf + 2 * pb;
+      ap->qb_n = buf + 3 * pb;
+      ap->qb_h = buf + 3 * pb + (pb + pb / 2);
+      ap->eb = buf + 3 * pb + 2 * (pb + pb / 2);
+      QST_CU(dalloc(c, &ap->amax, 8));
+      QST_CU(dalloc(c, &ap->sc, 8));
+    }
     c->sweeps = c->opt.eig_sweeps > 0 ? c->opt.eig_sweeps : 10;
     c->sweeps += c->sweeps & 1;
     c->warm_sweeps = c->opt.eig_warm_sweeps < 0 ? 0 : (c->opt.eig_warm_sweeps > 0 ? c->opt.eig_warm_sweeps : 2);
@@ -364,8 +388,9 @@ template <class R> struct Engine {
       QST_CU(cnn_output<R>(D, theta, w->hid, w->dt, amax_slot(c, CNT_AMAXT), c->stream));
       if (!mixed) QST_CU(net_hermitian_T<R>(D, w->dt, w->T, delta ? w->Y : nullptr, c->stream));
     } else {
-      QST_CU(net_build_T<R>(D, theta, w->hid, w->dt, mixed ? nullptr : w->T, amax_slot(c, CNT_AMAXT), c->stream,
-                            delta ? w->Y : nullptr));
+      const bool absp = c->opt.mapping == QST_MAP_ABS_P;  // the cold start's Jacobi sweeps read T itself
+      QST_CU(net_build_T<R>(D, theta, w->hid, w->dt, mixed && !absp ? nullptr : w->T, amax_slot(c, CNT_AMAXT),
+                            c->stream, delta ? w->Y : nullptr));
     }
     if (mixed) {
       QST_CU(tc_planes_T(D.d, reinterpret_cast<const float*>(w->dt), w->Tb, tc_fmt(c), w->scal,
@@ -377,10 +402,60 @@ template <class R> struct Engine {
       // the context's own parameters change slowly: start from the last eigenvectors
       const bool warm = own_params && c->warm_valid && c->warm_sweeps > 0;
       const int sw = warm ? c->warm_sweeps : c->sweeps;
-      QST_CU(abs_p_forward<R>(D.d, w->T, *reinterpret_cast<AbsPWork<R>*>(c->apw), sw, warm, c->opt.P, w->X,
-                              c->stream));
+      bool done = false;
+      if constexpr (std::is_same<R, float>::value) {
+        if (mixed && warm && c->oa_skip > 0) {
+          --c->oa_skip;  // T moved too far at the latest attempt: the sweeps, without trying first
+        } else if (mixed && warm) {
+          // Refinements of the previous eigenvectors on tensor cores, each judged by its largest correction
+          // max |E|: the eigenvectors are taken once it is at most kOaAccept (the error left is of its
+          // square); one above kOaGiveUp (T moved too far for a first-order correction), or kOaMaxIters of
+          // them, hand the step to Jacobi sweeps from the eigenvectors it started with.  Inside a graph
+          // capture there is no host check: two refinements, taken.
+          AbsPWork<float>& ap = *reinterpret_cast<AbsPWork<float>*>(c->apw);
+          const size_t qbytes = (size_t)D.d * D.d * sizeof(float2);
+          QST_CU(cudaMemcpyAsync(ap.Qh, ap.V0, qbytes, cudaMemcpyDeviceToDevice, c->stream));  // the start
+          for (int it = 0; it < kOaMaxIters && !done; ++it) {
+            QST_CU(abs_p_tc_correction(D.d, w->Tb, w->scal + kScaleT, ap, c->opt.P, tc_fmt(c), w->flags + 1,
+                                       c->stream));
+            c->launches += 12;
+            float emax = 0.f, left = 0.f;
+            if (!c->capturing) {
+              QST_CU(cudaMemcpyAsync(c->h_flags + 4, ap.amax + 2, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost,
+                                     c->stream));
+              QST_CU(cudaStreamSynchronize(c->stream));
+              memcpy(&emax, c->h_flags + 4, sizeof(float));
+              memcpy(&left, c->h_flags + 5, sizeof(float));
+              c->oa_last[0] = emax;
+              c->oa_last[1] = left;
+            }
+            if (!(emax <= kOaGiveUp) || !(left <= kOaLeft)) break;  // also NaN
+            QST_CU(abs_p_tc_update(D.d, ap, tc_fmt(c), w->flags + 1, c->stream));
+            c->launches += 4;
+            if (emax <= kOaAccept || (c->capturing && it == 1)) {
+              QST_CU(abs_p_tc_finish(D.d, ap, tc_fmt(c), reinterpret_cast<float2*>(w->X), w->flags + 1,
+                                     c->stream));
+              c->launches += 7;
+              c->oa_refinements += it + 1;
+              done = true;
+            }
+          }
+          if (!done) {  // back to the start, with its Q^dag for the sweeps' warm start
+            QST_CU(cudaMemcpyAsync(ap.V0, ap.Qh, qbytes, cudaMemcpyDeviceToDevice, c->stream));
+            QST_CU(abs_p_restore_q<float>(D.d, ap, c->stream));
+            c->oa_fallbacks += 1;
+            c->oa_skip = kOaBackoff;
+          }
+        }
+      }
+      if (!done) {
+        QST_CU(abs_p_forward<R>(D.d, w->T, *reinterpret_cast<AbsPWork<R>*>(c->apw), sw, warm, c->opt.P, w->X,
+                                c->stream));
+        c->launches += 4 + (long long)sw * (D.d - 1);
+      }
+      if (mixed && amax_slot(c, CNT_AMAXT))  // the planes of T are made: restart the max of the next t
+        QST_CU(cudaMemsetAsync(amax_slot(c, CNT_AMAXT), 0, sizeof(unsigned int), c->stream));
       c->warm_valid = own_params;
-      c->launches += 4 + (long long)sw * (D.d - 1);
     } else if (mixed) {
       QST_CU(tc_herm_square(D.d, w->Tb, tc_fmt(c), w->scal, reinterpret_cast<float2*>(w->X), w->flags + 1,
                             amax_slot(c, CNT_AMAXT), c->stream));
@@ -446,7 +521,18 @@ template <class R> struct Engine {
   static qst_status backward_state(qst_ctx* c) {
     Work<R>* w = W<R>(c);
     const Dims& D = c->D;
-    if (is_mixed(c)) {
+    if (is_mixed(c) && c->opt.mapping == QST_MAP_ABS_P) {
+      if constexpr (std::is_same<R, float>::value) {
+        QST_CU(abs_p_backward_tc(D.d, reinterpret_cast<const float2*>(w->G),
+                                 *reinterpret_cast<AbsPWork<float>*>(c->apw), tc_fmt(c),
+                                 reinterpret_cast<float2*>(w->Y), w->flags + 1, c->stream));
+      }
+      c->launches += 13;
+      tmark(c, QST_PH_GT);
+      QST_CU(net_symmetrize<R>(D, w->Y, w->dt, c->stream));
+      tmark(c, QST_PH_SYM);
+      c->launches += 1;
+    } else if (is_mixed(c)) {
       QST_CU(tc_split_G(D.d, reinterpret_cast<const float2*>(w->G), w->Gb, tc_fmt(c), w->scal,
                         amax_slot(c, CNT_AMAXG), c->stream));
       QST_CU(tc_gt_product(D.d, w->Gb, w->Tb, tc_fmt(c), w->scal, reinterpret_cast<float2*>(w->Y), w->flags + 1,
@@ -1195,7 +1281,6 @@ qst_status qst_init(qst_ctx** out, int N, const double* povm, int K, const qst_o
   if (o.fused_max_qubits < -1 || o.fused_max_qubits > kFusedMaxQubits) return QST_E_INVAL;
   if (o.mapping == QST_MAP_ABS_P) {
     if (!(o.P > 0.0) || !isfinite(o.P) || o.eig_sweeps < 0) return QST_E_INVAL;
-    if (o.precision == QST_MIXED || o.precision == QST_MIXED_BF16) return QST_E_UNSUPPORTED;
   }
   // steps within [2^-33, 2^30]: the Rprop state word then holds the previous sign exactly (rprop_encode)
   const double lo = ldexp(1.0, -33), hi = ldexp(1.0, 30);
@@ -1433,6 +1518,17 @@ qst_status qst_set_state(qst_ctx* c, const void* host_buf, size_t bytes) {
   c->params_set = true;
   c->hidden_valid = false;
   c->iters = (long long)hdr[2];
+  return QST_OK;
+}
+
+qst_status qst_eig_counts(const qst_ctx* c, long long* refinements, long long* fallbacks, double* last) {
+  if (!c) return QST_E_INVAL;
+  if (refinements) *refinements = c->oa_refinements;
+  if (fallbacks) *fallbacks = c->oa_fallbacks;
+  if (last) {
+    last[0] = c->oa_last[0];
+    last[1] = c->oa_last[1];
+  }
   return QST_OK;
 }
 

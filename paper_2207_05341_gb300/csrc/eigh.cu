@@ -307,6 +307,185 @@ cudaError_t abs_p_backward(int d, const cx_t<R>* G, AbsPWork<R>& w, cx_t<R>* Y, 
   return cgemm_simt<R>(d, w.W, w.Qh, Y, false, s);
 }
 
+// ------------------------------------------------------------------ tensor-core refinement
+// Warm-started steps of the mixed-precision path replace the Jacobi sweeps by one refinement of the
+// previous eigenvectors (Ogita and Aishima's iteration for symmetric / Hermitian matrices): four products
+// and a first-order correction, all of whose products run on k_tc_cgemm (gemm_tc.cu).  Pairs closer than
+// kOaTau max|lambda|, or whose first-order correction would exceed 1/2, are treated as a cluster
+// (E_ij = R_ij / 2: kept orthonormal, not separated); within a cluster |lambda|^P differs by little.
+namespace {
+
+constexpr float kOaTau = 1e-6f;
+
+// entry (i, j) of a Hermitian matrix of which only the 128 x 128 tiles I >= J were computed
+__device__ __forceinline__ float2 herm_entry(const float2* M, int d, int i, int j) {
+  if ((i >> 7) >= (j >> 7)) return M[(long long)i * d + j];
+  const float2 v = M[(long long)j * d + i];
+  return make_float2(v.x, -v.y);
+}
+
+// lambda_i = S_ii / (Q^dag Q)_ii, s_i = |lambda_i|^P, s'_i (as k_absp_spectrum), sc[6] = max |lambda|.  One block.
+__global__ void __launch_bounds__(1024) k_oa_spectrum(const float2* __restrict__ S, const float2* __restrict__ C1,
+                                                       int d, double P, double eps, float* lam, float* s, float* sp,
+                                                       double* sc) {
+  __shared__ float red[32];
+  float m = 0.f;
+  for (int i = threadIdx.x; i < d; i += blockDim.x) {
+    const float li = S[(long long)i * d + i].x / C1[(long long)i * d + i].x;
+    lam[i] = li;
+    m = fmaxf(m, fabsf(li));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) red[0] = v;
+  }
+  __syncthreads();
+  const double lmax = (double)red[0];
+  if (threadIdx.x == 0) sc[6] = lmax;
+  const double floor_v = P <= 1.0 ? eps * lmax : 0.0;
+  for (int i = threadIdx.x; i < d; i += blockDim.x) {
+    const double li = (double)lam[i];
+    const double ai = fabs(li);
+    const double ui = ai > floor_v ? ai : floor_v;
+    s[i] = (float)pow(ui, P);
+    sp[i] = ai > floor_v && ui > 0.0 ? (float)(P * pow(ui, P - 1.0) * (li >= 0.0 ? 1.0 : -1.0)) : 0.f;
+  }
+}
+
+// The correction E (full d x d) from S = Q^dag T Q and C1 = Q^dag Q (lower tiles), R = I - C1; max |E| -> amax[0],
+// and max |S_ij| / max |lambda| over the separated pairs whose first-order correction was too large (left as
+// a cluster) -> amax[1]: the size of what this refinement could not resolve.
+__global__ void __launch_bounds__(256) k_oa_correction(const float2* __restrict__ S, const float2* __restrict__ C1,
+                                                        const float* __restrict__ lam, const double* sc, int d,
+                                                        float2* __restrict__ E, unsigned int* amax) {
+  const long long nn = (long long)d * d;
+  const float lmax = (float)sc[6];
+  const float tau = kOaTau * lmax;
+  float m = 0.f, u = 0.f;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / d), j = (int)(e % d);
+    const float2 c = herm_entry(C1, d, i, j);
+    float2 r = make_float2(-c.x, -c.y);
+    float2 out;
+    if (i == j) {
+      out = make_float2(0.5f * (1.f - c.x), 0.f);
+    } else {
+      const float2 sij = herm_entry(S, d, i, j);
+      const float lj = lam[j], gap = lj - lam[i];
+      out = make_float2(0.5f * r.x, 0.5f * r.y);
+      if (fabsf(gap) > tau) {
+        const float2 q = make_float2((sij.x + lj * r.x) / gap, (sij.y + lj * r.y) / gap);
+        if (fmaxf(fabsf(q.x), fabsf(q.y)) <= 0.5f) out = q;
+        else u = fmaxf(u, fmaxf(fabsf(sij.x), fabsf(sij.y)) / lmax);
+      }
+    }
+    E[e] = out;
+    m = fmaxf(m, fmaxf(fabsf(out.x), fabsf(out.y)));
+  }
+  block_absmax_to(m, amax);
+  __syncthreads();
+  block_absmax_to(u, amax + 1);
+}
+
+__global__ void __launch_bounds__(256) k_add_to(float2* __restrict__ Q, const float2* __restrict__ D, long long nn) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += (long long)gridDim.x * blockDim.x) {
+    const float2 a = Q[e], b = D[e];
+    Q[e] = make_float2(a.x + b.x, a.y + b.y);
+  }
+}
+
+// planes of op(M) with the scale of M's own max (absmax_to into *amax first)
+cudaError_t planes_of(int d, const float2* M, int op, int np, void* P, int fmt, unsigned int* amax, double* sslot,
+                      bool fresh_amax, cudaStream_t s) {
+  cudaError_t e;
+  if (fresh_amax && (e = absmax_to((long long)d * d, M, amax, s)) != cudaSuccess) return e;
+  return tc_planes_op(d, M, op, np, P, fmt, amax, sslot, s);
+}
+
+}  // namespace
+
+size_t abs_p_tc_plane_bytes(int d) { return (size_t)4 * d * d * 2; }
+
+cudaError_t abs_p_tc_correction(int d, const void* Tb, const double* sT, AbsPWork<float>& w, double P, int fmt,
+                                unsigned int* err, cudaStream_t s) {
+  const long long nn = (long long)d * d;
+  float2* Q = w.V0;
+  unsigned int *amQ = w.amax, *amW = w.amax + 1, *amE = w.amax + 2;
+  double* sc = w.sc;
+  cudaError_t e;
+  // R = I - Q^dag Q and S = (Q^dag T) Q, both Hermitian (lower tiles)
+  if ((e = planes_of(d, Q, 1, 4, w.qa_h, fmt, amQ, sc + 1, true, s)) != cudaSuccess) return e;
+  if ((e = planes_of(d, Q, 1, 6, w.qb_h, fmt, amQ, sc + 3, false, s)) != cudaSuccess) return e;
+  if ((e = tc_product(d, w.qa_h, Tb, fmt, sc + 1, sT, w.W, false, err, s)) != cudaSuccess) return e;
+  if ((e = planes_of(d, w.W, 0, 4, w.wa, fmt, amW, sc + 4, true, s)) != cudaSuccess) return e;
+  if ((e = tc_product(d, w.wa, w.qb_h, fmt, sc + 4, sc + 3, w.A0, true, err, s)) != cudaSuccess) return e;
+  if ((e = tc_product(d, w.qa_h, w.qb_h, fmt, sc + 1, sc + 3, w.A1, true, err, s)) != cudaSuccess) return e;
+  k_oa_spectrum<<<1, 1024, 0, s>>>(w.A0, w.A1, d, P, 1e-7, w.lam, w.s, w.sp, sc);
+  if ((e = cudaMemsetAsync(amE, 0, 2 * sizeof(unsigned int), s)) != cudaSuccess) return e;
+  k_oa_correction<<<blocks_for(nn), 256, 0, s>>>(w.A0, w.A1, w.lam, sc, d, w.W, amE);
+  return cudaGetLastError();
+}
+
+cudaError_t abs_p_tc_update(int d, AbsPWork<float>& w, int fmt, unsigned int* err, cudaStream_t s) {
+  const long long nn = (long long)d * d;
+  float2* Q = w.V0;
+  cudaError_t e;
+  // Q <- Q + Q E (E in W, its max in amax[2])
+  if ((e = planes_of(d, w.W, 1, 6, w.eb, fmt, w.amax + 2, w.sc + 5, false, s)) != cudaSuccess) return e;
+  if ((e = planes_of(d, Q, 0, 4, w.qa_n, fmt, w.amax, w.sc + 0, false, s)) != cudaSuccess) return e;
+  if ((e = tc_product(d, w.qa_n, w.eb, fmt, w.sc + 0, w.sc + 5, w.V1, false, err, s)) != cudaSuccess) return e;
+  k_add_to<<<blocks_for(nn), 256, 0, s>>>(Q, w.V1, nn);
+  return cudaGetLastError();
+}
+
+cudaError_t abs_p_tc_finish(int d, AbsPWork<float>& w, int fmt, float2* X, unsigned int* err, cudaStream_t s) {
+  const long long nn = (long long)d * d;
+  float2* Q = w.V0;
+  double* sc = w.sc;
+  cudaError_t e;
+  // X = (Q diag(s)) Q^dag, lower tiles
+  k_scale_cols<float><<<blocks_for(nn), 256, 0, s>>>(Q, w.s, w.W, d);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = planes_of(d, w.W, 0, 4, w.wa, fmt, w.amax + 1, sc + 4, true, s)) != cudaSuccess) return e;
+  if ((e = planes_of(d, Q, 0, 6, w.qb_n, fmt, w.amax, sc + 2, true, s)) != cudaSuccess) return e;
+  if ((e = tc_product(d, w.wa, w.qb_n, fmt, sc + 4, sc + 2, X, true, err, s)) != cudaSuccess) return e;
+  w.A = w.A0;
+  w.Q = Q;
+  const int TS = d < 32 ? d : 32;
+  k_conj_transpose<float><<<dim3(d / TS, d / TS), 256, 0, s>>>(Q, w.Qh, d);
+  return cudaGetLastError();
+}
+
+cudaError_t abs_p_backward_tc(int d, const float2* G, AbsPWork<float>& w, int fmt, float2* Y, unsigned int* err,
+                              cudaStream_t s) {
+  const long long nn = (long long)d * d;
+  const float2* Q = w.Q;
+  float2* C = w.A0 == w.Q ? w.A1 : w.A0;
+  unsigned int *amQ = w.amax, *amW = w.amax + 1, *amE = w.amax + 2;
+  double* sc = w.sc;
+  cudaError_t e;
+  if ((e = planes_of(d, Q, 1, 4, w.qa_h, fmt, amQ, sc + 1, true, s)) != cudaSuccess) return e;
+  if ((e = planes_of(d, Q, 1, 6, w.qb_h, fmt, amQ, sc + 3, false, s)) != cudaSuccess) return e;
+  if ((e = planes_of(d, Q, 0, 4, w.qa_n, fmt, amQ, sc + 0, false, s)) != cudaSuccess) return e;
+  if ((e = planes_of(d, Q, 0, 6, w.qb_n, fmt, amQ, sc + 2, false, s)) != cudaSuccess) return e;
+  // C = (Q^dag G) Q
+  if ((e = planes_of(d, G, 1, 6, w.eb, fmt, amE, sc + 5, true, s)) != cudaSuccess) return e;
+  if ((e = tc_product(d, w.qa_h, w.eb, fmt, sc + 1, sc + 5, w.W, false, err, s)) != cudaSuccess) return e;
+  if ((e = planes_of(d, w.W, 0, 4, w.wa, fmt, amW, sc + 4, true, s)) != cudaSuccess) return e;
+  if ((e = tc_product(d, w.wa, w.qb_h, fmt, sc + 4, sc + 3, C, false, err, s)) != cudaSuccess) return e;
+  k_dk_scale<float><<<blocks_for(nn), 256, 0, s>>>(C, w.lam, w.s, w.sp, d, 1e-5f);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // Y = (Q C') Q^dag
+  if ((e = planes_of(d, C, 1, 6, w.eb, fmt, amE, sc + 5, true, s)) != cudaSuccess) return e;
+  if ((e = tc_product(d, w.qa_n, w.eb, fmt, sc + 0, sc + 5, w.W, false, err, s)) != cudaSuccess) return e;
+  if ((e = planes_of(d, w.W, 0, 4, w.wa, fmt, amW, sc + 4, true, s)) != cudaSuccess) return e;
+  return tc_product(d, w.wa, w.qb_n, fmt, sc + 4, sc + 2, Y, false, err, s);
+}
+
 template cudaError_t abs_p_forward<float>(int, const float2*, AbsPWork<float>&, int, bool, double, float2*,
                                           cudaStream_t);
 template cudaError_t abs_p_forward<double>(int, const double2*, AbsPWork<double>&, int, bool, double, double2*,

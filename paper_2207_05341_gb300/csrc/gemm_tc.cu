@@ -24,8 +24,9 @@
 // the small cross terms, so that the cross terms are not added into the large
 // running sum (the tensor core's FP32 accumulation truncates; keeping the chains
 // apart keeps that error on the large sum to the hi*hi steps alone).  Warp 0 lane 0 streams
-// operands with TMA (128B swizzle) into a 2-stage ring (96 KB per stage:
-// A_hi, A_lo, B_hi = [B1_hi; B2_hi], B_lo), warp 1 lane 0 issues tcgen05.mma
+// operands with TMA (64-byte swizzled rows of 32 K elements) into a 4-stage ring (48 KB per stage:
+// A_hi, A_lo, B_hi = [B1_hi; B2_hi], B_lo; three stages stay in flight, which covers the L2 latency
+// that a 2-stage ring of 96 KB stages left exposed), warp 1 lane 0 issues tcgen05.mma
 // (M = 128, N = 256, K = 16) and commits each stage back to the producer; all
 // four warps then read TMEM (tcgen05.ld 32x32b) and store the tile.  Every
 // mbarrier wait is bounded: on timeout the kernel raises an error flag, drains
@@ -43,9 +44,11 @@ namespace {
 
 constexpr int kBM = 128;              // output rows per tile
 constexpr int kBN = 128;              // complex output columns per tile (N = 256 reals)
-constexpr int kBK = 64;               // K elements per stage (128 bytes of BF16)
-constexpr int kStages = 2;
-constexpr int kTileBytes = 128 * kBK * 2;        // one 128-row x 64-col BF16 box: 16 KB
+constexpr int kBK = 32;               // K elements per stage (64 bytes of 16-bit operand per row)
+constexpr int kStages = 4;            // 3 stages in flight while the MMA warp consumes the fourth
+constexpr int kRowBytes = kBK * 2;    // one row of a box: the swizzle span (64 B)
+static_assert(kRowBytes == 64 || kRowBytes == 128, "64- or 128-byte swizzled rows");
+constexpr int kTileBytes = 128 * kBK * 2;        // one 128-row x 32-col 16-bit box: 8 KB
 constexpr int kStageBytes = 6 * kTileBytes;      // 96 KB
 constexpr int kTmemCols = 512;   // two 128 x 256 FP32 accumulators: hi*hi, and hi*lo + lo*hi
 constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
@@ -97,14 +100,14 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of 1024 bytes.
+// Shared-memory matrix descriptor: K-major, swizzled rows of kRowBytes, 8-row atoms of 8 kRowBytes bytes.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr & 0x3FFFFu) >> 4);        // start address
   d |= (uint64_t)1 << 16;                           // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset: one 8-row atom
+  d |= (uint64_t)((8 * kRowBytes) >> 4) << 32;      // stride byte offset: one 8-row atom
   d |= (uint64_t)1 << 46;                           // descriptor version
-  d |= (uint64_t)2 << 61;                           // 128-byte swizzle
+  d |= (uint64_t)(kRowBytes == 128 ? 2 : 4) << 61;  // 128- or 64-byte swizzle
   return d;
 }
 
@@ -404,6 +407,54 @@ __global__ void __launch_bounds__(256) k_hermitian_planes(const float* __restric
   for (int p = 0; p < 6; ++p) *reinterpret_cast<uint4*>(P + p * nn + idx) = pk[p].v;
 }
 
+// Largest |re|, |im| of n complex entries folded into *amax (float bits; the slot is cleared before).
+__global__ void __launch_bounds__(256) k_amax(const float2* __restrict__ M, long long n, unsigned int* amax) {
+  float m = 0.f;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float2 v = M[i];
+    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+  block_absmax_to(m, amax);
+}
+
+// 16-bit hi / lo planes of s * Z for a general product operand, Z = M (op 0) or M^dag (op 1), d x d
+// row-major: 4 planes (re, im; hi then lo: the left operand A of C = A B) or 6 planes (re, im, -im; hi
+// then lo: the right operand given as B^dag, which k_tc_cgemm reads row by row).  s = split_scale(amax),
+// written to *s_slot.  One CTA per 32 x 32 tile of Z; the transpose goes through shared memory.
+template <class H>
+__global__ void __launch_bounds__(256) k_planes_op(const float2* __restrict__ M, int d, int op, int six,
+                                                    H* __restrict__ P, const unsigned int* amax, double* s_slot) {
+  __shared__ float2 tile[32][33];
+  const double sd = split_scale(amax);
+  const float sc = (float)sd;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *s_slot = sd;
+  const long long nn = (long long)d * d;
+  const int bi = blockIdx.y, bj = blockIdx.x;  // tile (bi, bj) of Z
+  // Z tile (bi, bj) = M tile (bi, bj) (op 0) or the conjugate transpose of M tile (bj, bi) (op 1)
+  const int si = op ? bj : bi, sj = op ? bi : bj;
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    const int r = e >> 5, c = e & 31;
+    tile[r][c] = M[(long long)(si * 32 + r) * d + sj * 32 + c];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    const int r = e >> 5, c = e & 31;
+    float2 z = op ? tile[c][r] : tile[r][c];
+    if (op) z.y = -z.y;
+    const long long o = (long long)(bi * 32 + r) * d + bj * 32 + c;
+    H rh, rl, ih, il;
+    hi_lo(sc * z.x, rh, rl);
+    hi_lo(sc * z.y, ih, il);
+    if (six) {
+      H nh, nl;
+      hi_lo(-(sc * z.y), nh, nl);
+      P[o] = rh; P[nn + o] = ih; P[2 * nn + o] = nh; P[3 * nn + o] = rl; P[4 * nn + o] = il; P[5 * nn + o] = nl;
+    } else {
+      P[o] = rh; P[nn + o] = ih; P[2 * nn + o] = rl; P[3 * nn + o] = il;
+    }
+  }
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -422,7 +473,7 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 2-D map over one d x d BF16 plane, box 64 columns x 128 rows, 128-byte swizzle.
+// 2-D map over one d x d 16-bit plane, box kBK columns x 128 rows, rows swizzled over kRowBytes.
 bool make_plane_map(CUtensorMap* m, const void* plane, int d, int fmt) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
@@ -432,7 +483,8 @@ bool make_plane_map(CUtensorMap* m, const void* plane, int d, int fmt) {
   cuuint32_t estr[2] = {1u, 1u};
   return enc(m, fmt == TC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
              const_cast<void*>(plane), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, kRowBytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -526,6 +578,36 @@ cudaError_t tc_herm_square(int d, const void* Tb, int fmt, const double* scal, f
   cudaError_t e = build_maps(&M, d, Tb, 1, Tb, fmt);
   if (e != cudaSuccess) return e;
   return launch_tc(M, X, d, true, fmt, scal + kScaleT, scal + kScaleT, err, clear, s);
+}
+
+cudaError_t absmax_to(long long n, const float2* M, unsigned int* amax, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 1184) blocks = 1184;
+  k_amax<<<(unsigned)blocks, 256, 0, s>>>(M, n, amax);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_planes_op(int d, const float2* M, int op, int nplanes, void* P, int fmt, const unsigned int* amax,
+                         double* s_slot, cudaStream_t s) {
+  if (d < 32 || d % 32 || (nplanes != 4 && nplanes != 6)) return cudaErrorInvalidValue;
+  const dim3 grid(d / 32, d / 32);
+  const int six = nplanes == 6 ? 1 : 0;
+  if (fmt == TC_BF16)
+    k_planes_op<__nv_bfloat16><<<grid, 256, 0, s>>>(M, d, op, six, (__nv_bfloat16*)P, nullptr, s_slot);
+  else
+    k_planes_op<__half><<<grid, 256, 0, s>>>(M, d, op, six, (__half*)P, amax, s_slot);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_product(int d, const void* Ab, const void* Bb, int fmt, const double* sA, const double* sB, float2* C,
+                       bool lower, unsigned int* err, cudaStream_t s) {
+  if (d < 128 || d % 128) return cudaErrorInvalidValue;
+  TcMaps M;
+  cudaError_t e = build_maps(&M, d, Ab, 0, Bb, fmt);
+  if (e != cudaSuccess) return e;
+  return launch_tc(M, C, d, lower, fmt, sA, sB, err, nullptr, s);
 }
 
 cudaError_t tc_gt_product(int d, const void* Gb, const void* Tb, int fmt, const double* scal, float2* Y,

@@ -280,7 +280,30 @@ template <class R> struct AbsPWork {
   cx_t<R> *W, *Qh;             // scratch, Q^dag
   R *lam, *s, *sp;             // eigenvalues, |lambda|^P, derivative
   cx_t<R> *A, *Q;              // set by abs_p_forward: diagonalised matrix, eigenvectors
+  // tensor-core refinement (eigh_tc.cu; QST_MIXED / QST_MIXED_BF16): 16-bit operand planes of Q (4 planes
+  // of Q and of Q^dag, 6 planes of Q and of Q^dag), of an intermediate W (4) and of a right operand (6),
+  // max slots and scales
+  void *qa_n, *qa_h, *qb_n, *qb_h, *wa, *eb;
+  unsigned int* amax;          // [0] Q, [1] W, [2] right operand, [3] unresolved size of a refinement
+  double* sc;                  // scales of qa_n, qa_h, qb_n, qb_h, wa, eb; [6] max |lambda|, [7] refinement size
 };
+// Warm-started refinement of the eigenvectors in w.V0 for the Hermitian T (6 planes Tb with scale *sT) on
+// tensor cores, Ogita and Aishima's iteration:
+//   R = I - Q^dag Q,  S = Q^dag T Q,  lambda_i = S_ii / (1 - R_ii),
+//   E_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i)  (well separated i != j),  E_ij = R_ij / 2 otherwise,
+//   Q <- Q + Q E.
+// abs_p_tc_correction: lambda, |lambda|^P and its derivative, and E (in w.W, max |E| in w.amax[2], and in
+// amax[3] max |S_ij| / max |lambda| over the separated pairs too far apart for a first-order correction);
+// abs_p_tc_update: Q <- Q + Q E; abs_p_tc_finish: X = Q |Lambda|^P Q^dag (lower tiles) and Q^dag.
+// A timed-out wait of a product ORs into *err.
+cudaError_t abs_p_tc_correction(int d, const void* Tb, const double* sT, AbsPWork<float>& w, double P, int fmt,
+                                unsigned int* err, cudaStream_t s);
+cudaError_t abs_p_tc_update(int d, AbsPWork<float>& w, int fmt, unsigned int* err, cudaStream_t s);
+cudaError_t abs_p_tc_finish(int d, AbsPWork<float>& w, int fmt, float2* X, unsigned int* err, cudaStream_t s);
+// The backward of abs_p_forward (either form) with the products on tensor cores: Y with Y + Y^dag = dL/dT.
+cudaError_t abs_p_backward_tc(int d, const float2* G, AbsPWork<float>& w, int fmt, float2* Y, unsigned int* err,
+                              cudaStream_t s);
+size_t abs_p_tc_plane_bytes(int d);  // bytes of one 4-plane buffer (a 6-plane one is 1.5 times that)
 // X = Q |Lambda|^P Q^dag (lower tiles) from T via `sweeps` (even) Jacobi sweeps; warm == true starts
 // from the previous eigenvectors (V0, with Q^dag in Qh).  Leaves Q in V0 and Q^dag in Qh.
 template <class R> cudaError_t abs_p_forward(int d, const cx_t<R>* T, AbsPWork<R>& w, int sweeps, bool warm,
@@ -328,6 +351,16 @@ cudaError_t tc_herm_square(int d, const void* Tb, int fmt, const double* scal, f
 cudaError_t tc_gt_product(int d, const void* Gb, const void* Tb, int fmt, const double* scal, float2* Y,
                           unsigned int* err, unsigned int* clear, cudaStream_t s);
 bool tc_available();
+// General products on the same kernel: C = A B (lower: 128 x 128 tiles I >= J only) from the 4 planes of A
+// (re, im; hi then lo) and the 6 planes of B^dag (re, im, -im; hi then lo), with their scales sA, sB.
+cudaError_t tc_product(int d, const void* Ab, const void* Bb, int fmt, const double* sA, const double* sB, float2* C,
+                       bool lower, unsigned int* err, cudaStream_t s);
+// Planes of op(M) (op 0: M, 1: M^dag), nplanes 4 or 6 as above, scaled by the power of two that brings *amax
+// into [1, 2) (TC_FP16_SCALED; 1 for TC_BF16), the scale written to *s_slot.  d a multiple of 32.
+cudaError_t tc_planes_op(int d, const float2* M, int op, int nplanes, void* P, int fmt, const unsigned int* amax,
+                         double* s_slot, cudaStream_t s);
+// *amax = the largest |re|, |im| of n complex entries (float bits; the slot is cleared first)
+cudaError_t absmax_to(long long n, const float2* M, unsigned int* amax, cudaStream_t s);
 
 // ---- synthetic data on the GPU (sampler.cu) ----
 // rho = w |psi><psi| + (1 - w) I / d for the test state `kind` (QST_STATE_*), d x d complex.

@@ -119,6 +119,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "qst_get_state": (i, [vp, vp, sz]),
         "qst_set_state": (i, [vp, vp, sz]),
         "qst_iterations": (ctypes.c_longlong, [vp]),
+        "qst_eig_counts": (i, [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), pd]),
         "qst_kernel_launches": (ctypes.c_longlong, [vp]),
         "qst_sync": (i, [vp]),
         "qst_strerror": (ctypes.c_char_p, [i]),
@@ -347,6 +348,15 @@ QST_INJECT_WPASS_LOADS = 2
 def qst_inject_wait_timeout(what: int, count: int = 1) -> None:
     """Testing hook: the next `count` launches of a kernel kind issue no operand copies (see qst.h)."""
     _check(load().qst_inject_wait_timeout(int(what), int(count)), "qst_inject_wait_timeout")
+
+
+def qst_eig_counts(ctx: int, last: bool = False):
+    """(tensor-core refinements taken, steps handed to Jacobi sweeps) of a mixed A_P context; with
+    last=True also the latest refinement's (largest correction, unresolved coupling)."""
+    a, b = ctypes.c_longlong(), ctypes.c_longlong()
+    v = (ctypes.c_double * 2)()
+    _check(load().qst_eig_counts(ctx, ctypes.byref(a), ctypes.byref(b), v), "qst_eig_counts")
+    return (a.value, b.value, (v[0], v[1])) if last else (a.value, b.value)
 
 
 def qst_get_tuning() -> dict:

@@ -81,7 +81,7 @@ def test_option_validation_before_any_device_call(lib):
     assert status(2, network=qst.QST_NET_CNN) == qst.QST_E_INVAL  # 2^(N-3)-square pooling windows
     assert status(5, network=7) == qst.QST_E_INVAL
     assert status(8, mapping=qst.QST_MAP_CHOL_DELTA, precision=qst.QST_MIXED) == qst.QST_E_UNSUPPORTED
-    assert status(8, mapping=qst.QST_MAP_ABS_P, precision=qst.QST_MIXED) == qst.QST_E_UNSUPPORTED
+    assert status(6, mapping=qst.QST_MAP_ABS_P, precision=qst.QST_MIXED) == qst.QST_E_UNSUPPORTED
     assert status(4, mapping=qst.QST_MAP_ABS_P, P=0.0) == qst.QST_E_INVAL
     assert status(6, precision=qst.QST_MIXED) == qst.QST_E_UNSUPPORTED  # the tensor-core path starts at N = 7
     assert status(11, precision=qst.QST_FP64) == qst.QST_E_INVAL  # FP64 contexts stop at N = 10

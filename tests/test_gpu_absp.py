@@ -1,6 +1,7 @@
 """GPU parity of the P-order absolute projection (Sec. 3.2 eq. abs_P) against the oracle.
 
-The eigendecomposition is a Jacobi method run for a fixed number of sweeps; after
+The eigendecomposition is a Jacobi method run for a fixed number of sweeps (the mixed-precision
+path refines the previous eigenvectors on tensor cores from its second step on); after
 10 sweeps it has converged to rounding level for these sizes, so the FP64 path
 is held to 1e-8 and the FP32 path to 1e-4 on the loss and 2e-3 (normwise) on
 the gradient, whose Daleckii-Krein factors divide by eigenvalue gaps.  N = 8 and
@@ -58,7 +59,8 @@ def _gpu(N, theta, f, opt):
 
 CASES = [(qst.QST_FP64, N, P) for N in (1, 2, 4, 6) for P in (0.5, 1.5, 2.0, 4.0)] + \
         [(qst.QST_FP32, N, P) for N in (3, 6) for P in (1.0, 2.0, 3.0)] + \
-        [(prec, N, 1.5) for prec in (qst.QST_FP64, qst.QST_FP32) for N in (8, 10)]
+        [(prec, N, 1.5) for prec in (qst.QST_FP64, qst.QST_FP32) for N in (8, 10)] + \
+        [(qst.QST_MIXED, N, P) for N in (7, 9) for P in (1.5, 3.0)]
 
 
 @pytest.mark.parametrize("prec,N,P", CASES)
@@ -68,7 +70,7 @@ def test_abs_p_loss_grad_parity(prec, N, P):
     L_ref, g_ref, _ = O.loss_and_grad(theta.astype(dt).astype(np.float64), f.astype(dt).astype(np.float64), M, N,
                                       mapping="abs_p", P=P)
     L, g = _gpu(N, theta, f, _opt(prec, P=P))
-    tl, tg = (1e-8, 1e-8) if prec == qst.QST_FP64 else (1e-4, 2e-3)
+    tl, tg = (1e-8, 1e-8) if prec == qst.QST_FP64 else (1e-4, 2e-3)  # mixed: products on tensor cores
     rl = abs(L - L_ref) / abs(L_ref)
     rg = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
     assert rl <= tl and rg < tg, (rl, rg)
@@ -103,10 +105,46 @@ def test_abs_p_reconstruction_matches_oracle():
     assert abs(F - F_ref) < 1e-6, (F, F_ref)
 
 
-def test_abs_p_rejected_for_mixed_precision():
-    with pytest.raises(qst.QstError) as e:
-        qst.qst_init(8, opt=_opt(qst.QST_MIXED, P=1.5))
-    assert e.value.status == qst.QST_E_UNSUPPORTED
+@pytest.mark.parametrize("N,P,k,lr", [(7, 1.5, 6, 1e-7), (8, 3.0, 6, 1e-7), (10, 1.5, 3, 1e-7),
+                                      (7, 1.5, 4, 1e-3), (9, 1.5, 3, 1e-3)])
+def test_mixed_warm_steps_follow_the_oracle(N, P, k, lr):
+    """QST_MIXED: warm-started steps refine the previous eigenvectors on tensor cores, or hand the step to
+    Jacobi sweeps when T moved too far for a first-order correction.  Every step's loss is the oracle's
+    (exact FP64 eigendecomposition) at the parameters the GPU held before it, and every parameter the
+    step moved went against the sign of the oracle's gradient wherever that gradient is not small.
+    With steps of 1e-7, T moves little and the refinement is taken; with the paper's 1e-3 the steps after
+    the first move T too far and go to the sweeps."""
+    f, theta = _problem(N, 300 + N)
+    opt = _opt(qst.QST_MIXED, P=P)
+    opt.lr = lr
+    opt.step_min = min(opt.step_min, lr)
+    ctx = qst.qst_init(N, opt=opt)
+    try:
+        qst.qst_set_params(ctx, theta.astype(np.float32))
+        fd = torch.from_numpy(f.astype(np.float32)).cuda()
+        f64 = f.astype(np.float32).astype(np.float64)
+        out = torch.empty(theta.size, device="cuda")
+        qst.qst_get_params(ctx, out)
+        th = out.cpu().numpy().astype(np.float64)
+        for it in range(k):
+            L, _ = qst.qst_step(ctx, fd)
+            qst.qst_get_params(ctx, out)
+            th1 = out.cpu().numpy().astype(np.float64)
+            L_ref, g_ref, _ = O.loss_and_grad(th, f64, M, N, mapping="abs_p", P=P)
+            assert abs(L - L_ref) <= 1e-4 * abs(L_ref), (it, L, L_ref)
+            moved = th1 != th
+            big = np.abs(g_ref) > 1e-2 * np.abs(g_ref).max()
+            sel = moved & big
+            assert sel.sum() > 0
+            assert np.all(np.sign(th1[sel] - th[sel]) == -np.sign(g_ref[sel])), it
+            th = th1
+        refinements, fallbacks = qst.qst_eig_counts(ctx)
+        if lr < 1e-6:
+            assert refinements >= k - 1 and fallbacks == 0, (refinements, fallbacks)
+        else:
+            assert fallbacks >= 1, (refinements, fallbacks)
+    finally:
+        qst.qst_destroy(ctx)
 
 
 def _steps(N, theta, f, opt, k):
