@@ -407,6 +407,73 @@ __global__ void __launch_bounds__(256) k_hermitian_planes(const float* __restric
   for (int p = 0; p < 6; ++p) *reinterpret_cast<uint4*>(P + p * nn + idx) = pk[p].v;
 }
 
+// The same planes from 64 x 64 tile pairs (d a multiple of 64): every plane row segment a thread group
+// writes is 128 bytes, a whole L2 line (the 32 x 32 form writes half lines).  Threads 0-127 write tile
+// (I, J), 128-255 tile (J, I); each thread 8 adjacent columns of 4 rows.
+template <class H>
+__global__ void __launch_bounds__(256) k_hermitian_planes64(const float* __restrict__ t, int d, H* __restrict__ P,
+                                                             const unsigned int* amax, double* s_slot,
+                                                             const void* const* tab) {
+  rebind(tab, t, P, amax, s_slot);
+  __shared__ float Ra[64][65];
+  __shared__ float Rb[64][65];
+  const double sd = split_scale(amax);
+  const float sc = (float)sd;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *s_slot = sd;
+  const long long nn = (long long)d * d;
+  int I, J;
+  tri_decode(blockIdx.x, I, J);
+  const int tid = threadIdx.x;
+  {
+    float4 a[4], b[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {  // 1024 float4 per tile: row q >> 4, columns 4 (q & 15) ..
+      const int q = tid + 256 * k, row = q >> 4, col = (q & 15) * 4;
+      a[k] = *reinterpret_cast<const float4*>(t + (long long)(I * 64 + row) * d + J * 64 + col);
+      b[k] = I != J ? *reinterpret_cast<const float4*>(t + (long long)(J * 64 + row) * d + I * 64 + col)
+                    : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int q = tid + 256 * k, row = q >> 4, col = (q & 15) * 4;
+      Ra[row][col] = a[k].x; Ra[row][col + 1] = a[k].y; Ra[row][col + 2] = a[k].z; Ra[row][col + 3] = a[k].w;
+      Rb[row][col] = b[k].x; Rb[row][col + 1] = b[k].y; Rb[row][col + 2] = b[k].z; Rb[row][col + 3] = b[k].w;
+    }
+  }
+  __syncthreads();
+  const bool upper = tid >= 128;
+  if (upper && I == J) return;
+  union Pack {
+    uint4 v;
+    H h[8];
+  };
+  const int c = (tid & 7) * 8;
+#pragma unroll 1
+  for (int k = 0; k < 4; ++k) {
+    const int r = ((tid & 127) >> 3) + 16 * k;
+    float re[8], im[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int cc = c + u;
+      if (upper) { re[u] = Ra[cc][r]; im[u] = -Rb[r][cc]; }  // T[J 64 + r][I 64 + cc] = conj T[I 64 + cc][J 64 + r]
+      else if (I != J) { re[u] = Ra[r][cc]; im[u] = Rb[cc][r]; }
+      else if (r > cc) { re[u] = Ra[r][cc]; im[u] = Ra[cc][r]; }
+      else if (r < cc) { re[u] = Ra[cc][r]; im[u] = -Ra[r][cc]; }
+      else { re[u] = Ra[r][r]; im[u] = 0.f; }
+    }
+    Pack pk[6];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      hi_lo(sc * re[u], pk[0].h[u], pk[3].h[u]);
+      hi_lo(sc * im[u], pk[1].h[u], pk[4].h[u]);
+      hi_lo(-(sc * im[u]), pk[2].h[u], pk[5].h[u]);
+    }
+    const long long idx = upper ? (long long)(J * 64 + r) * d + I * 64 + c : (long long)(I * 64 + r) * d + J * 64 + c;
+#pragma unroll
+    for (int p = 0; p < 6; ++p) *reinterpret_cast<uint4*>(P + p * nn + idx) = pk[p].v;
+  }
+}
+
 // Largest |re|, |im| of n complex entries folded into *amax (float bits; the slot is cleared before).
 __global__ void __launch_bounds__(256) k_amax(const float2* __restrict__ M, long long n, unsigned int* amax) {
   float m = 0.f;
@@ -541,11 +608,22 @@ bool tc_available() {
 cudaError_t tc_planes_T(int d, const float* t, void* Tb, int fmt, double* scal, const unsigned int* amax,
                         cudaStream_t s) {
   if (d < 32 || d % 32) return cudaErrorInvalidValue;
-  const int nt = d / 32;
-  const unsigned pairs = (unsigned)(nt * (nt + 1) / 2);
   const unsigned int* am = fmt == TC_BF16 ? nullptr : amax;
   BatchArgs ba;
   if (batch_take(ba, {t, Tb, am, scal + kScaleT})) return cudaSuccess;
+  if (d % 64 == 0) {
+    const int n64 = d / 64;
+    const unsigned p64 = (unsigned)(n64 * (n64 + 1) / 2);
+    if (fmt == TC_BF16)
+      k_hermitian_planes64<__nv_bfloat16><<<dim3(p64, 1, ba.nz), 256, 0, s>>>(t, d, (__nv_bfloat16*)Tb, am,
+                                                                              scal + kScaleT, ba.tab);
+    else
+      k_hermitian_planes64<__half><<<dim3(p64, 1, ba.nz), 256, 0, s>>>(t, d, (__half*)Tb, am, scal + kScaleT,
+                                                                       ba.tab);
+    return cudaGetLastError();
+  }
+  const int nt = d / 32;
+  const unsigned pairs = (unsigned)(nt * (nt + 1) / 2);
   if (fmt == TC_BF16)
     k_hermitian_planes<__nv_bfloat16><<<dim3(pairs, 1, ba.nz), 256, 0, s>>>(t, d, (__nv_bfloat16*)Tb, am,
                                                                             scal + kScaleT, ba.tab);
