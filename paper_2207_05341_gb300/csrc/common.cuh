@@ -165,6 +165,10 @@ __device__ __forceinline__ void block_absmax_to(float m, unsigned int* amax) {
   }
 }
 
+// Programmatic dependent launch: wait until the previous kernel on the stream has completed and its
+// writes are visible (a no-op when the kernel was launched without the attribute).
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // A tensor map that host code copied into global memory: order the copy before this thread's next use
 // of the map by the tensor-map proxy (TMA).
 __device__ __forceinline__ void tensormap_acquire(const void* map) {

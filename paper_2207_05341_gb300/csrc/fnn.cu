@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(256) k_layer2(const R* __restrict__ theta, con
                                                  R* __restrict__ t, unsigned int* amax, const void* const* tab) {
   __shared__ R hs[H];
   rebind(tab, theta, hid, t, amax);
+  grid_dep_wait();
   if (threadIdx.x < H) hs[threadIdx.x] = hid[threadIdx.x];
   __syncthreads();
   using VV = Vec<R>;
@@ -372,6 +373,7 @@ __global__ void __launch_bounds__(256) k_symmetrize(const cx_t<R>* __restrict__ 
                                                      const void* const* tab) {
   __shared__ R Ar[32][33], Ai[32][33], Br[32][33], Bi[32][33];
   rebind(tab, Y, dt);
+  grid_dep_wait();
   const int TS = d < 32 ? d : 32;
   int I, J;
   tri_decode(blockIdx.x, I, J);
@@ -536,8 +538,11 @@ cudaError_t net_build_T(const Dims& D, const R* theta, const R* hid, R* t, cx_t<
     }();
     const long long grid = want < (long long)per_sm * sms ? want : (long long)per_sm * sms;
     BatchArgs ba;
-    if (!batch_take(ba, {theta, hid, t, amax}))
-      k_layer2<R, HH><<<dim3((unsigned)grid, 1, ba.nz), 256, 0, s>>>(theta, hid, D.n, t, amax, ba.tab);
+    if (!batch_take(ba, {theta, hid, t, amax})) {
+      cudaError_t e = launch_dep(k_layer2<R, HH>, dim3((unsigned)grid, 1, ba.nz), dim3(256), 0, s, theta, hid, D.n, t,
+                                 amax, ba.tab);
+      if (e != cudaSuccess) return e;
+    }
   });
   if (!T) return cudaGetLastError();
   return net_hermitian_T<R>(D, t, T, Tt, s);
@@ -593,8 +598,8 @@ template <class R> cudaError_t net_symmetrize(const Dims& D, const cx_t<R>* Y, R
   const int nt = D.d / TS;
   BatchArgs ba;
   if (batch_take(ba, {Y, dt})) return cudaSuccess;
-  k_symmetrize<R><<<dim3((unsigned)(nt * (nt + 1) / 2), 1, ba.nz), 256, 0, s>>>(Y, dt, D.d, ba.tab);
-  return cudaGetLastError();
+  return launch_dep(k_symmetrize<R>, dim3((unsigned)(nt * (nt + 1) / 2), 1, ba.nz), dim3(256), 0, s, Y, dt, D.d,
+                    ba.tab);
 }
 
 template <class R> cudaError_t net_tri_grad(const Dims& D, const cx_t<R>* Z, R* dt, cudaStream_t s) {

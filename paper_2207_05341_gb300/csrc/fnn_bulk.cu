@@ -166,6 +166,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_wpass_bulk(const __gri
   using S = Stage<H, W2>;
   const WMaps* mp = &maps;
   rebind(tab, mp, theta, step, vec, hidv, pre, dpre_io, pre_out, hid_out, scal, partials, counter, flags);
+  grid_dep_wait();
   extern __shared__ __align__(128) uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((128u - (s_u32(smem_raw) & 127u)) & 127u);  // 128-byte aligned ring
   constexpr int kStages = S::kStages;
@@ -452,11 +453,9 @@ template <int H, bool W2> cudaError_t launch_bulk(float* theta, float* step, con
                  sizeof(WMaps)))
     return cudaSuccess;
   const int no_loads = inject_take(INJ_WPASS_LOADS) ? 1 : 0;
-  k_wpass_bulk<H, W2><<<dim3((unsigned)grid, 1, ba.nz), kThreads, smem, s>>>(maps, theta, step, vec, hid, pre, dpre,
-                                                                             pre_out, hid_out, scal, n, ob2, ob1,
-                                                                             partials, counter, flags, rc, slope,
-                                                                             no_loads, ba.tab);
-  return cudaGetLastError();
+  return launch_dep(k_wpass_bulk<H, W2>, dim3((unsigned)grid, 1, ba.nz), dim3(kThreads), (size_t)smem, s, maps, theta,
+                    step, vec, hid, pre, dpre, pre_out, hid_out, scal, n, ob2, ob1, partials, counter, flags, rc,
+                    slope, no_loads, ba.tab);
 }
 
 }  // namespace

@@ -146,6 +146,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_cgemm(const __grid_constant__ TcM
                                                       int no_loads, const void* const* tab) {
   const TcMaps* mp = &maps;
   rebind(tab, mp, C, sA, sB, err, clear);
+  grid_dep_wait();
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
@@ -323,6 +324,7 @@ template <class H>
 __global__ void __launch_bounds__(256) k_split(const float2* __restrict__ A, H* __restrict__ P, long long nn,
                                                 const unsigned int* amax, double* s_slot, const void* const* tab) {
   rebind(tab, A, P, amax, s_slot);
+  grid_dep_wait();
   const double sd = split_scale(amax);
   const float sc = (float)sd;
   if (blockIdx.x == 0 && threadIdx.x == 0) *s_slot = sd;
@@ -415,6 +417,7 @@ __global__ void __launch_bounds__(256) k_hermitian_planes64(const float* __restr
                                                              const unsigned int* amax, double* s_slot,
                                                              const void* const* tab) {
   rebind(tab, t, P, amax, s_slot);
+  grid_dep_wait();
   __shared__ float Ra[64][65];
   __shared__ float Rb[64][65];
   const double sd = split_scale(amax);
@@ -583,13 +586,11 @@ cudaError_t launch_tc(const TcMaps& M, float2* C, int d, bool lower, int fmt, co
   if (batch_take(ba, {C, sA, sB, err, clear}, &M, sizeof(TcMaps))) return cudaSuccess;
   const int no_loads = inject_take(INJ_TC_LOADS) ? 1 : 0;
   if (lower) {
-    k_tc_cgemm<<<dim3((unsigned)(nt * (nt + 1) / 2), 1, ba.nz), 128, kSmemBytes, s>>>(M, C, d, 1, make_idesc(fmt), sA,
-                                                                                      sB, err, clear, no_loads, ba.tab);
-  } else {
-    k_tc_cgemm<<<dim3(nt, nt, ba.nz), 128, kSmemBytes, s>>>(M, C, d, 0, make_idesc(fmt), sA, sB, err, clear, no_loads,
-                                                            ba.tab);
+    return launch_dep(k_tc_cgemm, dim3((unsigned)(nt * (nt + 1) / 2), 1, ba.nz), dim3(128), (size_t)kSmemBytes, s, M,
+                      C, d, 1, make_idesc(fmt), sA, sB, err, clear, no_loads, ba.tab);
   }
-  return cudaGetLastError();
+  return launch_dep(k_tc_cgemm, dim3(nt, nt, ba.nz), dim3(128), (size_t)kSmemBytes, s, M, C, d, 0, make_idesc(fmt), sA,
+                    sB, err, clear, no_loads, ba.tab);
 }
 
 }  // namespace
@@ -615,12 +616,10 @@ cudaError_t tc_planes_T(int d, const float* t, void* Tb, int fmt, double* scal, 
     const int n64 = d / 64;
     const unsigned p64 = (unsigned)(n64 * (n64 + 1) / 2);
     if (fmt == TC_BF16)
-      k_hermitian_planes64<__nv_bfloat16><<<dim3(p64, 1, ba.nz), 256, 0, s>>>(t, d, (__nv_bfloat16*)Tb, am,
-                                                                              scal + kScaleT, ba.tab);
-    else
-      k_hermitian_planes64<__half><<<dim3(p64, 1, ba.nz), 256, 0, s>>>(t, d, (__half*)Tb, am, scal + kScaleT,
-                                                                       ba.tab);
-    return cudaGetLastError();
+      return launch_dep(k_hermitian_planes64<__nv_bfloat16>, dim3(p64, 1, ba.nz), dim3(256), 0, s, t, d,
+                        (__nv_bfloat16*)Tb, am, scal + kScaleT, ba.tab);
+    return launch_dep(k_hermitian_planes64<__half>, dim3(p64, 1, ba.nz), dim3(256), 0, s, t, d, (__half*)Tb, am,
+                      scal + kScaleT, ba.tab);
   }
   const int nt = d / 32;
   const unsigned pairs = (unsigned)(nt * (nt + 1) / 2);
@@ -642,10 +641,10 @@ cudaError_t tc_split_G(int d, const float2* G, void* Gb, int fmt, double* scal, 
   BatchArgs ba;
   if (batch_take(ba, {G, Gb, am, scal + kScaleG})) return cudaSuccess;
   if (fmt == TC_BF16)
-    k_split<__nv_bfloat16><<<dim3((unsigned)blocks, 1, ba.nz), 256, 0, s>>>(G, (__nv_bfloat16*)Gb, nn, am,
-                                                                            scal + kScaleG, ba.tab);
-  else
-    k_split<__half><<<dim3((unsigned)blocks, 1, ba.nz), 256, 0, s>>>(G, (__half*)Gb, nn, am, scal + kScaleG, ba.tab);
+    return launch_dep(k_split<__nv_bfloat16>, dim3((unsigned)blocks, 1, ba.nz), dim3(256), 0, s, G,
+                      (__nv_bfloat16*)Gb, nn, am, scal + kScaleG, ba.tab);
+  return launch_dep(k_split<__half>, dim3((unsigned)blocks, 1, ba.nz), dim3(256), 0, s, G, (__half*)Gb, nn, am,
+                    scal + kScaleG, ba.tab);
   return cudaGetLastError();
 }
 

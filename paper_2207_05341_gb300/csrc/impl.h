@@ -43,6 +43,24 @@ struct BatchArgs {
 bool batch_take(BatchArgs& ba, std::initializer_list<const void*> ptrs, const void* blob = nullptr,
                 size_t blob_bytes = 0);
 
+// Launch with programmatic stream serialisation: the kernel's CTAs may start while the previous kernel
+// on the stream drains (its launch and prologue then overlap that tail); the kernel calls
+// grid_dep_wait() before its first access to global memory.
+template <class... KArgs, class... Args>
+cudaError_t launch_dep(void (*fn)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, fn, static_cast<KArgs>(args)...);
+}
+
 // Process-wide launch parameters (qst_set_tuning; defaults in tuned.h).
 struct Tuning {
   int bulk_chunks_per_cta;  // least 256-column chunks per CTA of a bulk weight pass (fixes its partition)

@@ -384,6 +384,7 @@ __global__ void __launch_bounds__(256) k_trace(const cx_t<R>* __restrict__ X, in
                                                 const void* const* tab) {
   __shared__ double red[8];
   rebind(tab, X, scal);
+  grid_dep_wait();
   // every diagonal load of a thread is issued before the first add (one memory latency, not d / 256)
   constexpr int kPer = 16;  // d <= 4096 = 16 x 256
   R v[kPer];
@@ -489,8 +490,7 @@ template <class R> cudaError_t trace_X(const Dims& D, const cx_t<R>* X, double* 
   if (D.d > 4096) return cudaErrorInvalidValue;
   BatchArgs ba;
   if (batch_take(ba, {X, scal})) return cudaSuccess;
-  k_trace<R><<<dim3(1, 1, ba.nz), 256, 0, s>>>(X, D.d, scal, ba.tab);
-  return cudaGetLastError();
+  return launch_dep(k_trace<R>, dim3(1, 1, ba.nz), dim3(256), 0, s, X, D.d, scal, ba.tab);
 }
 
 template <class R>

@@ -708,12 +708,13 @@ cudaError_t povm_lo_fwd_fast(const Dims& D, const float2* X, float* W, const Pov
   if (batch_take(ba, {X, W})) return cudaSuccess;
   if (P.structured) {
     const MapStruct m = map_struct(P);
-    k_lo_fwd_fast<MapStruct, true><<<dim3(tiles, 1, ba.nz), kLoThreads, 0, s>>>(X, W, D.N, m, o, ba.tab);
+    return launch_dep(k_lo_fwd_fast<MapStruct, true>, dim3(tiles, 1, ba.nz), dim3(kLoThreads), 0, s, X, W, D.N, m, o,
+                      ba.tab);
   } else {
     const MapGeneric m = map_generic(P);
-    k_lo_fwd_fast<MapGeneric, false><<<dim3(tiles, 1, ba.nz), kLoThreads, 0, s>>>(X, W, D.N, m, o, ba.tab);
+    return launch_dep(k_lo_fwd_fast<MapGeneric, false>, dim3(tiles, 1, ba.nz), dim3(kLoThreads), 0, s, X, W, D.N, m,
+                      o, ba.tab);
   }
-  return cudaGetLastError();
 }
 
 cudaError_t povm_fwd_fast(const Dims& D, const float2* X, float* W, float* p, const PovmPlan& P, cudaStream_t s) {
