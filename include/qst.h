@@ -322,6 +322,9 @@ qst_status qst_graph_enable(qst_ctx* ctx, int enable);
  *   fused_ctas_per_sm    resident CTAs per SM of the persistent launch of a batch's fused tomographies
  *                        (1 or 2); results do not depend on it.
  *   fused_max_qubits     the limit qst_options.fused_max_qubits = 0 stands for (0..7; 0 = never).
+ *   batch_concurrent_runs 1: the runs of one qubit count of a batch iteration start together (their
+ *                        kernels share the GPU), 0: one after another, largest first; results do not
+ *                        depend on it.
  * Set them between iterations, with no call of the library running on another thread; a batch captured
  * earlier keeps the values it was captured with until its inputs change.  QST_E_INVAL for values out of
  * range (nothing changed). */
@@ -341,6 +344,7 @@ typedef struct qst_tuning {
     int bulk_chunks_per_cta;
     int fused_ctas_per_sm;
     int fused_max_qubits;
+    int batch_concurrent_runs;
 } qst_tuning;
 void qst_get_tuning(qst_tuning* t);
 qst_status qst_set_tuning(const qst_tuning* t);

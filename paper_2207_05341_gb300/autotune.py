@@ -11,8 +11,9 @@ step is the headline workload), which the chunk parameter of the weight passes a
 
 Stage 1 picks bulk_chunks_per_cta (least 256-column chunks per CTA of a weight pass) by the mixed
 batch's time, among the values that keep every guard step within 5 % of its time at the smallest
-value (smaller tomographies run mostly in batches, where few CTAs per tomography pay off); stage 2 picks fused_max_qubits and fused_ctas_per_sm by the sum of the FP32 and mixed batch
-times.  Every candidate is timed with CUDA events on the batch's stream after warm-up iterations.
+value (smaller tomographies run mostly in batches, where few CTAs per tomography pay off); stage 2
+picks fused_max_qubits and fused_ctas_per_sm, stage 3 batch_concurrent_runs, each by the sum of the
+FP32 and mixed batch times.  Every candidate is timed with CUDA events on the batch's stream after warm-up iterations.
 """
 import argparse
 import json
@@ -97,8 +98,10 @@ def write_tuned(best):
     path = os.path.join(HERE, "csrc", "tuned.h")
     src = open(path).read()
     names = {"bulk_chunks_per_cta": "kTunedBulkChunksPerCta", "fused_ctas_per_sm": "kTunedFusedCtasPerSm",
-             "fused_max_qubits": "kTunedFusedMaxQubits"}
+             "fused_max_qubits": "kTunedFusedMaxQubits", "batch_concurrent_runs": "kTunedBatchConcurrentRuns"}
     for key, const in names.items():
+        if key not in best:
+            continue
         src, k = re.subn(r"(constexpr int %s = )\d+;" % const, r"\g<1>%d;" % best[key], src)
         if k != 1:
             raise RuntimeError(f"{const} not found in {path}")
@@ -163,6 +166,21 @@ def main(argv=None):
             if best2 is None or fp32 + mixed < best2[2]:
                 best2 = (fm, fc, fp32 + mixed)
     best = {"bulk_chunks_per_cta": best1[0], "fused_max_qubits": best2[0], "fused_ctas_per_sm": best2[1]}
+    qst.qst_set_tuning(**best)
+
+    # stage 3: runs of one size one after another, or all at once
+    best3 = None
+    log["stage3"] = []
+    for conc in (0, 1):
+        qst.qst_set_tuning(batch_concurrent_runs=conc)
+        fp32 = time_batch(torch, qst, synth, Ns, qst.QST_FP32, args.steps)
+        mixed = time_batch(torch, qst, synth, Ns, qst.QST_MIXED, args.steps)
+        row = {"batch_concurrent_runs": conc, "batch_fp32_ms": fp32, "batch_mixed_ms": mixed}
+        log["stage3"].append(row)
+        print(json.dumps(row), flush=True)
+        if best3 is None or fp32 + mixed < best3[1]:
+            best3 = (conc, fp32 + mixed)
+    best["batch_concurrent_runs"] = best3[0]
     qst.qst_set_tuning(**best)
     log["best"] = best
     print(json.dumps({"best": best}), flush=True)

@@ -58,8 +58,11 @@ int check_povm(const double* povm, int K, PovmB<double>* Bd) {
 static std::atomic<int> g_bulk_chunks{kTunedBulkChunksPerCta};
 static std::atomic<int> g_fused_ctas{kTunedFusedCtasPerSm};
 static std::atomic<int> g_fused_max{kTunedFusedMaxQubits};
+static std::atomic<int> g_concurrent{kTunedBatchConcurrentRuns};
 
-Tuning tuning() { return Tuning{g_bulk_chunks.load(), g_fused_ctas.load(), g_fused_max.load()}; }
+Tuning tuning() {
+  return Tuning{g_bulk_chunks.load(), g_fused_ctas.load(), g_fused_max.load(), g_concurrent.load()};
+}
 
 static std::atomic<int> g_inject[INJ_SITES];
 
@@ -1177,7 +1180,8 @@ qst_status batch_capture(qst_batch* bt, const void* const* f) {
   // mixed, against about 14 ms as the sum of its same-N groups).
   for (size_t r = 0; r < runs.size() && st == QST_OK && e == cudaSuccess; ++r) {
     const int i = runs[r].first, j = runs[r].second;
-    e = cudaEventRecord(bt->fork, bt->root);  // the run starts when the previous one has joined
+    // the run starts when the previous one has joined, or (batch_concurrent_runs) with all the others
+    if (r == 0 || !tuning().batch_concurrent_runs) e = cudaEventRecord(bt->fork, bt->root);
     if (e != cudaSuccess) break;
     if (run_group[r] >= 0) {  // one launch per kernel, on the first member's stream
       BatchRec& rec = bt->groups[run_group[r]];
@@ -1594,15 +1598,18 @@ void qst_get_tuning(qst_tuning* t) {
   t->bulk_chunks_per_cta = u.bulk_chunks_per_cta;
   t->fused_ctas_per_sm = u.fused_ctas_per_sm;
   t->fused_max_qubits = u.fused_max_qubits;
+  t->batch_concurrent_runs = u.batch_concurrent_runs;
 }
 
 qst_status qst_set_tuning(const qst_tuning* t) {
   if (!t || t->bulk_chunks_per_cta < 1 || t->bulk_chunks_per_cta > (1 << 20) || t->fused_ctas_per_sm < 1 ||
-      t->fused_ctas_per_sm > kFusedCtasPerSmMax || t->fused_max_qubits < 0 || t->fused_max_qubits > kFusedMaxQubits)
+      t->fused_ctas_per_sm > kFusedCtasPerSmMax || t->fused_max_qubits < 0 || t->fused_max_qubits > kFusedMaxQubits ||
+      (t->batch_concurrent_runs != 0 && t->batch_concurrent_runs != 1))
     return QST_E_INVAL;
   g_bulk_chunks.store(t->bulk_chunks_per_cta);
   g_fused_ctas.store(t->fused_ctas_per_sm);
   g_fused_max.store(t->fused_max_qubits);
+  g_concurrent.store(t->batch_concurrent_runs);
   return QST_OK;
 }
 

@@ -66,6 +66,7 @@ struct Tuning {
   int bulk_chunks_per_cta;  // least 256-column chunks per CTA of a bulk weight pass (fixes its partition)
   int fused_ctas_per_sm;    // resident CTAs per SM of the persistent fused batch launch (1 or 2)
   int fused_max_qubits;     // largest N run as one fused iteration when the context asks for the default
+  int batch_concurrent_runs;  // 1: a batch's runs of one size start together, 0: one after another
 };
 Tuning tuning();
 // qst_inject_wait_timeout: true when this launch of `site` is to issue no operand copies (counts it off)

@@ -77,6 +77,7 @@ class qst_tuning(ctypes.Structure):
         ("bulk_chunks_per_cta", ctypes.c_int),
         ("fused_ctas_per_sm", ctypes.c_int),
         ("fused_max_qubits", ctypes.c_int),
+        ("batch_concurrent_runs", ctypes.c_int),
     ]
 
 

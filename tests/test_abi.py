@@ -152,7 +152,7 @@ def _tuned_defaults():
     src = open(os.path.join(os.path.dirname(__file__), "..", "paper_2207_05341_gb300", "csrc", "tuned.h")).read()
     get = lambda name: int(re.search(r"constexpr int %s = (\d+);" % name, src).group(1))
     return {"bulk_chunks_per_cta": get("kTunedBulkChunksPerCta"), "fused_ctas_per_sm": get("kTunedFusedCtasPerSm"),
-            "fused_max_qubits": get("kTunedFusedMaxQubits")}
+            "fused_max_qubits": get("kTunedFusedMaxQubits"), "batch_concurrent_runs": get("kTunedBatchConcurrentRuns")}
 
 
 def test_tuning_defaults_and_validation(lib):
@@ -162,7 +162,7 @@ def test_tuning_defaults_and_validation(lib):
     assert start == _tuned_defaults()
     try:
         for bad in ({"bulk_chunks_per_cta": 0}, {"fused_ctas_per_sm": 3}, {"fused_ctas_per_sm": 0},
-                    {"fused_max_qubits": 8}, {"fused_max_qubits": -1}):
+                    {"fused_max_qubits": 8}, {"fused_max_qubits": -1}, {"batch_concurrent_runs": 2}):
             with pytest.raises(qst.QstError) as e:
                 qst.qst_set_tuning(**bad)
             assert e.value.status == qst.QST_E_INVAL

@@ -145,8 +145,9 @@ def test_batch_matches_individual_contexts():
         qst.qst_batch_destroy(bt)
 
 
-@pytest.mark.parametrize("prec,fused_max", [(qst.QST_FP32, 6), (qst.QST_MIXED, 0), (qst.QST_MIXED_BF16, 0)])
-def test_grouped_batch_matches_individual_contexts(prec, fused_max):
+@pytest.mark.parametrize("prec,fused_max,conc", [(qst.QST_FP32, 6, 0), (qst.QST_MIXED, 0, 1), (qst.QST_MIXED_BF16, 0, 0),
+                                                  (qst.QST_FP32, 6, 1)])
+def test_grouped_batch_matches_individual_contexts(prec, fused_max, conc):
     """Runs of tomographies of one size (N = 7, 8, 9) launch each kernel of their iteration once for the
     whole run: losses and parameters bit-identical to each tomography run on its own context, and far
     fewer launches per iteration than one chain per tomography."""
@@ -158,6 +159,8 @@ def test_grouped_batch_matches_individual_contexts(prec, fused_max):
     o = qst.qst_default_options()
     o.precision = prec
     o.fused_max_qubits = fused_max
+    tuning = qst.qst_get_tuning()
+    qst.qst_set_tuning(batch_concurrent_runs=conc)  # the runs one after another, or all at once
     bt = qst.qst_batch_init(Ns, opt=o, stream=stream.cuda_stream)
     try:
         fds = [torch.from_numpy(f).cuda() for f, _ in data]
@@ -179,3 +182,4 @@ def test_grouped_batch_matches_individual_contexts(prec, fused_max):
         assert per_iter <= 3 * 16, per_iter
     finally:
         qst.qst_batch_destroy(bt)
+        qst.qst_set_tuning(**tuning)
