@@ -639,6 +639,40 @@ def profile_only(args):
     torch.cuda.synchronize()
 
 
+def profile_batch(args):
+    """Profiling aid: the 512-tomography batch of batch_c4 (uniform random frequencies instead of sampled
+    counts, which do not change the kernels), 3 warm-up iterations, then args.profile_batch_steps
+    iterations inside the NVTX range "timed" (for ncu --nvtx --nvtx-include "timed/")."""
+    import torch
+
+    from paper_2207_05341_gb300 import qst, synth
+    qst.load()
+    dev = torch.device("cuda", 0)
+    Ns = [int(x) for x in np.random.default_rng(30).integers(3, 10, 512)]
+    stream = torch.cuda.Stream(device=dev)
+    o = qst.qst_default_options()
+    if args.profile_batch == "mixed":
+        o.precision = qst.QST_MIXED
+    bt = qst.qst_batch_init(Ns, opt=o, stream=stream.cuda_stream)
+    try:
+        fds = []
+        for b, N in enumerate(Ns):
+            f = np.random.default_rng(1000 + b).random(4 ** N).astype(np.float32)
+            fds.append(torch.from_numpy(f / f.sum()).to(dev))
+            qst.qst_batch_set_params(bt, b, synth.init_theta(N, 2000 + b).astype(np.float32))
+        torch.cuda.synchronize()
+        for _ in range(3):
+            qst.qst_batch_step(bt, fds)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed")
+        for _ in range(args.profile_batch_steps):
+            qst.qst_batch_step(bt, fds)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+    finally:
+        qst.qst_batch_destroy(bt)
+
+
 def main_ours(args):
     import torch
 
@@ -871,6 +905,10 @@ def main():
                     help="profiling aid: only run this many plain and mixed steps at N=11 and exit (no JSON line)")
     ap.add_argument("--profile-net", choices=["fnn", "cnn"], default="fnn",
                     help="with --profile-steps: the FNN in FP32, mixed FP16x3 and BF16x3, or the CNN (mixed)")
+    ap.add_argument("--profile-batch", choices=["mixed", "fp32"], default=None,
+                    help="profiling aid: only run the 512-tomography batch, its timed iterations in the NVTX "
+                         "range 'timed', and exit (no JSON line)")
+    ap.add_argument("--profile-batch-steps", type=int, default=2)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -878,6 +916,8 @@ def main():
         main_reference(args)
     elif args.profile_steps > 0:
         profile_only(args)
+    elif args.profile_batch:
+        profile_batch(args)
     else:
         main_ours(args)
 
