@@ -648,7 +648,7 @@ def profile_batch(args):
     from paper_2207_05341_gb300 import qst, synth
     qst.load()
     dev = torch.device("cuda", 0)
-    Ns = [int(x) for x in np.random.default_rng(30).integers(3, 10, 512)]
+    Ns = [int(x) for x in np.random.default_rng(30).integers(3, args.profile_batch_max_n + 1, 512)]
     stream = torch.cuda.Stream(device=dev)
     o = qst.qst_default_options()
     if args.profile_batch == "mixed":
@@ -909,6 +909,8 @@ def main():
                     help="profiling aid: only run the 512-tomography batch, its timed iterations in the NVTX "
                          "range 'timed', and exit (no JSON line)")
     ap.add_argument("--profile-batch-steps", type=int, default=2)
+    ap.add_argument("--profile-batch-max-n", type=int, default=9,
+                    help="with --profile-batch: N ~ U{3..this} (a smaller case for full ncu captures)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -8,7 +8,7 @@ namespace qst {
 constexpr int kFusedThreads = 512;          // threads of the CTA that runs one tomography's iteration
 constexpr int kFusedCtasPerSmMax = 2;       // register budget of that kernel: resident CTAs per SM at most
 constexpr int kTunedFusedCtasPerSm = 2;     // resident CTAs per SM of the persistent batch launch
-constexpr int kTunedFusedMaxQubits = 7;     // largest N run as one fused iteration by default
+constexpr int kTunedFusedMaxQubits = 6;     // largest N run as one fused iteration by default
 constexpr int kTunedBulkChunksPerCta = 32;  // least 256-column chunks per CTA of a bulk weight pass
-constexpr int kTunedBatchConcurrentRuns = 0;  // 1: a batch's runs of one size start together
+constexpr int kTunedBatchConcurrentRuns = 1;  // 1: a batch's runs of one size start together
 }  // namespace qst

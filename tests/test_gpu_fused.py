@@ -36,13 +36,13 @@ def _problem(N, seed):
     return f.astype(np.float32), synth.init_theta(N, 720 + seed).astype(np.float32)
 
 
-def _opt(fused_max=0):
+def _opt(fused_max=7):
     o = qst.qst_default_options()
     o.fused_max_qubits = fused_max
     return o
 
 
-def _steps(N, f, theta, steps, fused_max=0, timing=False):
+def _steps(N, f, theta, steps, fused_max=7, timing=False):
     ctx = qst.qst_init(N, opt=_opt(fused_max))
     try:
         if timing:
@@ -72,7 +72,7 @@ def test_fused_step_matches_oracle(N):
     # step's loss at the parameters the GPU held after its first step (the next hidden layer)
     st = O.RpropState(th.size)
     want1 = O.rprop_update(th64, g_ref, st)
-    ctx = qst.qst_init(N)
+    ctx = qst.qst_init(N, opt=_opt())
     try:
         qst.qst_set_params(ctx, torch.from_numpy(th).cuda())
         qst.qst_step(ctx, torch.from_numpy(f).cuda())
@@ -123,6 +123,14 @@ def test_fused_limit_option():
     _, _, _, k_on = _steps(5, f, th, 3)
     _, _, _, k_off = _steps(5, f, th, 3, fused_max=4)
     assert k_off > k_on
+    # 0: the process-wide tuned limit
+    lim = qst.qst_get_tuning()["fused_max_qubits"]
+    for N in (lim, lim + 1):
+        if 1 <= N <= 7:
+            fN, thN = _problem(N, 42)
+            _, _, _, k_def = _steps(N, fN, thN, 3, fused_max=0)
+            _, _, _, k_fused = _steps(N, fN, thN, 3, fused_max=7)
+            assert (k_def == k_fused) == (N <= lim), (N, lim, k_def, k_fused)
 
 
 def test_ragged_batch_with_more_tomographies_than_ctas_is_bit_identical():
@@ -136,7 +144,7 @@ def test_ragged_batch_with_more_tomographies_than_ctas_is_bit_identical():
     data = [_problem(N, 100 + b) for b, N in enumerate(Ns)]
     steps = 3
     stream = torch.cuda.Stream()
-    bt = qst.qst_batch_init(Ns, stream=stream.cuda_stream)
+    bt = qst.qst_batch_init(Ns, opt=_opt(), stream=stream.cuda_stream)
     try:
         fds = [torch.from_numpy(f).cuda() for f, _ in data]
         for b, (_, th) in enumerate(data):

@@ -66,7 +66,7 @@ def test_graph_replay_is_bit_identical(N, prec):
     assert np.array_equal(ta, tb)
 
 
-@pytest.mark.parametrize("prec,fused_max", [(qst.QST_FP32, -1), (qst.QST_FP32, 0), (qst.QST_MIXED, 0)])
+@pytest.mark.parametrize("prec,fused_max", [(qst.QST_FP32, -1), (qst.QST_FP32, 7), (qst.QST_MIXED, 0)])
 def test_timed_graph_replay(prec, fused_max):
     """Phase events captured as graph nodes: same results and launch count as the
     launch-by-launch path, and every phase of the latest replay is timed once (an FP32
@@ -81,7 +81,7 @@ def test_timed_graph_replay(prec, fused_max):
     tm = xb["timing"]
     timed = [p for p in qst.PHASES if tm[p][1] > 0]
     assert "hidden" not in timed  # a replay does not recompute the f-dependent activation
-    fused = prec == qst.QST_FP32 and fused_max == 0
+    fused = prec == qst.QST_FP32 and fused_max == 7
     last = "fused" if fused else "w2"
     if fused:
         assert timed == ["fused"]
