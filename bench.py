@@ -673,6 +673,28 @@ def profile_batch(args):
         qst.qst_batch_destroy(bt)
 
 
+def profile_absp(args):
+    """Profiling aid: one A_P (P = 1.5) context at N = args.profile_absp on the mixed path, its cold first
+    step and one warm-started step, with uniform random frequencies."""
+    import torch
+
+    from paper_2207_05341_gb300 import qst, synth
+    qst.load()
+    N = args.profile_absp
+    o = qst.qst_default_options()
+    o.precision, o.mapping, o.P = qst.QST_MIXED, qst.QST_MAP_ABS_P, 1.5
+    ctx = qst.qst_init(N, opt=o)
+    try:
+        f = np.random.default_rng(N).random(4 ** N).astype(np.float32)
+        fd = torch.from_numpy(f / f.sum()).cuda()
+        qst.qst_set_params(ctx, synth.init_theta(N, 3).astype(np.float32))
+        for _ in range(2):
+            qst.qst_step(ctx, fd)
+        qst.qst_sync(ctx)
+    finally:
+        qst.qst_destroy(ctx)
+
+
 def main_ours(args):
     import torch
 
@@ -909,6 +931,8 @@ def main():
                     help="profiling aid: only run the 512-tomography batch, its timed iterations in the NVTX "
                          "range 'timed', and exit (no JSON line)")
     ap.add_argument("--profile-batch-steps", type=int, default=2)
+    ap.add_argument("--profile-absp", type=int, default=0,
+                    help="profiling aid: one mixed A_P context at this N, a cold and a warm step, and exit")
     ap.add_argument("--profile-batch-max-n", type=int, default=9,
                     help="with --profile-batch: N ~ U{3..this} (a smaller case for full ncu captures)")
     args = ap.parse_args()
@@ -920,6 +944,8 @@ def main():
         profile_only(args)
     elif args.profile_batch:
         profile_batch(args)
+    elif args.profile_absp:
+        profile_absp(args)
     else:
         main_ours(args)
 
