@@ -262,13 +262,14 @@ qst_status qst_set_state(qst_ctx* ctx, const void* host_buf, size_t bytes);
 long long qst_iterations(const qst_ctx* ctx);
 
 /* QST_MAP_ABS_P with QST_MIXED / QST_MIXED_BF16 (instrumentation): a warm-started step refines the
- * previous eigenvectors on tensor cores (Ogita and Aishima's iteration, up to 4 times until the largest
- * correction is at most 5e-3) and hands the step to Jacobi sweeps from the previous eigenvectors when T
- * moved too far for that (a correction above 0.25, a coupling left unresolved above 1e-5 max |lambda|, or
- * 4 refinements without convergence); after such a step the next 15 warm steps go to the sweeps directly.
- * Counts since
- * qst_init: refinements taken, and steps handed to the sweeps; last (2 doubles, may be NULL): the latest
- * refinement's largest correction and its largest unresolved coupling relative to max |lambda|. */
+ * previous eigenvectors on tensor cores (Ogita and Aishima's iteration; couplings of near-degenerate
+ * pairs that a first-order correction leaves unresolved go to exact Jacobi diagonalisations of 64 x 64
+ * blocks of neighbours in the order of the eigenvalues), up to 6 refinements until the largest
+ * correction is at most 5e-3 with no coupling above 1e-5 max |lambda| unresolved, and hands the step to
+ * Jacobi sweeps from the previous eigenvectors otherwise; after such a step the next 15 warm steps go to
+ * the sweeps directly.  Counts since qst_init: refinements taken, and steps handed to the sweeps; last
+ * (2 doubles, may be NULL): the latest refinement's largest correction and its largest unresolved
+ * coupling relative to max |lambda|. */
 qst_status qst_eig_counts(const qst_ctx* ctx, long long* refinements, long long* fallbacks, double* last);
 
 /* Number of kernel launches the library has enqueued on this context (graph

@@ -115,10 +115,9 @@ bool batch_take(BatchArgs& ba, std::initializer_list<const void*> ptrs, const vo
 
 namespace {
 
-// tensor-core eigenvector refinement of QST_MIXED A_P steps: accept / give up thresholds on max |E|
+// tensor-core eigenvector refinement of QST_MIXED A_P steps: acceptance threshold on max |E|
 constexpr float kOaAccept = 5e-3f;
-constexpr float kOaGiveUp = 0.25f;
-constexpr int kOaMaxIters = 4;
+constexpr int kOaMaxIters = 6;
 constexpr float kOaLeft = 1e-5f;  // largest unresolved coupling, relative to max |lambda|
 constexpr int kOaBackoff = 15;    // after a step handed to the sweeps, the next attempt comes 16 steps later
 
@@ -322,6 +321,10 @@ template <class R> qst_status alloc_work(qst_ctx* c) {
       ap->eb = buf + 3 * pb + 2 * (pb + pb / 2);
       QST_CU(dalloc(c, &ap->amax, 8));
       QST_CU(dalloc(c, &ap->sc, 8));
+      QST_CU(dalloc(c, &ap->perm, (size_t)D.d));
+      float2* ublk = nullptr;
+      QST_CU(dalloc(c, &ublk, (size_t)D.d * 64));
+      ap->ublk = ublk;
     }
     c->sweeps = c->opt.eig_sweeps > 0 ? c->opt.eig_sweeps : 10;
     c->sweeps += c->sweeps & 1;
@@ -411,10 +414,12 @@ template <class R> struct Engine {
           --c->oa_skip;  // T moved too far at the latest attempt: the sweeps, without trying first
         } else if (mixed && warm) {
           // Refinements of the previous eigenvectors on tensor cores, each judged by its largest correction
-          // max |E|: the eigenvectors are taken once it is at most kOaAccept (the error left is of its
-          // square); one above kOaGiveUp (T moved too far for a first-order correction), or kOaMaxIters of
-          // them, hand the step to Jacobi sweeps from the eigenvectors it started with.  Inside a graph
-          // capture there is no host check: two refinements, taken.
+          // max |E| and the largest coupling it left unresolved (near-degenerate pairs): a refinement with
+          // unresolved couplings is followed by the block passes over neighbours in the order of lambda,
+          // any other is applied, and the eigenvectors are taken once max |E| is at most kOaAccept (the
+          // error left is of its square) with nothing unresolved.  kOaMaxIters refinements without that
+          // (or a correction above 1) hand the step to Jacobi sweeps from the eigenvectors it started with.
+          // Inside a graph capture there is no host check: two refinements, taken.
           AbsPWork<float>& ap = *reinterpret_cast<AbsPWork<float>*>(c->apw);
           const size_t qbytes = (size_t)D.d * D.d * sizeof(float2);
           QST_CU(cudaMemcpyAsync(ap.Qh, ap.V0, qbytes, cudaMemcpyDeviceToDevice, c->stream));  // the start
@@ -432,7 +437,15 @@ template <class R> struct Engine {
               c->oa_last[0] = emax;
               c->oa_last[1] = left;
             }
-            if (!(emax <= kOaGiveUp) || !(left <= kOaLeft)) break;  // also NaN
+            if (emax != emax || left != left || emax > 1.f) break;
+            if (!(left <= kOaLeft)) {
+              // couplings of near-degenerate pairs: exact Jacobi diagonalisations of blocks of neighbours in
+              // the order of lambda, then another correction
+              if (c->capturing || it + 1 >= kOaMaxIters) break;
+              QST_CU(abs_p_tc_block_phase(D.d, w->Tb, w->scal + kScaleT, ap, tc_fmt(c), w->flags + 1, c->stream));
+              c->launches += 14;
+              continue;
+            }
             QST_CU(abs_p_tc_update(D.d, ap, tc_fmt(c), w->flags + 1, c->stream));
             c->launches += 4;
             if (emax <= kOaAccept || (c->capturing && it == 1)) {

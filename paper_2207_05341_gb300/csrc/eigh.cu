@@ -15,6 +15,9 @@
 // once per round (double-buffered), and V accumulates the rotations, V <- V R.
 #include <float.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "impl.h"
 
 namespace qst {
@@ -406,28 +409,176 @@ cudaError_t planes_of(int d, const float2* M, int op, int np, void* P, int fmt, 
   return tc_planes_op(d, M, op, np, P, fmt, amax, sslot, s);
 }
 
+// ---- sorted-eigenvalue block passes (the couplings a first-order correction cannot resolve)
+// In the order of increasing lambda, the eigenvectors that T's change mixes by more than their gap are
+// neighbours: kBJ x kBJ diagonal blocks of S = Q^dag T Q are diagonalised exactly by Jacobi sweeps in
+// shared memory (one CTA per block), Q's columns of each block are rotated by the block's unitary, and a
+// second pass on blocks shifted by kBJ / 2 covers the couplings across block borders.
+constexpr int kBJ = 64;
+constexpr int kBJS = kBJ + 1;
+constexpr int kBJSweeps = 8;
+
+__global__ void __launch_bounds__(256) k_block_jacobi(const float2* __restrict__ S, const int* __restrict__ perm,
+                                                       int d, int offset, float2* __restrict__ U) {
+  extern __shared__ __align__(16) unsigned char sraw[];
+  float2* Sb = reinterpret_cast<float2*>(sraw);
+  float2* Ub = Sb + kBJ * kBJS;
+  constexpr int NP = kBJ / 2;
+  __shared__ float2 r_pp[NP], r_qp[NP], r_qq[NP], r_pq[NP];
+  __shared__ int pi[NP], qi[NP];
+  const int base = offset + kBJ * (int)blockIdx.x;
+  for (int e = threadIdx.x; e < kBJ * kBJ; e += blockDim.x) {
+    const int a = e / kBJ, b = e % kBJ;
+    const int ga = perm ? perm[base + a] : base + a, gb = perm ? perm[base + b] : base + b;
+    Sb[a * kBJS + b] = herm_entry(S, d, ga, gb);
+    Ub[a * kBJS + b] = make_float2(a == b ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  for (int sw = 0; sw < kBJSweeps; ++sw) {
+    for (int r = 0; r < kBJ - 1; ++r) {
+      if (threadIdx.x < NP) {  // the round's rotations, from the block before the round
+        const int k = threadIdx.x;
+        const int x = player_at(k, r, kBJ), y = player_at(kBJ - 1 - k, r, kBJ);
+        const int p = x < y ? x : y, q = x < y ? y : x;
+        float2 al, be;
+        rot_coeffs<float>(Sb, kBJS, p, q, al, be);
+        r_pp[k] = al;
+        r_qp[k] = be;
+        rot_coeffs<float>(Sb, kBJS, q, p, al, be);
+        r_qq[k] = al;
+        r_pq[k] = be;
+        pi[k] = p;
+        qi[k] = q;
+      }
+      __syncthreads();
+      // S <- R^dag S R on the 2 x 2 blocks (pair k rows, pair l columns), each entry in one block
+      for (int w = threadIdx.x; w < NP * NP; w += blockDim.x) {
+        const int k = w / NP, l = w % NP;
+        const int pk = pi[k], qk = qi[k], pl = pi[l], ql = qi[l];
+        const float2 m_pp = Sb[pk * kBJS + pl], m_pq = Sb[pk * kBJS + ql];
+        const float2 m_qp = Sb[qk * kBJS + pl], m_qq = Sb[qk * kBJS + ql];
+        const float2 u_pp = cadd(cmul(m_pp, r_pp[l]), cmul(m_pq, r_qp[l]));
+        const float2 u_pq = cadd(cmul(m_pp, r_pq[l]), cmul(m_pq, r_qq[l]));
+        const float2 u_qp = cadd(cmul(m_qp, r_pp[l]), cmul(m_qq, r_qp[l]));
+        const float2 u_qq = cadd(cmul(m_qp, r_pq[l]), cmul(m_qq, r_qq[l]));
+        Sb[pk * kBJS + pl] = cadd(cmulc(r_pp[k], u_pp), cmulc(r_qp[k], u_qp));
+        Sb[pk * kBJS + ql] = cadd(cmulc(r_pp[k], u_pq), cmulc(r_qp[k], u_qq));
+        Sb[qk * kBJS + pl] = cadd(cmulc(r_pq[k], u_pp), cmulc(r_qq[k], u_qp));
+        Sb[qk * kBJS + ql] = cadd(cmulc(r_pq[k], u_pq), cmulc(r_qq[k], u_qq));
+      }
+      // U <- U R (columns p_l, q_l of every row)
+      for (int w = threadIdx.x; w < kBJ * NP; w += blockDim.x) {
+        const int row = w / NP, l = w % NP;
+        const int pl = pi[l], ql = qi[l];
+        const float2 vp = Ub[row * kBJS + pl], vq = Ub[row * kBJS + ql];
+        Ub[row * kBJS + pl] = cadd(cmul(vp, r_pp[l]), cmul(vq, r_qp[l]));
+        Ub[row * kBJS + ql] = cadd(cmul(vp, r_pq[l]), cmul(vq, r_qq[l]));
+      }
+      __syncthreads();
+    }
+  }
+  float2* out = U + (size_t)blockIdx.x * kBJ * kBJ;
+  for (int e = threadIdx.x; e < kBJ * kBJ; e += blockDim.x) out[e] = Ub[(e / kBJ) * kBJS + e % kBJ];
+}
+
+// Q[:, block m] <- Q[:, block m] U_m for the blocks of a pass (columns offset + kBJ m ..), in place: CTA
+// (row chunk, m) reads its 64 x kBJ piece of Q and U_m into shared memory before writing the product.
+__global__ void __launch_bounds__(256) k_block_apply(float2* __restrict__ Q, int d, int offset,
+                                                      const float2* __restrict__ U) {
+  extern __shared__ __align__(16) unsigned char sraw[];
+  float2* Qt = reinterpret_cast<float2*>(sraw);
+  float2* Ut = Qt + 64 * kBJS;
+  const int r0 = 64 * (int)blockIdx.x, c0 = offset + kBJ * (int)blockIdx.y;
+  const float2* Um = U + (size_t)blockIdx.y * kBJ * kBJ;
+  for (int e = threadIdx.x; e < 64 * kBJ; e += blockDim.x) {
+    const int r = e / kBJ, c = e % kBJ;
+    Qt[r * kBJS + c] = Q[(long long)(r0 + r) * d + c0 + c];
+    Ut[r * kBJS + c] = Um[e];
+  }
+  __syncthreads();
+  const int r = threadIdx.x >> 2, j0 = (threadIdx.x & 3) * 16;
+  float2 acc[16];
+#pragma unroll
+  for (int jj = 0; jj < 16; ++jj) acc[jj] = make_float2(0.f, 0.f);
+  for (int a = 0; a < kBJ; ++a) {
+    const float2 q = Qt[r * kBJS + a];
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj) acc[jj] = cadd(acc[jj], cmul(q, Ut[a * kBJS + j0 + jj]));
+  }
+  float2* dst = Q + (long long)(r0 + r) * d + c0 + j0;
+#pragma unroll
+  for (int jj = 0; jj < 16; ++jj) dst[jj] = acc[jj];
+}
+
+__global__ void __launch_bounds__(256) k_permute_cols(const float2* __restrict__ Qi, float2* __restrict__ Qo,
+                                                       const int* __restrict__ perm, int d) {
+  const long long nn = (long long)d * d;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += (long long)gridDim.x * blockDim.x)
+    Qo[e] = Qi[(e / d) * d + perm[e % d]];
+}
+
 }  // namespace
 
 size_t abs_p_tc_plane_bytes(int d) { return (size_t)4 * d * d * 2; }
 
+// S = Q^dag T Q into w.A0 (lower tiles); the planes of Q^dag stay in qa_h (4) and qb_h (6)
+cudaError_t abs_p_tc_rotated(int d, const void* Tb, const double* sT, AbsPWork<float>& w, int fmt, unsigned int* err,
+                             cudaStream_t s) {
+  float2* Q = w.V0;
+  double* sc = w.sc;
+  cudaError_t e;
+  if ((e = planes_of(d, Q, 1, 4, w.qa_h, fmt, w.amax, sc + 1, true, s)) != cudaSuccess) return e;
+  if ((e = planes_of(d, Q, 1, 6, w.qb_h, fmt, w.amax, sc + 3, false, s)) != cudaSuccess) return e;
+  if ((e = tc_product(d, w.qa_h, Tb, fmt, sc + 1, sT, w.W, false, err, s)) != cudaSuccess) return e;
+  if ((e = planes_of(d, w.W, 0, 4, w.wa, fmt, w.amax + 1, sc + 4, true, s)) != cudaSuccess) return e;
+  return tc_product(d, w.wa, w.qb_h, fmt, sc + 4, sc + 3, w.A0, true, err, s);
+}
+
 cudaError_t abs_p_tc_correction(int d, const void* Tb, const double* sT, AbsPWork<float>& w, double P, int fmt,
                                 unsigned int* err, cudaStream_t s) {
   const long long nn = (long long)d * d;
-  float2* Q = w.V0;
-  unsigned int *amQ = w.amax, *amW = w.amax + 1, *amE = w.amax + 2;
+  unsigned int* amE = w.amax + 2;
   double* sc = w.sc;
   cudaError_t e;
-  // R = I - Q^dag Q and S = (Q^dag T) Q, both Hermitian (lower tiles)
-  if ((e = planes_of(d, Q, 1, 4, w.qa_h, fmt, amQ, sc + 1, true, s)) != cudaSuccess) return e;
-  if ((e = planes_of(d, Q, 1, 6, w.qb_h, fmt, amQ, sc + 3, false, s)) != cudaSuccess) return e;
-  if ((e = tc_product(d, w.qa_h, Tb, fmt, sc + 1, sT, w.W, false, err, s)) != cudaSuccess) return e;
-  if ((e = planes_of(d, w.W, 0, 4, w.wa, fmt, amW, sc + 4, true, s)) != cudaSuccess) return e;
-  if ((e = tc_product(d, w.wa, w.qb_h, fmt, sc + 4, sc + 3, w.A0, true, err, s)) != cudaSuccess) return e;
+  // S = (Q^dag T) Q and C1 = Q^dag Q = I - R, both Hermitian (lower tiles)
+  if ((e = abs_p_tc_rotated(d, Tb, sT, w, fmt, err, s)) != cudaSuccess) return e;
   if ((e = tc_product(d, w.qa_h, w.qb_h, fmt, sc + 1, sc + 3, w.A1, true, err, s)) != cudaSuccess) return e;
   k_oa_spectrum<<<1, 1024, 0, s>>>(w.A0, w.A1, d, P, 1e-7, w.lam, w.s, w.sp, sc);
   if ((e = cudaMemsetAsync(amE, 0, 2 * sizeof(unsigned int), s)) != cudaSuccess) return e;
   k_oa_correction<<<blocks_for(nn), 256, 0, s>>>(w.A0, w.A1, w.lam, sc, d, w.W, amE);
   return cudaGetLastError();
+}
+
+cudaError_t abs_p_tc_block_phase(int d, const void* Tb, const double* sT, AbsPWork<float>& w, int fmt,
+                                 unsigned int* err, cudaStream_t s) {
+  if (d % kBJ || d < 2 * kBJ) return cudaErrorInvalidValue;
+  const long long nn = (long long)d * d;
+  cudaError_t e;
+  // the order of increasing lambda (lambda of the latest correction, S of the current Q in A0)
+  std::vector<float> lam(d);
+  std::vector<int> perm(d);
+  if ((e = cudaMemcpyAsync(lam.data(), w.lam, d * sizeof(float), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  for (int i = 0; i < d; ++i) perm[i] = i;
+  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return lam[a] < lam[b]; });
+  if ((e = cudaMemcpyAsync(w.perm, perm.data(), d * sizeof(int), cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+  k_permute_cols<<<blocks_for(nn), 256, 0, s>>>(w.V0, w.V1, w.perm, d);
+  if ((e = cudaMemcpyAsync(w.V0, w.V1, nn * sizeof(float2), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+  const size_t smem = 2 * (size_t)64 * kBJS * sizeof(float2);
+  if ((e = ensure_dynamic_smem((const void*)k_block_jacobi, smem)) != cudaSuccess) return e;
+  if ((e = ensure_dynamic_smem((const void*)k_block_apply, smem)) != cudaSuccess) return e;
+  float2* U = static_cast<float2*>(w.ublk);
+  // pass 1: blocks [kBJ m, kBJ (m + 1)) of S in the sorted order (read through perm)
+  const int nb1 = d / kBJ, nb2 = d / kBJ - 1;
+  k_block_jacobi<<<nb1, 256, smem, s>>>(w.A0, w.perm, d, 0, U);
+  k_block_apply<<<dim3(d / 64, nb1), 256, smem, s>>>(w.V0, d, 0, U);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // pass 2 on the rotated S, blocks shifted by kBJ / 2
+  if ((e = abs_p_tc_rotated(d, Tb, sT, w, fmt, err, s)) != cudaSuccess) return e;
+  k_block_jacobi<<<nb2, 256, smem, s>>>(w.A0, nullptr, d, kBJ / 2, U);
+  k_block_apply<<<dim3(d / 64, nb2), 256, smem, s>>>(w.V0, d, kBJ / 2, U);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);  // the host vectors of the copies go out of scope here
 }
 
 cudaError_t abs_p_tc_update(int d, AbsPWork<float>& w, int fmt, unsigned int* err, cudaStream_t s) {

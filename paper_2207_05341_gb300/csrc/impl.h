@@ -304,6 +304,8 @@ template <class R> struct AbsPWork {
   // max slots and scales
   void *qa_n, *qa_h, *qb_n, *qb_h, *wa, *eb;
   unsigned int* amax;          // [0] Q, [1] W, [2] right operand, [3] unresolved size of a refinement
+  int* perm;                   // the order of increasing lambda (d) and the unitaries of a block pass
+  void* ublk;                  // (d / 64 blocks of 64 x 64 complex)
   double* sc;                  // scales of qa_n, qa_h, qb_n, qb_h, wa, eb; [6] max |lambda|, [7] refinement size
 };
 // Warm-started refinement of the eigenvectors in w.V0 for the Hermitian T (6 planes Tb with scale *sT) on
@@ -318,6 +320,11 @@ template <class R> struct AbsPWork {
 cudaError_t abs_p_tc_correction(int d, const void* Tb, const double* sT, AbsPWork<float>& w, double P, int fmt,
                                 unsigned int* err, cudaStream_t s);
 cudaError_t abs_p_tc_update(int d, AbsPWork<float>& w, int fmt, unsigned int* err, cudaStream_t s);
+// The couplings a first-order correction cannot resolve (near-degenerate pairs): Q's columns sorted by
+// the latest lambda, then two passes of exact Jacobi diagonalisations of 64 x 64 diagonal blocks of
+// S = Q^dag T Q (the second shifted by 32), each block's unitary applied to Q's columns.  Synchronises.
+cudaError_t abs_p_tc_block_phase(int d, const void* Tb, const double* sT, AbsPWork<float>& w, int fmt,
+                                 unsigned int* err, cudaStream_t s);
 cudaError_t abs_p_tc_finish(int d, AbsPWork<float>& w, int fmt, float2* X, unsigned int* err, cudaStream_t s);
 // The backward of abs_p_forward (either form) with the products on tensor cores: Y with Y + Y^dag = dL/dT.
 cudaError_t abs_p_backward_tc(int d, const float2* G, AbsPWork<float>& w, int fmt, float2* Y, unsigned int* err,
