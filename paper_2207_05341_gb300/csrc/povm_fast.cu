@@ -394,10 +394,10 @@ __device__ __forceinline__ float nll_term(float q, float fk, float gconst, float
 // MODE 0: q into p.  MODE 1: likelihood (loss -> scal[2]) and, with adjoint, the transformed adjoint
 // of the high qubits into Wadj (slot (x, r) = the transform over z back to r; pass-1 adjoint splits it
 // into Re = (a + b) / 2 and Im = (a - b) / 2 of the pair).
-// Outcome pairs per CTA: 16 for the forward map (one CTA of 16 NB threads per SM at NB = 32), 8 for the
-// likelihood and adjoint (two CTAs per SM, so that one CTA's loads overlap the other's arithmetic); at
+// Outcome pairs per CTA: 8 (two CTAs per SM at NB = 32, so that one CTA's loads overlap the other's
+// arithmetic, and the forward map's 256 CTAs cover every SM where 16 pairs left 24 of 152 idle); at
 // least 16 when NB = 2 so that a CTA is a whole warp.
-template <int NB, int MODE> constexpr int cta_pairs() { return (MODE == 0 || NB < 4) ? 16 : 8; }
+template <int NB, int MODE> constexpr int cta_pairs() { return NB < 4 ? 16 : 8; }
 
 // BATCH: the grouped variant (a separate instantiation, so that the single-tomography kernel keeps its
 // register allocation)
