@@ -538,12 +538,20 @@ def batch_c4(torch, qst, synth, dev, steps, warmup, seed=30, B=512, prec=None):
             launches = qst.qst_batch_kernel_launches(bt) - l0
             losses = qst.qst_batch_step(bt, fds, want_losses=True)
         it_s = B * steps / (ms / 1e3)
+        # algorithmic HBM bytes of one iteration of all B (the per-phase bytes of the single-context
+        # rooflines, summed over the memory phases of each tomography)
+        mem_phases = ("build_T", "povm_lo", "povm_hi", "povm_adj", "sym", "w2", "w1")
+        hbm_bytes = sum(phase_work(ph, N, prec is not None and N >= 7)[1] for N in Ns for ph in mem_phases)
+        floor_ms = hbm_bytes / (load_peaks()[0]["hbm_gbs"] * 1e9) * 1e3
         return {"workload": "512 tomographies, N ~ U{3..9}, rank-r Ginibre (r ~ U{1..2^N}), 10^5 N shots, "
                             + ("FP32" if prec is None else "mixed FP16x3 for N >= 7, FP32 below"),
                 "Ns_hist": {str(k): Ns.count(k) for k in range(3, 10)},
                 "ms_per_batch_iteration": ms / steps, "aggregate_iters_per_s": it_s,
                 "tomographies_per_s_at_1000_iters": it_s / 1000.0,
                 "graph_nodes_per_iteration": launches // max(steps, 1),
+                "hbm_bytes_per_iteration": hbm_bytes,
+                "hbm_floor_ms": floor_ms,
+                "frac_of_hbm_floor": floor_ms / (ms / steps),
                 "all_losses_finite": bool(np.all(np.isfinite(losses)))}
     finally:
         qst.qst_batch_destroy(bt)
