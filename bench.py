@@ -656,7 +656,8 @@ def profile_batch(args):
     from paper_2207_05341_gb300 import qst, synth
     qst.load()
     dev = torch.device("cuda", 0)
-    Ns = [int(x) for x in np.random.default_rng(30).integers(3, args.profile_batch_max_n + 1, 512)]
+    Ns = [int(x) for x in np.random.default_rng(30).integers(args.profile_batch_min_n, args.profile_batch_max_n + 1,
+                                                             args.profile_batch_count)]
     stream = torch.cuda.Stream(device=dev)
     o = qst.qst_default_options()
     if args.profile_batch == "mixed":
@@ -942,7 +943,9 @@ def main():
     ap.add_argument("--profile-absp", type=int, default=0,
                     help="profiling aid: one mixed A_P context at this N, a cold and a warm step, and exit")
     ap.add_argument("--profile-batch-max-n", type=int, default=9,
-                    help="with --profile-batch: N ~ U{3..this} (a smaller case for full ncu captures)")
+                    help="with --profile-batch: N ~ U{min..this} (a smaller case for full ncu captures)")
+    ap.add_argument("--profile-batch-min-n", type=int, default=3)
+    ap.add_argument("--profile-batch-count", type=int, default=512)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
