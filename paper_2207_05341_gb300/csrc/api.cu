@@ -467,7 +467,7 @@ template <class R> struct Engine {
       if (!done) {
         QST_CU(abs_p_forward<R>(D.d, w->T, *reinterpret_cast<AbsPWork<R>*>(c->apw), sw, warm, c->opt.P, w->X,
                                 c->stream));
-        c->launches += 4 + (long long)sw * (D.d - 1);
+        c->launches += 4 + (long long)sw * jacobi_passes_per_sweep(D.d);
       }
       if (mixed && amax_slot(c, CNT_AMAXT))  // the planes of T are made: restart the max of the next t
         QST_CU(cudaMemsetAsync(amax_slot(c, CNT_AMAXT), 0, sizeof(unsigned int), c->stream));
@@ -945,7 +945,7 @@ template <class R> struct Engine {
     if (!absp) {
       const int sw = (sweeps > 0 ? sweeps : c->sweeps) + ((sweeps > 0 ? sweeps : c->sweeps) & 1);
       QST_CU(jacobi_values_project<R>(D.d, w->T, ap, sw, 2.0, psi, phi, c->stream));
-      c->launches += 1 + (long long)sw * (D.d - 1);
+      c->launches += 1 + (long long)sw * jacobi_passes_per_sweep(D.d);
     }
     double* out = w->scal + 8;
     QST_CU(state_fidelity_from_decomposition<R>(D.d, absp ? ap.Qh : nullptr, phi, ap.s, psi, wgt, c->fq, out,
@@ -1545,6 +1545,17 @@ qst_status qst_eig_counts(const qst_ctx* c, long long* refinements, long long* f
   if (last) {
     last[0] = c->oa_last[0];
     last[1] = c->oa_last[1];
+  }
+  return QST_OK;
+}
+
+qst_status qst_jacobi_schedule(int N, int* count, int* a, int* b, int cap) {
+  if (N < 1 || N > 12 || !count || cap < 0 || (cap > 0 && (!a || !b))) return QST_E_INVAL;
+  const std::vector<qst::JacobiPass>& s = qst::jacobi_schedule(N);
+  *count = (int)s.size();
+  for (int k = 0; k < cap && k < (int)s.size(); ++k) {
+    a[k] = s[k].a;
+    b[k] = s[k].b;
   }
   return QST_OK;
 }

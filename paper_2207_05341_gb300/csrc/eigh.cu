@@ -4,18 +4,21 @@
 //   dL/dT = Q (D o (Q^dag G Q)) Q^dag,  D_ij = (s_i - s_j) / (lambda_i - lambda_j),  D_ii = s'(lambda_i),
 // where G = dL/dX comes from the adjoint POVM map.
 //
-// The eigendecomposition is a cyclic two-sided Jacobi method for complex
-// Hermitian matrices with the parallel round-robin ordering: a sweep is d - 1
-// rounds, each rotating d / 2 disjoint index pairs at once.  For a pair (p, q)
-// with c = A_pq = |c| e^{i phi}, the 2 x 2 block is first made real by
-// diag(1, e^{-i phi}) and then zeroed by the real rotation of Golub and Van
-// Loan (tan theta = sign(tau) / (|tau| + sqrt(1 + tau^2)), tau = (a_qq - a_pp) / 2|c|).
-// One kernel per round: each thread owns the 2 x 2 block (rows of one pair) x
-// (columns of another pair) of A and of V, so every entry is read and written
-// once per round (double-buffered), and V accumulates the rotations, V <- V R.
+// The eigendecomposition is a cyclic two-sided Jacobi method for complex Hermitian matrices (d = 2^N) in the
+// XOR ordering: a sweep is the d - 1 rounds m = 1 .. d - 1, round m rotating the d / 2 disjoint pairs
+// {x, x ^ m} at once.  For a pair (p, q) with c = A_pq = |c| e^{i phi}, the 2 x 2 block is first made real by
+// diag(1, e^{-i phi}) and then zeroed by the real rotation of Golub and Van Loan (tan theta =
+// sign(tau) / (|tau| + sqrt(1 + tau^2)), tau = (a_qq - a_pp) / 2|c|).  The three rounds a, b, a ^ b of a
+// 2-dimensional subspace of GF(2)^N all act within its cosets {x, x ^ a, x ^ b, x ^ a ^ b}, so the rounds of a
+// sweep are grouped by a partition of the nonzero vectors of GF(2)^N into such subspaces (for odd N, all but
+// four single rounds), and one kernel applies the three rounds of a subspace at once: each thread owns the
+// 4 x 4 block (rows of one coset) x (columns of another) of A and of V, multiplies it by the cosets' 4 x 4
+// unitaries, and every entry is read and written once per pass (double-buffered); V accumulates the
+// rotations, V <- V U.  At N = 11 a sweep is 685 passes (2047 rounds), at N = 12 1365 (4095).
 #include <float.h>
 
 #include <algorithm>
+#include <utility>
 #include <vector>
 
 #include "impl.h"
@@ -31,117 +34,321 @@ template <class R> __device__ __forceinline__ R eps_of();
 template <> __device__ __forceinline__ float eps_of<float>() { return FLT_EPSILON; }
 template <> __device__ __forceinline__ double eps_of<double>() { return DBL_EPSILON; }
 
-__device__ __forceinline__ int player_at(int m, int r, int d) { return m == 0 ? 0 : 1 + ((m - 1 + r) % (d - 1)); }
-__device__ __forceinline__ int position_of(int x, int r, int d) {
-  if (x == 0) return 0;
-  int m = (x - 1 - r) % (d - 1);
-  if (m < 0) m += d - 1;
-  return m + 1;
-}
-__device__ __forceinline__ int partner_of(int x, int r, int d) { return player_at(d - 1 - position_of(x, r, d), r, d); }
+// Rotation zeroing entry (p, q) of the Hermitian 2 x 2 block [[a, c], [conj c, b]] (a, b real, c = |c| e^{i phi}):
+// R = [[cs, sn], [-e^{-i phi} sn, e^{-i phi} cs]] in the order (p, q).
+template <class R> struct Rot2 {
+  R cs, sn;
+  cx_t<R> emph;  // e^{-i phi}
+};
 
-// Coefficients of column x of the round's rotation R: R[x][x] = alpha, R[partner][x] = beta.
-template <class R>
-__device__ __forceinline__ void rot_coeffs(const cx_t<R>* A, int d, int x, int px, cx_t<R>& alpha, cx_t<R>& beta) {
-  using V = cx_t<R>;
-  const int p = x < px ? x : px, q = x < px ? px : x;
-  const R a = A[(long long)p * d + p].x, b = A[(long long)q * d + q].x;
-  const V c = A[(long long)p * d + q];
+template <class R> __device__ __forceinline__ Rot2<R> rotation_for(R a, R b, cx_t<R> c) {
+  Rot2<R> o;
+  o.cs = R(1);
+  o.sn = R(0);
+  o.emph = cmake<cx_t<R>>(R(1), R(0));
   // |c| by hypot (no underflow of c.x^2 once the entry is tiny), and no rotation for entries that are
   // negligible against the diagonal: otherwise e^{i phi} = c / |c| loses unit modulus and the
   // accumulated eigenvectors drift from unitarity.
   const R r = hypot(c.x, c.y);
-  R cs = R(1), sn = R(0);
-  V eph = cmake<V>(R(1), R(0));  // e^{i phi}
   if (r > eps_of<R>() * R(1e-4) * (fabs(a) + fabs(b)) && r > tiny_normal<R>() * R(1e8)) {
     const R tau = (b - a) / (R(2) * r);
     const R t = (tau >= R(0) ? R(1) : R(-1)) / (fabs(tau) + sqrt(R(1) + tau * tau));
-    cs = R(1) / sqrt(R(1) + t * t);
-    sn = t * cs;
-    eph = cmake<V>(c.x / r, c.y / r);
+    o.cs = R(1) / sqrt(R(1) + t * t);
+    o.sn = t * o.cs;
+    o.emph = cmake<cx_t<R>>(c.x / r, -c.y / r);
   }
-  const V emph = cconj(eph);  // e^{-i phi}
-  if (x == p) {
-    alpha = cmake<V>(cs, R(0));
-    beta = cmake<V>(-emph.x * sn, -emph.y * sn);
-  } else {
-    alpha = cmake<V>(emph.x * cs, emph.y * cs);
-    beta = cmake<V>(sn, R(0));
-  }
+  return o;
 }
 
 template <class V> __device__ __forceinline__ V cmul(V a, V b) { return cmake<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 template <class V> __device__ __forceinline__ V cmulc(V a, V b) { return cmake<V>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x); }  // conj(a) b
 
-// Rotation of pair k of round r: indices p < q and the 2 x 2 block R = [[cs, sn], [-e^{-i phi} sn, e^{-i phi} cs]]
-// (rows / columns in the order p, q), from the current A.
-template <class R> struct PairRot {
-  int p, q;
-  cx_t<R> r_pp, r_pq, r_qp, r_qq;
-};
+__device__ __forceinline__ int insert_zero(int x, int p) { return ((x >> p) << (p + 1)) | (x & ((1 << p) - 1)); }
 
-template <class R>
-__device__ __forceinline__ PairRot<R> pair_rotation(const cx_t<R>* A, int d, int k, int r) {
-  using V = cx_t<R>;
-  const int x = player_at(k, r, d), y = player_at(d - 1 - k, r, d);
-  PairRot<R> pr;
-  pr.p = x < y ? x : y;
-  pr.q = x < y ? y : x;
-  V alpha, beta;
-  rot_coeffs<R>(A, d, pr.p, pr.q, alpha, beta);  // column p: R[p][p] = alpha, R[q][p] = beta
-  pr.r_pp = alpha;
-  pr.r_qp = beta;
-  rot_coeffs<R>(A, d, pr.q, pr.p, alpha, beta);  // column q: R[q][q] = alpha, R[p][q] = beta
-  pr.r_qq = alpha;
-  pr.r_pq = beta;
-  return pr;
+// Coset number c of the pass's subspace: G = 2, {x, x ^ a}; G = 4, {x, x ^ a, x ^ b, x ^ a ^ b}, where the
+// representative x has the pivot bits (plo, and phi for G = 4) clear and local index i = (bit 0: a, bit 1: b).
+template <int G>
+__device__ __forceinline__ void coset_of(int c, int a, int b, int plo, int phi, int (&e)[G]) {
+  const int x = G == 2 ? insert_zero(c, plo) : insert_zero(insert_zero(c, plo), phi);
+#pragma unroll
+  for (int i = 0; i < G; ++i) e[i] = x ^ ((i & 1) ? a : 0) ^ ((i & 2) ? b : 0);
 }
 
-// One round: every thread owns the 2 x 2 block (rows of pair k) x (columns of pair l) of A and of V,
-// so each entry is read and written once: A' = R^dag A R on the block, V' = V R on rows {p_k, q_k}.
-// Vi == NULL: no eigenvectors are accumulated; phi != NULL: the vector phi <- R^dag phi in place (the
-// first block column, one thread per pair), so that after the sweeps phi = Q^dag phi_0.
-template <class R>
-__global__ void __launch_bounds__(256) k_jacobi_round(const cx_t<R>* __restrict__ A, cx_t<R>* __restrict__ Ao,
-                                                       const cx_t<R>* __restrict__ Vi, cx_t<R>* __restrict__ Vo,
-                                                       cx_t<R>* __restrict__ phi, int d, int r) {
+template <class R> __device__ __forceinline__ R lane_shfl(R v, int src, int width) {
+  return __shfl_sync(0xffffffffu, v, src, width);
+}
+template <class R> __device__ __forceinline__ R lane_xor(R v, int m, int width) {
+  return __shfl_xor_sync(0xffffffffu, v, m, width);
+}
+template <class R> __device__ __forceinline__ Rot2<R> rot_from_lane(const Rot2<R>& r, int src, int width) {
+  Rot2<R> o;
+  o.cs = lane_shfl(r.cs, src, width);
+  o.sn = lane_shfl(r.sn, src, width);
+  o.emph = cmake<cx_t<R>>(lane_shfl(r.emph.x, src, width), lane_shfl(r.emph.y, src, width));
+  return o;
+}
+
+// X <- X R on columns (p, q) of one row x of B or U (R = [[cs, sn], [-e^{-i phi} sn, e^{-i phi} cs]]).
+template <class R, int G>
+__device__ __forceinline__ void rotate_cols(cx_t<R> (&x)[G], int p, int q, const Rot2<R>& r) {
+  using V = cx_t<R>;
+  const V rqp = cmake<V>(-r.emph.x * r.sn, -r.emph.y * r.sn), rqq = cmake<V>(r.emph.x * r.cs, r.emph.y * r.cs);
+  const V xp = x[p], xq = x[q];
+  x[p] = cadd(cmake<V>(xp.x * r.cs, xp.y * r.cs), cmul(xq, rqp));
+  x[q] = cadd(cmake<V>(xp.x * r.sn, xp.y * r.sn), cmul(xq, rqq));
+}
+
+// The pass's rotations on one coset, in the order of its rounds (round s pairs local i with i ^ s,
+// s = 1 .. G - 1), each computed from the 2 x 2 principal blocks of the coset's G x G principal block B of A
+// after the rounds before it: U = R_1 ... R_{G-1}, so that U^dag A[e, e] U is that block after the pass.
+// The G lanes of an aligned group take one coset; lane i holds row i of B and of U and returns row i of U.
+// A pair's rotation is computed on its lower lane and broadcast; rows are exchanged by shuffles.
+template <class R, int G>
+__device__ __forceinline__ void coset_unitary_row(const cx_t<R>* __restrict__ A, int d, const int (&e)[G], int i,
+                                                  cx_t<R> (&u)[G]) {
+  using V = cx_t<R>;
+  V b[G];
+  int ei = e[0];
+#pragma unroll
+  for (int jj = 1; jj < G; ++jj)
+    if (jj == i) ei = e[jj];
+#pragma unroll
+  for (int j = 0; j < G; ++j) {
+    b[j] = A[(long long)ei * d + e[j]];
+    u[j] = cmake<V>(i == j ? R(1) : R(0), R(0));
+  }
+#pragma unroll
+  for (int s = 1; s < G; ++s) {
+    R di = R(0);
+    V cij = cmake<V>(R(0), R(0));
+#pragma unroll
+    for (int jj = 0; jj < G; ++jj) {
+      if (jj == i) di = b[jj].x;
+      if (jj == (i ^ s)) cij = b[jj];
+    }
+    const R dj = lane_xor(di, s, G);
+    const Rot2<R> mine = rotation_for<R>(di, dj, cij);  // the pair's rotation where this lane is the lower one
+    const int p1 = s == 1 ? 2 : 1;                      // lower index of the round's second pair (G = 4)
+    const Rot2<R> r0 = rot_from_lane(mine, 0, G);
+    const Rot2<R> r1 = G == 4 ? rot_from_lane(mine, p1, G) : r0;
+    rotate_cols<R, G>(b, 0, s, r0);
+    rotate_cols<R, G>(u, 0, s, r0);
+    if (G == 4) {
+      rotate_cols<R, G>(b, p1 % G, (p1 ^ s) % G, r1);
+      rotate_cols<R, G>(u, p1 % G, (p1 ^ s) % G, r1);
+    }
+    // rows p, q of B <- R^dag rows (p, q): this lane's row with its partner's
+    V o[G];
+#pragma unroll
+    for (int j = 0; j < G; ++j) o[j] = cmake<V>(lane_xor(b[j].x, s, G), lane_xor(b[j].y, s, G));
+    const Rot2<R> r = (i == 0 || i == s) ? r0 : r1;
+    const V rqp = cmake<V>(-r.emph.x * r.sn, -r.emph.y * r.sn), rqq = cmake<V>(r.emph.x * r.cs, r.emph.y * r.cs);
+    const bool lower = i < (i ^ s);
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+      // lower: conj(R_pp) b_p + conj(R_qp) b_q; upper: conj(R_pq) b_p + conj(R_qq) b_q (b_p the partner's)
+      b[j] = lower ? cadd(cmake<V>(r.cs * b[j].x, r.cs * b[j].y), cmulc(rqp, o[j]))
+                   : cadd(cmake<V>(r.sn * o[j].x, r.sn * o[j].y), cmulc(rqq, b[j]));
+    }
+  }
+}
+
+// The unitaries of a CTA's cosets in shared memory, entry (r, c) of coset slot s at [r][c][s] (consecutive
+// cosets in consecutive words: the 16 column cosets a warp reads are in distinct banks).  FP32 keeps the
+// forms the packed products take: u and (u.y, u.x) for products X U, conj(u) and (u.y, u.x) for U^dag X.
+template <class R, int G> struct PassSmem {
+  cx_t<R> uk[G][G][16], ul[G][G][16];
+  cx_t<R> uk2[G][G][16], ul2[G][G][16];  // FP32: conj(u_k), (u_l.y, u_l.x); FP64: unused
+  int ek[16][G];
+};
+
+// s += m u (complex) as two packed FP32 FMAs: (m.x, m.x) (u.x, u.y) + (-m.y, m.y) (u.y, u.x).
+__device__ __forceinline__ float2 cmac2(float2 s, float2 mxx, float2 myn, float2 u, float2 usw) {
+  return __ffma2_rn(myn, usw, __ffma2_rn(mxx, u, s));
+}
+
+// One pass: the rounds of the subspace {a, b, a ^ b} (G = 4) or the single round a (G = 2).  Every thread owns
+// the G x G block (rows of coset k) x (columns of coset l) of A and of V, so each entry is read and written once
+// per pass (double-buffered): A' = U_k^dag A U_l, V' = V U_l on rows e_k.  A thread loads its block of A
+// first; meanwhile G warps form the unitaries of the CTA's 16 row and 16 column cosets from A.  Vi == NULL:
+// no eigenvectors are accumulated; phi != NULL: the vector phi <- U^dag phi in place (the first block
+// column, one thread per coset), so that after the sweeps phi = Q^dag phi_0.
+template <class R, int G>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_jacobi_pass(const cx_t<R>* __restrict__ A, cx_t<R>* __restrict__ Ao,
+                                                      const cx_t<R>* __restrict__ Vi, cx_t<R>* __restrict__ Vo,
+                                                      cx_t<R>* __restrict__ phi, int d, int a, int b, int plo,
+                                                      int phi_bit) {
   using V = cx_t<R>;
   constexpr int TP = 16;
-  __shared__ PairRot<R> rk[TP], rl[TP];
-  const int half = d >> 1;
+  constexpr bool kF32 = sizeof(R) == 4;
+  __shared__ PassSmem<R, G> sm;
+  const int nc = d / G;
   const int k0 = blockIdx.y * TP, l0 = blockIdx.x * TP;
   const int t = threadIdx.x;
-  if (t < TP && k0 + t < half) rk[t] = pair_rotation<R>(A, d, k0 + t, r);
-  else if (t >= 32 && t < 32 + TP && l0 + t - 32 < half) rl[t - 32] = pair_rotation<R>(A, d, l0 + t - 32, r);
-  __syncthreads();
-  if (phi != nullptr && blockIdx.x == 0 && t < TP && k0 + t < half) {
-    const PairRot<R> a = rk[t];
-    const V xp = phi[a.p], xq = phi[a.q];
-    phi[a.p] = cadd(cmulc(a.r_pp, xp), cmulc(a.r_qp, xq));
-    phi[a.q] = cadd(cmulc(a.r_pq, xp), cmulc(a.r_qq, xq));
+  const int kk = t / TP, ll = t % TP;
+  const bool active = k0 + kk < nc && l0 + ll < nc;
+  long long row[G];
+  int col[G];
+  {
+    int er[G], ec[G];
+    coset_of<G>(min(k0 + kk, nc - 1), a, b, plo, phi_bit, er);
+    coset_of<G>(min(l0 + ll, nc - 1), a, b, plo, phi_bit, ec);
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+      row[i] = (long long)er[i] * d;
+      col[i] = ec[i];
+    }
   }
-  const int k = k0 + t / TP, l = l0 + t % TP;
-  if (k >= half || l >= half) return;
-  const PairRot<R> a = rk[t / TP], b = rl[t % TP];
-  const long long rp = (long long)a.p * d, rq = (long long)a.q * d;
-  const V m_pp = A[rp + b.p], m_pq = A[rp + b.q], m_qp = A[rq + b.p], m_qq = A[rq + b.q];
-  // M R_l (columns p_l, q_l)
-  const V u_pp = cadd(cmul(m_pp, b.r_pp), cmul(m_pq, b.r_qp));
-  const V u_pq = cadd(cmul(m_pp, b.r_pq), cmul(m_pq, b.r_qq));
-  const V u_qp = cadd(cmul(m_qp, b.r_pp), cmul(m_qq, b.r_qp));
-  const V u_qq = cadd(cmul(m_qp, b.r_pq), cmul(m_qq, b.r_qq));
-  // R_k^dag (M R_l): row p' = conj(R[p][p]) row p + conj(R[q][p]) row q; row q' = conj(R[p][q]) row p + conj(R[q][q]) row q
-  Ao[rp + b.p] = cadd(cmulc(a.r_pp, u_pp), cmulc(a.r_qp, u_qp));
-  Ao[rp + b.q] = cadd(cmulc(a.r_pp, u_pq), cmulc(a.r_qp, u_qq));
-  Ao[rq + b.p] = cadd(cmulc(a.r_pq, u_pp), cmulc(a.r_qq, u_qp));
-  Ao[rq + b.q] = cadd(cmulc(a.r_pq, u_pq), cmulc(a.r_qq, u_qq));
-  if (Vi == nullptr) return;
-  // V' = V R on rows p_k, q_k, columns p_l, q_l
-  const V v_pp = Vi[rp + b.p], v_pq = Vi[rp + b.q], v_qp = Vi[rq + b.p], v_qq = Vi[rq + b.q];
-  Vo[rp + b.p] = cadd(cmul(v_pp, b.r_pp), cmul(v_pq, b.r_qp));
-  Vo[rp + b.q] = cadd(cmul(v_pp, b.r_pq), cmul(v_pq, b.r_qq));
-  Vo[rq + b.p] = cadd(cmul(v_qp, b.r_pp), cmul(v_qq, b.r_qp));
-  Vo[rq + b.q] = cadd(cmul(v_qp, b.r_pq), cmul(v_qq, b.r_qq));
+  V M[G][G];
+  if (active) {
+#pragma unroll
+    for (int i = 0; i < G; ++i)
+#pragma unroll
+      for (int j = 0; j < G; ++j) M[i][j] = A[row[i] + col[j]];
+  }
+  if (t < 32 * G) {  // G warps: each aligned group of G lanes one coset, 16 of rows then 16 of columns
+    const int grp = t / G, i = t % G;
+    const bool isrow = grp < TP;
+    const int slot = isrow ? grp : grp - TP;
+    const int c0 = (isrow ? k0 : l0) + slot;
+    const int c = c0 < nc ? c0 : nc - 1;  // every lane of these warps takes part in the shuffles
+    int e[G];
+    coset_of<G>(c, a, b, plo, phi_bit, e);
+    V u[G];
+    coset_unitary_row<R, G>(A, d, e, i, u);
+    if (c0 < nc) {
+#pragma unroll
+      for (int j = 0; j < G; ++j) {
+        if (isrow) {
+          sm.uk[i][j][slot] = u[j];
+          if (kF32) sm.uk2[i][j][slot] = cmake<V>(u[j].x, -u[j].y);
+          if (i == 0) sm.ek[slot][j] = e[j];
+        } else {
+          sm.ul[i][j][slot] = u[j];
+          if (kF32) sm.ul2[i][j][slot] = cmake<V>(u[j].y, u[j].x);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (phi != nullptr && blockIdx.x == 0 && t < TP && k0 + t < nc) {
+    V x[G];
+#pragma unroll
+    for (int i = 0; i < G; ++i) x[i] = phi[sm.ek[t][i]];
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+      V y = cmake<V>(R(0), R(0));
+#pragma unroll
+      for (int r = 0; r < G; ++r) y = cadd(y, cmulc(sm.uk[r][i][t], x[r]));
+      phi[sm.ek[t][i]] = y;
+    }
+  }
+  if (!active) return;
+  if constexpr (kF32) {
+    // T = M U_l (column c of M at a time), O = U_k^dag T (row r of T at a time), V' = V U_l
+    float2 T[G][G];
+#pragma unroll
+    for (int r = 0; r < G; ++r)
+#pragma unroll
+      for (int j = 0; j < G; ++j) T[r][j] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < G; ++c) {
+      float2 mxx[G], myn[G];
+#pragma unroll
+      for (int r = 0; r < G; ++r) {
+        mxx[r] = make_float2(M[r][c].x, M[r][c].x);
+        myn[r] = make_float2(-M[r][c].y, M[r][c].y);
+      }
+#pragma unroll
+      for (int j = 0; j < G; ++j) {
+        const float2 u = sm.ul[c][j][ll], usw = sm.ul2[c][j][ll];
+#pragma unroll
+        for (int r = 0; r < G; ++r) T[r][j] = cmac2(T[r][j], mxx[r], myn[r], u, usw);
+      }
+    }
+    // conj(u) t = (t.x, t.x) conj(u) + (t.y, t.y) (u.y, u.x)
+    float2 O[G][G];
+#pragma unroll
+    for (int i = 0; i < G; ++i)
+#pragma unroll
+      for (int j = 0; j < G; ++j) O[i][j] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < G; ++r) {
+#pragma unroll
+      for (int i = 0; i < G; ++i) {
+        const float2 cu = sm.uk2[r][i][kk];
+        const float2 u = sm.uk[r][i][kk];
+        const float2 usw = make_float2(u.y, u.x);
+#pragma unroll
+        for (int j = 0; j < G; ++j)
+          O[i][j] = __ffma2_rn(make_float2(T[r][j].y, T[r][j].y), usw,
+                               __ffma2_rn(make_float2(T[r][j].x, T[r][j].x), cu, O[i][j]));
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < G; ++i)
+#pragma unroll
+      for (int j = 0; j < G; ++j) Ao[row[i] + col[j]] = O[i][j];
+    if (Vi == nullptr) return;
+    asm volatile("" ::: "memory");  // V's loads after A's stores: A's and V's blocks are not live together
+    float2 Vb[G][G], W[G][G];
+#pragma unroll
+    for (int i = 0; i < G; ++i)
+#pragma unroll
+      for (int j = 0; j < G; ++j) {
+        Vb[i][j] = Vi[row[i] + col[j]];
+        W[i][j] = make_float2(0.f, 0.f);
+      }
+#pragma unroll
+    for (int c = 0; c < G; ++c) {
+#pragma unroll
+      for (int j = 0; j < G; ++j) {
+        const float2 u = sm.ul[c][j][ll], usw = sm.ul2[c][j][ll];
+#pragma unroll
+        for (int i = 0; i < G; ++i)
+          W[i][j] = cmac2(W[i][j], make_float2(Vb[i][c].x, Vb[i][c].x), make_float2(-Vb[i][c].y, Vb[i][c].y), u,
+                          usw);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < G; ++i)
+#pragma unroll
+      for (int j = 0; j < G; ++j) Vo[row[i] + col[j]] = W[i][j];
+  } else {
+    V T[G][G];  // M U_l
+#pragma unroll
+    for (int r = 0; r < G; ++r)
+#pragma unroll
+      for (int j = 0; j < G; ++j) {
+        V s = cmake<V>(R(0), R(0));
+#pragma unroll
+        for (int c = 0; c < G; ++c) s = cadd(s, cmul(M[r][c], sm.ul[c][j][ll]));
+        T[r][j] = s;
+      }
+#pragma unroll
+    for (int i = 0; i < G; ++i)
+#pragma unroll
+      for (int j = 0; j < G; ++j) {
+        V s = cmake<V>(R(0), R(0));
+#pragma unroll
+        for (int r = 0; r < G; ++r) s = cadd(s, cmulc(sm.uk[r][i][kk], T[r][j]));
+        Ao[row[i] + col[j]] = s;
+      }
+    if (Vi == nullptr) return;
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+      V v[G];
+#pragma unroll
+      for (int c = 0; c < G; ++c) v[c] = Vi[row[i] + col[c]];
+#pragma unroll
+      for (int j = 0; j < G; ++j) {
+        V s = cmake<V>(R(0), R(0));
+#pragma unroll
+        for (int c = 0; c < G; ++c) s = cadd(s, cmul(v[c], sm.ul[c][j][ll]));
+        Vo[row[i] + col[j]] = s;
+      }
+    }
+  }
 }
 
 template <class R>
@@ -229,7 +436,100 @@ int blocks_for(long long n) {
   return (int)(b > 4096 ? 4096 : (b < 1 ? 1 : b));
 }
 
+// Partition of the nonzero vectors of GF(2)^n into lines {u, v, u ^ v} and, for odd n, one plane span{p1, p2, p3},
+// built from V(n) = V(n - 2) + V(2) (the new coordinates are bits n - 2 and n - 1): the line of the new
+// coordinates; each line {u1, u2, u1 ^ u2} of V(n - 2) lifted to the four lines {u1 + x, u2 + w x,
+// u1 ^ u2 + (1 + w) x} for x in V(2) = GF(4) (w x and (1 + w) x = w^2 x run over GF(4) with x, so the 12 points
+// over the line are each covered once); the plane of V(n - 2) kept, with its 21 points over V(2) \ 0 as the
+// seven lines {p(y) + 01, p(a y) + 10, p((1 + a) y) + 11}, y in GF(8)* = GF(2)[a] / (a^3 + a + 1) \ 0 and p
+// the coordinates in the plane's basis.  Base cases: V(1) = {1} (a single point), V(2) one line, V(3) one plane.
+struct VecPartition {
+  std::vector<std::pair<int, int>> lines;
+  int plane[3] = {0, 0, 0};
+};
+
+VecPartition vec_partition(int n) {
+  VecPartition out;
+  if (n == 2) out.lines.push_back({1, 2});
+  if (n == 3) out.plane[0] = 1, out.plane[1] = 2, out.plane[2] = 4;
+  if (n <= 3) return out;
+  static const int kTimesW[4] = {0, 2, 3, 1};                 // x -> w x in GF(4), bit 0 = 1, bit 1 = w
+  static const int kTimesA[8] = {0, 2, 4, 6, 3, 1, 7, 5};     // y -> a y in GF(8), bits 1, a, a^2
+  const VecPartition low = vec_partition(n - 2);
+  const int s = n - 2;
+  out.lines.push_back({1 << s, 2 << s});
+  for (const auto& l : low.lines)
+    for (int x = 0; x < 4; ++x) out.lines.push_back({l.first | (x << s), l.second | (kTimesW[x] << s)});
+  if (low.plane[0] != 0) {
+    const int* P = low.plane;
+    auto p = [P](int y) { return ((y & 1) ? P[0] : 0) ^ ((y & 2) ? P[1] : 0) ^ ((y & 4) ? P[2] : 0); };
+    for (int y = 1; y < 8; ++y) out.lines.push_back({p(y) | (1 << s), p(kTimesA[y]) | (2 << s)});
+    out.plane[0] = P[0], out.plane[1] = P[1], out.plane[2] = P[2];
+  }
+  return out;
+}
+
+int top_bit(int x) { return 31 - __builtin_clz((unsigned)x); }
+
+JacobiPass make_pass(int a, int b) {
+  JacobiPass p;
+  if (b == 0) {
+    p.a = a, p.b = 0, p.plo = top_bit(a), p.phi = 0;
+    return p;
+  }
+  if (top_bit(b) > top_bit(a)) std::swap(a, b);
+  if (top_bit(b) == top_bit(a)) b ^= a;
+  if ((a >> top_bit(b)) & 1) a ^= b;
+  p.a = a, p.b = b, p.plo = top_bit(b), p.phi = top_bit(a);
+  return p;
+}
+
+std::vector<JacobiPass> build_schedule(int N) {
+  std::vector<JacobiPass> out;
+  if (N == 1) {
+    out.push_back(make_pass(1, 0));
+    return out;
+  }
+  const VecPartition part = vec_partition(N);
+  for (const auto& l : part.lines) out.push_back(make_pass(l.first, l.second));
+  if (part.plane[0] != 0) {  // the plane as one line and its four other points
+    const int p1 = part.plane[0], p2 = part.plane[1], p3 = part.plane[2];
+    out.push_back(make_pass(p1, p2));
+    for (int m : {p3, p1 ^ p3, p2 ^ p3, p1 ^ p2 ^ p3}) out.push_back(make_pass(m, 0));
+  }
+  return out;
+}
+
+constexpr int kMaxScheduleN = 14;
+
+// One sweep: every pass of the schedule, ping-ponging (Ain, Aout) and (Vin, Vout).
+template <class R>
+cudaError_t jacobi_sweep(int d, cx_t<R>*& Ain, cx_t<R>*& Aout, cx_t<R>*& Vin, cx_t<R>*& Vout, cx_t<R>* phi,
+                         cudaStream_t s) {
+  const std::vector<JacobiPass>& sched = jacobi_schedule(top_bit(d));
+  const int n4 = d / 4, n2 = d / 2;
+  const dim3 g4((n4 + 15) / 16, (n4 + 15) / 16), g2((n2 + 15) / 16, (n2 + 15) / 16);
+  for (const JacobiPass& p : sched) {
+    if (p.b != 0) k_jacobi_pass<R, 4><<<g4, 256, 0, s>>>(Ain, Aout, Vin, Vout, phi, d, p.a, p.b, p.plo, p.phi);
+    else k_jacobi_pass<R, 2><<<g2, 256, 0, s>>>(Ain, Aout, Vin, Vout, phi, d, p.a, 0, p.plo, 0);
+    std::swap(Ain, Aout);
+    if (Vin != nullptr) std::swap(Vin, Vout);
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+const std::vector<JacobiPass>& jacobi_schedule(int N) {
+  static const std::vector<std::vector<JacobiPass>> all = [] {
+    std::vector<std::vector<JacobiPass>> v(kMaxScheduleN + 1);
+    for (int n = 1; n <= kMaxScheduleN; ++n) v[n] = build_schedule(n);
+    return v;
+  }();
+  return all[N < 1 ? 1 : (N > kMaxScheduleN ? kMaxScheduleN : N)];
+}
+
+long long jacobi_passes_per_sweep(int d) { return (long long)jacobi_schedule(top_bit(d)).size(); }
 
 template <class R>
 cudaError_t abs_p_forward(int d, const cx_t<R>* T, AbsPWork<R>& w, int sweeps, bool warm, double P, cx_t<R>* X,
@@ -245,17 +545,15 @@ cudaError_t abs_p_forward(int d, const cx_t<R>* T, AbsPWork<R>& w, int sweeps, b
     if ((e = cudaMemcpyAsync(w.A0, T, nn * sizeof(V), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
     k_identity<R><<<blocks_for(nn), 256, 0, s>>>(w.V0, d);
   }
-  // an even number of sweeps of d - 1 (odd) rounds brings both ping-pong pairs back to A0 / V0
+  // an even number of sweeps of an odd number of passes brings both ping-pong pairs back to A0 / V0
   V *Ain = w.A0, *Aout = w.A1, *Vin = w.V0, *Vout = w.V1;
-  const dim3 grid((d / 2 + 15) / 16, (d / 2 + 15) / 16);
-  for (int sw = 0; sw < sweeps; ++sw) {
-    for (int r = 0; r < d - 1; ++r) {
-      k_jacobi_round<R><<<grid, 256, 0, s>>>(Ain, Aout, Vin, Vout, nullptr, d, r);
-      V* t = Ain; Ain = Aout; Aout = t;
-      t = Vin; Vin = Vout; Vout = t;
-    }
+  for (int sw = 0; sw < sweeps; ++sw)
+    if ((e = jacobi_sweep<R>(d, Ain, Aout, Vin, Vout, nullptr, s)) != cudaSuccess) return e;
+  if (Vin != w.V0) {  // an odd number of sweeps: the eigenvectors are kept in V0
+    if ((e = cudaMemcpyAsync(w.V0, Vin, nn * sizeof(V), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+    Vin = w.V0;
   }
-  w.A = Ain;  // diagonalised (A0)
+  w.A = Ain;  // diagonalised
   w.Q = Vin;  // eigenvectors in columns (V0)
   k_absp_spectrum<R><<<1, 1024, 0, s>>>(w.A, w.lam, w.s, w.sp, d, P, sizeof(R) == 4 ? 1e-7 : 1e-15);
   k_scale_cols<R><<<blocks_for(nn), 256, 0, s>>>(w.Q, w.s, w.W, d);
@@ -275,14 +573,9 @@ cudaError_t jacobi_values_project(int d, const cx_t<R>* T, AbsPWork<R>& w, int s
   cudaError_t e;
   if ((e = cudaMemcpyAsync(w.A0, T, nn * sizeof(V), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(phi, psi, (size_t)d * sizeof(V), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
-  V *Ain = w.A0, *Aout = w.A1;
-  const dim3 grid((d / 2 + 15) / 16, (d / 2 + 15) / 16);
-  for (int sw = 0; sw < sweeps; ++sw) {
-    for (int r = 0; r < d - 1; ++r) {
-      k_jacobi_round<R><<<grid, 256, 0, s>>>(Ain, Aout, nullptr, nullptr, phi, d, r);
-      V* t = Ain; Ain = Aout; Aout = t;
-    }
-  }
+  V *Ain = w.A0, *Aout = w.A1, *Vin = nullptr, *Vout = nullptr;
+  for (int sw = 0; sw < sweeps; ++sw)
+    if ((e = jacobi_sweep<R>(d, Ain, Aout, Vin, Vout, phi, s)) != cudaSuccess) return e;
   w.A = Ain;
   k_absp_spectrum<R><<<1, 1024, 0, s>>>(w.A, w.lam, w.s, w.sp, d, P, sizeof(R) == 4 ? 1e-7 : 1e-15);
   return cudaGetLastError();
@@ -436,17 +729,14 @@ __global__ void __launch_bounds__(256) k_block_jacobi(const float2* __restrict__
   __syncthreads();
   for (int sw = 0; sw < kBJSweeps; ++sw) {
     for (int r = 0; r < kBJ - 1; ++r) {
-      if (threadIdx.x < NP) {  // the round's rotations, from the block before the round
-        const int k = threadIdx.x;
-        const int x = player_at(k, r, kBJ), y = player_at(kBJ - 1 - k, r, kBJ);
-        const int p = x < y ? x : y, q = x < y ? y : x;
-        float2 al, be;
-        rot_coeffs<float>(Sb, kBJS, p, q, al, be);
-        r_pp[k] = al;
-        r_qp[k] = be;
-        rot_coeffs<float>(Sb, kBJS, q, p, al, be);
-        r_qq[k] = al;
-        r_pq[k] = be;
+      if (threadIdx.x < NP) {  // round m = r + 1 pairs p with p ^ m; its rotations, from the block before it
+        const int k = threadIdx.x, m = r + 1;
+        const int p = insert_zero(k, 31 - __clz(m)), q = p ^ m;
+        const Rot2<float> ro = rotation_for<float>(Sb[p * kBJS + p].x, Sb[q * kBJS + q].x, Sb[p * kBJS + q]);
+        r_pp[k] = make_float2(ro.cs, 0.f);
+        r_pq[k] = make_float2(ro.sn, 0.f);
+        r_qp[k] = make_float2(-ro.emph.x * ro.sn, -ro.emph.y * ro.sn);
+        r_qq[k] = make_float2(ro.emph.x * ro.cs, ro.emph.y * ro.cs);
         pi[k] = p;
         qi[k] = q;
       }

@@ -330,6 +330,15 @@ cudaError_t abs_p_tc_finish(int d, AbsPWork<float>& w, int fmt, float2* X, unsig
 cudaError_t abs_p_backward_tc(int d, const float2* G, AbsPWork<float>& w, int fmt, float2* Y, unsigned int* err,
                               cudaStream_t s);
 size_t abs_p_tc_plane_bytes(int d);  // bytes of one 4-plane buffer (a 6-plane one is 1.5 times that)
+// One sweep of the Jacobi eigensolver for d = 2^N in the XOR ordering (round m rotates the pairs {x, x ^ m},
+// m = 1 .. d - 1), as passes: b != 0, the three rounds a, b, a ^ b of one 2-dimensional subspace (they act
+// within its cosets), in reduced form (pivot bits phi = top bit of a > plo = top bit of b, a has bit plo
+// clear); b == 0, the single round a (plo = top bit of a).  The number of passes is odd for every N.
+struct JacobiPass {
+  int a, b, plo, phi;
+};
+const std::vector<JacobiPass>& jacobi_schedule(int N);  // 1 <= N <= 14
+long long jacobi_passes_per_sweep(int d);
 // X = Q |Lambda|^P Q^dag (lower tiles) from T via `sweeps` (even) Jacobi sweeps; warm == true starts
 // from the previous eigenvectors (V0, with Q^dag in Qh).  Leaves Q in V0 and Q^dag in Qh.
 template <class R> cudaError_t abs_p_forward(int d, const cx_t<R>* T, AbsPWork<R>& w, int sweeps, bool warm,

@@ -47,7 +47,7 @@ EXPORTED = [
     "qst_batch_init", "qst_batch_context", "qst_batch_set_params", "qst_batch_step",
     "qst_batch_reconstruct", "qst_batch_kernel_launches", "qst_batch_sync", "qst_batch_destroy",
     "qst_classical_fidelity", "qst_test_state", "qst_sample_counts", "qst_theta_size_net",
-    "qst_state_fidelity",
+    "qst_state_fidelity", "qst_jacobi_schedule",
 ]
 
 PHASES = ["hidden", "build_T", "x_fwd", "povm_lo", "povm_hi", "povm_adj", "gt", "sym", "w2", "w1", "fused"]
@@ -121,6 +121,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "qst_set_state": (i, [vp, vp, sz]),
         "qst_iterations": (ctypes.c_longlong, [vp]),
         "qst_eig_counts": (i, [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), pd]),
+        "qst_jacobi_schedule": (i, [i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), i]),
         "qst_kernel_launches": (ctypes.c_longlong, [vp]),
         "qst_sync": (i, [vp]),
         "qst_strerror": (ctypes.c_char_p, [i]),
@@ -358,6 +359,16 @@ def qst_eig_counts(ctx: int, last: bool = False):
     v = (ctypes.c_double * 2)()
     _check(load().qst_eig_counts(ctx, ctypes.byref(a), ctypes.byref(b), v), "qst_eig_counts")
     return (a.value, b.value, (v[0], v[1])) if last else (a.value, b.value)
+
+
+def qst_jacobi_schedule(N: int):
+    """Passes of one Jacobi sweep at N qubits (host only): a list of (a, b), b == 0 for a single round."""
+    cnt = ctypes.c_int()
+    _check(load().qst_jacobi_schedule(int(N), ctypes.byref(cnt), None, None, 0), "qst_jacobi_schedule")
+    a = (ctypes.c_int * cnt.value)()
+    b = (ctypes.c_int * cnt.value)()
+    _check(load().qst_jacobi_schedule(int(N), ctypes.byref(cnt), a, b, cnt.value), "qst_jacobi_schedule")
+    return list(zip(a, b))
 
 
 def qst_get_tuning() -> dict:
