@@ -274,12 +274,13 @@ qst_status qst_eig_counts(const qst_ctx* ctx, long long* refinements, long long*
 
 /* The ordering of the Jacobi eigensolver behind QST_MAP_ABS_P and qst_state_fidelity (Sec. 3.2,
  * eq. abs_P; inspection only, no GPU needed): for d = 2^N, round m of a sweep rotates the index pairs
- * {x, x ^ m}, m = 1 .. d - 1, and one kernel launch (a pass) applies either the three rounds a, b, a ^ b
- * of a 2-dimensional subspace of GF(2)^N (b != 0, reduced form: a and b are the subspace's basis with
- * distinct top bits, the top bit of b clear in a) or the single round a (b == 0).  count = passes per
- * sweep; the first min(count, cap) passes go to a[], b[] (host arrays; may be NULL when cap == 0).
- * QST_E_INVAL for N outside 1..12 or NULL arrays with cap > 0. */
-qst_status qst_jacobi_schedule(int N, int* count, int* a, int* b, int cap);
+ * {x, x ^ m}, m = 1 .. d - 1, and each pass applies the 2^k - 1 rounds of one k-dimensional subspace of
+ * GF(2)^N (its nonzero elements; they act within the subspace's cosets of 2^k indices), k = 1 .. 4: a
+ * partition of GF(2)^N \ {0} into such subspaces is one sweep.  count = passes per sweep; for the first
+ * min(count, cap) passes, dims[p] = k and basis[4 p .. 4 p + k) the subspace's basis in reduced form (top
+ * bits distinct and ascending, each top bit clear in the other vectors; unused entries 0).  Host arrays;
+ * may be NULL when cap == 0.  QST_E_INVAL for N outside 1..12 or NULL arrays with cap > 0. */
+qst_status qst_jacobi_schedule(int N, int* count, int* dims, int* basis, int cap);
 
 /* Number of kernel launches the library has enqueued on this context (graph
  * replays count every kernel node). */

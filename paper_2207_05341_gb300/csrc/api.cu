@@ -309,6 +309,7 @@ template <class R> qst_status alloc_work(qst_ctx* c) {
     QST_CU(dalloc(c, &ap->lam, (size_t)D.d));
     QST_CU(dalloc(c, &ap->s, (size_t)D.d));
     QST_CU(dalloc(c, &ap->sp, (size_t)D.d));
+    QST_CU(dalloc(c, &ap->ucos, 16 * (size_t)D.d));
     if (is_mixed(c)) {  // operand planes of the tensor-core refinement
       const size_t pb = abs_p_tc_plane_bytes(D.d);
       unsigned char* buf = nullptr;
@@ -922,7 +923,7 @@ template <class R> struct Engine {
         QST_CU(net_build_T<R>(D, w->theta, w->hid, w->dt, w->T, nullptr, c->stream));
       }
       c->launches += 2;
-      if (!c->apw) {  // the eigenvalue workspace only: two d x d buffers and three d-vectors
+      if (!c->apw) {  // the eigenvalue workspace only: two d x d buffers, three d-vectors, coset unitaries
         AbsPWork<R>* ap = new (std::nothrow) AbsPWork<R>();
         if (!ap) return QST_E_NOMEM;
         memset(ap, 0, sizeof(*ap));
@@ -933,6 +934,7 @@ template <class R> struct Engine {
         QST_CU(dalloc(c, &ap->lam, (size_t)D.d));
         QST_CU(dalloc(c, &ap->s, (size_t)D.d));
         QST_CU(dalloc(c, &ap->sp, (size_t)D.d));
+        QST_CU(dalloc(c, &ap->ucos, 16 * (size_t)D.d));
       }
     }
     const V* psi = (const V*)stage_input(c, psi_user, (size_t)D.d * sizeof(V), w->Wlo, &st);
@@ -1549,13 +1551,13 @@ qst_status qst_eig_counts(const qst_ctx* c, long long* refinements, long long* f
   return QST_OK;
 }
 
-qst_status qst_jacobi_schedule(int N, int* count, int* a, int* b, int cap) {
-  if (N < 1 || N > 12 || !count || cap < 0 || (cap > 0 && (!a || !b))) return QST_E_INVAL;
+qst_status qst_jacobi_schedule(int N, int* count, int* dims, int* basis, int cap) {
+  if (N < 1 || N > 12 || !count || cap < 0 || (cap > 0 && (!dims || !basis))) return QST_E_INVAL;
   const std::vector<qst::JacobiPass>& s = qst::jacobi_schedule(N);
   *count = (int)s.size();
   for (int k = 0; k < cap && k < (int)s.size(); ++k) {
-    a[k] = s[k].a;
-    b[k] = s[k].b;
+    dims[k] = s[k].k;
+    for (int i = 0; i < 4; ++i) basis[4 * k + i] = i < s[k].k ? s[k].basis[i] : 0;
   }
   return QST_OK;
 }

@@ -168,6 +168,16 @@ __device__ __forceinline__ void block_absmax_to(float m, unsigned int* amax) {
 // Programmatic dependent launch: wait until the previous kernel on the stream has completed and its
 // writes are visible (a no-op when the kernel was launched without the attribute).
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// After grid_dep_wait(): the pointers pass through an empty asm that the compiler must take as changing them,
+// so that no load through them is moved above the wait (a load through a const __restrict__ pointer may be).
+template <class P> __device__ __forceinline__ int opaque_ptr(P& p) {
+  asm volatile("" : "+l"(p));
+  return 0;
+}
+template <class... P> __device__ __forceinline__ void after_wait(P&... ps) {
+  const int unused[] = {0, opaque_ptr(ps)...};
+  (void)unused;
+}
 
 // A tensor map that host code copied into global memory: order the copy before this thread's next use
 // of the map by the tensor-map proxy (TMA).

@@ -351,6 +351,269 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_jacobi_pass(con
   }
 }
 
+// ---- passes over cosets of 8 or 16 indices (N >= 6): the unitaries first, then the blocks
+__device__ __forceinline__ int coset_rep(int c, const JacobiPass& p) {
+  int x = c;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (i < p.k) x = insert_zero(x, p.piv[i]);
+  return x;
+}
+__device__ __forceinline__ int coset_element(int rep, int j, const JacobiPass& p) {
+  int x = rep;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (i < p.k && ((j >> i) & 1)) x ^= p.basis[i];
+  return x;
+}
+
+// Loads of data the preceding kernel wrote, issued after grid_dep_wait(): volatile, so that the compiler does
+// not move them above the wait (a const __restrict__ load may be hoisted across it).
+__device__ __forceinline__ float2 ld_after_wait(const float2* p) {
+  float2 v;
+  asm volatile("ld.global.cg.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ double2 ld_after_wait(const double2* p) {
+  double2 v;
+  asm volatile("ld.global.cg.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p) : "memory");
+  return v;
+}
+
+// One warp per coset: the G x G principal block B of A on the coset and U = R_1 ... R_{G-1} in shared memory,
+// round s (s = 1 .. G - 1, the subspace element of local index s) rotating the local pairs {x, x ^ s}, each
+// rotation computed from B after the rounds before it (B <- R^dag B R, U <- U R).  Writes U to Ug[coset].
+// Lets the pass's block kernel start (its loads of A do not depend on U).
+template <class R, int G>
+__global__ void __launch_bounds__(32) k_coset_unitaries(const cx_t<R>* __restrict__ A, int d, JacobiPass p,
+                                                        cx_t<R>* __restrict__ Ug) {
+  using V = cx_t<R>;
+  asm volatile("griddepcontrol.launch_dependents;");
+  __shared__ V B[G][G + 1], U[G][G + 1];
+  __shared__ Rot2<R> rot[G / 2];
+  __shared__ int e[G];
+  const int c = blockIdx.x, lane = threadIdx.x;
+  if (lane < G) e[lane] = coset_element(coset_rep(c, p), lane, p);
+  __syncwarp();
+  for (int x = lane; x < G * G; x += 32) {
+    const int i = x / G, j = x % G;
+    B[i][j] = A[(long long)e[i] * d + e[j]];
+    U[i][j] = cmake<V>(i == j ? R(1) : R(0), R(0));
+  }
+  __syncwarp();
+  for (int s = 1; s < G; ++s) {
+    const int hb = 31 - __clz(s);
+    if (lane < G / 2) {
+      const int pp = insert_zero(lane, hb), q = pp ^ s;
+      rot[lane] = rotation_for<R>(B[pp][pp].x, B[q][q].x, B[pp][q]);
+    }
+    __syncwarp();
+    for (int x = lane; x < G * (G / 2); x += 32) {  // columns p, q of row i of B and of U: X <- X R
+      const int i = x / (G / 2), l = x % (G / 2);
+      const int pp = insert_zero(l, hb), q = pp ^ s;
+      const Rot2<R> r = rot[l];
+      const V rqp = cmake<V>(-r.emph.x * r.sn, -r.emph.y * r.sn), rqq = cmake<V>(r.emph.x * r.cs, r.emph.y * r.cs);
+      const V bp = B[i][pp], bq = B[i][q];
+      B[i][pp] = cadd(cmake<V>(bp.x * r.cs, bp.y * r.cs), cmul(bq, rqp));
+      B[i][q] = cadd(cmake<V>(bp.x * r.sn, bp.y * r.sn), cmul(bq, rqq));
+      const V up = U[i][pp], uq = U[i][q];
+      U[i][pp] = cadd(cmake<V>(up.x * r.cs, up.y * r.cs), cmul(uq, rqp));
+      U[i][q] = cadd(cmake<V>(up.x * r.sn, up.y * r.sn), cmul(uq, rqq));
+    }
+    __syncwarp();
+    for (int x = lane; x < (G / 2) * G; x += 32) {  // rows p, q of B: B <- R^dag B
+      const int l = x / G, j = x % G;
+      const int pp = insert_zero(l, hb), q = pp ^ s;
+      const Rot2<R> r = rot[l];
+      const V rqp = cmake<V>(-r.emph.x * r.sn, -r.emph.y * r.sn), rqq = cmake<V>(r.emph.x * r.cs, r.emph.y * r.cs);
+      const V bp = B[pp][j], bq = B[q][j];
+      B[pp][j] = cadd(cmake<V>(r.cs * bp.x, r.cs * bp.y), cmulc(rqp, bq));
+      B[q][j] = cadd(cmake<V>(r.sn * bp.x, r.sn * bp.y), cmulc(rqq, bq));
+    }
+    __syncwarp();
+  }
+  V* out = Ug + (size_t)c * G * G;
+  for (int x = lane; x < G * G; x += 32) out[x] = U[x / G][x % G];
+}
+
+// Asynchronous copy of one complex entry from global to shared memory (no register on the way), and the wait
+// for all of this thread's copies.
+template <class V> __device__ __forceinline__ void cp_async_entry(V* dst, const V* src) {
+  const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  if constexpr (sizeof(V) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// The block kernel's shared memory: the TS x TS tiles of A and V (rows: TS / G row cosets, columns: TS / G
+// column cosets, coset-major), the cosets' unitaries (FP32: the packed forms (u.x, u.x) and (u.y, u.y);
+// FP64: u), the tile's row and column indices and the first block column's piece of phi.
+template <class R, int G, int TS> struct TileSmem {
+  // column c of a tile at c + c / G (one word after each coset) and one more per row: the reads of a column
+  // across the row's cosets, and of a row across the column blocks, fall in distinct banks
+  static constexpr int LD = TS + TS / G + 1;
+  cx_t<R> a[TS][LD], v[TS][LD];
+  cx_t<R> ul[TS / G][G][G], ul2[TS / G][G][G], uk[TS / G][G][G], uk2[TS / G][G][G];
+  int ridx[TS], cidx[TS];
+  cx_t<R> ph[TS];
+};
+
+// One pass over cosets of G indices: CTA (x, y) stages the tiles of A and V on row cosets y TS / G .. and
+// column cosets x TS / G .. in shared memory (loaded before waiting for the pass's unitaries), computes
+// T = A U_l and V' = V U_l (U block-diagonal over the cosets), then A' = U_k^dag T, each thread an RB x RB
+// block of outputs, and writes both tiles back.  Every entry is read and written once per pass.
+template <class R, int G, int TS>
+__global__ void __launch_bounds__(256) k_jacobi_tile(const cx_t<R>* __restrict__ A, cx_t<R>* __restrict__ Ao,
+                                                      const cx_t<R>* __restrict__ Vi, cx_t<R>* __restrict__ Vo,
+                                                      cx_t<R>* __restrict__ phi, int d, JacobiPass p,
+                                                      const cx_t<R>* Ug) {
+  using V = cx_t<R>;
+  constexpr int TPC = TS / G, RB = TS / 16;
+  constexpr bool kF32 = sizeof(R) == 4;
+  extern __shared__ __align__(16) unsigned char sraw[];
+  TileSmem<R, G, TS>& S = *reinterpret_cast<TileSmem<R, G, TS>*>(sraw);
+  const int k0 = blockIdx.y * TPC, l0 = blockIdx.x * TPC;
+  const int t = threadIdx.x;
+  if (t < TS) S.ridx[t] = coset_element(coset_rep(k0 + t / G, p), t % G, p);
+  else if (t < 2 * TS) S.cidx[t - TS] = coset_element(coset_rep(l0 + (t - TS) / G, p), (t - TS) % G, p);
+  __syncthreads();
+  for (int e = t; e < TS * TS; e += 256) {  // every copy of the tiles in flight at once
+    const int r = e / TS, c = e % TS;
+    const long long off = (long long)S.ridx[r] * d + S.cidx[c];
+    cp_async_entry(&S.a[r][c + c / G], A + off);
+    if (Vi != nullptr) cp_async_entry(&S.v[r][c + c / G], Vi + off);
+  }
+  const bool with_phi = phi != nullptr && blockIdx.x == 0;
+  if (with_phi && t < TS) S.ph[t] = phi[S.ridx[t]];
+  grid_dep_wait();  // the unitaries of this pass
+  after_wait(Ug);
+  for (int e = t; e < TPC * G * G; e += 256) {
+    const int cc = e / (G * G), rc = (e / G) % G, jc = e % G;
+    const V ul = ld_after_wait(Ug + (size_t)(l0 + cc) * G * G + rc * G + jc);
+    const V uk = ld_after_wait(Ug + (size_t)(k0 + cc) * G * G + rc * G + jc);
+    if (kF32) {
+      S.ul[cc][rc][jc] = cmake<V>(ul.x, ul.x);
+      S.ul2[cc][rc][jc] = cmake<V>(ul.y, ul.y);
+      S.uk[cc][rc][jc] = cmake<V>(uk.x, uk.x);
+      S.uk2[cc][rc][jc] = cmake<V>(uk.y, uk.y);
+    } else {
+      S.ul[cc][rc][jc] = ul;
+      S.uk[cc][rc][jc] = uk;
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  if (with_phi && t < TS) {  // phi <- U_k^dag phi on the row cosets
+    const int rc = t / G, i = t % G;
+    V y = cmake<V>(R(0), R(0));
+    for (int r = 0; r < G; ++r) {
+      const V u = kF32 ? cmake<V>(S.uk[rc][r][i].x, S.uk2[rc][r][i].x) : S.uk[rc][r][i];
+      y = cadd(y, cmulc(u, S.ph[rc * G + r]));
+    }
+    phi[S.ridx[t]] = y;
+  }
+  // T = A U_l, V' = V U_l: lane l of warp w takes rows rr + 16 i (rr = l % 16) and the RB columns of column
+  // block cb = 2 w + l / 16 (inside column coset cc): a warp reads one column of 16 rows (distinct banks) and
+  // at most two unitary entries per step
+  const int lane = t & 31, warp = t >> 5;
+  V acc[RB][RB], accv[RB][RB];
+  {
+    const int rr = lane % 16, cb = 2 * warp + lane / 16;
+    const int c0 = cb * RB, cc = c0 / G, j0 = c0 % G;
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+#pragma unroll
+      for (int j = 0; j < RB; ++j) acc[i][j] = accv[i][j] = cmake<V>(R(0), R(0));
+#pragma unroll 4
+    for (int q = 0; q < G; ++q) {
+      V ux[RB], uy[RB];
+#pragma unroll
+      for (int j = 0; j < RB; ++j) {
+        ux[j] = S.ul[cc][q][j0 + j];
+        if (kF32) uy[j] = S.ul2[cc][q][j0 + j];
+      }
+#pragma unroll
+      for (int i = 0; i < RB; ++i) {
+        const V m = S.a[rr + 16 * i][cc * (G + 1) + q];
+        const V w = Vi != nullptr ? S.v[rr + 16 * i][cc * (G + 1) + q] : cmake<V>(R(0), R(0));
+        if constexpr (kF32) {
+          const float2 msw = make_float2(-m.y, m.x), wsw = make_float2(-w.y, w.x);  // i m, i w
+#pragma unroll
+          for (int j = 0; j < RB; ++j) {  // m u = u.x m + u.y (i m)
+            acc[i][j] = __ffma2_rn(uy[j], msw, __ffma2_rn(ux[j], m, acc[i][j]));
+            accv[i][j] = __ffma2_rn(uy[j], wsw, __ffma2_rn(ux[j], w, accv[i][j]));
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < RB; ++j) {
+            acc[i][j] = cadd(acc[i][j], cmul(m, ux[j]));
+            accv[i][j] = cadd(accv[i][j], cmul(w, ux[j]));
+          }
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+#pragma unroll
+      for (int j = 0; j < RB; ++j) {
+        S.a[rr + 16 * i][c0 + j + cc] = acc[i][j];
+        S.v[rr + 16 * i][c0 + j + cc] = accv[i][j];
+      }
+  }
+  __syncthreads();
+  {  // A' = U_k^dag T: lane l of warp w takes the RB rows of row block rb = 2 w + l / 16 (inside row coset rc)
+     // and columns cs + 16 j (cs = l % 16)
+    const int cs = lane % 16, rb = 2 * warp + lane / 16;
+    const int r0 = rb * RB, rc = r0 / G, i0 = r0 % G;
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+#pragma unroll
+      for (int j = 0; j < RB; ++j) acc[i][j] = cmake<V>(R(0), R(0));
+#pragma unroll 4
+    for (int q = 0; q < G; ++q) {
+      V ux[RB], uy[RB];
+#pragma unroll
+      for (int i = 0; i < RB; ++i) {
+        ux[i] = S.uk[rc][q][i0 + i];
+        if (kF32) uy[i] = S.uk2[rc][q][i0 + i];
+      }
+#pragma unroll
+      for (int j = 0; j < RB; ++j) {
+        const int c = cs + 16 * j;
+        const V tv = S.a[rc * G + q][c + c / G];
+        if constexpr (kF32) {
+          const float2 tsw = make_float2(tv.y, -tv.x);  // -i t
+#pragma unroll
+          for (int i = 0; i < RB; ++i)  // conj(u) t = u.x t + u.y (-i t)
+            acc[i][j] = __ffma2_rn(uy[i], tsw, __ffma2_rn(ux[i], tv, acc[i][j]));
+        } else {
+#pragma unroll
+          for (int i = 0; i < RB; ++i) acc[i][j] = cadd(acc[i][j], cmulc(ux[i], tv));
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+#pragma unroll
+      for (int j = 0; j < RB; ++j) {
+        const int c = cs + 16 * j;
+        S.a[r0 + i][c + c / G] = acc[i][j];
+      }
+  }
+  __syncthreads();
+#pragma unroll 4
+  for (int e = t; e < TS * TS; e += 256) {
+    const int r = e / TS, c = e % TS;
+    const long long off = (long long)S.ridx[r] * d + S.cidx[c];
+    Ao[off] = S.a[r][c + c / G];
+    if (Vi != nullptr) Vo[off] = S.v[r][c + c / G];
+  }
+}
+
 template <class R>
 __global__ void k_identity(cx_t<R>* V, int d) {
   using Vt = cx_t<R>;
@@ -436,86 +699,148 @@ int blocks_for(long long n) {
   return (int)(b > 4096 ? 4096 : (b < 1 ? 1 : b));
 }
 
-// Partition of the nonzero vectors of GF(2)^n into lines {u, v, u ^ v} and, for odd n, one plane span{p1, p2, p3},
-// built from V(n) = V(n - 2) + V(2) (the new coordinates are bits n - 2 and n - 1): the line of the new
-// coordinates; each line {u1, u2, u1 ^ u2} of V(n - 2) lifted to the four lines {u1 + x, u2 + w x,
-// u1 ^ u2 + (1 + w) x} for x in V(2) = GF(4) (w x and (1 + w) x = w^2 x run over GF(4) with x, so the 12 points
-// over the line are each covered once); the plane of V(n - 2) kept, with its 21 points over V(2) \ 0 as the
-// seven lines {p(y) + 01, p(a y) + 10, p((1 + a) y) + 11}, y in GF(8)* = GF(2)[a] / (a^3 + a + 1) \ 0 and p
-// the coordinates in the plane's basis.  Base cases: V(1) = {1} (a single point), V(2) one line, V(3) one plane.
-struct VecPartition {
-  std::vector<std::pair<int, int>> lines;
-  int plane[3] = {0, 0, 0};
-};
+// Partitions of the nonzero vectors of GF(2)^n into subspaces (each a basis), built from V(n) = V(n - k) + V(k),
+// the new coordinates at bits n - k .. n - 1: the subspace V(k) of the new coordinates, and each subspace S of
+// the partition of V(n - k) (dimension m <= k, basis u_0 .. u_{m-1}) lifted to the 2^k subspaces with bases
+// u_i + c x^i (c in GF(2^k), x^i the field's basis element i, the product in GF(2^k)): for u != 0 in S the map
+// c -> c iota(u) (iota(u_i) = x^i) is a bijection onto GF(2^k), so every point (u, y) with u in S \ 0 lies in
+// exactly one lifted subspace.  For small N the lines (k = 2) and single rounds of the 4-index passes; for
+// N >= 6 subspaces of dimension 3 and 4 (8- and 16-index cosets), the lift sizes chosen for the fewest passes.
+using Basis = std::vector<int>;
 
-VecPartition vec_partition(int n) {
-  VecPartition out;
-  if (n == 2) out.lines.push_back({1, 2});
-  if (n == 3) out.plane[0] = 1, out.plane[1] = 2, out.plane[2] = 4;
-  if (n <= 3) return out;
-  static const int kTimesW[4] = {0, 2, 3, 1};                 // x -> w x in GF(4), bit 0 = 1, bit 1 = w
-  static const int kTimesA[8] = {0, 2, 4, 6, 3, 1, 7, 5};     // y -> a y in GF(8), bits 1, a, a^2
-  const VecPartition low = vec_partition(n - 2);
-  const int s = n - 2;
-  out.lines.push_back({1 << s, 2 << s});
-  for (const auto& l : low.lines)
-    for (int x = 0; x < 4; ++x) out.lines.push_back({l.first | (x << s), l.second | (kTimesW[x] << s)});
-  if (low.plane[0] != 0) {
-    const int* P = low.plane;
-    auto p = [P](int y) { return ((y & 1) ? P[0] : 0) ^ ((y & 2) ? P[1] : 0) ^ ((y & 4) ? P[2] : 0); };
-    for (int y = 1; y < 8; ++y) out.lines.push_back({p(y) | (1 << s), p(kTimesA[y]) | (2 << s)});
-    out.plane[0] = P[0], out.plane[1] = P[1], out.plane[2] = P[2];
-  }
+int gf_mul(int k, int a, int b) {  // GF(2^k), moduli x^2 + x + 1, x^3 + x + 1, x^4 + x + 1
+  static const int kMod[5] = {0, 0, 0x7, 0xB, 0x13};
+  int r = 0;
+  for (int i = 0; i < k; ++i)
+    if ((b >> i) & 1) r ^= a << i;
+  for (int i = 2 * k - 2; i >= k; --i)
+    if ((r >> i) & 1) r ^= kMod[k] << (i - k);
+  return k == 1 ? (a & b & 1) : r;
+}
+
+std::vector<Basis> lift(const std::vector<Basis>& low, int s, int k) {
+  std::vector<Basis> out;
+  Basis top;
+  for (int i = 0; i < k; ++i) top.push_back(1 << (s + i));
+  out.push_back(top);
+  for (const Basis& S : low)
+    for (int c = 0; c < (1 << k); ++c) {
+      Basis b;
+      for (size_t i = 0; i < S.size(); ++i) b.push_back(S[i] | (gf_mul(k, c, 1 << i) << s));
+      out.push_back(b);
+    }
   return out;
+}
+
+// fewest subspaces of dimension <= m partitioning V(n) \ 0 by repeated lifting (and the first lift size)
+long long min_parts(int n, int m, int* best_k) {
+  if (n <= m) {
+    if (best_k) *best_k = 0;
+    return 1;
+  }
+  long long best = -1;
+  for (int k = 1; k <= m && k < n; ++k) {
+    const long long v = 1 + ((long long)1 << k) * min_parts(n - k, k, nullptr);
+    if (best < 0 || v < best) {
+      best = v;
+      if (best_k) *best_k = k;
+    }
+  }
+  return best;
+}
+
+std::vector<Basis> subspace_partition(int n, int m) {
+  int k = 0;
+  min_parts(n, m, &k);
+  if (k == 0) {
+    Basis all;
+    for (int i = 0; i < n; ++i) all.push_back(1 << i);
+    return {all};
+  }
+  return lift(subspace_partition(n - k, k), n - k, k);
 }
 
 int top_bit(int x) { return 31 - __builtin_clz((unsigned)x); }
 
-JacobiPass make_pass(int a, int b) {
-  JacobiPass p;
-  if (b == 0) {
-    p.a = a, p.b = 0, p.plo = top_bit(a), p.phi = 0;
-    return p;
+JacobiPass make_pass(Basis v) {  // reduced echelon form, pivots ascending
+  JacobiPass p = {};
+  p.k = (int)v.size();
+  for (size_t r = 0; r < v.size(); ++r) {
+    size_t best = r;
+    for (size_t q = r + 1; q < v.size(); ++q)
+      if (top_bit(v[q]) > top_bit(v[best])) best = q;
+    std::swap(v[r], v[best]);
+    const int pb = top_bit(v[r]);
+    for (size_t q = 0; q < v.size(); ++q)
+      if (q != r && ((v[q] >> pb) & 1)) v[q] ^= v[r];
   }
-  if (top_bit(b) > top_bit(a)) std::swap(a, b);
-  if (top_bit(b) == top_bit(a)) b ^= a;
-  if ((a >> top_bit(b)) & 1) a ^= b;
-  p.a = a, p.b = b, p.plo = top_bit(b), p.phi = top_bit(a);
+  std::sort(v.begin(), v.end());
+  for (int i = 0; i < p.k; ++i) {
+    p.basis[i] = v[i];
+    p.piv[i] = top_bit(v[i]);
+  }
   return p;
 }
 
 std::vector<JacobiPass> build_schedule(int N) {
   std::vector<JacobiPass> out;
   if (N == 1) {
-    out.push_back(make_pass(1, 0));
+    out.push_back(make_pass({1}));
     return out;
   }
-  const VecPartition part = vec_partition(N);
-  for (const auto& l : part.lines) out.push_back(make_pass(l.first, l.second));
-  if (part.plane[0] != 0) {  // the plane as one line and its four other points
-    const int p1 = part.plane[0], p2 = part.plane[1], p3 = part.plane[2];
-    out.push_back(make_pass(p1, p2));
-    for (int m : {p3, p1 ^ p3, p2 ^ p3, p1 ^ p2 ^ p3}) out.push_back(make_pass(m, 0));
+  if (N >= 6) {
+    for (const Basis& b : subspace_partition(N, 4)) out.push_back(make_pass(b));
+    return out;
+  }
+  // lines (lifted through GF(4)), and for odd N one plane taken as a line and its four other points
+  for (const Basis& b : subspace_partition(N, 3)) {
+    if (b.size() <= 2) {
+      out.push_back(make_pass(b));
+    } else {
+      out.push_back(make_pass({b[0], b[1]}));
+      for (int m : {b[2], b[0] ^ b[2], b[1] ^ b[2], b[0] ^ b[1] ^ b[2]}) out.push_back(make_pass({m}));
+    }
   }
   return out;
 }
 
 constexpr int kMaxScheduleN = 14;
 
-// One sweep: every pass of the schedule, ping-ponging (Ain, Aout) and (Vin, Vout).
+template <class R, int G>
+cudaError_t tile_pass(int d, const JacobiPass& p, const cx_t<R>* A, cx_t<R>* Ao, const cx_t<R>* Vi, cx_t<R>* Vo,
+                      cx_t<R>* phi, cx_t<R>* ucos, cudaStream_t s) {
+  constexpr int TS = sizeof(R) == 4 ? 64 : 32;
+  const size_t smem = sizeof(TileSmem<R, G, TS>);
+  cudaError_t e = ensure_dynamic_smem((const void*)k_jacobi_tile<R, G, TS>, smem);
+  if (e != cudaSuccess) return e;
+  k_coset_unitaries<R, G><<<d / G, 32, 0, s>>>(A, d, p, ucos);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return launch_dep(k_jacobi_tile<R, G, TS>, dim3(d / TS, d / TS), dim3(256), smem, s, A, Ao, Vi, Vo, phi, d, p,
+                    (const cx_t<R>*)ucos);
+}
+
+// One sweep: every pass of the schedule, ping-ponging (Ain, Aout) and (Vin, Vout).  Passes over cosets of 8
+// or 16 indices (N >= 6) are a unitary kernel and a block kernel; those over 2 or 4 indices one kernel.
 template <class R>
 cudaError_t jacobi_sweep(int d, cx_t<R>*& Ain, cx_t<R>*& Aout, cx_t<R>*& Vin, cx_t<R>*& Vout, cx_t<R>* phi,
-                         cudaStream_t s) {
+                         cx_t<R>* ucos, cudaStream_t s) {
   const std::vector<JacobiPass>& sched = jacobi_schedule(top_bit(d));
   const int n4 = d / 4, n2 = d / 2;
   const dim3 g4((n4 + 15) / 16, (n4 + 15) / 16), g2((n2 + 15) / 16, (n2 + 15) / 16);
   for (const JacobiPass& p : sched) {
-    if (p.b != 0) k_jacobi_pass<R, 4><<<g4, 256, 0, s>>>(Ain, Aout, Vin, Vout, phi, d, p.a, p.b, p.plo, p.phi);
-    else k_jacobi_pass<R, 2><<<g2, 256, 0, s>>>(Ain, Aout, Vin, Vout, phi, d, p.a, 0, p.plo, 0);
+    cudaError_t e = cudaSuccess;
+    if (p.k == 4) e = tile_pass<R, 16>(d, p, Ain, Aout, Vin, Vout, phi, ucos, s);
+    else if (p.k == 3) e = tile_pass<R, 8>(d, p, Ain, Aout, Vin, Vout, phi, ucos, s);
+    else if (p.k == 2)
+      k_jacobi_pass<R, 4><<<g4, 256, 0, s>>>(Ain, Aout, Vin, Vout, phi, d, p.basis[1], p.basis[0], p.piv[0], p.piv[1]);
+    else
+      k_jacobi_pass<R, 2><<<g2, 256, 0, s>>>(Ain, Aout, Vin, Vout, phi, d, p.basis[0], 0, p.piv[0], 0);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     std::swap(Ain, Aout);
     if (Vin != nullptr) std::swap(Vin, Vout);
   }
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -548,7 +873,7 @@ cudaError_t abs_p_forward(int d, const cx_t<R>* T, AbsPWork<R>& w, int sweeps, b
   // an even number of sweeps of an odd number of passes brings both ping-pong pairs back to A0 / V0
   V *Ain = w.A0, *Aout = w.A1, *Vin = w.V0, *Vout = w.V1;
   for (int sw = 0; sw < sweeps; ++sw)
-    if ((e = jacobi_sweep<R>(d, Ain, Aout, Vin, Vout, nullptr, s)) != cudaSuccess) return e;
+    if ((e = jacobi_sweep<R>(d, Ain, Aout, Vin, Vout, nullptr, w.ucos, s)) != cudaSuccess) return e;
   if (Vin != w.V0) {  // an odd number of sweeps: the eigenvectors are kept in V0
     if ((e = cudaMemcpyAsync(w.V0, Vin, nn * sizeof(V), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
     Vin = w.V0;
@@ -575,7 +900,7 @@ cudaError_t jacobi_values_project(int d, const cx_t<R>* T, AbsPWork<R>& w, int s
   if ((e = cudaMemcpyAsync(phi, psi, (size_t)d * sizeof(V), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
   V *Ain = w.A0, *Aout = w.A1, *Vin = nullptr, *Vout = nullptr;
   for (int sw = 0; sw < sweeps; ++sw)
-    if ((e = jacobi_sweep<R>(d, Ain, Aout, Vin, Vout, phi, s)) != cudaSuccess) return e;
+    if ((e = jacobi_sweep<R>(d, Ain, Aout, Vin, Vout, phi, w.ucos, s)) != cudaSuccess) return e;
   w.A = Ain;
   k_absp_spectrum<R><<<1, 1024, 0, s>>>(w.A, w.lam, w.s, w.sp, d, P, sizeof(R) == 4 ? 1e-7 : 1e-15);
   return cudaGetLastError();

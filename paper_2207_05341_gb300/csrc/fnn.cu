@@ -130,6 +130,7 @@ __global__ void __launch_bounds__(256) k_layer2(const R* __restrict__ theta, con
   __shared__ R hs[H];
   rebind(tab, theta, hid, t, amax);
   grid_dep_wait();
+  after_wait(theta, hid, t, amax);
   if (threadIdx.x < H) hs[threadIdx.x] = hid[threadIdx.x];
   __syncthreads();
   using VV = Vec<R>;
@@ -374,6 +375,7 @@ __global__ void __launch_bounds__(256) k_symmetrize(const cx_t<R>* __restrict__ 
   __shared__ R Ar[32][33], Ai[32][33], Br[32][33], Bi[32][33];
   rebind(tab, Y, dt);
   grid_dep_wait();
+  after_wait(Y, dt);
   const int TS = d < 32 ? d : 32;
   int I, J;
   tri_decode(blockIdx.x, I, J);

@@ -167,6 +167,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_wpass_bulk(const __gri
   const WMaps* mp = &maps;
   rebind(tab, mp, theta, step, vec, hidv, pre, dpre_io, pre_out, hid_out, scal, partials, counter, flags);
   grid_dep_wait();
+  after_wait(mp, theta, step, vec, hidv, pre, dpre_io, pre_out, hid_out, scal, partials, counter, flags);
   extern __shared__ __align__(128) uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((128u - (s_u32(smem_raw) & 127u)) & 127u);  // 128-byte aligned ring
   constexpr int kStages = S::kStages;

@@ -147,6 +147,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_cgemm(const __grid_constant__ TcM
   const TcMaps* mp = &maps;
   rebind(tab, mp, C, sA, sB, err, clear);
   grid_dep_wait();
+  after_wait(mp, C, sA, sB, err, clear);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
@@ -325,6 +326,7 @@ __global__ void __launch_bounds__(256) k_split(const float2* __restrict__ A, H* 
                                                 const unsigned int* amax, double* s_slot, const void* const* tab) {
   rebind(tab, A, P, amax, s_slot);
   grid_dep_wait();
+  after_wait(A, P, amax, s_slot);
   const double sd = split_scale(amax);
   const float sc = (float)sd;
   if (blockIdx.x == 0 && threadIdx.x == 0) *s_slot = sd;
@@ -418,6 +420,7 @@ __global__ void __launch_bounds__(256) k_hermitian_planes64(const float* __restr
                                                              const void* const* tab) {
   rebind(tab, t, P, amax, s_slot);
   grid_dep_wait();
+  after_wait(t, P, amax, s_slot);
   __shared__ float Ra[64][65];
   __shared__ float Rb[64][65];
   const double sd = split_scale(amax);

@@ -307,6 +307,7 @@ template <class R> struct AbsPWork {
   int* perm;                   // the order of increasing lambda (d) and the unitaries of a block pass
   void* ublk;                  // (d / 64 blocks of 64 x 64 complex)
   double* sc;                  // scales of qa_n, qa_h, qb_n, qb_h, wa, eb; [6] max |lambda|, [7] refinement size
+  cx_t<R>* ucos;               // the coset unitaries of a Jacobi pass (16 d complex)
 };
 // Warm-started refinement of the eigenvectors in w.V0 for the Hermitian T (6 planes Tb with scale *sT) on
 // tensor cores, Ogita and Aishima's iteration:
@@ -331,11 +332,14 @@ cudaError_t abs_p_backward_tc(int d, const float2* G, AbsPWork<float>& w, int fm
                               cudaStream_t s);
 size_t abs_p_tc_plane_bytes(int d);  // bytes of one 4-plane buffer (a 6-plane one is 1.5 times that)
 // One sweep of the Jacobi eigensolver for d = 2^N in the XOR ordering (round m rotates the pairs {x, x ^ m},
-// m = 1 .. d - 1), as passes: b != 0, the three rounds a, b, a ^ b of one 2-dimensional subspace (they act
-// within its cosets), in reduced form (pivot bits phi = top bit of a > plo = top bit of b, a has bit plo
-// clear); b == 0, the single round a (plo = top bit of a).  The number of passes is odd for every N.
+// m = 1 .. d - 1), as passes: each pass applies the 2^k - 1 rounds of one k-dimensional subspace of GF(2)^N
+// (they act within its cosets of 2^k indices), k = 1 .. 4.  basis[0 .. k) is the subspace's basis in reduced
+// form: piv[i] = top bit of basis[i], ascending, and bit piv[i] clear in every other basis vector; local
+// index j of a coset stands for rep ^ (XOR of basis[i] over the bits i of j), rep having the pivot bits clear.
 struct JacobiPass {
-  int a, b, plo, phi;
+  int k;
+  int basis[4];
+  int piv[4];
 };
 const std::vector<JacobiPass>& jacobi_schedule(int N);  // 1 <= N <= 14
 long long jacobi_passes_per_sweep(int d);

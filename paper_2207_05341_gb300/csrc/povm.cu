@@ -385,6 +385,7 @@ __global__ void __launch_bounds__(256) k_trace(const cx_t<R>* __restrict__ X, in
   __shared__ double red[8];
   rebind(tab, X, scal);
   grid_dep_wait();
+  after_wait(X, scal);
   // every diagonal load of a thread is issued before the first add (one memory latency, not d / 256)
   constexpr int kPer = 16;  // d <= 4096 = 16 x 256
   R v[kPer];

@@ -195,6 +195,7 @@ __global__ void __launch_bounds__(kLoThreads, 4) k_lo_fwd_fast(const float2* __r
   const int t = threadIdx.x;
   float2 x[4][4];
   pdl_wait();
+  after_wait(X, W);
   {  // sweep A: the 4 x 4 block straight from X (rows 4 rho + k, columns 4 kappa + l)
     const int kap = t & 15, rho = t >> 4;
     const float2* src = X + ((long long)I * kTile + 4 * rho) * d + (long long)J * kTile + 4 * kap;
@@ -288,6 +289,7 @@ __global__ void __launch_bounds__(kLoThreads, 4) k_lo_adj_fast(const float* Wadj
   const int t = threadIdx.x;
   float2 x[4][4];
   pdl_wait();
+  after_wait(Wadj, G, amax);
   const int i03 = (int)compact_bits((uint32_t)t >> 1), j03 = (int)compact_bits((uint32_t)t);
   {  // sweep C: the packed adjoint of the tile pair, then qubits 4, 5
     const unsigned out = outmap.bits;
@@ -430,6 +432,7 @@ __global__ void __launch_bounds__(kCP * NB, (NB == 32 && kCP == 8) ? 2 : 1) k_hi
   }
   __syncthreads();
   pdl_wait();
+  after_wait(f);
   // ---- thread (cp, x = wv): the sequence of the diagonal x, transformed r -> z -> zeta
   float2 w[NB];
   {

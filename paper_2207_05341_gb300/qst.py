@@ -362,13 +362,13 @@ def qst_eig_counts(ctx: int, last: bool = False):
 
 
 def qst_jacobi_schedule(N: int):
-    """Passes of one Jacobi sweep at N qubits (host only): a list of (a, b), b == 0 for a single round."""
+    """Passes of one Jacobi sweep at N qubits (host only): a list of subspace bases (tuples of 1 to 4 ints)."""
     cnt = ctypes.c_int()
     _check(load().qst_jacobi_schedule(int(N), ctypes.byref(cnt), None, None, 0), "qst_jacobi_schedule")
-    a = (ctypes.c_int * cnt.value)()
-    b = (ctypes.c_int * cnt.value)()
-    _check(load().qst_jacobi_schedule(int(N), ctypes.byref(cnt), a, b, cnt.value), "qst_jacobi_schedule")
-    return list(zip(a, b))
+    dims = (ctypes.c_int * cnt.value)()
+    basis = (ctypes.c_int * (4 * cnt.value))()
+    _check(load().qst_jacobi_schedule(int(N), ctypes.byref(cnt), dims, basis, cnt.value), "qst_jacobi_schedule")
+    return [tuple(basis[4 * p:4 * p + dims[p]]) for p in range(cnt.value)]
 
 
 def qst_get_tuning() -> dict:

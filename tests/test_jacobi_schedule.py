@@ -2,12 +2,12 @@
 iteration).  No GPU: qst_jacobi_schedule is host-only.
 
 A sweep is the d - 1 rounds m = 1 .. d - 1 of the XOR ordering (round m rotates the pairs {x, x ^ m}); a
-pass applies the three rounds {a, b, a ^ b} of one 2-dimensional subspace of GF(2)^N, or a single round.
-Checked here: every round appears exactly once per sweep, the passes are in the reduced form the kernel's
-coset numbering assumes, the cosets that numbering gives (pivot bits inserted as zeros) partition
-0 .. d - 1 within bounds, and a NumPy run of the pass algorithm (each coset's 4 x 4 unitary built from the
-rounds in order, then U^dag A U on every block) diagonalises a random Hermitian matrix to the eigenvalues
-numpy.linalg.eigvalsh gives.
+pass applies the 2^k - 1 rounds of one k-dimensional subspace of GF(2)^N (k = 1, 2 for N <= 5; 3, 4 for
+N >= 6).  Checked here: every round appears exactly once per sweep, the passes are in the reduced form the
+kernels' coset numbering assumes, the cosets that numbering gives (pivot bits inserted as zeros) partition
+0 .. d - 1 within bounds, and a NumPy run of the pass algorithm (each coset's unitary built from the
+subspace's rounds in order, then U^dag A U on every block) diagonalises a random Hermitian matrix to the
+eigenvalues numpy.linalg.eigvalsh gives.
 """
 import os
 
@@ -33,40 +33,47 @@ def _insert_zero(x, p):
     return ((x >> p) << (p + 1)) | (x & ((1 << p) - 1))
 
 
-def _cosets(N, a, b):
-    """The kernel's numbering: coset c of the pass -> its G elements (local index bit 0: a, bit 1: b)."""
+def _span(basis):
+    out = [0]
+    for v in basis:
+        out = out + [x ^ v for x in out]
+    return out  # local index j -> XOR of basis[i] over the bits i of j
+
+
+def _cosets(N, basis):
+    """The kernels' numbering: coset c -> its 2^k elements (pivot bits of the representative clear)."""
     d = 1 << N
-    if b == 0:
-        c = np.arange(d // 2)
-        x = _insert_zero(c, _top(a))
-        return np.stack([x, x ^ a], 1)
-    c = np.arange(d // 4)
-    x = _insert_zero(_insert_zero(c, _top(b)), _top(a))
-    return np.stack([x, x ^ a, x ^ b, x ^ a ^ b], 1)
+    piv = sorted(_top(v) for v in basis)
+    x = np.arange(d >> len(basis))
+    for p in piv:
+        x = _insert_zero(x, p)
+    return np.stack([x ^ s for s in _span(basis)], 1)
+
+
+PASSES = {1: 1, 2: 1, 3: 5, 4: 5, 5: 13, 6: 9, 7: 17, 8: 17, 9: 73, 10: 145, 11: 273, 12: 273}
 
 
 @pytest.mark.parametrize("N", list(range(1, 13)))
 def test_every_round_once_per_sweep(N):
     d = 1 << N
     sched = qst.qst_jacobi_schedule(N)
+    assert len(sched) == PASSES[N]
     assert len(sched) % 2 == 1  # an even number of sweeps returns the ping-pong buffers to the first pair
     seen = np.zeros(d, dtype=int)
-    for a, b in sched:
-        assert 0 < a < d and 0 <= b < d
-        if b == 0:
-            seen[a] += 1
-            continue
-        assert _top(b) < _top(a) and not (a >> _top(b)) & 1, (a, b)
-        for m in (a, b, a ^ b):
+    for basis in sched:
+        k = len(basis)
+        assert (1 <= k <= 2) if N <= 5 else (3 <= k <= 4), basis
+        tops = [_top(v) for v in basis]
+        assert tops == sorted(set(tops)), basis  # reduced form: distinct pivots, ascending
+        for i, v in enumerate(basis):
+            assert 0 < v < d
+            assert all(not (v >> t) & 1 for jj, t in enumerate(tops) if jj != i), basis
+        for m in _span(basis)[1:]:
             seen[m] += 1
     assert seen[0] == 0 and np.all(seen[1:] == 1)
-    lines = sum(1 for _, b in sched if b)
-    # even N: a partition into lines; odd N >= 3: (d - 8) / 3 lines, and a plane as one line and 4 rounds
-    assert lines == ((d - 1) // 3 if N % 2 == 0 else ((d - 8) // 3 + 1 if N > 1 else 0))
 
 
-def test_passes_per_sweep():
-    assert [len(qst.qst_jacobi_schedule(N)) for N in (1, 2, 3, 10, 11, 12)] == [1, 1, 5, 341, 685, 1365]
+def test_schedule_arguments():
     with pytest.raises(qst.QstError):
         qst.qst_jacobi_schedule(0)
     with pytest.raises(qst.QstError):
@@ -76,14 +83,12 @@ def test_passes_per_sweep():
 @pytest.mark.parametrize("N", list(range(1, 13)))
 def test_coset_numbering_partitions_the_indices(N):
     d = 1 << N
-    for a, b in qst.qst_jacobi_schedule(N):
-        e = _cosets(N, a, b)
+    for basis in qst.qst_jacobi_schedule(N):
+        e = _cosets(N, basis)
         assert e.min() >= 0 and e.max() < d
-        assert np.array_equal(np.sort(e.ravel()), np.arange(d)), (a, b)
-        # the local pairs of each round are the round's pairs {x, x ^ m}
-        if b:
-            assert np.all(e[:, 1] ^ e[:, 0] == a) and np.all(e[:, 2] ^ e[:, 0] == b)
-            assert np.all(e[:, 3] ^ e[:, 0] == a ^ b)
+        assert np.array_equal(np.sort(e.ravel()), np.arange(d)), basis
+        # local index j of every coset differs from its representative by the subspace element j
+        assert np.all((e ^ e[:, :1]) == np.array(_span(basis))[None, :])
 
 
 def _rotation(a, b, c):
@@ -113,7 +118,7 @@ def _coset_unitary(B):
     return U
 
 
-@pytest.mark.parametrize("N", [3, 4, 5])
+@pytest.mark.parametrize("N", [3, 4, 5, 6, 7])
 def test_pass_algorithm_diagonalises(N):
     d = 1 << N
     rng = np.random.default_rng(N)
@@ -122,10 +127,9 @@ def test_pass_algorithm_diagonalises(N):
     A, V = T.copy(), np.eye(d, dtype=complex)
     sched = qst.qst_jacobi_schedule(N)
     for _ in range(10):
-        for a, b in sched:
-            e = _cosets(N, a, b)
+        for basis in sched:
             U = np.zeros((d, d), dtype=complex)
-            for row in e:
+            for row in _cosets(N, basis):
                 U[np.ix_(row, row)] = _coset_unitary(A[np.ix_(row, row)])
             A = U.conj().T @ A @ U
             V = V @ U
