@@ -438,7 +438,7 @@ def fidelity_eval(torch, qst, dev, stream, theta0, lam, seed, steps=200, samples
         out["Fq_gpu"] = val
         out["Fq_gpu_ms"] = best * 1e3
         out["note"] = ("F_c >= F_q (eq. F_CF is an upper bound); Fq_harness is the harness's complex128 "
-                       "evaluation, Fq_gpu the library's (qst_state_fidelity, 10 FP32 Jacobi sweeps on T)")
+                       "evaluation, Fq_gpu the library's (qst_state_fidelity, 12 FP32 Jacobi sweeps on T)")
         return out
     finally:
         qst.qst_destroy(ctx)

@@ -95,7 +95,7 @@ typedef struct qst_options {
     double step_min;    /* Rprop step lower bound (1e-6) */
     double step_max;    /* Rprop step upper bound (50) */
     double leaky_slope; /* LeakyReLU negative slope (0.01) */
-    int eig_sweeps;     /* QST_MAP_ABS_P: Jacobi sweeps from a cold start (0 = default 10; rounded up
+    int eig_sweeps;     /* QST_MAP_ABS_P: Jacobi sweeps from a cold start (0 = default 12; rounded up
                            to even) */
     int eig_warm_sweeps;/* QST_MAP_ABS_P: sweeps when qst_step starts from the previous iteration's
                            eigenvectors (0 = default 2; -1 = always cold; rounded up to even) */
@@ -219,7 +219,7 @@ qst_status qst_classical_fidelity(qst_ctx* ctx, const void* f, const void* P, lo
  * sweeps (pure: w = 1; white noise of strength p: w = p; depolarising channel lambda: w = 1 - lambda),
  * computed on the GPU by the decomposition route of eq. fq_decom.  The decomposition of rho^ comes from
  * that of T (Sec. 3.2: T = Q Lambda Q^dag, rho^ = Q g(Lambda) Q^dag / Tr g(Lambda), g = lambda^2 for
- * Chol_H, |lambda|^P for A_P): for Chol_H a cold Jacobi run of `sweeps` sweeps (0: 10; rounded up to
+ * Chol_H, |lambda|^P for A_P): for Chol_H a cold Jacobi run of `sweeps` sweeps (0: 12; rounded up to
  * even), for A_P the decomposition of the forward pass.  The eigenvalues of sqrt(rho^) rho sqrt(rho^)
  * (diagonal plus rank one in the basis Q) are the roots of its secular equation, found by bisection in
  * FP64; F_q = (sum sqrt(eigenvalue))^2.

@@ -163,7 +163,7 @@ struct qst_ctx {
   long long oa_fallbacks = 0;
   double oa_last[2] = {0.0, 0.0};  // max |E| and the unresolved coupling of the latest refinement
   int oa_skip = 0;                 // warm steps left that go to the sweeps without a refinement attempt
-  int sweeps = 10;       // cold-start Jacobi sweeps
+  int sweeps = 12;       // cold-start Jacobi sweeps
   int warm_sweeps = 2;   // warm-start sweeps (0: never warm-start)
   bool warm_valid = false;
   bool bulk_passes = true;  // FP32 weight passes with bulk-copy staging (fnn_bulk.cu)
@@ -327,7 +327,7 @@ template <class R> qst_status alloc_work(qst_ctx* c) {
       QST_CU(dalloc(c, &ublk, (size_t)D.d * 64));
       ap->ublk = ublk;
     }
-    c->sweeps = c->opt.eig_sweeps > 0 ? c->opt.eig_sweeps : 10;
+    c->sweeps = c->opt.eig_sweeps > 0 ? c->opt.eig_sweeps : 12;
     c->sweeps += c->sweeps & 1;
     c->warm_sweeps = c->opt.eig_warm_sweeps < 0 ? 0 : (c->opt.eig_warm_sweeps > 0 ? c->opt.eig_warm_sweeps : 2);
     c->warm_sweeps += c->warm_sweeps & 1;

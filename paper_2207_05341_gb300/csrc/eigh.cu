@@ -128,20 +128,26 @@ __device__ __forceinline__ void coset_unitary_row(const cx_t<R>* __restrict__ A,
     }
     const R dj = lane_xor(di, s, G);
     const Rot2<R> mine = rotation_for<R>(di, dj, cij);  // the pair's rotation where this lane is the lower one
-    const int p1 = s == 1 ? 2 : 1;                      // lower index of the round's second pair (G = 4)
-    const Rot2<R> r0 = rot_from_lane(mine, 0, G);
-    const Rot2<R> r1 = G == 4 ? rot_from_lane(mine, p1, G) : r0;
-    rotate_cols<R, G>(b, 0, s, r0);
-    rotate_cols<R, G>(u, 0, s, r0);
-    if (G == 4) {
-      rotate_cols<R, G>(b, p1 % G, (p1 ^ s) % G, r1);
-      rotate_cols<R, G>(u, p1 % G, (p1 ^ s) % G, r1);
+    const int hb = s >= 8 ? 3 : (s >= 4 ? 2 : (s >= 2 ? 1 : 0));
+    Rot2<R> rs[G / 2];  // every pair's rotation, from its lower lane
+#pragma unroll
+    for (int l = 0; l < G / 2; ++l) rs[l] = rot_from_lane(mine, insert_zero(l, hb), G);
+#pragma unroll
+    for (int l = 0; l < G / 2; ++l) {
+      const int pl = insert_zero(l, hb), ql = pl ^ s;
+      rotate_cols<R, G>(b, pl, ql, rs[l]);
+      rotate_cols<R, G>(u, pl, ql, rs[l]);
     }
     // rows p, q of B <- R^dag rows (p, q): this lane's row with its partner's
     V o[G];
 #pragma unroll
     for (int j = 0; j < G; ++j) o[j] = cmake<V>(lane_xor(b[j].x, s, G), lane_xor(b[j].y, s, G));
-    const Rot2<R> r = (i == 0 || i == s) ? r0 : r1;
+    const int pi = (i >> hb) & 1 ? i ^ s : i;                        // the lower index of this lane's pair
+    const int li = ((pi >> (hb + 1)) << hb) | (pi & ((1 << hb) - 1));  // and the pair's number
+    Rot2<R> r = rs[0];
+#pragma unroll
+    for (int l = 1; l < G / 2; ++l)
+      if (l == li) r = rs[l];
     const V rqp = cmake<V>(-r.emph.x * r.sn, -r.emph.y * r.sn), rqq = cmake<V>(r.emph.x * r.cs, r.emph.y * r.cs);
     const bool lower = i < (i ^ s);
 #pragma unroll
@@ -447,15 +453,34 @@ template <class V> __device__ __forceinline__ void cp_async_entry(V* dst, const 
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// RB consecutive unitary entries from shared memory: FP32 two per 16-byte load, as the broadcast pairs
+// (u.x, u.x) in ux and (u.y, u.y) in uy that the packed products take; FP64 as they are (uy unused).
+template <class R, int RB>
+__device__ __forceinline__ void load_u_row(const cx_t<R>* src, cx_t<R> (&ux)[RB], cx_t<R> (&uy)[RB]) {
+  if constexpr (sizeof(R) == 4) {
+#pragma unroll
+    for (int h = 0; h < RB / 2; ++h) {
+      const float4 w = reinterpret_cast<const float4*>(src)[h];
+      ux[2 * h] = make_float2(w.x, w.x);
+      uy[2 * h] = make_float2(w.y, w.y);
+      ux[2 * h + 1] = make_float2(w.z, w.z);
+      uy[2 * h + 1] = make_float2(w.w, w.w);
+    }
+  } else {
+#pragma unroll
+    for (int h = 0; h < RB; ++h) ux[h] = src[h];
+  }
+}
+
 // The block kernel's shared memory: the TS x TS tiles of A and V (rows: TS / G row cosets, columns: TS / G
-// column cosets, coset-major), the cosets' unitaries (FP32: the packed forms (u.x, u.x) and (u.y, u.y);
-// FP64: u), the tile's row and column indices and the first block column's piece of phi.
+// column cosets, coset-major), the cosets' unitaries, the tile's row and column indices and the first block
+// column's piece of phi.
 template <class R, int G, int TS> struct TileSmem {
   // column c of a tile at c + c / G (one word after each coset) and one more per row: the reads of a column
   // across the row's cosets, and of a row across the column blocks, fall in distinct banks
   static constexpr int LD = TS + TS / G + 1;
   cx_t<R> a[TS][LD], v[TS][LD];
-  cx_t<R> ul[TS / G][G][G], ul2[TS / G][G][G], uk[TS / G][G][G], uk2[TS / G][G][G];
+  cx_t<R> ul[TS / G][G][G], uk[TS / G][G][G];
   int ridx[TS], cidx[TS];
   cx_t<R> ph[TS];
 };
@@ -493,15 +518,8 @@ __global__ void __launch_bounds__(256) k_jacobi_tile(const cx_t<R>* __restrict__
     const int cc = e / (G * G), rc = (e / G) % G, jc = e % G;
     const V ul = ld_after_wait(Ug + (size_t)(l0 + cc) * G * G + rc * G + jc);
     const V uk = ld_after_wait(Ug + (size_t)(k0 + cc) * G * G + rc * G + jc);
-    if (kF32) {
-      S.ul[cc][rc][jc] = cmake<V>(ul.x, ul.x);
-      S.ul2[cc][rc][jc] = cmake<V>(ul.y, ul.y);
-      S.uk[cc][rc][jc] = cmake<V>(uk.x, uk.x);
-      S.uk2[cc][rc][jc] = cmake<V>(uk.y, uk.y);
-    } else {
-      S.ul[cc][rc][jc] = ul;
-      S.uk[cc][rc][jc] = uk;
-    }
+    S.ul[cc][rc][jc] = ul;
+    S.uk[cc][rc][jc] = uk;
   }
   cp_async_wait_all();
   __syncthreads();
@@ -509,8 +527,7 @@ __global__ void __launch_bounds__(256) k_jacobi_tile(const cx_t<R>* __restrict__
     const int rc = t / G, i = t % G;
     V y = cmake<V>(R(0), R(0));
     for (int r = 0; r < G; ++r) {
-      const V u = kF32 ? cmake<V>(S.uk[rc][r][i].x, S.uk2[rc][r][i].x) : S.uk[rc][r][i];
-      y = cadd(y, cmulc(u, S.ph[rc * G + r]));
+      y = cadd(y, cmulc(S.uk[rc][r][i], S.ph[rc * G + r]));
     }
     phi[S.ridx[t]] = y;
   }
@@ -528,12 +545,8 @@ __global__ void __launch_bounds__(256) k_jacobi_tile(const cx_t<R>* __restrict__
       for (int j = 0; j < RB; ++j) acc[i][j] = accv[i][j] = cmake<V>(R(0), R(0));
 #pragma unroll 4
     for (int q = 0; q < G; ++q) {
-      V ux[RB], uy[RB];
-#pragma unroll
-      for (int j = 0; j < RB; ++j) {
-        ux[j] = S.ul[cc][q][j0 + j];
-        if (kF32) uy[j] = S.ul2[cc][q][j0 + j];
-      }
+      V ux[RB], uy[RB];  // FP32: (u.x, u.x) and (u.y, u.y) of entries j0 .. j0 + RB of row q of U_l
+      load_u_row<R, RB>(&S.ul[cc][q][j0], ux, uy);
 #pragma unroll
       for (int i = 0; i < RB; ++i) {
         const V m = S.a[rr + 16 * i][cc * (G + 1) + q];
@@ -575,11 +588,7 @@ __global__ void __launch_bounds__(256) k_jacobi_tile(const cx_t<R>* __restrict__
 #pragma unroll 4
     for (int q = 0; q < G; ++q) {
       V ux[RB], uy[RB];
-#pragma unroll
-      for (int i = 0; i < RB; ++i) {
-        ux[i] = S.uk[rc][q][i0 + i];
-        if (kF32) uy[i] = S.uk2[rc][q][i0 + i];
-      }
+      load_u_row<R, RB>(&S.uk[rc][q][i0], ux, uy);
 #pragma unroll
       for (int j = 0; j < RB; ++j) {
         const int c = cs + 16 * j;

@@ -2,11 +2,11 @@
 
 The eigendecomposition is a Jacobi method run for a fixed number of sweeps (the mixed-precision
 path refines the previous eigenvectors on tensor cores from its second step on); after
-10 sweeps it has converged to rounding level for these sizes, so the FP64 path
+12 sweeps it has converged to rounding level for these sizes, so the FP64 path
 is held to 1e-8 and the FP32 path to 1e-4 on the loss and 2e-3 (normwise) on
 the gradient, whose Daleckii-Krein factors divide by eigenvalue gaps.  N = 8 and
-N = 10 (d = 256, 1024) exercise the pair-blocked rounds at the sizes where their
-blocks change shape.
+N = 10 (d = 256, 1024) run the sweeps as passes over cosets of 16 (N = 8) and of 16 and 8
+indices (N = 10), N <= 5 as passes over cosets of 4 and 2.
 """
 import numpy as np
 import pytest
@@ -157,7 +157,7 @@ def _steps(N, theta, f, opt, k):
 
 def test_warm_start_follows_cold_start_trajectory():
     """Warm-started eigendecompositions (2 sweeps from the last eigenvectors) give the same
-    iteration as a cold start every step (10 sweeps)."""
+    iteration as a cold start every step (12 sweeps)."""
     N, P = 5, 1.5
     f, theta = _problem(N, 91)
     warm = _opt(qst.QST_FP64, P=P)

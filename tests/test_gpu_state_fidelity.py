@@ -3,8 +3,8 @@
 The oracle evaluates eq. F_QF by its singular-value route (`fidelity`) on its own rho^ from the same
 parameters; for the pure target (w = 1) it uses <psi|rho^|psi> (Sec. 2.3), which is exact, whereas
 the singular-value route carries ~1e-8 from the square roots of the zero eigenvalues of a rank-one
-matrix.  Bars: FP64 1e-9.  FP32: the eigenvectors come out of 10 Jacobi sweeps, each entry the
-product of about 10 d plane rotations rounded in FP32, so their error grows like sqrt(10 d) u
+matrix.  Bars: FP64 1e-9.  FP32: the eigenvectors come out of 12 Jacobi sweeps, each entry the
+product of about 12 d plane rotations rounded in FP32, so their error grows like sqrt(12 d) u
 (u = 2^-24; 9e-6 at d = 2048), and F, a smooth function of them, is held to ten times that.
 """
 import numpy as np
@@ -48,7 +48,7 @@ def _setup(N, lam, seed, network="fnn"):
 
 
 def _tol32(N):
-    return 10.0 * np.sqrt(10.0 * (1 << N)) * 2.0 ** -24
+    return 10.0 * np.sqrt(12.0 * (1 << N)) * 2.0 ** -24
 
 
 def _want(theta, f, N, psi, w, dt, mapping="chol_h", P=2.0, network="fnn"):
