@@ -560,8 +560,9 @@ def batch_c4(torch, qst, synth, dev, steps, warmup, seed=30, B=512, prec=None):
 def c5_leg(torch, qst, synth, dev, steps, seed=40):
     """N = 12 (rho 4096 x 4096, 4^12 outcomes), 10^8 shots, depolarised rank-r Ginibre state:
     Chol_H (= A_2, Sec. 3.2) on the mixed tensor-core path, and A_P with P = 1.5: mixed (cold Jacobi
-    first step, then one tensor-core refinement of the previous eigenvectors per step) and FP32 (cold
-    first step, then warm-started Jacobi sweeps)."""
+    first step, then tensor-core refinements of the previous eigenvectors, handed to the sweeps when they
+    do not converge), mixed with every warm step on the sweeps (eig_refine = 0), and FP32 (cold first
+    step, then warm-started Jacobi sweeps)."""
     N = 12
     rng = np.random.default_rng(seed)
     r = int(np.exp(rng.uniform(0, np.log(64))))
@@ -583,9 +584,12 @@ def c5_leg(torch, qst, synth, dev, steps, seed=40):
         theta = synth.init_theta(N, seed + 2).astype(np.float32)
         for name, prec, mapping, p_ord in (("chol_h_mixed_fp16x3", qst.QST_MIXED, qst.QST_MAP_CHOL_H, 2.0),
                                            ("abs_p1.5_mixed_tc_refinement", qst.QST_MIXED, qst.QST_MAP_ABS_P, 1.5),
+                                           ("abs_p1.5_mixed_sweeps", qst.QST_MIXED, qst.QST_MAP_ABS_P, 1.5),
                                            ("abs_p1.5_fp32_jacobi", qst.QST_FP32, qst.QST_MAP_ABS_P, 1.5)):
             o = qst.qst_default_options()
             o.precision, o.mapping, o.P = prec, mapping, p_ord
+            if name.endswith("_sweeps"):
+                o.eig_refine = 0  # warm steps straight to the sweeps (products on tensor cores)
             ctx = qst.qst_init(N, opt=o, stream=stream.cuda_stream)
             try:
                 qst.qst_set_params(ctx, theta)

@@ -108,6 +108,9 @@ typedef struct qst_options {
                            run each qst_step iteration (and their share of a batch iteration) as one
                            kernel on one CTA (QST_PH_FUSED); 0 = qst_tuning.fused_max_qubits, -1 =
                            never; at most 7.  The result is the same method, summed in another order. */
+    int eig_refine;     /* QST_MAP_ABS_P with QST_MIXED / QST_MIXED_BF16: 1 (default) = a warm-started step
+                           first refines the previous eigenvectors on tensor cores (qst_eig_counts); 0 = warm
+                           steps go to the Jacobi sweeps directly (their products on tensor cores) */
 } qst_options;
 
 /* Mapping networks.  QST_NET_FNN: the 3-layer network of Sec. 3.1, theta as described above.

@@ -413,7 +413,7 @@ template <class R> struct Engine {
       if constexpr (std::is_same<R, float>::value) {
         if (mixed && warm && c->oa_skip > 0) {
           --c->oa_skip;  // T moved too far at the latest attempt: the sweeps, without trying first
-        } else if (mixed && warm) {
+        } else if (mixed && warm && c->opt.eig_refine) {
           // Refinements of the previous eigenvectors on tensor cores, each judged by its largest correction
           // max |E| and the largest coupling it left unresolved (near-degenerate pairs): a refinement with
           // unresolved couplings is followed by the block passes over neighbours in the order of lambda,
@@ -466,9 +466,21 @@ template <class R> struct Engine {
         }
       }
       if (!done) {
-        QST_CU(abs_p_forward<R>(D.d, w->T, *reinterpret_cast<AbsPWork<R>*>(c->apw), sw, warm, c->opt.P, w->X,
-                                c->stream));
-        c->launches += 4 + (long long)sw * jacobi_passes_per_sweep(D.d);
+        bool on_tc = false;
+        if constexpr (std::is_same<R, float>::value) {
+          if (mixed && warm) {  // the products around the sweeps (Q^dag T Q, X) on tensor cores
+            QST_CU(abs_p_forward_tc_warm(D.d, w->Tb, w->scal + kScaleT, *reinterpret_cast<AbsPWork<float>*>(c->apw),
+                                         sw, c->opt.P, tc_fmt(c), reinterpret_cast<float2*>(w->X), w->flags + 1,
+                                         c->stream));
+            c->launches += 17 + (long long)sw * jacobi_kernels_per_sweep(D.d);
+            on_tc = true;
+          }
+        }
+        if (!on_tc) {
+          QST_CU(abs_p_forward<R>(D.d, w->T, *reinterpret_cast<AbsPWork<R>*>(c->apw), sw, warm, c->opt.P, w->X,
+                                  c->stream));
+          c->launches += 4 + (long long)sw * jacobi_kernels_per_sweep(D.d);
+        }
       }
       if (mixed && amax_slot(c, CNT_AMAXT))  // the planes of T are made: restart the max of the next t
         QST_CU(cudaMemsetAsync(amax_slot(c, CNT_AMAXT), 0, sizeof(unsigned int), c->stream));
@@ -947,7 +959,7 @@ template <class R> struct Engine {
     if (!absp) {
       const int sw = (sweeps > 0 ? sweeps : c->sweeps) + ((sweeps > 0 ? sweeps : c->sweeps) & 1);
       QST_CU(jacobi_values_project<R>(D.d, w->T, ap, sw, 2.0, psi, phi, c->stream));
-      c->launches += 1 + (long long)sw * jacobi_passes_per_sweep(D.d);
+      c->launches += 1 + (long long)sw * jacobi_kernels_per_sweep(D.d);
     }
     double* out = w->scal + 8;
     QST_CU(state_fidelity_from_decomposition<R>(D.d, absp ? ap.Qh : nullptr, phi, ap.s, psi, wgt, c->fq, out,
@@ -1269,6 +1281,7 @@ void qst_default_options(qst_options* o) {
   o->network = QST_NET_FNN;
   o->device_memory_limit = 0;
   o->fused_max_qubits = 0;
+  o->eig_refine = 1;
 }
 
 size_t qst_theta_size(int N) {
@@ -1298,6 +1311,7 @@ qst_status qst_init(qst_ctx** out, int N, const double* povm, int K, const qst_o
   if (o.network != QST_NET_FNN && o.network != QST_NET_CNN) return QST_E_INVAL;
   if (o.network == QST_NET_CNN && N < 3) return QST_E_INVAL;  // 2^(N-3)-square pooling windows
   if (o.fused_max_qubits < -1 || o.fused_max_qubits > kFusedMaxQubits) return QST_E_INVAL;
+  if (o.eig_refine != 0 && o.eig_refine != 1) return QST_E_INVAL;
   if (o.mapping == QST_MAP_ABS_P) {
     if (!(o.P > 0.0) || !isfinite(o.P) || o.eig_sweeps < 0) return QST_E_INVAL;
   }

@@ -865,6 +865,12 @@ const std::vector<JacobiPass>& jacobi_schedule(int N) {
 
 long long jacobi_passes_per_sweep(int d) { return (long long)jacobi_schedule(top_bit(d)).size(); }
 
+long long jacobi_kernels_per_sweep(int d) {
+  long long k = 0;
+  for (const JacobiPass& p : jacobi_schedule(top_bit(d))) k += p.k >= 3 ? 2 : 1;
+  return k;
+}
+
 template <class R>
 cudaError_t abs_p_forward(int d, const cx_t<R>* T, AbsPWork<R>& w, int sweeps, bool warm, double P, cx_t<R>* X,
                           cudaStream_t s) {
@@ -1233,6 +1239,50 @@ cudaError_t abs_p_tc_finish(int d, AbsPWork<float>& w, int fmt, float2* X, unsig
   const int TS = d < 32 ? d : 32;
   k_conj_transpose<float><<<dim3(d / TS, d / TS), 256, 0, s>>>(Q, w.Qh, d);
   return cudaGetLastError();
+}
+
+namespace {
+
+// M[i][j] = conj(M[j][i]) wherever the 128 x 128 tile of (i, j) lies above the diagonal: a Hermitian matrix
+// of which only the tiles I >= J were computed, made whole.  CTA (x, y): the 32 x 32 block (y, x), read
+// transposed from block (x, y) through shared memory.
+__global__ void __launch_bounds__(256) k_mirror_upper_tiles(float2* M, int d) {
+  __shared__ float2 tile[32][33];
+  const int bi = blockIdx.y, bj = blockIdx.x;
+  if ((bi >> 2) >= (bj >> 2)) return;  // not above the diagonal at 128-tile granularity
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    const int r = e / 32, c = e % 32;
+    tile[r][c] = M[(long long)(bj * 32 + r) * d + bi * 32 + c];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    const int r = e / 32, c = e % 32;
+    const float2 v = tile[c][r];
+    M[(long long)(bi * 32 + r) * d + bj * 32 + c] = make_float2(v.x, -v.y);
+  }
+}
+
+}  // namespace
+
+cudaError_t abs_p_forward_tc_warm(int d, const void* Tb, const double* sT, AbsPWork<float>& w, int sweeps, double P,
+                                  int fmt, float2* X, unsigned int* err, cudaStream_t s) {
+  const long long nn = (long long)d * d;
+  cudaError_t e;
+  // A0 = Q^dag T Q (Q = V0) on tensor cores, lower tiles, then the upper ones
+  if ((e = abs_p_tc_rotated(d, Tb, sT, w, fmt, err, s)) != cudaSuccess) return e;
+  k_mirror_upper_tiles<<<dim3(d / 32, d / 32), 256, 0, s>>>(w.A0, d);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  float2 *Ain = w.A0, *Aout = w.A1, *Vin = w.V0, *Vout = w.V1;
+  for (int sw = 0; sw < sweeps; ++sw)
+    if ((e = jacobi_sweep<float>(d, Ain, Aout, Vin, Vout, nullptr, w.ucos, s)) != cudaSuccess) return e;
+  if (Vin != w.V0 && (e = cudaMemcpyAsync(w.V0, Vin, nn * sizeof(float2), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    return e;
+  if (Ain != w.A0 && (e = cudaMemcpyAsync(w.A0, Ain, nn * sizeof(float2), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    return e;
+  k_absp_spectrum<float><<<1, 1024, 0, s>>>(w.A0, w.lam, w.s, w.sp, d, P, 1e-7);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // X = Q |Lambda|^P Q^dag on tensor cores (lower tiles), and Q^dag
+  return abs_p_tc_finish(d, w, fmt, X, err, s);
 }
 
 cudaError_t abs_p_backward_tc(int d, const float2* G, AbsPWork<float>& w, int fmt, float2* Y, unsigned int* err,

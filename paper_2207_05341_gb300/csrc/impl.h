@@ -343,6 +343,12 @@ struct JacobiPass {
 };
 const std::vector<JacobiPass>& jacobi_schedule(int N);  // 1 <= N <= 14
 long long jacobi_passes_per_sweep(int d);
+long long jacobi_kernels_per_sweep(int d);  // a pass over cosets of 8 or 16 indices is two kernels
+// A warm-started step of the mixed path on the Jacobi sweeps: A0 = Q^dag T Q (Q in V0, T as its 6 planes Tb
+// with scale *sT) and X = Q |Lambda|^P Q^dag (lower tiles) on tensor cores, `sweeps` (even) sweeps between;
+// leaves Q in V0 and Q^dag in Qh, as abs_p_forward does.
+cudaError_t abs_p_forward_tc_warm(int d, const void* Tb, const double* sT, AbsPWork<float>& w, int sweeps, double P,
+                                  int fmt, float2* X, unsigned int* err, cudaStream_t s);
 // X = Q |Lambda|^P Q^dag (lower tiles) from T via `sweeps` (even) Jacobi sweeps; warm == true starts
 // from the previous eigenvectors (V0, with Q^dag in Qh).  Leaves Q in V0 and Q^dag in Qh.
 template <class R> cudaError_t abs_p_forward(int d, const cx_t<R>* T, AbsPWork<R>& w, int sweeps, bool warm,

@@ -69,6 +69,7 @@ class qst_options(ctypes.Structure):
         ("network", ctypes.c_int),
         ("device_memory_limit", ctypes.c_size_t),
         ("fused_max_qubits", ctypes.c_int),
+        ("eig_refine", ctypes.c_int),
     ]
 
 

@@ -88,6 +88,8 @@ def test_option_validation_before_any_device_call(lib):
     assert status(13) == qst.QST_E_INVAL
     assert status(4, mapping=9) == qst.QST_E_INVAL
     assert status(4, eta_plus=1.0) == qst.QST_E_INVAL
+    assert status(8, mapping=qst.QST_MAP_ABS_P, precision=qst.QST_MIXED, eig_refine=2) == qst.QST_E_INVAL
+    assert qst.qst_default_options().eig_refine == 1
 
 
 def test_parameter_counts_of_both_networks(lib):

@@ -146,6 +146,41 @@ def test_mixed_warm_steps_follow_the_oracle(N, P, k, lr):
         qst.qst_destroy(ctx)
 
 
+@pytest.mark.parametrize("N", [8, 10])
+def test_mixed_warm_steps_on_the_sweeps_follow_the_oracle(N):
+    """QST_MIXED with eig_refine = 0: every warm step runs the Jacobi sweeps from the previous eigenvectors,
+    with Q^dag T Q and X = Q |Lambda|^P Q^dag on tensor cores (the path the refinement hands its steps to).
+    Each step's loss is the oracle's at the parameters the GPU held before it, every moved parameter went
+    against the sign of the oracle's gradient where that gradient is not small, and no refinement ran."""
+    P, k = 1.5, 4
+    f, theta = _problem(N, 320 + N)
+    opt = _opt(qst.QST_MIXED, P=P)
+    opt.eig_refine = 0
+    ctx = qst.qst_init(N, opt=opt)
+    try:
+        qst.qst_set_params(ctx, theta.astype(np.float32))
+        fd = torch.from_numpy(f.astype(np.float32)).cuda()
+        f64 = f.astype(np.float32).astype(np.float64)
+        out = torch.empty(theta.size, device="cuda")
+        qst.qst_get_params(ctx, out)
+        th = out.cpu().numpy().astype(np.float64)
+        for it in range(k):
+            L, _ = qst.qst_step(ctx, fd)
+            qst.qst_get_params(ctx, out)
+            th1 = out.cpu().numpy().astype(np.float64)
+            L_ref, g_ref, _ = O.loss_and_grad(th, f64, M, N, mapping="abs_p", P=P)
+            assert abs(L - L_ref) <= 1e-4 * abs(L_ref), (it, L, L_ref)
+            moved = th1 != th
+            big = np.abs(g_ref) > 1e-2 * np.abs(g_ref).max()
+            sel = moved & big
+            assert sel.sum() > 0
+            assert np.all(np.sign(th1[sel] - th[sel]) == -np.sign(g_ref[sel])), it
+            th = th1
+        assert qst.qst_eig_counts(ctx) == (0, 0)
+    finally:
+        qst.qst_destroy(ctx)
+
+
 def _steps(N, theta, f, opt, k):
     ctx = qst.qst_init(N, opt=opt)
     try:
