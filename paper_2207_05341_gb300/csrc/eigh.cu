@@ -8,13 +8,14 @@
 // XOR ordering: a sweep is the d - 1 rounds m = 1 .. d - 1, round m rotating the d / 2 disjoint pairs
 // {x, x ^ m} at once.  For a pair (p, q) with c = A_pq = |c| e^{i phi}, the 2 x 2 block is first made real by
 // diag(1, e^{-i phi}) and then zeroed by the real rotation of Golub and Van Loan (tan theta =
-// sign(tau) / (|tau| + sqrt(1 + tau^2)), tau = (a_qq - a_pp) / 2|c|).  The three rounds a, b, a ^ b of a
-// 2-dimensional subspace of GF(2)^N all act within its cosets {x, x ^ a, x ^ b, x ^ a ^ b}, so the rounds of a
-// sweep are grouped by a partition of the nonzero vectors of GF(2)^N into such subspaces (for odd N, all but
-// four single rounds), and one kernel applies the three rounds of a subspace at once: each thread owns the
-// 4 x 4 block (rows of one coset) x (columns of another) of A and of V, multiplies it by the cosets' 4 x 4
-// unitaries, and every entry is read and written once per pass (double-buffered); V accumulates the
-// rotations, V <- V U.  At N = 11 a sweep is 685 passes (2047 rounds), at N = 12 1365 (4095).
+// sign(tau) / (|tau| + sqrt(1 + tau^2)), tau = (a_qq - a_pp) / 2|c|).  The 2^k - 1 rounds of a k-dimensional
+// subspace S of GF(2)^N all act within S's cosets, so the rounds of a sweep are grouped by a partition of the
+// nonzero vectors of GF(2)^N into subspaces, and one pass applies all rounds of a subspace, exactly as they
+// would run one after another, with one read and one write of A and V: A' = U^dag A U and V' = V U with U
+// block-diagonal over the cosets.  N <= 5: lines and single rounds, one kernel per pass (each thread a 4 x 4
+// or 2 x 2 block, the CTA's coset unitaries formed by groups of lanes).  N >= 6: subspaces of dimension 3
+// and 4, two kernels per pass (the coset unitaries, a warp per coset; then 64 x 64 tiles of A and V in
+// shared memory).  At N = 11 and 12 a sweep is 273 passes (2047 / 4095 rounds).
 #include <float.h>
 
 #include <algorithm>
