@@ -76,6 +76,23 @@ def test_abs_p_loss_grad_parity(prec, N, P):
     assert rl <= tl and rg < tg, (rl, rg)
 
 
+@pytest.mark.parametrize("prec", [qst.QST_FP32, qst.QST_MIXED])
+def test_abs_p_full_size_n11(prec):
+    """N = 11 (d = 2048, 4^11 outcomes, 10^7 shots of a depolarised Haar state): the A_P loss and gradient
+    of a cold start (12 FP32 sweeps, passes over cosets of 16 and 8 indices; on the mixed path the products
+    and the Daleckii-Krein backward on tensor cores) against the oracle, at the FP32 bars above."""
+    N, P = 11, 1.5
+    rho = synth.depolarized(synth.haar_pure(N, 30), 0.1)
+    f = synth.frequencies(synth.multinomial_counts(O.born_probabilities(rho, M).real, 10**7, 31))
+    theta = synth.init_theta(N, 32)
+    L_ref, g_ref, _ = O.loss_and_grad(theta.astype(np.float32).astype(np.float64), f.astype(np.float32).astype(np.float64),
+                                      M, N, mapping="abs_p", P=P)
+    L, g = _gpu(N, theta, f, _opt(prec, P=P))
+    rl = abs(L - L_ref) / abs(L_ref)
+    rg = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
+    assert rl <= 1e-4 and rg < 2e-3, (rl, rg)
+
+
 def test_abs_p2_equals_chol_h():
     """Sec. 3.2: A_P with P = 2 is the unified Chol_H map."""
     N = 5
